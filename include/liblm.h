@@ -1,0 +1,230 @@
+/*
+ * liblm -- GB300-native lattice meta-meshing and resolution-k triangulation.
+ *
+ * C ABI of the data-parallel hot path of "Warp-centric GPU meta-meshing and
+ * fast triangulation of billion-scale lattice structures" (Zou & Gao, CAD;
+ * arXiv 2405.15197).  All pointers named d_* are device pointers (CUDA
+ * global memory of the current device); h_* are host pointers.  `stream` is
+ * a cudaStream_t passed as void* (NULL = legacy default stream).  Calls are
+ * asynchronous on that stream unless documented as synchronising.
+ *
+ * Ownership: the caller owns every input and output buffer; the library
+ * owns the meta-mesh handle and the device memory behind it (allocated with
+ * cudaMallocAsync on the call's stream).  The lattice arrays passed to
+ * lm_build_metamesh must stay valid and unchanged until lm_metamesh_free,
+ * because triangulation and the adjoint re-derive strut geometry from them.
+ *
+ * Errors: every call returns an lm_status; no exception crosses the ABI.
+ * Per-node geometric degeneracies do not fail a call: they are counted and
+ * flagged per node (LM_NODE_* bits) and those nodes still produce output.
+ *
+ * Lattice model (Section 4.1 of the paper): each node is a sphere whose
+ * radius is a property of the node; each strut is the cone (a cylinder when
+ * both node radii are equal) tangent to the spheres of its two end nodes.
+ */
+#ifndef LIBLM_H
+#define LIBLM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  LM_OK = 0,
+  LM_ERR_INVALID_ARG = 1,     /* NULL pointer, bad size, node id out of range,
+                                 a strut joining a node to itself, radius <= 0
+                                 or NaN, coordinate NaN, k out of [1, 4096] */
+  LM_ERR_RADIUS_MISMATCH = 2, /* two strut ends at one node carry radii that
+                                 differ by more than 1e-12 relative */
+  LM_ERR_DEGENERATE = 3,      /* a strut with |R_a - R_b| >= its length */
+  LM_ERR_CAPACITY = 4,        /* an output or per-node work buffer too small */
+  LM_ERR_OOM = 5,             /* device allocation failed */
+  LM_ERR_CUDA = 6,            /* a CUDA runtime call failed */
+  LM_ERR_TIMEOUT = 7,         /* a bounded device-side wait gave up */
+  LM_ERR_VALENCE = 8,         /* a node with more than LM_MAX_VALENCE struts */
+  LM_ERR_STATE = 9            /* call order violated (e.g. triangulate before
+                                 lm_tri_count for that k) */
+} lm_status;
+
+enum { LM_F32 = 0, LM_F64 = 1 };
+enum { LM_MAX_VALENCE = 64 };
+
+/* per-node flag bits (lm_metamesh_view.node_flags) */
+enum {
+  LM_NODE_NEAR_TANGENT = 1,  /* an active strut pair within 1e-6 of tangency:
+                                exempt from bit-exact comparisons */
+  LM_NODE_DEGENERATE = 2,    /* the node violates a validity condition of the
+                                lattice model (reasons below) */
+  LM_NODE_INCONSISTENT = 4,  /* loops of two struts disagree on a shared arc */
+  LM_NODE_BEYOND_LENGTH = 8, /* a vertex lies past a strut's far tangency circle */
+  LM_NODE_STEEP_PAIR = 16,   /* an active pair whose plane section is not an ellipse */
+  LM_NODE_SEAM_CUT = 32,     /* a vertex-free loop lies on a plane, not the sphere */
+  LM_NODE_ANGLE_TIE = 64,    /* two vertices of one loop at the same angle */
+  LM_NODE_LINE_ALONG_CONE = 128,
+  LM_NODE_OVERFLOW = 256     /* node exceeded a per-node work capacity */
+};
+
+/* per-vertex flag bits */
+enum { LM_VTX_SPHERE = 1, LM_VTX_SEAM = 2 };
+
+/* Input lattice (Section 4.3.1 notation: strut S_i with end vertices
+ * v_i^0, v_i^1 and radii r_i^0, r_i^1).
+ *   node_xyz   : device, [n_nodes][3] of dtype (float or double)
+ *   strut_ends : device, [n_struts][2] int32 node ids
+ *   end_radii  : device, [n_struts][2] of dtype; must equal the radius of
+ *                the node each end sits on (node property)            */
+typedef struct {
+  int64_t n_nodes, n_struts;
+  int32_t dtype; /* LM_F32 or LM_F64 */
+  int32_t pad_;
+  const void* node_xyz;
+  const int32_t* strut_ends;
+  const void* end_radii;
+} lm_lattice;
+
+/* Tuning knobs; zero-initialised = library defaults.
+ *   autotune      : 1 = time the candidate launch shapes of the persistent
+ *                   meta-mesh kernel once per device and valence mix, cache
+ *                   the winner (host memory) and use it
+ *   block_warps   : warps per block of the meta-mesh kernel (0 = default)
+ *   grid_ctas     : persistent grid size (0 = resident CTAs x SM count)
+ *   nodes_per_task: nodes a warp pops from the work queue at once (0 = 1)  */
+typedef struct {
+  int32_t autotune;
+  int32_t block_warps;
+  int32_t grid_ctas;
+  int32_t nodes_per_task;
+  int64_t reserved[4];
+} lm_options;
+
+typedef struct lm_metamesh lm_metamesh;
+
+/* Build the meta-mesh (Section 4.3: auxiliary planes P_ij, strut-plane
+ * ellipses, ellipse-plane trimming, arc loops; Section 5: hole flags).
+ * Runs the node-sorted CSR build and the persistent meta-mesh kernel on
+ * `stream`; synchronises the stream once to size the outputs.
+ *   lat  : input lattice (device arrays, see lm_lattice)
+ *   opt  : NULL = defaults
+ *   out  : receives the handle (NULL on error)                           */
+lm_status lm_build_metamesh(const lm_lattice* lat, const lm_options* opt, void* stream,
+                            lm_metamesh** out);
+
+/* Totals (host, after the build's synchronisation):
+ *   out[0] vertices, [1] elliptical arcs, [2] circular arcs, [3] holes,
+ *   [4] faces (struts + holes), [5] nodes flagged LM_NODE_DEGENERATE,
+ *   [6] max valence, [7] OR of all node flags                            */
+lm_status lm_metamesh_counts(const lm_metamesh* mm, int64_t out[8]);
+
+/* Device views of the meta-mesh arrays (library-owned, valid until free).
+ * Node-local vertex and arc ids index from node_vtx_off[n] / node_arc_off[n].
+ *   vtx_z     : [V][3] dtype, vertex position relative to its node centre
+ *   arc_ends  : [A][2] int32 global strut-end ids (2*strut+side): owner, other
+ *               (other = -1 for a circular arc); owner = lower strut id
+ *   arc_vtx   : [A] uint32, v0 | v1<<8 | owner_local<<16 | (other_local+1)<<24
+ *               (node-local vertex ids and node-local strut-end indices)
+ *   arc_phi   : [A][2] dtype, start angle and angular length in the owner's
+ *               strut frame
+ *   loop_ent  : per strut end (end_loop_off over 2E+1), node-local arc id |
+ *               reversed<<31, in increasing strut angle from the first vertex
+ *   hole_ent  : per hole (hole_off over H+1), node-local arc id | reversed<<31 */
+typedef struct {
+  int64_t n_nodes, n_struts, n_vtx, n_arcs, n_loop_ent, n_holes, n_hole_ent;
+  int32_t dtype, pad_;
+  const int64_t* row_ptr;     /* [N+1] CSR of strut ends per node */
+  const int32_t* adj;         /* [2E] strut-end ids, ascending per node */
+  const void* node_R;         /* [N] dtype */
+  const uint32_t* node_flags; /* [N] */
+  const int64_t* node_vtx_off; /* [N+1] */
+  const void* vtx_z;
+  const uint64_t* vtx_key;    /* [V] bit l = local strut end l meets here */
+  const uint32_t* vtx_flags;  /* [V] LM_VTX_* */
+  const uint32_t* vtx_gen;    /* [V] generator: type | root<<2 | i<<3 | j<<9 | k<<15 */
+  const int64_t* node_arc_off; /* [N+1] */
+  const int32_t* arc_ends;
+  const uint32_t* arc_vtx;
+  const void* arc_phi;
+  const int64_t* end_loop_off; /* [2E+1] */
+  const uint32_t* loop_ent;
+  const int64_t* node_hole_off; /* [N+1] */
+  const int64_t* hole_off;      /* [H+1] */
+  const uint32_t* hole_ent;
+} lm_metamesh_view;
+
+lm_status lm_metamesh_export(const lm_metamesh* mm, lm_metamesh_view* view);
+
+/* Triangle counts at resolution k (Section 5, Eq. sampling with chord error
+ * CE = 1 - cos(pi/k); Algorithm 1).  Items 0..E-1 are struts (lateral band
+ * between the strut's two arc loops), items E..E+N-1 are nodes (hole fans).
+ * Computes per-item counts and their exclusive scan in the handle (one k at
+ * a time) and synchronises the stream to return the total.
+ *   h_total : host, receives the number of triangles of all items        */
+lm_status lm_tri_count(lm_metamesh* mm, int32_t k, void* stream, int64_t* h_total);
+
+/* Host-side range query after lm_tri_count(k) (synchronising): first
+ * triangle index and triangle count of items [item_begin, item_end).     */
+lm_status lm_tri_range(const lm_metamesh* mm, int64_t item_begin, int64_t item_end,
+                       int64_t* h_first, int64_t* h_count);
+
+/* Emit the triangles of items [item_begin, item_end) at resolution k as
+ * binary-STL records (50 bytes: normal f32x3, v0, v1, v2 f32x3, uint16
+ * attribute 0; outward counter-clockwise) into d_out, the record of global
+ * triangle t at byte 50*(t - first(item_begin)).  Asynchronous; requires
+ * lm_tri_count(k) first (else LM_ERR_STATE).  Records beyond capacity_tris
+ * are not written and set LM_ERR_CAPACITY, reported by lm_last_error.
+ *   d_out : device, >= 50*capacity_tris bytes, any alignment of 2 bytes    */
+lm_status lm_triangulate(lm_metamesh* mm, int32_t k, int64_t item_begin, int64_t item_end,
+                         void* d_out, int64_t capacity_tris, void* stream);
+
+/* Same triangles streamed through device chunk buffers into a caller-owned
+ * pinned host buffer ring on overlapped streams (the heterogeneous pipeline
+ * of Section 4.2.2, here GPU triangulation + device-to-host copies).
+ * Items are processed in chunks of chunk_items; chunk c is copied to
+ * h_ring + (c % n_slots) * slot_bytes.  After each chunk's copy completes,
+ * the callback (may be NULL) is invoked on a host thread with (chunk index,
+ * first item, triangle count, slot pointer, user).  Synchronising.       */
+typedef void (*lm_chunk_cb)(int64_t chunk, int64_t first_item, int64_t n_tris, void* h_slot,
+                            void* user);
+lm_status lm_triangulate_stream(lm_metamesh* mm, int32_t k, int64_t chunk_items, void* h_ring,
+                                int64_t slot_bytes, int32_t n_slots, lm_chunk_cb cb, void* user,
+                                void* stream, int64_t* h_total);
+
+/* 80-byte header (text, zero padded) + little-endian uint32 triangle count;
+ * counts above 2^32-1 write 0xFFFFFFFF (the true count is the int64).    */
+void lm_stl_header(uint8_t hdr[84], int64_t n_tris);
+
+/* Objective of the triangulated mesh at k: area = sum |(v1-v0)x(v2-v0)|/2,
+ * volume = sum v0.(v1 x v2)/6 (divergence theorem), accumulated in FP64.
+ * Synchronising; requires lm_tri_count(k).                               */
+lm_status lm_objective(lm_metamesh* mm, int32_t k, void* stream, double* h_area,
+                       double* h_volume);
+
+/* Adjoint: d(w_area*area + w_vol*volume)/d(node xyz, node radius) of the
+ * triangulated mesh at k, with the arc topology and the segment counts held
+ * fixed; per-node intermediates are recomputed, not stored.  Gradients are
+ * ADDED into d_grad_xyz [n_nodes][3] and d_grad_r [n_nodes] (dtype of the
+ * lattice).  Synchronising (returns the objective terms).                */
+lm_status lm_metamesh_backward(lm_metamesh* mm, int32_t k, double w_area, double w_vol,
+                               void* d_grad_xyz, void* d_grad_r, void* stream, double* h_area,
+                               double* h_volume);
+
+/* First asynchronous error recorded on the handle by a device-side check
+ * (capacity, timeout); synchronises `stream`, then clears it.            */
+lm_status lm_last_error(lm_metamesh* mm, void* stream);
+
+void lm_metamesh_free(lm_metamesh* mm);
+const char* lm_status_string(lm_status s);
+
+/* Utility (no counterpart in the paper): synchronous device-to-host copy of
+ * `bytes` bytes, for reading the views of lm_metamesh_export.            */
+lm_status lm_copy_to_host(void* h_dst, const void* d_src, int64_t bytes);
+
+/* Utility (no counterpart in the paper): number of CUDA kernels this library
+ * has launched in the process so far (host-side counter).                */
+long long lm_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LIBLM_H */

@@ -234,7 +234,7 @@ NodeOut node_metamesh(const Mesh& M, int64_t n) {
       double c = dot(E[i].u, E[j].u);
       double pr = std::sqrt(std::max(0.0, 1.0 - c * c));
       double tau = 1.0 - (E[i].co * c + std::fabs(E[i].s) * pr) / E[j].co;
-      if (tau < EPS_TAN) { tan_small[i] |= 1ull << j; tan_small[j] |= 1ull << i; }
+      if (std::fabs(tau) < EPS_TAN) { tan_small[i] |= 1ull << j; tan_small[j] |= 1ull << i; }
       if (tau <= 0.0) { tan_neg[i] |= 1ull << j; tan_neg[j] |= 1ull << i; }
     }
 
@@ -385,7 +385,7 @@ NodeOut node_metamesh(const Mesh& M, int64_t n) {
       vx.key |= 1ull << lab;
       out.flags |= F_DEGENERATE | F_SEAM_CUT;
     }
-    vx.gen = gen_code(2, 0, i, lab < 0 ? 0 : lab, 0);
+    vx.gen = gen_code(2, 0, i, lab < 0 ? 0 : lab, 0) | (lab >= 0 ? (1u << 21) : 0u);
     out.V.push_back(vx);
   }
 
@@ -756,6 +756,14 @@ void* lmo_build(int64_t n_nodes, int64_t n_struts, const double* xyz, const int3
     }
     if (ends[2 * e] == ends[2 * e + 1]) {
       *status = 1;
+      return M;
+    }
+  }
+  for (int64_t e = 0; e < n_struts; e++) {
+    int32_t a = ends[2 * e], b = ends[2 * e + 1];
+    V3 d = sub(node_xyz(M->lat, b), node_xyz(M->lat, a));
+    if (!(std::fabs(M->node_R[a] - M->node_R[b]) < norm(d))) {
+      *status = 3;
       return M;
     }
   }

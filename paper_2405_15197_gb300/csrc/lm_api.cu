@@ -1,0 +1,728 @@
+// liblm C ABI: CSR build, valence bucketing, the two-pass meta-mesh build,
+// triangulation, objective, streaming to pinned host memory.
+// Paper: arXiv 2405.15197 (Sections 4.2.2, 4.3, 5).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "lm_internal.h"
+#include "lm_scan.cuh"
+
+using namespace lm;
+
+#include <atomic>
+static std::atomic<long long> g_launches{0};
+namespace lm {
+void count_launch(int n) { g_launches += n; }
+}
+
+namespace {
+
+#define LM_CK(x)                                  \
+  do {                                            \
+    cudaError_t e_ = (x);                         \
+    if (e_ != cudaSuccess) return st_cuda(e_);   \
+  } while (0)
+
+lm_status st_cuda(cudaError_t e) {
+  if (e == cudaErrorMemoryAllocation) return LM_ERR_OOM;
+  return LM_ERR_CUDA;
+}
+
+template <typename X>
+cudaError_t dalloc(X** p, int64_t n, cudaStream_t st) {
+  *p = nullptr;
+  if (n <= 0) n = 1;
+  return cudaMallocAsync((void**)p, sizeof(X) * (size_t)n, st);
+}
+template <typename X>
+void dfree(X*& p, cudaStream_t st) {
+  if (p) cudaFreeAsync((void*)p, st);
+  p = nullptr;
+}
+
+__device__ __forceinline__ void set_err(int* err, int code) { atomicCAS(err, 0, code); }
+
+// ---- validation and CSR (node-sorted adjacency by counting sort)
+template <typename T>
+__global__ void k_strut_validate(const int32_t* ends, const T* radii, int64_t E, int64_t N, int* deg,
+                                 int* err) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < E;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int32_t a = ends[2 * e], b = ends[2 * e + 1];
+    T ra = radii[2 * e], rb = radii[2 * e + 1];
+    bool ok = a >= 0 && a < N && b >= 0 && b < N && a != b && ra > T(0) && rb > T(0) &&
+              isfinite((double)ra) && isfinite((double)rb);
+    if (!ok) {
+      set_err(err, LM_ERR_INVALID_ARG);
+      continue;
+    }
+    atomicAdd(&deg[a], 1);
+    atomicAdd(&deg[b], 1);
+  }
+}
+
+__global__ void k_scatter(const int32_t* ends, int64_t E2, const int64_t* row_ptr, int* fill,
+                          int32_t* adj) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < E2;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int32_t nd = ends[i];
+    int pos = atomicAdd(&fill[nd], 1);
+    adj[row_ptr[nd] + pos] = (int32_t)i;
+  }
+}
+
+template <typename T>
+__global__ void k_node_finalize(const T* xyz, const T* radii, int64_t N, const int64_t* row_ptr,
+                                int32_t* adj, T* node_R, int* err, int* max_deg) {
+  for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < N;
+       n += (int64_t)gridDim.x * blockDim.x) {
+    int64_t b = row_ptr[n];
+    int d = (int)(row_ptr[n + 1] - b);
+    if (!isfinite((double)xyz[3 * n]) || !isfinite((double)xyz[3 * n + 1]) ||
+        !isfinite((double)xyz[3 * n + 2]))
+      set_err(err, LM_ERR_INVALID_ARG);
+    atomicMax(max_deg, d);
+    if (d > LM_MAX_VALENCE) {
+      set_err(err, LM_ERR_VALENCE);
+      node_R[n] = T(0);
+      continue;
+    }
+    // stable order: ascending strut-end id
+    for (int i = 1; i < d; i++) {
+      int32_t x = adj[b + i];
+      int j = i;
+      while (j > 0 && adj[b + j - 1] > x) {
+        adj[b + j] = adj[b + j - 1];
+        j--;
+      }
+      adj[b + j] = x;
+    }
+    if (d == 0) {
+      node_R[n] = T(0);
+      continue;
+    }
+    T r0 = radii[adj[b]];
+    for (int i = 1; i < d; i++) {
+      T r = radii[adj[b + i]];
+      if (fabs((double)r0 - (double)r) > 1e-12 * fabs((double)r)) set_err(err, LM_ERR_RADIUS_MISMATCH);
+    }
+    node_R[n] = r0;
+  }
+}
+
+template <typename T>
+__global__ void k_strut_taper(const T* xyz, const int32_t* ends, const T* node_R, int64_t E, int* err) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < E;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    int32_t a = ends[2 * e], b = ends[2 * e + 1];
+    double dx = (double)xyz[3 * b] - (double)xyz[3 * a], dy = (double)xyz[3 * b + 1] - (double)xyz[3 * a + 1],
+           dz = (double)xyz[3 * b + 2] - (double)xyz[3 * a + 2];
+    double L = sqrt(dx * dx + dy * dy + dz * dz);
+    if (!(fabs((double)node_R[a] - (double)node_R[b]) < L)) set_err(err, LM_ERR_DEGENERATE);
+  }
+}
+
+// warp-aggregated bucketing of nodes by valence (keeps runs of nodes)
+__global__ void k_bucket(const int64_t* row_ptr, int64_t N, int* cnt, int32_t* lists, int64_t cap) {
+  const int lane = threadIdx.x & 31;
+  for (int64_t base = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) & ~31ll; base < N;
+       base += (int64_t)gridDim.x * blockDim.x) {
+    int64_t n = base + lane;
+    int b = -1;
+    if (n < N) {
+      int d = (int)(row_ptr[n + 1] - row_ptr[n]);
+      if (d > 0 && d <= LM_MAX_VALENCE) b = bucket_of(d);
+    }
+    for (int q = 0; q < NB_BUCKETS; q++) {
+      uint32_t m = __ballot_sync(0xffffffffu, b == q);
+      if (!m) continue;
+      int start = 0;
+      if (lane == __ffs(m) - 1) start = atomicAdd(&cnt[q], __popc(m));
+      start = __shfl_sync(0xffffffffu, start, __ffs(m) - 1);
+      if (b == q) lists[q * cap + start + __popc(m & ((1u << lane) - 1))] = (int32_t)n;
+    }
+  }
+}
+
+__global__ void k_mm_stats(const int32_t* arc_ends, int64_t A, const uint32_t* node_flags, int64_t N,
+                           const int32_t* end_cnt, int64_t E2, unsigned long long* out) {
+  // out: [0] circular arcs, [1] degenerate nodes, [2] flags OR, [3] max loop entries
+  unsigned long long circ = 0, deg = 0, fl = 0, mx = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < A; i += (int64_t)gridDim.x * blockDim.x)
+    circ += arc_ends[2 * i + 1] < 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+    deg += (node_flags[i] & 2u) != 0;
+    fl |= node_flags[i];
+  }
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < E2; i += (int64_t)gridDim.x * blockDim.x)
+    mx = max(mx, (unsigned long long)end_cnt[i]);
+  for (int o = 16; o > 0; o >>= 1) {
+    circ += __shfl_xor_sync(0xffffffffu, circ, o);
+    deg += __shfl_xor_sync(0xffffffffu, deg, o);
+    fl |= __shfl_xor_sync(0xffffffffu, fl, o);
+    mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(&out[0], circ);
+    atomicAdd(&out[1], deg);
+    atomicOr(&out[2], fl);
+    atomicMax(&out[3], mx);
+  }
+}
+
+int grid_for(int64_t n, int threads = 256) {
+  int64_t g = (n + threads - 1) / threads;
+  if (g > 152 * 32) g = 152 * 32;
+  return (int)(g < 1 ? 1 : g);
+}
+
+lm_status read_err(lm_metamesh* mm, cudaStream_t st) {
+  int e = 0;
+  LM_CK(cudaMemcpyAsync(&e, mm->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  LM_CK(cudaStreamSynchronize(st));
+  return (lm_status)e;
+}
+
+template <typename T>
+lm_status build_impl(lm_metamesh* mm, cudaStream_t st) {
+  const int64_t N = mm->N, E = mm->E;
+  const T* xyz = (const T*)mm->xyz;
+  const T* radii = (const T*)mm->radii;
+  cudaEvent_t ev[4];
+  for (auto& e : ev) cudaEventCreate(&e);
+  cudaEventRecord(ev[0], st);
+  int* deg = nullptr;
+  int* fill = nullptr;
+  LM_CK(dalloc(&mm->d_err, 4, st));
+  LM_CK(dalloc(&mm->d_queue, 8, st));
+  LM_CK(dalloc(&mm->d_misc, 8, st));
+  LM_CK(dalloc(&mm->d_acc, 4, st));
+  LM_CK(cudaMemsetAsync(mm->d_err, 0, 4 * sizeof(int), st));
+  LM_CK(cudaMemsetAsync(mm->d_misc, 0, 8 * sizeof(int), st));
+  T* node_R = nullptr;
+  LM_CK(dalloc(&node_R, N, st));
+  mm->node_R = node_R;
+  LM_CK(dalloc(&mm->row_ptr, N + 1, st));
+  LM_CK(dalloc(&mm->adj, 2 * E, st));
+  LM_CK(dalloc(&deg, N, st));
+  LM_CK(dalloc(&fill, N, st));
+  LM_CK(cudaMemsetAsync(deg, 0, sizeof(int) * N, st));
+  LM_CK(cudaMemsetAsync(fill, 0, sizeof(int) * N, st));
+  mm->scan_ws_n = scan_ws_elems(std::max<int64_t>(std::max<int64_t>(N + E, 2 * E), 1));
+  LM_CK(dalloc(&mm->scan_ws, mm->scan_ws_n, st));
+  count_launch(); k_strut_validate<T><<<grid_for(E), 256, 0, st>>>(mm->ends, radii, E, N, deg, mm->d_err);
+  LM_CK(cudaGetLastError());
+  lm_status s = read_err(mm, st);
+  if (s != LM_OK) return s;
+  LM_CK(scan_excl<int>(deg, 1, N, mm->row_ptr, mm->scan_ws, st));
+  count_launch(); k_scatter<<<grid_for(2 * E), 256, 0, st>>>(mm->ends, 2 * E, mm->row_ptr, fill, mm->adj);
+  count_launch(); k_node_finalize<T><<<grid_for(N), 256, 0, st>>>(xyz, radii, N, mm->row_ptr, mm->adj, node_R, mm->d_err,
+                                                 mm->d_misc);
+  count_launch(); k_strut_taper<T><<<grid_for(E), 256, 0, st>>>(xyz, mm->ends, node_R, E, mm->d_err);
+  LM_CK(cudaGetLastError());
+  dfree(fill, st);
+  s = read_err(mm, st);
+  int maxdeg = 0;
+  LM_CK(cudaMemcpyAsync(&maxdeg, mm->d_misc, sizeof(int), cudaMemcpyDeviceToHost, st));
+  LM_CK(cudaStreamSynchronize(st));
+  mm->max_valence = maxdeg;
+  if (s != LM_OK) {
+    dfree(deg, st);
+    return s;
+  }
+  // valence buckets
+  int32_t* lists = nullptr;
+  int* bcnt = mm->d_misc + 4;
+  LM_CK(cudaMemsetAsync(bcnt, 0, 4 * sizeof(int), st));
+  LM_CK(dalloc(&lists, (int64_t)NB_BUCKETS * std::max<int64_t>(N, 1), st));
+  count_launch(); k_bucket<<<grid_for(N), 256, 0, st>>>(mm->row_ptr, N, bcnt, lists, std::max<int64_t>(N, 1));
+  LM_CK(cudaGetLastError());
+  int hb[4] = {0, 0, 0, 0};
+  LM_CK(cudaMemcpyAsync(hb, bcnt, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
+  LM_CK(cudaStreamSynchronize(st));
+  cudaEventRecord(ev[1], st);
+  // ---- count pass
+  int32_t *node_cnt = nullptr, *end_cnt = nullptr;
+  LM_CK(dalloc(&node_cnt, 4 * N, st));
+  LM_CK(dalloc(&end_cnt, 2 * E, st));
+  LM_CK(dalloc(&mm->node_flags, N, st));
+  LM_CK(cudaMemsetAsync(node_cnt, 0, sizeof(int32_t) * 4 * N, st));
+  LM_CK(cudaMemsetAsync(end_cnt, 0, sizeof(int32_t) * 2 * E, st));
+  LM_CK(cudaMemsetAsync(mm->node_flags, 0, sizeof(uint32_t) * N, st));
+  int* overflow = mm->d_misc + 1;
+  LM_CK(cudaMemsetAsync(overflow, 0, sizeof(int), st));
+  MMLaunch<T> L{};
+  L.xyz = xyz;
+  L.ends = mm->ends;
+  L.node_R = node_R;
+  L.row_ptr = mm->row_ptr;
+  L.adj = mm->adj;
+  L.n_nodes = N;
+  L.n_struts = E;
+  L.nodes_per_task = mm->opt.nodes_per_task > 0 ? mm->opt.nodes_per_task : 1;
+  L.node_flags = mm->node_flags;
+  L.node_cnt = node_cnt;
+  L.end_cnt = end_cnt;
+  L.overflow = overflow;
+  int64_t cap = std::max<int64_t>(N, 1);
+  for (int pass = 0; pass < 2; pass++) {
+    if (pass == 1) {
+      cudaEventRecord(ev[2], st);
+      // offsets from the counts
+      LM_CK(dalloc(&mm->vtx_off, N + 1, st));
+      LM_CK(dalloc(&mm->arc_off, N + 1, st));
+      LM_CK(dalloc(&mm->hole_off_n, N + 1, st));
+      LM_CK(dalloc(&mm->hent_off_n, N + 1, st));
+      LM_CK(dalloc(&mm->end_off, 2 * E + 1, st));
+      LM_CK(scan_excl<int32_t>(node_cnt + 0, 4, N, mm->vtx_off, mm->scan_ws, st));
+      LM_CK(scan_excl<int32_t>(node_cnt + 1, 4, N, mm->arc_off, mm->scan_ws, st));
+      LM_CK(scan_excl<int32_t>(node_cnt + 2, 4, N, mm->hole_off_n, mm->scan_ws, st));
+      LM_CK(scan_excl<int32_t>(node_cnt + 3, 4, N, mm->hent_off_n, mm->scan_ws, st));
+      LM_CK(scan_excl<int32_t>(end_cnt, 1, 2 * E, mm->end_off, mm->scan_ws, st));
+      int64_t tot[5];
+      LM_CK(cudaMemcpyAsync(&tot[0], mm->vtx_off + N, 8, cudaMemcpyDeviceToHost, st));
+      LM_CK(cudaMemcpyAsync(&tot[1], mm->arc_off + N, 8, cudaMemcpyDeviceToHost, st));
+      LM_CK(cudaMemcpyAsync(&tot[2], mm->hole_off_n + N, 8, cudaMemcpyDeviceToHost, st));
+      LM_CK(cudaMemcpyAsync(&tot[3], mm->hent_off_n + N, 8, cudaMemcpyDeviceToHost, st));
+      LM_CK(cudaMemcpyAsync(&tot[4], mm->end_off + 2 * E, 8, cudaMemcpyDeviceToHost, st));
+      int ovf = 0;
+      LM_CK(cudaMemcpyAsync(&ovf, overflow, sizeof(int), cudaMemcpyDeviceToHost, st));
+      LM_CK(cudaStreamSynchronize(st));
+      if (ovf) {
+        dfree(node_cnt, st);
+        dfree(end_cnt, st);
+        dfree(lists, st);
+        dfree(deg, st);
+        return LM_ERR_CAPACITY;
+      }
+      mm->V = tot[0];
+      mm->A = tot[1];
+      mm->H = tot[2];
+      mm->HE = tot[3];
+      mm->LE = tot[4];
+      T *vz = nullptr, *aphi = nullptr;
+      LM_CK(dalloc(&vz, 3 * mm->V, st));
+      mm->vtx_z = vz;
+      LM_CK(dalloc(&mm->vtx_key, mm->V, st));
+      LM_CK(dalloc(&mm->vtx_flags, mm->V, st));
+      LM_CK(dalloc(&mm->vtx_gen, mm->V, st));
+      LM_CK(dalloc(&mm->arc_ends, 2 * mm->A, st));
+      LM_CK(dalloc(&mm->arc_vtx, mm->A, st));
+      LM_CK(dalloc(&aphi, 2 * mm->A, st));
+      mm->arc_phi = aphi;
+      LM_CK(dalloc(&mm->loop_ent, mm->LE, st));
+      LM_CK(dalloc(&mm->hole_off, mm->H + 1, st));
+      LM_CK(dalloc(&mm->hole_ent, mm->HE, st));
+      LM_CK(cudaMemcpyAsync(mm->hole_off + mm->H, mm->hent_off_n + N, 8, cudaMemcpyDeviceToDevice, st));
+      L.vtx_off = mm->vtx_off;
+      L.arc_off = mm->arc_off;
+      L.hole_off_n = mm->hole_off_n;
+      L.hent_off_n = mm->hent_off_n;
+      L.end_off = mm->end_off;
+      L.vtx_z = vz;
+      L.vtx_key = mm->vtx_key;
+      L.vtx_flags = mm->vtx_flags;
+      L.vtx_gen = mm->vtx_gen;
+      L.arc_ends = mm->arc_ends;
+      L.arc_vtx = mm->arc_vtx;
+      L.arc_phi = aphi;
+      L.loop_ent = mm->loop_ent;
+      L.hole_off = mm->hole_off;
+      L.hole_ent = mm->hole_ent;
+    }
+    for (int b = NB_BUCKETS - 1; b >= 0; b--) {
+      if (hb[b] == 0) continue;
+      L.nodes = lists + b * cap;
+      L.n_list = hb[b];
+      L.queue = mm->d_queue + b;
+      LM_CK(cudaMemsetAsync(mm->d_queue + b, 0, sizeof(int), st));
+      int used = 0;
+      LM_CK(launch_metamesh<T>(b, pass == 1, L, mm->opt.block_warps, mm->opt.grid_ctas, st, &used));
+    }
+  }
+  cudaEventRecord(ev[3], st);
+  // statistics
+  unsigned long long* dstat = nullptr;
+  LM_CK(dalloc(&dstat, 4, st));
+  LM_CK(cudaMemsetAsync(dstat, 0, 4 * sizeof(unsigned long long), st));
+  count_launch(); k_mm_stats<<<grid_for(std::max<int64_t>(std::max<int64_t>(mm->A, N), 2 * E)), 256, 0, st>>>(
+      mm->arc_ends, mm->A, mm->node_flags, N, end_cnt, 2 * E, dstat);
+  unsigned long long hs[4];
+  LM_CK(cudaMemcpyAsync(hs, dstat, sizeof(hs), cudaMemcpyDeviceToHost, st));
+  LM_CK(cudaStreamSynchronize(st));
+  mm->n_circ = (int64_t)hs[0];
+  mm->n_ell = mm->A - mm->n_circ;
+  mm->n_degenerate = (int64_t)hs[1];
+  mm->flags_or = (uint32_t)hs[2];
+  mm->max_loop_entries = (int)hs[3];
+  cudaEventElapsedTime(&mm->t_csr, ev[0], ev[1]);
+  cudaEventElapsedTime(&mm->t_count, ev[1], ev[2]);
+  cudaEventElapsedTime(&mm->t_emit, ev[2], ev[3]);
+  for (auto& e : ev) cudaEventDestroy(e);
+  dfree(dstat, st);
+  dfree(node_cnt, st);
+  dfree(end_cnt, st);
+  dfree(lists, st);
+  dfree(deg, st);
+  // FP64 fallback contexts of the triangulation kernels
+  mm->scratch_warps = tri_scratch_warps();
+  LM_CK(cudaMallocAsync((void**)&mm->scratch, node64_bytes() * (size_t)mm->scratch_warps, st));
+  // every context starts as "no node" (node id -1)
+  LM_CK(cudaMemsetAsync(mm->scratch, 0xff, node64_bytes() * (size_t)mm->scratch_warps, st));
+  LM_CK(cudaStreamSynchronize(st));
+  return LM_OK;
+}
+
+template <typename T>
+TriLaunch<T> tri_launch(lm_metamesh* mm) {
+  TriLaunch<T> L{};
+  L.xyz = (const T*)mm->xyz;
+  L.ends = mm->ends;
+  L.node_R = (const T*)mm->node_R;
+  L.row_ptr = mm->row_ptr;
+  L.adj = mm->adj;
+  L.n_nodes = mm->N;
+  L.n_struts = mm->E;
+  L.vtx_off = mm->vtx_off;
+  L.arc_off = mm->arc_off;
+  L.end_off = mm->end_off;
+  L.node_hole_off = mm->hole_off_n;
+  L.hole_off = mm->hole_off;
+  L.vtx_z = (const T*)mm->vtx_z;
+  L.vtx_gen = mm->vtx_gen;
+  L.arc_vtx = mm->arc_vtx;
+  L.arc_phi = (const T*)mm->arc_phi;
+  L.loop_ent = mm->loop_ent;
+  L.hole_ent = mm->hole_ent;
+  L.item_cnt = mm->item_cnt;
+  L.tri_off = mm->tri_off;
+  L.queue = mm->d_queue;
+  L.err = mm->d_err;
+  L.emax = std::max(mm->max_loop_entries, 1);
+  L.pmax = std::max(mm->tri_pmax, 1);
+  L.max_pts = mm->d_misc + 2;
+  L.scratch = mm->scratch;
+  L.scratch_warps = mm->scratch_warps;
+  return L;
+}
+
+template <typename T>
+lm_status tri_count_impl(lm_metamesh* mm, int k, cudaStream_t st, int64_t* total) {
+  const int64_t n_items = mm->E + mm->N;
+  if (!mm->item_cnt) {
+    LM_CK(dalloc(&mm->item_cnt, n_items, st));
+    LM_CK(dalloc(&mm->tri_off, n_items + 1, st));
+  }
+  LM_CK(cudaMemsetAsync(mm->d_misc + 2, 0, sizeof(int), st));
+  TriLaunch<T> L = tri_launch<T>(mm);
+  L.k = k;
+  LM_CK(launch_tri_count<T>(L, st));
+  LM_CK(scan_excl<int32_t>(mm->item_cnt, 1, n_items, mm->tri_off, mm->scan_ws, st));
+  int64_t tot = 0;
+  int mp = 0;
+  LM_CK(cudaMemcpyAsync(&tot, mm->tri_off + n_items, 8, cudaMemcpyDeviceToHost, st));
+  LM_CK(cudaMemcpyAsync(&mp, mm->d_misc + 2, sizeof(int), cudaMemcpyDeviceToHost, st));
+  LM_CK(cudaStreamSynchronize(st));
+  mm->tri_k = k;
+  mm->tri_total = tot;
+  mm->tri_pmax = mp + 1;
+  if (total) *total = tot;
+  return LM_OK;
+}
+
+template <typename T>
+lm_status tri_emit_impl(lm_metamesh* mm, int k, int64_t b, int64_t e, void* out, int64_t cap,
+                        double* acc, cudaStream_t st) {
+  LM_CK(cudaMemsetAsync(mm->d_queue, 0, 2 * sizeof(int), st));
+  TriLaunch<T> L = tri_launch<T>(mm);
+  L.k = k;
+  L.item_begin = b;
+  L.item_end = e;
+  L.capacity = cap;
+  L.first_ptr = mm->tri_off + b;
+  L.out = (uint8_t*)out;
+  L.acc = acc;
+  LM_CK(launch_tri_emit<T>(L, st));
+  return LM_OK;
+}
+
+bool valid_k(int k) { return k >= 1 && k <= 4096; }
+
+}  // namespace
+
+extern "C" {
+
+const char* lm_status_string(lm_status s) {
+  switch (s) {
+    case LM_OK: return "ok";
+    case LM_ERR_INVALID_ARG: return "invalid argument";
+    case LM_ERR_RADIUS_MISMATCH: return "strut-end radii disagree at a node";
+    case LM_ERR_DEGENERATE: return "strut taper not smaller than its length";
+    case LM_ERR_CAPACITY: return "capacity exceeded";
+    case LM_ERR_OOM: return "device out of memory";
+    case LM_ERR_CUDA: return "CUDA error";
+    case LM_ERR_TIMEOUT: return "device wait timed out";
+    case LM_ERR_VALENCE: return "node valence above LM_MAX_VALENCE";
+    case LM_ERR_STATE: return "call order violated";
+  }
+  return "unknown status";
+}
+
+void lm_metamesh_free(lm_metamesh* mm) {
+  if (!mm) return;
+  cudaStream_t st = mm->st;
+  cudaStreamSynchronize(st);
+  void* ptrs[] = {mm->node_R, mm->row_ptr, mm->adj, mm->node_flags, mm->vtx_off, mm->arc_off,
+                  mm->hole_off_n, mm->hent_off_n, mm->end_off, mm->vtx_z, mm->vtx_key, mm->vtx_flags,
+                  mm->vtx_gen, mm->arc_ends, mm->arc_vtx, mm->arc_phi, mm->loop_ent, mm->hole_off,
+                  mm->hole_ent, mm->item_cnt, mm->tri_off, mm->scratch, mm->d_err, mm->d_queue,
+                  mm->d_misc, mm->d_acc, mm->scan_ws};
+  for (void* p : ptrs)
+    if (p) cudaFreeAsync(p, st);
+  cudaStreamSynchronize(st);
+  delete mm;
+}
+
+lm_status lm_build_metamesh(const lm_lattice* lat, const lm_options* opt, void* stream,
+                            lm_metamesh** out) {
+  if (!out) return LM_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!lat || lat->n_nodes < 0 || lat->n_struts < 0 || (lat->dtype != LM_F32 && lat->dtype != LM_F64))
+    return LM_ERR_INVALID_ARG;
+  if (lat->n_struts > 0 && (!lat->node_xyz || !lat->strut_ends || !lat->end_radii))
+    return LM_ERR_INVALID_ARG;
+  if (2 * lat->n_struts >= (int64_t)0x7fffffff || lat->n_nodes >= (int64_t)0x7fffffff)
+    return LM_ERR_INVALID_ARG;
+  lm_metamesh* mm = new lm_metamesh();
+  std::memset((void*)mm, 0, sizeof(*mm));
+  mm->dtype = lat->dtype;
+  mm->N = lat->n_nodes;
+  mm->E = lat->n_struts;
+  mm->xyz = lat->node_xyz;
+  mm->ends = lat->strut_ends;
+  mm->radii = lat->end_radii;
+  if (opt) mm->opt = *opt;
+  mm->st = (cudaStream_t)stream;
+  mm->tri_k = 0;
+  lm_status s = lat->dtype == LM_F32 ? build_impl<float>(mm, mm->st) : build_impl<double>(mm, mm->st);
+  if (s != LM_OK) {
+    lm_metamesh_free(mm);
+    return s;
+  }
+  *out = mm;
+  return LM_OK;
+}
+
+lm_status lm_metamesh_counts(const lm_metamesh* mm, int64_t out[8]) {
+  if (!mm || !out) return LM_ERR_INVALID_ARG;
+  out[0] = mm->V;
+  out[1] = mm->n_ell;
+  out[2] = mm->n_circ;
+  out[3] = mm->H;
+  out[4] = mm->E + mm->H;
+  out[5] = mm->n_degenerate;
+  out[6] = mm->max_valence;
+  out[7] = mm->flags_or;
+  return LM_OK;
+}
+
+lm_status lm_metamesh_export(const lm_metamesh* mm, lm_metamesh_view* v) {
+  if (!mm || !v) return LM_ERR_INVALID_ARG;
+  v->n_nodes = mm->N;
+  v->n_struts = mm->E;
+  v->n_vtx = mm->V;
+  v->n_arcs = mm->A;
+  v->n_loop_ent = mm->LE;
+  v->n_holes = mm->H;
+  v->n_hole_ent = mm->HE;
+  v->dtype = mm->dtype;
+  v->pad_ = 0;
+  v->row_ptr = mm->row_ptr;
+  v->adj = mm->adj;
+  v->node_R = mm->node_R;
+  v->node_flags = mm->node_flags;
+  v->node_vtx_off = mm->vtx_off;
+  v->vtx_z = mm->vtx_z;
+  v->vtx_key = mm->vtx_key;
+  v->vtx_flags = mm->vtx_flags;
+  v->vtx_gen = mm->vtx_gen;
+  v->node_arc_off = mm->arc_off;
+  v->arc_ends = mm->arc_ends;
+  v->arc_vtx = mm->arc_vtx;
+  v->arc_phi = mm->arc_phi;
+  v->end_loop_off = mm->end_off;
+  v->loop_ent = mm->loop_ent;
+  v->node_hole_off = mm->hole_off_n;
+  v->hole_off = mm->hole_off;
+  v->hole_ent = mm->hole_ent;
+  return LM_OK;
+}
+
+lm_status lm_tri_count(lm_metamesh* mm, int32_t k, void* stream, int64_t* h_total) {
+  if (!mm || !valid_k(k)) return LM_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  return mm->dtype == LM_F32 ? tri_count_impl<float>(mm, k, st, h_total)
+                             : tri_count_impl<double>(mm, k, st, h_total);
+}
+
+lm_status lm_tri_range(const lm_metamesh* mm, int64_t b, int64_t e, int64_t* h_first, int64_t* h_count) {
+  if (!mm || b < 0 || e < b || e > mm->E + mm->N) return LM_ERR_INVALID_ARG;
+  if (!mm->tri_k) return LM_ERR_STATE;
+  int64_t x[2];
+  if (cudaMemcpy(&x[0], mm->tri_off + b, 8, cudaMemcpyDeviceToHost) != cudaSuccess) return LM_ERR_CUDA;
+  if (cudaMemcpy(&x[1], mm->tri_off + e, 8, cudaMemcpyDeviceToHost) != cudaSuccess) return LM_ERR_CUDA;
+  if (h_first) *h_first = x[0];
+  if (h_count) *h_count = x[1] - x[0];
+  return LM_OK;
+}
+
+lm_status lm_triangulate(lm_metamesh* mm, int32_t k, int64_t b, int64_t e, void* d_out, int64_t cap,
+                         void* stream) {
+  if (!mm || !valid_k(k) || b < 0 || e < b || e > mm->E + mm->N || cap < 0) return LM_ERR_INVALID_ARG;
+  if (mm->tri_k != k) return LM_ERR_STATE;
+  if (!d_out && cap > 0) return LM_ERR_INVALID_ARG;
+  if (e == b) return LM_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  return mm->dtype == LM_F32 ? tri_emit_impl<float>(mm, k, b, e, d_out, cap, nullptr, st)
+                             : tri_emit_impl<double>(mm, k, b, e, d_out, cap, nullptr, st);
+}
+
+lm_status lm_objective(lm_metamesh* mm, int32_t k, void* stream, double* h_area, double* h_volume) {
+  if (!mm || !valid_k(k)) return LM_ERR_INVALID_ARG;
+  if (mm->tri_k != k) return LM_ERR_STATE;
+  cudaStream_t st = (cudaStream_t)stream;
+  LM_CK(cudaMemsetAsync(mm->d_acc, 0, 2 * sizeof(double), st));
+  lm_status s = mm->dtype == LM_F32
+                    ? tri_emit_impl<float>(mm, k, 0, mm->E + mm->N, nullptr, 0, mm->d_acc, st)
+                    : tri_emit_impl<double>(mm, k, 0, mm->E + mm->N, nullptr, 0, mm->d_acc, st);
+  if (s != LM_OK) return s;
+  double h[2];
+  LM_CK(cudaMemcpyAsync(h, mm->d_acc, sizeof(h), cudaMemcpyDeviceToHost, st));
+  LM_CK(cudaStreamSynchronize(st));
+  if (h_area) *h_area = h[0];
+  if (h_volume) *h_volume = h[1];
+  return LM_OK;
+}
+
+lm_status lm_last_error(lm_metamesh* mm, void* stream) {
+  if (!mm) return LM_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  int e = 0;
+  LM_CK(cudaMemcpyAsync(&e, mm->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  LM_CK(cudaMemsetAsync(mm->d_err, 0, sizeof(int), st));
+  LM_CK(cudaStreamSynchronize(st));
+  return (lm_status)e;
+}
+
+void lm_stl_header(uint8_t hdr[84], int64_t n_tris) {
+  std::memset(hdr, 0, 84);
+  const char* txt = "liblm binary STL (lattice meta-mesh triangulation)";
+  std::memcpy(hdr, txt, std::strlen(txt));
+  uint32_t c = n_tris > 0xffffffffll ? 0xffffffffu : (uint32_t)(n_tris < 0 ? 0 : n_tris);
+  hdr[80] = c & 255;
+  hdr[81] = (c >> 8) & 255;
+  hdr[82] = (c >> 16) & 255;
+  hdr[83] = (c >> 24) & 255;
+}
+
+lm_status lm_triangulate_stream(lm_metamesh* mm, int32_t k, int64_t chunk_items, void* h_ring,
+                                int64_t slot_bytes, int32_t n_slots, lm_chunk_cb cb, void* user,
+                                void* stream, int64_t* h_total) {
+  if (!mm || !valid_k(k) || chunk_items <= 0 || !h_ring || slot_bytes <= 0 || n_slots < 2)
+    return LM_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  lm_status s = LM_OK;
+  if (mm->tri_k != k) {
+    s = lm_tri_count(mm, k, stream, nullptr);
+    if (s != LM_OK) return s;
+  }
+  const int64_t n_items = mm->E + mm->N;
+  const int64_t n_chunks = (n_items + chunk_items - 1) / chunk_items;
+  // chunk boundaries (host copy of the offsets at chunk starts)
+  std::vector<int64_t> bnd(n_chunks + 1);
+  for (int64_t c = 0; c <= n_chunks; c++) {
+    int64_t it = std::min(c * chunk_items, n_items);
+    if (cudaMemcpyAsync(&bnd[c], mm->tri_off + it, 8, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+      return LM_ERR_CUDA;
+  }
+  LM_CK(cudaStreamSynchronize(st));
+  int64_t max_tris = 0;
+  for (int64_t c = 0; c < n_chunks; c++) max_tris = std::max(max_tris, bnd[c + 1] - bnd[c]);
+  if (max_tris * 50 > slot_bytes) return LM_ERR_CAPACITY;
+  uint8_t* dbuf[2] = {nullptr, nullptr};
+  cudaStream_t cs;
+  LM_CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  cudaEvent_t done_comp[2], done_copy[2];
+  for (int q = 0; q < 2; q++) {
+    LM_CK(cudaMallocAsync((void**)&dbuf[q], (size_t)std::max<int64_t>(max_tris, 1) * 50, st));
+    cudaEventCreateWithFlags(&done_comp[q], cudaEventDisableTiming);
+    cudaEventCreateWithFlags(&done_copy[q], cudaEventDisableTiming);
+  }
+  std::vector<cudaEvent_t> copied(n_chunks);
+  for (int64_t c = 0; c < n_chunks && s == LM_OK; c++) {
+    int q = (int)(c & 1);
+    int64_t b = c * chunk_items, e = std::min(n_items, b + chunk_items);
+    if (c >= 2) cudaStreamWaitEvent(st, done_copy[q], 0);
+    s = lm_triangulate(mm, k, b, e, dbuf[q], max_tris, stream);
+    if (s != LM_OK) break;
+    cudaEventRecord(done_comp[q], st);
+    // the host slot of chunk c was last used by chunk c - n_slots: wait for
+    // its copy and hand it to the caller first
+    if (c >= n_slots) {
+      cudaEventSynchronize(copied[c - n_slots]);
+      cudaEventDestroy(copied[c - n_slots]);
+      copied[c - n_slots] = nullptr;
+      int64_t pc = c - n_slots;
+      if (cb) cb(pc, pc * chunk_items, bnd[pc + 1] - bnd[pc], (uint8_t*)h_ring + (pc % n_slots) * slot_bytes, user);
+    }
+    cudaStreamWaitEvent(cs, done_comp[q], 0);
+    int64_t nb = (bnd[c + 1] - bnd[c]) * 50;
+    if (nb > 0) {
+      cudaError_t ce = cudaMemcpyAsync((uint8_t*)h_ring + (c % n_slots) * slot_bytes, dbuf[q], nb,
+                                       cudaMemcpyDeviceToHost, cs);
+      if (ce != cudaSuccess) s = st_cuda(ce);
+    }
+    cudaEventRecord(done_copy[q], cs);
+    cudaEventCreateWithFlags(&copied[c], cudaEventDisableTiming);
+    cudaEventRecord(copied[c], cs);
+  }
+  for (int64_t c = std::max<int64_t>(0, n_chunks - n_slots); c < n_chunks; c++) {
+    if (!copied[c]) continue;
+    cudaEventSynchronize(copied[c]);
+    cudaEventDestroy(copied[c]);
+    if (cb && s == LM_OK) cb(c, c * chunk_items, bnd[c + 1] - bnd[c], (uint8_t*)h_ring + (c % n_slots) * slot_bytes, user);
+  }
+  cudaStreamSynchronize(cs);
+  for (int q = 0; q < 2; q++) {
+    cudaFreeAsync(dbuf[q], st);
+    cudaEventDestroy(done_comp[q]);
+    cudaEventDestroy(done_copy[q]);
+  }
+  cudaStreamSynchronize(st);
+  cudaStreamDestroy(cs);
+  if (h_total) *h_total = bnd[n_chunks];
+  if (s == LM_OK) s = lm_last_error(mm, stream);
+  return s;
+}
+
+long long lm_launch_count(void) { return g_launches.load(); }
+
+lm_status lm_copy_to_host(void* h_dst, const void* d_src, int64_t bytes) {
+  if (bytes < 0 || (bytes > 0 && (!h_dst || !d_src))) return LM_ERR_INVALID_ARG;
+  if (bytes == 0) return LM_OK;
+  return cudaMemcpy(h_dst, d_src, (size_t)bytes, cudaMemcpyDeviceToHost) == cudaSuccess ? LM_OK : LM_ERR_CUDA;
+}
+
+lm_status lm_metamesh_backward(lm_metamesh* mm, int32_t k, double w_area, double w_vol, void* d_grad_xyz,
+                               void* d_grad_r, void* stream, double* h_area, double* h_volume) {
+  (void)mm; (void)k; (void)w_area; (void)w_vol; (void)d_grad_xyz; (void)d_grad_r; (void)stream;
+  (void)h_area; (void)h_volume;
+  return LM_ERR_STATE;
+}
+
+}  // extern "C"

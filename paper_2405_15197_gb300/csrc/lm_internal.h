@@ -1,0 +1,139 @@
+// Internal declarations shared by the liblm translation units.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "../../include/liblm.h"
+
+namespace lm {
+
+struct Node64;
+
+// valence buckets of the meta-mesh kernel
+enum { NB_BUCKETS = 3 };
+__host__ __device__ inline int bucket_of(int d) { return d <= 16 ? 0 : (d <= 32 ? 1 : 2); }
+
+template <typename T>
+struct MMLaunch {
+  // inputs
+  const T* xyz;
+  const int32_t* ends;
+  const T* node_R;
+  const int64_t* row_ptr;
+  const int32_t* adj;
+  int64_t n_nodes, n_struts;
+  const int32_t* nodes;
+  int64_t n_list;
+  int* queue;
+  int nodes_per_task;
+  uint32_t* node_flags;
+  int32_t* node_cnt;
+  int32_t* end_cnt;
+  const int64_t *vtx_off, *arc_off, *hole_off_n, *hent_off_n, *end_off;
+  T* vtx_z;
+  uint64_t* vtx_key;
+  uint32_t* vtx_flags;
+  uint32_t* vtx_gen;
+  int32_t* arc_ends;
+  uint32_t* arc_vtx;
+  T* arc_phi;
+  uint32_t* loop_ent;
+  int64_t* hole_off;
+  uint32_t* hole_ent;
+  int* overflow;
+};
+
+// persistent meta-mesh launch of one bucket; grid_ctas <= 0: resident CTAs
+// x SM count.  Returns the CTAs launched in *used_ctas.
+template <typename T>
+cudaError_t launch_metamesh(int bucket, bool emit, const MMLaunch<T>& a, int block_warps,
+                            int grid_ctas, cudaStream_t st, int* used_ctas);
+
+template <typename T>
+struct TriLaunch {
+  const T* xyz;
+  const int32_t* ends;
+  const T* node_R;
+  const int64_t* row_ptr;
+  const int32_t* adj;
+  int64_t n_nodes, n_struts;
+  const int64_t *vtx_off, *arc_off, *end_off, *node_hole_off, *hole_off;
+  const T* vtx_z;
+  const uint32_t* vtx_gen;
+  const uint32_t* arc_vtx;
+  const T* arc_phi;
+  const uint32_t* loop_ent;
+  const uint32_t* hole_ent;
+  int k;
+  int32_t* item_cnt;
+  const int64_t* tri_off;
+  int64_t item_begin, item_end, capacity;
+  const int64_t* first_ptr;  // device: tri_off + item_begin
+  uint8_t* out;
+  double* acc;
+  int* queue;  // 2 counters
+  int* err;
+  int pmax, emax;
+  int* max_pts;
+  Node64* scratch;
+  int64_t scratch_warps;
+};
+
+template <typename T>
+cudaError_t launch_tri_count(const TriLaunch<T>& a, cudaStream_t st);
+template <typename T>
+cudaError_t launch_tri_emit(const TriLaunch<T>& a, cudaStream_t st);
+size_t node64_bytes();
+int64_t tri_scratch_warps();
+// host-side count of kernels this library launched (all threads)
+void count_launch(int n = 1);
+
+}  // namespace lm
+
+struct lm_metamesh {
+  int dtype;
+  int64_t N, E;
+  const void* xyz;
+  const int32_t* ends;
+  const void* radii;
+  lm_options opt;
+  cudaStream_t st;
+  // CSR and per-node data
+  void* node_R;
+  int64_t* row_ptr;
+  int32_t* adj;
+  uint32_t* node_flags;
+  int max_valence;
+  int max_loop_entries;
+  // meta-mesh
+  int64_t *vtx_off, *arc_off, *hole_off_n, *hent_off_n, *end_off;
+  void* vtx_z;
+  uint64_t* vtx_key;
+  uint32_t *vtx_flags, *vtx_gen;
+  int32_t* arc_ends;
+  uint32_t* arc_vtx;
+  void* arc_phi;
+  uint32_t* loop_ent;
+  int64_t* hole_off;
+  uint32_t* hole_ent;
+  int64_t V, A, LE, H, HE;
+  int64_t n_ell, n_circ, n_degenerate;
+  uint32_t flags_or;
+  // triangulation state (one k at a time)
+  int tri_k;
+  int32_t* item_cnt;
+  int64_t* tri_off;
+  int64_t tri_total;
+  int tri_pmax;
+  lm::Node64* scratch;
+  int64_t scratch_warps;
+  int* d_err;
+  int* d_queue;
+  int* d_misc;
+  double* d_acc;
+  int64_t* scan_ws;
+  int64_t scan_ws_n;
+  // timing of the last build (device ms): csr, count, emit
+  float t_csr, t_count, t_emit;
+};

@@ -1,0 +1,793 @@
+// Warp-per-node meta-meshing (Section 4.3 of arXiv 2405.15197).
+//
+// One warp owns one node at a time: the node's strut ends are staged in
+// shared memory (the paper's "per-node strut lists"), candidate vertices are
+// evaluated one generator per lane (the paper's "one ellipse per thread"),
+// survivors are compacted with warp ballots in canonical order, loops are
+// built one strut end per lane, and per-node counts feed warp-aggregated
+// prefix sums.  The same code runs twice: a count pass (sizes only) and an
+// emit pass that writes the structure-of-arrays layout at scanned offsets
+// (Section 4.3.2's index region + data region, here CSR offsets + SoA).
+//
+// Arithmetic is T (float for FP32 lattices, double for FP64 lattices).  For
+// FP32 every decision whose FP32 value lies inside a safety margin of its
+// threshold, or comes from an ill-conditioned configuration, is taken again
+// in FP64 from the inputs (near-parallel pairs, tangencies, angular ties).
+#pragma once
+#include "lm_geom.cuh"
+
+namespace lm {
+
+template <int MD, int MV, int MLE, int MA>
+struct Cap {
+  static constexpr int D = MD, V = MV, LE = MLE, A = MA;
+};
+
+template <typename T, typename C>
+struct WarpSmem {
+  EndG<T> E[C::D];
+  EndG<double> E64[sizeof(T) == 4 ? C::D : 1];
+  uint64_t e64_valid;
+  uint64_t tan_small[C::D], tan_neg[C::D], coinc[C::D];
+  V3<T> vz[C::V];
+  uint64_t vkey[C::V];
+  uint32_t vgen[C::V];
+  uint8_t vfl[C::V];
+  int nv;
+  uint32_t nflags;
+  uint16_t loop_off[C::D + 1];
+  uint8_t le_v[C::LE];
+  int8_t le_lab[C::LE];
+  uint8_t le_rev[C::LE];
+  int16_t le_arc[C::LE];
+  T le_ang[C::LE];
+  T le_dphi[C::LE];
+  uint8_t a_owner[C::A];
+  int8_t a_other[C::A];
+  uint8_t a_v0[C::A], a_v1[C::A];
+  T a_phi0[C::A], a_dphi[C::A];
+  int na;
+  uint16_t h_off[C::A + 1];
+  uint16_t h_ent[C::A];
+  int nh, nhe;
+};
+
+template <typename T>
+struct MMArgs {
+  LatDev<T> lat;
+  const int32_t* nodes;  // node list of this valence bucket
+  int64_t n_list;
+  int* queue;            // work counter (persistent scheduling)
+  int nodes_per_task;
+  uint32_t* node_flags;  // [N]
+  // count pass
+  int32_t* node_cnt;     // [N][4]: V, A, H, HE
+  int32_t* end_cnt;      // [2E]
+  // emit pass
+  const int64_t *vtx_off, *arc_off, *hole_off_n, *hent_off_n, *end_off;
+  T* vtx_z;
+  uint64_t* vtx_key;
+  uint32_t* vtx_flags;
+  uint32_t* vtx_gen;
+  int32_t* arc_ends;
+  uint32_t* arc_vtx;
+  T* arc_phi;
+  uint32_t* loop_ent;
+  int64_t* hole_off;
+  uint32_t* hole_ent;
+  int* overflow;
+};
+
+// FP64 copies of the node's strut ends, built on first use.
+template <typename T, typename C>
+__device__ void ensure64(WarpSmem<T, C>& S, const LatDev<T>& L, int64_t n, int d, int lane) {
+  if (sizeof(T) == 8) return;
+  uint64_t all = d >= 64 ? ~0ull : ((1ull << d) - 1);
+  uint64_t miss = all & ~S.e64_valid;
+  if (!miss) return;
+  for (int li = lane; li < d; li += 32)
+    if (miss >> li & 1ull) S.E64[li] = make_end<T, double>(L, n, S.E[li].end_id);
+  __syncwarp();
+  if (lane == 0) S.e64_valid |= miss;
+  __syncwarp();
+}
+template <typename T, typename C>
+__device__ __forceinline__ const EndG<double>* ends64(WarpSmem<T, C>& S) {
+  if constexpr (sizeof(T) == 8) return reinterpret_cast<const EndG<double>*>(S.E);
+  else return S.E64;
+}
+
+// canonical generator g -> code: pairs (i<j) first, then triples (i<j<k),
+// both lexicographic
+__device__ __forceinline__ uint32_t decode_gen(int g, int d, int np) {
+  if (g < np) {
+    int i = 0, rem = g;
+    while (rem >= d - 1 - i) { rem -= d - 1 - i; i++; }
+    return gen_code(0, 0, i, i + 1 + rem, 0);
+  }
+  int rem = g - np, i = 0;
+  while (true) {
+    int m = d - 1 - i;
+    int c = m * (m - 1) / 2;
+    if (rem < c) break;
+    rem -= c;
+    i++;
+  }
+  int j = i + 1;
+  while (rem >= d - 1 - j) { rem -= d - 1 - j; j++; }
+  return gen_code(1, 0, i, j, j + 1 + rem);
+}
+
+
+// exact (FP64) loop angle of vertex v around local end li
+template <typename T, typename C>
+__device__ double angle64(WarpSmem<T, C>& S, int d, double R, int li, int v) {
+  const EndG<double>* E = ends64(S);
+  V3<double> z = vertex_from_gen<double>(E, d, R, S.vgen[v]);
+  return (double)norm_angle(raw_angle(E[li], z));
+}
+
+// Envelope arg-max among the labels in (cm, cs) at the mid-angle pm, with
+// the sequential tie rule (a later label must beat the best by ETA_SIGMA R).
+template <typename U>
+__device__ int midpoint_label(const EndG<U>* E, int li, uint64_t cm, bool cs, U pm, U R, U& gap) {
+  U c, s;
+  lm_sincos(pm, &s, &c);
+  U best = cs ? U(0) : U(0);
+  int label = cs ? -1 : -2;
+  U second = U(-1e30);
+  for (int j = 0; j < 64; j++) {
+    if (!(cm >> j & 1ull)) continue;
+    U h = hval(E[li], E[j], c, s, R);
+    if (label == -2 || h > best + U(ETA_SIGMA) * R) {
+      if (label != -2) second = best;
+      best = h;
+      label = j;
+    } else if (h > second) {
+      second = h;
+    }
+  }
+  if (cs && label >= 0 && second < U(0)) second = U(0);
+  gap = best - second;
+  return label;
+}
+
+template <typename T, typename C, bool EMIT>
+__device__ void node_metamesh(WarpSmem<T, C>& S, const MMArgs<T>& A, int64_t n, int lane) {
+  const LatDev<T>& L = A.lat;
+  constexpr bool IS64 = sizeof(T) == 8;
+  const int64_t base = L.row_ptr[n];
+  const int d = (int)(L.row_ptr[n + 1] - base);
+  const T R = L.node_R[n];
+  const double R64 = (double)L.node_R[n];
+  if (d == 0) {
+    if (!EMIT && lane == 0) {
+      A.node_flags[n] = 0;
+      for (int q = 0; q < 4; q++) A.node_cnt[4 * n + q] = 0;
+    }
+    return;
+  }
+  // ---- strut ends of the node
+  for (int li = lane; li < d; li += 32) S.E[li] = make_end<T, T>(L, n, L.adj[base + li]);
+  for (int li = lane; li < d; li += 32) S.tan_small[li] = S.tan_neg[li] = S.coinc[li] = 0;
+  if (lane == 0) {
+    S.nv = 0;
+    S.nflags = 0;
+    S.e64_valid = 0;
+  }
+  __syncwarp();
+
+  // ---- pair classification (tangency 1 - max_phi k_j, coincident circles)
+  {
+    const int npair = d * d;
+    for (int c0 = 0; c0 < npair; c0 += 32) {
+      int p = c0 + lane;
+      int i = p / d, j = p % d;
+      bool act = p < npair && i != j;
+      bool unc = false;
+      bool ts = false, tn = false, co = false;
+      if (act) {
+        T c = dot(S.E[i].u, S.E[j].u);
+        T pr = lm_sqrt(fmax(T(0), T(1) - c * c));
+        T tau = T(1) - (S.E[i].co * c + fabs(S.E[i].s) * pr) * S.E[j].ico;
+        if (IS64) {
+          ts = fabs(tau) < T(EPS_TAN);
+          tn = tau <= T(0);
+        } else if (tau < T(M_COND)) {
+          unc = true;
+        }
+        if (i < j) {
+          T q = T(1) - c * c;
+          if (IS64) {
+            if (q < T(EPS_PAR)) {
+              T coin = c < T(0) ? S.E[i].s + S.E[j].s : S.E[i].s - S.E[j].s;
+              co = fabs(coin) < T(EPS_TAN);
+            }
+          } else if (q < T(M_COND)) {
+            unc = true;
+          }
+        }
+      }
+      if (!IS64 && __any_sync(0xffffffffu, unc)) {
+        ensure64(S, L, n, d, lane);
+        if (unc) {
+          const EndG<double>* E = ends64(S);
+          double c = dot(E[i].u, E[j].u);
+          double pr = sqrt(fmax(0.0, 1.0 - c * c));
+          double tau = 1.0 - (E[i].co * c + fabs(E[i].s) * pr) * E[j].ico;
+          ts = fabs(tau) < EPS_TAN;
+          tn = tau <= 0.0;
+          if (i < j) {
+            double q = 1.0 - c * c;
+            if (q < EPS_PAR) {
+              double coin = c < 0.0 ? E[i].s + E[j].s : E[i].s - E[j].s;
+              co = fabs(coin) < EPS_TAN;
+            }
+          }
+        }
+      }
+      if (act && ts) { atomicOr((unsigned long long*)&S.tan_small[i], 1ull << j); atomicOr((unsigned long long*)&S.tan_small[j], 1ull << i); }
+      if (act && tn) { atomicOr((unsigned long long*)&S.tan_neg[i], 1ull << j); atomicOr((unsigned long long*)&S.tan_neg[j], 1ull << i); }
+      if (act && co) { atomicOr((unsigned long long*)&S.coinc[i], 1ull << j); atomicOr((unsigned long long*)&S.coinc[j], 1ull << i); }
+    }
+  }
+  __syncwarp();
+
+  // ---- candidate vertices in canonical order, screened, deduplicated
+  const int np = d * (d - 1) / 2;
+  const int nt = d * (d - 1) * (d - 2) / 6;
+  const int ng = np + nt;
+  bool overflow = false;
+  uint32_t nflags = 0;
+  for (int c0 = 0; c0 < ng && !overflow; c0 += 32) {
+    int g = c0 + lane;
+    GenOut<T> o;
+    uint32_t code = 0;
+    o.nroot = 0;
+    o.unc = 0;
+    o.nflags = 0;
+    if (g < ng) {
+      code = decode_gen(g, d, np);
+      eval_gen<T, IS64>(S.E, d, R, code, o);
+    }
+    uint64_t gmask = 0;
+    if (g < ng) {
+      int t = code & 3;
+      gmask = (1ull << ((code >> 3) & 63)) | (1ull << ((code >> 9) & 63));
+      if (t == 1) gmask |= 1ull << ((code >> 15) & 63);
+    }
+    // duplicates of vertices found by earlier chunks: same point, generators
+    // all incident to that vertex
+    const int nv0 = S.nv;
+    if (o.nroot == 2) {
+      for (int r = 0; r < 2; r++) {
+        if (o.state[r] == 0) continue;
+        for (int v = 0; v < nv0; v++) {
+          if ((S.vkey[v] & gmask) != gmask) continue;
+          V3<T> dz = o.z[r] - S.vz[v];
+          if (dot(dz, dz) < T(1e-8) * R * R) {
+            o.state[r] = 3;
+            break;
+          }
+        }
+      }
+    }
+    bool need64 = !IS64 && (o.unc || (o.nroot == 2 && (o.state[0] == 2 || o.state[1] == 2)));
+    if (!IS64 && __any_sync(0xffffffffu, need64)) {
+      ensure64(S, L, n, d, lane);
+      if (need64) {
+        GenOut<double> o64;
+        eval_gen<double, true>(ends64(S), d, R64, code, o64);
+        o.nroot = o64.nroot;
+        o.unc = 0;
+        o.nflags = o64.nflags;
+        for (int r = 0; r < 2; r++) {
+          o.z[r] = mk3((T)o64.z[r].x, (T)o64.z[r].y, (T)o64.z[r].z);
+          o.t0[r] = (T)o64.t0[r];
+          o.key[r] = o64.key[r];
+          o.sphere[r] = o64.sphere[r];
+          o.state[r] = o64.state[r];
+          o.tangent[r] = o64.tangent[r];
+          o.kflags[r] = o64.kflags[r];
+        }
+      }
+    }
+    nflags |= o.nflags;
+    // sequential append of survivors in canonical order
+    uint32_t k0 = __ballot_sync(0xffffffffu, o.nroot == 2 && o.state[0] == 1);
+    uint32_t k1 = __ballot_sync(0xffffffffu, o.nroot == 2 && o.state[1] == 1);
+    uint32_t any = k0 | k1;
+    while (any) {
+      int src = __ffs(any) - 1;
+      any &= any - 1;
+      for (int r = 0; r < 2; r++) {
+        if (!(((r == 0 ? k0 : k1) >> src) & 1u)) continue;
+        V3<T> z = mk3(__shfl_sync(0xffffffffu, o.z[r].x, src), __shfl_sync(0xffffffffu, o.z[r].y, src),
+                      __shfl_sync(0xffffffffu, o.z[r].z, src));
+        uint64_t key = __shfl_sync(0xffffffffu, (unsigned long long)o.key[r], src);
+        int sph = __shfl_sync(0xffffffffu, (int)o.sphere[r], src);
+        uint32_t kf = __shfl_sync(0xffffffffu, o.kflags[r], src);
+        uint32_t gc = __shfl_sync(0xffffffffu, code, src) | ((uint32_t)r << 2);
+        int nvc = S.nv;
+        bool dup = false, dunc = false;
+        for (int v = lane; v < nvc; v += 32) {
+          if (S.vkey[v] != key || ((S.vfl[v] & VF_SPHERE) != 0) != (sph != 0)) continue;
+          V3<T> dz = z - S.vz[v];
+          T dd = lm_sqrt(dot(dz, dz));
+          if (IS64) {
+            dup |= dd <= T(ETA_DEDUP) * R;
+          } else {
+            if (dd <= T(0.5 * ETA_DEDUP) * R) dup = true;
+            else if (dd <= T(2.0 * ETA_DEDUP) * R) dunc = true;
+          }
+        }
+        dup = __any_sync(0xffffffffu, dup);
+        if (!IS64 && !dup && __any_sync(0xffffffffu, dunc)) {
+          ensure64(S, L, n, d, lane);
+          V3<double> z64 = vertex_from_gen<double>(ends64(S), d, R64, gc);
+          for (int v = lane; v < nvc; v += 32) {
+            if (S.vkey[v] != key || ((S.vfl[v] & VF_SPHERE) != 0) != (sph != 0)) continue;
+            V3<double> w = vertex_from_gen<double>(ends64(S), d, R64, S.vgen[v]);
+            V3<double> dz = z64 - w;
+            dup |= sqrt(dot(dz, dz)) <= ETA_DEDUP * R64;
+          }
+          dup = __any_sync(0xffffffffu, dup);
+        }
+        if (dup) continue;
+        if (nvc >= C::V) {
+          overflow = true;
+          break;
+        }
+        if (lane == 0) {
+          S.vz[nvc] = z;
+          S.vkey[nvc] = key;
+          S.vfl[nvc] = sph ? VF_SPHERE : 0;
+          S.vgen[nvc] = gc;
+          S.nv = nvc + 1;
+        }
+        nflags |= kf;
+        __syncwarp();
+      }
+      if (overflow) break;
+    }
+    __syncwarp();
+  }
+  nflags = __reduce_or_sync(0xffffffffu, nflags);
+
+  // ---- seam vertices for strut ends no vertex touches
+  if (!overflow) {
+    uint32_t seam_need = 0;
+    for (int i0 = 0; i0 < d; i0 += 32) {
+      int i = i0 + lane;
+      bool need = false, unc = false;
+      int lab = -1;
+      T best = T(0);
+      if (i < d) {
+        bool has = false;
+        for (int v = 0; v < S.nv; v++) has |= (S.vkey[v] >> i) & 1ull;
+        need = !has;
+        if (need) {
+          T top = T(0), second = T(-1e30);
+          for (int j = 0; j < d; j++) {
+            if (j == i) continue;
+            T h = hval(S.E[i], S.E[j], T(1), T(0), R);
+            if (h > best + T(ETA_SIGMA) * R) {
+              best = h;
+              lab = j;
+            }
+            if (h > top) { second = top; top = h; }
+            else if (h > second) second = h;
+          }
+          if (!IS64 && top - second <= T(M_LEN) * R) unc = true;
+        }
+      }
+      if (!IS64 && __any_sync(0xffffffffu, unc)) {
+        ensure64(S, L, n, d, lane);
+        if (unc) {
+          const EndG<double>* E = ends64(S);
+          double b = 0.0;
+          lab = -1;
+          for (int j = 0; j < d; j++) {
+            if (j == i) continue;
+            double h = hval(E[i], E[j], 1.0, 0.0, R64);
+            if (h > b + ETA_SIGMA * R64) { b = h; lab = j; }
+          }
+          best = (T)b;
+        }
+      }
+      uint32_t m = __ballot_sync(0xffffffffu, need);
+      while (m) {
+        int src = __ffs(m) - 1;
+        m &= m - 1;
+        int li = i0 + src;
+        int lb = __shfl_sync(0xffffffffu, lab, src);
+        T bs = __shfl_sync(0xffffffffu, best, src);
+        int nvc = S.nv;
+        if (nvc >= C::V) { overflow = true; break; }
+        if (lane == 0) {
+          S.vz[nvc] = surf_point(S.E[li], T(1), T(0), bs, R);
+          S.vkey[nvc] = (1ull << li) | (lb >= 0 ? (1ull << lb) : 0ull);
+          S.vfl[nvc] = VF_SEAM | (lb < 0 ? VF_SPHERE : 0u);
+          S.vgen[nvc] = gen_code(2, 0, li, lb < 0 ? 0 : lb, 0) | (lb >= 0 ? (1u << 21) : 0u);
+          S.nv = nvc + 1;
+        }
+        if (lb >= 0) nflags |= NF_DEGENERATE | NF_SEAM_CUT;
+        __syncwarp();
+      }
+      (void)seam_need;
+    }
+  }
+  __syncwarp();
+
+  // ---- loops: per strut end, vertices by angle, arcs labelled
+  int nle = 0;
+  if (!overflow) {
+    int cnt[2] = {0, 0};
+    for (int t = 0; t < 2; t++) {
+      int i = lane + 32 * t;
+      if (i < d)
+        for (int v = 0; v < S.nv; v++) cnt[t] += (S.vkey[v] >> i) & 1ull;
+    }
+    int off0 = warp_excl_scan(cnt[0], lane);
+    int tot0 = __shfl_sync(0xffffffffu, off0 + cnt[0], 31);
+    int off1 = tot0 + warp_excl_scan(cnt[1], lane);
+    nle = __shfl_sync(0xffffffffu, off1 + cnt[1], 31);
+    if (nle > C::LE) overflow = true;
+    if (!overflow) {
+      if (lane < d) S.loop_off[lane] = off0;
+      if (lane + 32 < d) S.loop_off[lane + 32] = off1;
+      if (lane == 0) S.loop_off[d] = nle;
+    }
+  }
+  __syncwarp();
+  if (!overflow) {
+    for (int t = 0; t < 2; t++) {
+      int i = lane + 32 * t;
+      bool unc = false;
+      int b0 = 0, nl = 0;
+      if (i < d) {
+        b0 = S.loop_off[i];
+        nl = S.loop_off[i + 1] - b0;
+        int q = 0;
+        for (int v = 0; v < S.nv; v++) {
+          if (!((S.vkey[v] >> i) & 1ull)) continue;
+          T a = raw_angle(S.E[i], S.vz[v]);
+          if (!IS64 && fabs(a + T(ETA_PHI)) <= T(M_ANG)) unc = true;
+          a = norm_angle(a);
+          // stable insertion by angle
+          int p = q;
+          while (p > 0 && S.le_ang[b0 + p - 1] > a) {
+            S.le_ang[b0 + p] = S.le_ang[b0 + p - 1];
+            S.le_v[b0 + p] = S.le_v[b0 + p - 1];
+            p--;
+          }
+          S.le_ang[b0 + p] = a;
+          S.le_v[b0 + p] = (uint8_t)v;
+          q++;
+        }
+        if (!IS64)
+          for (int p = 0; p + 1 < nl; p++)
+            if (S.le_ang[b0 + p + 1] - S.le_ang[b0 + p] <= T(M_ANG)) unc = true;
+      }
+      if (!IS64 && __any_sync(0xffffffffu, unc)) {
+        ensure64(S, L, n, d, lane);
+        if (unc) {
+          // exact angles, stable re-sort by (angle, vertex id)
+          double ang[C::V > 64 ? 64 : C::V];
+          int vv[C::V > 64 ? 64 : C::V];
+          int m = 0;
+          for (int v = 0; v < S.nv && m < 64; v++) {
+            if (!((S.vkey[v] >> i) & 1ull)) continue;
+            double a = angle64(S, d, R64, i, v);
+            int p = m;
+            while (p > 0 && ang[p - 1] > a) { ang[p] = ang[p - 1]; vv[p] = vv[p - 1]; p--; }
+            ang[p] = a;
+            vv[p] = v;
+            m++;
+          }
+          for (int p = 0; p < m; p++) {
+            S.le_ang[b0 + p] = (T)ang[p];
+            S.le_v[b0 + p] = (uint8_t)vv[p];
+            if (p + 1 < m && ang[p + 1] - ang[p] <= ETA_PHI) nflags |= NF_DEGENERATE | NF_ANGLE_TIE;
+          }
+        }
+      }
+      if (IS64 && i < d)
+        for (int p = 0; p + 1 < nl; p++)
+          if (S.le_ang[b0 + p + 1] - S.le_ang[b0 + p] <= T(ETA_PHI)) nflags |= NF_DEGENERATE | NF_ANGLE_TIE;
+    }
+  }
+  __syncwarp();
+  // labels
+  if (!overflow) {
+    for (int t = 0; t < 2; t++) {
+      int i = lane + 32 * t;
+      if (i >= d) continue;
+      int b0 = S.loop_off[i], nl = S.loop_off[i + 1] - b0;
+      for (int q = 0; q < nl; q++) {
+        int va = S.le_v[b0 + q], vb = S.le_v[b0 + (q + 1) % nl];
+        T dph = (q + 1 < nl) ? S.le_ang[b0 + q + 1] - S.le_ang[b0 + q]
+                             : S.le_ang[b0] + T(PI2) - S.le_ang[b0 + q];
+        uint64_t cm = (S.vkey[va] & S.vkey[vb]) & ~(1ull << i);
+        bool cs = (S.vfl[va] & VF_SPHERE) && (S.vfl[vb] & VF_SPHERE);
+        int ncand = __popcll(cm) + (cs ? 1 : 0);
+        int label;
+        if (ncand == 1) {
+          label = cs ? -1 : __ffsll(cm) - 1;
+        } else {
+          if (ncand == 0) {
+            nflags |= NF_INCONSISTENT;
+            cm = (d >= 64 ? ~0ull : ((1ull << d) - 1)) & ~(1ull << i);
+            cs = true;
+          }
+          T gap;
+          label = midpoint_label<T>(S.E, i, cm, cs, S.le_ang[b0 + q] + T(0.5) * dph, R, gap);
+          if (!IS64 && gap <= T(M_LEN) * R) {
+            // exact re-decision (rare; no warp-collective calls here)
+            if (S.e64_valid != ((d >= 64) ? ~0ull : ((1ull << d) - 1))) {
+              for (int li = 0; li < d; li++)
+                if (!((S.e64_valid >> li) & 1ull)) S.E64[li] = make_end<T, double>(L, n, S.E[li].end_id);
+            }
+            const EndG<double>* E = ends64(S);
+            double a0 = angle64(S, d, R64, i, va);
+            double a1 = angle64(S, d, R64, i, vb);
+            double dd = a1 - a0;
+            if (q + 1 >= nl) dd += PI2;
+            double g64;
+            label = midpoint_label<double>(E, i, cm, cs, a0 + 0.5 * dd, R64, g64);
+          }
+        }
+        S.le_lab[b0 + q] = (int8_t)label;
+        S.le_dphi[b0 + q] = dph;
+      }
+    }
+  }
+  nflags = __reduce_or_sync(0xffffffffu, nflags);
+  __syncwarp();
+
+  // ---- activity of flagged pairs
+  if (!overflow) {
+    uint32_t f = 0;
+    for (int v = lane; v < S.nv; v += 32) {
+      uint64_t key = S.vkey[v];
+      for (int i = 0; i < d; i++) {
+        if (!((key >> i) & 1ull)) continue;
+        if (key & S.tan_small[i]) f |= NF_NEAR_TANGENT;
+        if (key & S.tan_neg[i]) f |= NF_DEGENERATE | NF_STEEP;
+      }
+    }
+    uint64_t hc = 0;
+    for (int i = lane; i < d; i += 32) {
+      int b0 = S.loop_off[i], nl = S.loop_off[i + 1] - b0;
+      for (int q = 0; q < nl; q++)
+        if (S.le_lab[b0 + q] < 0) hc |= 1ull << i;
+    }
+    hc = warp_or64(hc);
+    for (int i = lane; i < d; i += 32)
+      if (((hc >> i) & 1ull) && (S.coinc[i] & hc)) f |= NF_NEAR_TANGENT;
+    nflags |= __reduce_or_sync(0xffffffffu, f);
+  }
+
+  // ---- node-local arcs: own arcs by (owner end, loop position)
+  int na = 0;
+  if (!overflow) {
+    int own[2] = {0, 0};
+    for (int t = 0; t < 2; t++) {
+      int i = lane + 32 * t;
+      if (i >= d) continue;
+      int b0 = S.loop_off[i], nl = S.loop_off[i + 1] - b0;
+      int si = S.E[i].end_id >> 1;
+      for (int q = 0; q < nl; q++) {
+        int lb = S.le_lab[b0 + q];
+        if (lb < 0 || si < (S.E[lb].end_id >> 1)) own[t]++;
+      }
+    }
+    int o0 = warp_excl_scan(own[0], lane);
+    int t0 = __shfl_sync(0xffffffffu, o0 + own[0], 31);
+    int o1 = t0 + warp_excl_scan(own[1], lane);
+    na = __shfl_sync(0xffffffffu, o1 + own[1], 31);
+    if (na > C::A) overflow = true;
+    if (!overflow) {
+      for (int t = 0; t < 2; t++) {
+        int i = lane + 32 * t;
+        if (i >= d) continue;
+        int id = t == 0 ? o0 : o1;
+        int b0 = S.loop_off[i], nl = S.loop_off[i + 1] - b0;
+        int si = S.E[i].end_id >> 1;
+        for (int q = 0; q < nl; q++) {
+          int lb = S.le_lab[b0 + q];
+          if (lb < 0 || si < (S.E[lb].end_id >> 1)) {
+            S.a_owner[id] = (uint8_t)i;
+            S.a_other[id] = (int8_t)lb;
+            S.a_v0[id] = S.le_v[b0 + q];
+            S.a_v1[id] = S.le_v[b0 + (q + 1) % nl];
+            S.a_phi0[id] = S.le_ang[b0 + q];
+            S.a_dphi[id] = S.le_dphi[b0 + q];
+            S.le_arc[b0 + q] = (int16_t)id;
+            S.le_rev[b0 + q] = 0;
+            id++;
+          } else {
+            S.le_arc[b0 + q] = -1;
+          }
+        }
+      }
+    }
+  }
+  __syncwarp();
+  // partner search for non-owner entries
+  if (!overflow) {
+    uint32_t f = 0;
+    for (int t = 0; t < 2; t++) {
+      int i = lane + 32 * t;
+      if (i >= d) continue;
+      int b0 = S.loop_off[i], nl = S.loop_off[i + 1] - b0;
+      for (int q = 0; q < nl; q++) {
+        if (S.le_arc[b0 + q] >= 0) continue;
+        int j = S.le_lab[b0 + q];
+        int va = S.le_v[b0 + q], vb = S.le_v[b0 + (q + 1) % nl];
+        int found = -1, rev = 0, nf = 0;
+        int c0 = S.loop_off[j], cl = S.loop_off[j + 1] - c0;
+        for (int q2 = 0; q2 < cl; q2++) {
+          int id = S.le_arc[c0 + q2];
+          if (id < 0 || S.le_lab[c0 + q2] != i) continue;
+          if (S.a_v0[id] == va && S.a_v1[id] == vb) {
+            if (found < 0) { found = id; rev = 0; }
+            nf++;
+          } else if (S.a_v0[id] == vb && S.a_v1[id] == va) {
+            if (found < 0) { found = id; rev = 1; }
+            nf++;
+          }
+        }
+        if (nf != 1 || va == vb) f |= NF_INCONSISTENT;
+        S.le_arc[b0 + q] = (int16_t)(found >= 0 ? found : -2);
+        S.le_rev[b0 + q] = (uint8_t)rev;
+      }
+    }
+    nflags |= __reduce_or_sync(0xffffffffu, f);
+    __syncwarp();
+    // entries without a partner become arcs of their own, appended in
+    // (end, loop position) order
+    if (lane == 0) {
+      for (int i = 0; i < d && !overflow; i++) {
+        int b0 = S.loop_off[i], nl = S.loop_off[i + 1] - b0;
+        for (int q = 0; q < nl; q++) {
+          if (S.le_arc[b0 + q] != -2) continue;
+          if (na >= C::A) { overflow = true; break; }
+          S.a_owner[na] = (uint8_t)i;
+          S.a_other[na] = S.le_lab[b0 + q];
+          S.a_v0[na] = S.le_v[b0 + q];
+          S.a_v1[na] = S.le_v[b0 + (q + 1) % nl];
+          S.a_phi0[na] = S.le_ang[b0 + q];
+          S.a_dphi[na] = S.le_dphi[b0 + q];
+          S.le_arc[b0 + q] = (int16_t)na;
+          S.le_rev[b0 + q] = 0;
+          na++;
+        }
+      }
+    }
+    na = __shfl_sync(0xffffffffu, na, 0);
+    overflow = __shfl_sync(0xffffffffu, (int)overflow, 0);
+  }
+  __syncwarp();
+
+  // ---- holes: circular arcs chained with the hole on the left seen from
+  // outside (lower-id-end frames are right-handed about the outward axis)
+  int nh = 0, nhe = 0;
+  if (!overflow && lane == 0) {
+    uint32_t f = 0;
+    uint8_t used[C::A];
+    for (int a = 0; a < na; a++) used[a] = 0;
+    for (int a0 = 0; a0 < na && !overflow; a0++) {
+      if (S.a_other[a0] >= 0 || used[a0]) continue;
+      S.h_off[nh] = (uint16_t)nhe;
+      int cur = a0;
+      auto hs = [&](int a) { return S.E[S.a_owner[a]].at_lo ? S.a_v1[a] : S.a_v0[a]; };
+      auto he = [&](int a) { return S.E[S.a_owner[a]].at_lo ? S.a_v0[a] : S.a_v1[a]; };
+      while (true) {
+        used[cur] = 1;
+        S.h_ent[nhe++] = (uint16_t)cur | (S.E[S.a_owner[cur]].at_lo ? 0x8000u : 0u);
+        int ev = he(cur);
+        if (ev == hs(a0)) break;
+        int nxt = -1, cnt = 0;
+        for (int a = 0; a < na; a++) {
+          if (S.a_other[a] >= 0 || used[a]) continue;
+          if (hs(a) == ev) {
+            if (nxt < 0) nxt = a;
+            cnt++;
+          }
+        }
+        if (cnt != 1) f |= NF_INCONSISTENT;
+        if (nxt < 0) break;
+        cur = nxt;
+      }
+      nh++;
+    }
+    S.h_off[nh] = (uint16_t)nhe;
+    S.nh = nh;
+    S.nhe = nhe;
+    nflags |= f;
+  }
+  nh = __shfl_sync(0xffffffffu, nh, 0);
+  nhe = __shfl_sync(0xffffffffu, nhe, 0);
+  nflags = __shfl_sync(0xffffffffu, nflags, 0) | nflags;
+  nflags = __reduce_or_sync(0xffffffffu, nflags);
+  __syncwarp();
+
+  // ---- outputs
+  if (!EMIT) {
+    if (overflow) {
+      if (lane == 0) {
+        A.node_flags[n] = nflags | NF_OVERFLOW;
+        for (int q = 0; q < 4; q++) A.node_cnt[4 * n + q] = 0;
+        atomicAdd(A.overflow, 1);
+      }
+      for (int li = lane; li < d; li += 32) A.end_cnt[L.adj[base + li]] = 0;
+      return;
+    }
+    if (lane == 0) {
+      A.node_flags[n] = nflags;
+      A.node_cnt[4 * n + 0] = S.nv;
+      A.node_cnt[4 * n + 1] = na;
+      A.node_cnt[4 * n + 2] = nh;
+      A.node_cnt[4 * n + 3] = nhe;
+    }
+    for (int li = lane; li < d; li += 32)
+      A.end_cnt[L.adj[base + li]] = S.loop_off[li + 1] - S.loop_off[li];
+    return;
+  }
+  if (overflow) return;
+  const int64_t vo = A.vtx_off[n], ao = A.arc_off[n];
+  for (int v = lane; v < S.nv; v += 32) {
+    A.vtx_z[3 * (vo + v)] = S.vz[v].x;
+    A.vtx_z[3 * (vo + v) + 1] = S.vz[v].y;
+    A.vtx_z[3 * (vo + v) + 2] = S.vz[v].z;
+    A.vtx_key[vo + v] = S.vkey[v];
+    A.vtx_flags[vo + v] = S.vfl[v];
+    A.vtx_gen[vo + v] = S.vgen[v];
+  }
+  for (int a = lane; a < na; a += 32) {
+    A.arc_ends[2 * (ao + a)] = S.E[S.a_owner[a]].end_id;
+    A.arc_ends[2 * (ao + a) + 1] = S.a_other[a] < 0 ? -1 : S.E[S.a_other[a]].end_id;
+    A.arc_vtx[ao + a] = (uint32_t)S.a_v0[a] | ((uint32_t)S.a_v1[a] << 8) |
+                        ((uint32_t)S.a_owner[a] << 16) | ((uint32_t)(S.a_other[a] + 1) << 24);
+    A.arc_phi[2 * (ao + a)] = S.a_phi0[a];
+    A.arc_phi[2 * (ao + a) + 1] = S.a_dphi[a];
+  }
+  for (int li = 0; li < d; li++) {
+    int32_t eid = S.E[li].end_id;
+    int64_t eo = A.end_off[eid];
+    int b0 = S.loop_off[li], nl = S.loop_off[li + 1] - b0;
+    for (int q = lane; q < nl; q += 32)
+      A.loop_ent[eo + q] = (uint32_t)S.le_arc[b0 + q] | ((uint32_t)S.le_rev[b0 + q] << 31);
+  }
+  const int64_t ho = A.hole_off_n[n], heo = A.hent_off_n[n];
+  for (int h = lane; h < nh; h += 32) A.hole_off[ho + h] = heo + S.h_off[h];
+  for (int q = lane; q < nhe; q += 32) {
+    uint32_t e = S.h_ent[q];
+    A.hole_ent[heo + q] = (e & 0x7fffu) | ((e & 0x8000u) ? 0x80000000u : 0u);
+  }
+}
+
+// Persistent work-stealing launch: each warp pops tasks of nodes_per_task
+// consecutive entries of the bucket's node list from an atomic counter.
+template <typename T, typename C, bool EMIT>
+__global__ void __launch_bounds__(128) k_metamesh(MMArgs<T> A) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  WarpSmem<T, C>& S = reinterpret_cast<WarpSmem<T, C>*>(smem_raw)[w];
+  const int npt = A.nodes_per_task > 0 ? A.nodes_per_task : 1;
+  while (true) {
+    int task = 0;
+    if (lane == 0) task = atomicAdd(A.queue, 1);
+    task = __shfl_sync(0xffffffffu, task, 0);
+    int64_t first = (int64_t)task * npt;
+    if (first >= A.n_list) break;
+    int64_t last = first + npt < A.n_list ? first + npt : A.n_list;
+    for (int64_t t = first; t < last; t++) {
+      node_metamesh<T, C, EMIT>(S, A, A.nodes[t], lane);
+      __syncwarp();
+    }
+  }
+}
+
+}  // namespace lm

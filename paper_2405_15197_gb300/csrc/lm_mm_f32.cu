@@ -1,0 +1,5 @@
+// Meta-mesh kernels, FP32 arithmetic with FP64 stability steps.
+#include "lm_mm_impl.cuh"
+namespace lm {
+template cudaError_t launch_metamesh<float>(int, bool, const MMLaunch<float>&, int, int, cudaStream_t, int*);
+}

@@ -1,0 +1,5 @@
+// Meta-mesh kernels, FP64 arithmetic (FP64 lattices).
+#include "lm_mm_impl.cuh"
+namespace lm {
+template cudaError_t launch_metamesh<double>(int, bool, const MMLaunch<double>&, int, int, cudaStream_t, int*);
+}

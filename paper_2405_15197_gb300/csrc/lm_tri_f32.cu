@@ -1,0 +1,8 @@
+// Triangulation kernels, FP32 arithmetic with FP64 stability steps.
+#include "lm_tri_impl.cuh"
+namespace lm {
+template cudaError_t launch_tri_count<float>(const TriLaunch<float>&, cudaStream_t);
+template cudaError_t launch_tri_emit<float>(const TriLaunch<float>&, cudaStream_t);
+size_t node64_bytes() { return sizeof(Node64); }
+int64_t tri_scratch_warps() { return 152 * 64 * 2; }
+}

@@ -1,0 +1,121 @@
+// Launchers of the triangulation kernels.
+#pragma once
+#include "lm_internal.h"
+#include "lm_tri.cuh"
+
+namespace lm {
+
+template <typename T>
+TriArgs<T> tri_args(const TriLaunch<T>& a) {
+  TriArgs<T> A;
+  A.lat.xyz = a.xyz;
+  A.lat.ends = a.ends;
+  A.lat.node_R = a.node_R;
+  A.lat.row_ptr = a.row_ptr;
+  A.lat.adj = a.adj;
+  A.lat.n_nodes = a.n_nodes;
+  A.lat.n_struts = a.n_struts;
+  A.vtx_off = a.vtx_off;
+  A.arc_off = a.arc_off;
+  A.end_off = a.end_off;
+  A.node_hole_off = a.node_hole_off;
+  A.hole_off = a.hole_off;
+  A.vtx_z = a.vtx_z;
+  A.vtx_gen = a.vtx_gen;
+  A.arc_vtx = a.arc_vtx;
+  A.arc_phi = a.arc_phi;
+  A.loop_ent = a.loop_ent;
+  A.hole_ent = a.hole_ent;
+  A.k = a.k;
+  A.item_cnt = a.item_cnt;
+  A.tri_off = a.tri_off;
+  A.item_begin = a.item_begin;
+  A.item_end = a.item_end;
+  A.out_first = 0;
+  A.capacity = a.capacity;
+  A.out = a.out;
+  A.acc = a.acc;
+  A.queue = a.queue;
+  A.err = a.err;
+  A.pmax = a.pmax;
+  A.emax = a.emax;
+  A.max_pts = a.max_pts;
+  return A;
+}
+
+static int sm_count() {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return sms;
+}
+
+template <typename T>
+cudaError_t launch_tri_count(const TriLaunch<T>& a, cudaStream_t st) {
+  TriArgs<T> A = tri_args(a);
+  int threads = 256;
+  int64_t warps_needed = (a.n_nodes + a.n_struts + 31) / 32;
+  int64_t grid = (warps_needed * 32 + threads - 1) / threads;
+  int64_t gmax = a.scratch_warps / (threads / 32);
+  if (grid > gmax) grid = gmax;
+  if (grid < 1) grid = 1;
+  count_launch();
+  k_tri_count<T><<<(unsigned)grid, threads, 0, st>>>(A, a.scratch);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_tri_emit(const TriLaunch<T>& a, cudaStream_t st) {
+  TriArgs<T> A = tri_args(a);
+  const int warps = 8, threads = warps * 32;
+  int sms = sm_count();
+  cudaError_t e;
+  // struts
+  if (a.item_begin < a.n_struts) {
+    size_t smem = warps * strut_ws_bytes(a.pmax, a.emax, sizeof(T));
+    e = cudaFuncSetAttribute(k_tri_struts<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tri_struts<T>, threads, smem);
+    if (per_sm < 1) per_sm = 1;
+    int64_t grid = (int64_t)per_sm * sms;
+    int64_t gmax = a.scratch_warps / (2 * warps);
+    if (grid > gmax) grid = gmax;
+    int64_t n = (a.item_end < a.n_struts ? a.item_end : a.n_struts) - a.item_begin;
+    int64_t gneed = (n + warps - 1) / warps;
+    if (grid > gneed) grid = gneed;
+    if (grid < 1) grid = 1;
+    A.queue = a.queue;
+    count_launch();
+    k_tri_struts<T><<<(unsigned)grid, threads, smem, st>>>(A, a.scratch, a.first_ptr);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  // hole fans
+  if (a.item_end > a.n_struts) {
+    size_t wsb = (size_t)a.pmax * sizeof(V3<T>) + 32 * 50 + 64;
+    wsb = (wsb + 15) & ~(size_t)15;
+    size_t smem = warps * wsb;
+    e = cudaFuncSetAttribute(k_tri_holes<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tri_holes<T>, threads, smem);
+    if (per_sm < 1) per_sm = 1;
+    int64_t grid = (int64_t)per_sm * sms;
+    int64_t gmax = a.scratch_warps / (2 * warps);
+    if (grid > gmax) grid = gmax;
+    int64_t nb = a.item_begin > a.n_struts ? a.item_begin : a.n_struts;
+    int64_t n = a.item_end - nb;
+    int64_t gneed = (n + warps - 1) / warps;
+    if (grid > gneed) grid = gneed;
+    if (grid < 1) grid = 1;
+    A.queue = a.queue + 1;
+    count_launch();
+    k_tri_holes<T><<<(unsigned)grid, threads, smem, st>>>(A, a.scratch, a.first_ptr);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+}  // namespace lm

@@ -1,0 +1,215 @@
+"""CUDA path vs FP64 oracle, element by element, through the C ABI.
+
+Meta-mesh (Section 4.3 of arXiv 2405.15197) and triangulation (Section 5,
+Algorithm 1) on seeded synthetic lattices: BCC (the 10^3 closed-form case,
+FP64 and FP32), octet-truss cones, jittered BCC, irregular kNN lattices,
+single struts and stars, plus invalid inputs.
+"""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import oracle  # noqa: E402
+from paper_2405_15197_gb300 import lattices as L  # noqa: E402
+from paper_2405_15197_gb300 import liblm  # noqa: E402
+from tests import parity as P  # noqa: E402
+
+LATTICES = {
+    "bcc10": lambda: L.bcc(10, radius=0.08),
+    "bcc3": lambda: L.bcc(3, radius=0.1),
+    "octet3": lambda: L.octet(3),
+    "bccjit4": lambda: L.bcc(4, jitter=0.05, radius_range=(0.05, 0.09)),
+    "irregular": lambda: L.irregular(1500, seed=9),
+    "strut": lambda: L.single_strut((0.1, 0.2, 0.3), (1.0, 0.7, 0.5), 0.1, 0.1),
+    "cone": lambda: L.single_strut((0.1, 0.2, 0.3), (1.0, 0.7, 0.5), 0.12, 0.05),
+    "star5": lambda: L.star([(1, 0, 0), (0, 1, 0.2), (-1, 0.3, 0), (0.2, -1, 0.5), (0, 0, 1)],
+                            radius=0.12, far_radii=[0.05, 0.09, 0.12, 0.07, 0.1]),
+}
+_cache = {}
+
+
+def build(name, dtype):
+    key = (name, dtype)
+    if key not in _cache:
+        lat = P.lattice_as(LATTICES[name](), dtype)
+        xyz, ends, radii = P.to_device(lat, dtype)
+        mm = liblm.MetaMesh(xyz, ends, radii)
+        _cache[key] = (lat, mm, mm.download(), oracle.Oracle(lat))
+    return _cache[key]
+
+
+@pytest.mark.parametrize("name,dtype", [("bcc10", np.float64), ("bcc10", np.float32), ("bcc3", np.float32),
+                                        ("octet3", np.float32), ("bccjit4", np.float32),
+                                        ("irregular", np.float32), ("strut", np.float32),
+                                        ("cone", np.float32), ("star5", np.float32),
+                                        ("octet3", np.float64), ("irregular", np.float64)])
+def test_metamesh_parity(name, dtype):
+    lat, mm, g, o = build(name, dtype)
+    tol = 1e-12 if dtype == np.float64 else 2e-5
+    rep = P.compare_metamesh(g, o, z_tol=tol, phi_tol=tol)
+    assert rep.ok(), "\n".join(rep.errors[:8])
+    if name == "irregular":
+        # kNN lattice with radii up to 0.45 x the shortest strut: most nodes
+        # violate the lattice model (reported as the degenerate fraction)
+        print(f"irregular: {rep.exempt_nodes}/{o.N} nodes exempt (flags {getattr(rep, 'exempt_flags', 0)})")
+        assert rep.checked_nodes >= 0.2 * o.N
+    else:
+        assert rep.exempt_nodes == 0 and rep.checked_nodes == o.N
+    cnt = mm.counts()
+    V, ne, nc, H = o.totals()
+    if rep.exempt_nodes == 0:
+        assert cnt[:4] == [V, ne, nc, H]
+
+
+def test_bcc10_totals_gpu():
+    """BCC 10^3, R = 0.08 (closed form): V 13,028, 22,800 elliptical and
+    2,168 circular arcs, 602 holes, 293,296 triangles at k = 16."""
+    for dt in (np.float64, np.float32):
+        lat, mm, g, o = build("bcc10", dt)
+        assert mm.counts()[:4] == [13028, 22800, 2168, 602]
+        assert mm.tri_count(16) == 293296
+
+
+def item_counts(mm, n_items):
+    return np.array([liblm.lm_tri_range(mm.h, i, i + 1)[1] for i in range(n_items)])
+
+
+@pytest.mark.parametrize("name,dtype,k", [("bcc10", np.float64, 16), ("bcc10", np.float32, 16),
+                                          ("bcc3", np.float32, 8), ("octet3", np.float32, 8),
+                                          ("octet3", np.float32, 32), ("bccjit4", np.float32, 32),
+                                          ("irregular", np.float32, 16), ("strut", np.float32, 8),
+                                          ("cone", np.float32, 33), ("star5", np.float32, 16),
+                                          ("octet3", np.float64, 32)])
+def test_triangles_parity(name, dtype, k):
+    lat, mm, g, o = build(name, dtype)
+    exempt = {n for n in range(o.N) if (o.node(n)["flags"] | int(g["node_flags"][n])) & P.EXEMPT}
+    total = mm.tri_count(k)
+    oc = o.tri_counts(k)
+    n_items = o.E + o.N
+    gc = item_counts(mm, n_items) if n_items <= 20000 else None
+    ends = lat["ends"]
+    if not exempt:
+        assert total == int(oc.sum())
+        if gc is not None:
+            assert np.array_equal(gc, oc)
+        rec = mm.triangulate(k).cpu().numpy()
+        gn, gv = P.parse_stl(rec)
+        ot, oa, ov = o.triangulate(k)
+        errs, dv, dn = P.compare_triangles(gn, gv, ot, float(lat["radii"].max()),
+                                           tol=2e-5 if dtype == np.float32 else 1e-7)
+        assert not errs, errs
+        ga, gvol = mm.objective(k)
+        assert ga == pytest.approx(oa, rel=1e-5) and gvol == pytest.approx(ov, rel=1e-5)
+    else:
+        # compare item by item, skipping items touching an exempt node
+        assert gc is not None
+        ok_items = [i for i in range(n_items)
+                    if (i < o.E and ends[i, 0] not in exempt and ends[i, 1] not in exempt)
+                    or (i >= o.E and (i - o.E) not in exempt)]
+        assert np.array_equal(gc[ok_items], oc[ok_items])
+        rec = mm.triangulate(k).cpu().numpy()
+        gn, gv = P.parse_stl(rec)
+        goff = np.concatenate([[0], np.cumsum(gc)])
+        for i in ok_items[:: max(1, len(ok_items) // 400)]:
+            ot, _, _ = o.triangulate(k, i, i + 1)
+            errs, _, _ = P.compare_triangles(gn[goff[i]:goff[i + 1]], gv[goff[i]:goff[i + 1]], ot,
+                                             float(lat["radii"].max()))
+            assert not errs, (i, errs)
+
+
+def test_stl_layout_and_header():
+    """Binary STL records: 50 bytes, normal + 3 vertices f32, attribute 0;
+    header count field little-endian, saturating at 2^32 - 1."""
+    lat, mm, g, o = build("bcc3", np.float32)
+    k = 8
+    n = mm.tri_count(k)
+    rec = mm.triangulate(k).cpu().numpy()
+    assert rec.shape == (n, 50)
+    assert np.all(rec[:, 48:] == 0)
+    h = liblm.lm_stl_header(n)
+    assert len(h) == 84 and int.from_bytes(h[80:], "little") == n
+    assert int.from_bytes(liblm.lm_stl_header(5_000_000_000)[80:], "little") == 0xFFFFFFFF
+
+
+def test_item_ranges_and_capacity():
+    """Sub-ranges of items write the same records as the whole; a short
+    output buffer is reported as LM_ERR_CAPACITY without writing past it."""
+    lat, mm, g, o = build("octet3", np.float32)
+    k = 8
+    n = mm.tri_count(k)
+    full = mm.triangulate(k).cpu().numpy()
+    E, N = mm.n_struts, mm.n_nodes
+    for b, e in [(0, 7), (5, E + 3), (E - 1, E + N), (E + 10, E + 11)]:
+        first, cnt = liblm.lm_tri_range(mm.h, b, e)
+        part = mm.triangulate(k, b, e).cpu().numpy()
+        assert np.array_equal(part, full[first:first + cnt])
+    out = torch.full((11, 50), 7, dtype=torch.uint8, device="cuda")
+    liblm.lm_triangulate(mm.h, k, 0, E, out.data_ptr(), 10, None)
+    assert liblm.lm_last_error(mm.h) == 4
+    assert torch.all(out[10] == 7)
+
+
+def test_empty_and_invalid_inputs():
+    dev = "cuda"
+    # no struts: an empty meta-mesh, no triangles
+    xyz = torch.zeros((3, 3), dtype=torch.float32, device=dev)
+    ends = torch.zeros((0, 2), dtype=torch.int32, device=dev)
+    radii = torch.zeros((0, 2), dtype=torch.float32, device=dev)
+    mm = liblm.MetaMesh(xyz, ends, radii)
+    assert mm.counts()[:4] == [0, 0, 0, 0]
+    assert mm.tri_count(8) == 0
+    base = L.bcc(1, radius=0.1)
+
+    def status(mut):
+        lat = {k: v.copy() for k, v in base.items() if k != "name"}
+        mut(lat)
+        x, e, r = P.to_device(lat, np.float32)
+        with pytest.raises(liblm.LmError) as ei:
+            liblm.MetaMesh(x, e, r)
+        return ei.value.status
+
+    assert status(lambda l: l["radii"].__setitem__((0, 0), 0.2)) == 2          # radius mismatch
+    assert status(lambda l: l["ends"].__setitem__((0, 1), 999)) == 1           # node out of range
+    assert status(lambda l: l["ends"].__setitem__((0, 1), l["ends"][0, 0])) == 1  # self loop
+    assert status(lambda l: l["radii"].__setitem__((1, 1), np.nan)) == 1       # NaN radius
+    assert status(lambda l: l["xyz"].__setitem__((0, 0), np.nan)) == 1         # NaN coordinate
+
+    def taper(l):
+        l["radii"][:, 0] = 0.99
+    assert status(taper) == 3                                                 # cone taper >= length
+    star = L.star(np.random.default_rng(0).normal(size=(65, 3)), radius=0.01)
+    x, e, r = P.to_device(star, np.float32)
+    with pytest.raises(liblm.LmError) as ei:
+        liblm.MetaMesh(x, e, r)
+    assert ei.value.status == 8                                               # valence > 64
+    with pytest.raises(liblm.LmError):
+        liblm.lm_triangulate(mm.h, 9, 0, 1, 0, 0, None)                       # k without count
+
+
+def test_streaming_matches_direct():
+    """Chunked triangulation streamed to pinned host slots (overlapped
+    device-to-host copies) reproduces the direct output."""
+    lat, mm, g, o = build("octet3", np.float32)
+    k = 32
+    n = mm.tri_count(k)
+    full = mm.triangulate(k).cpu().numpy()
+    chunk = 97
+    n_items = mm.n_struts + mm.n_nodes
+    max_chunk = max(liblm.lm_tri_range(mm.h, c, min(n_items, c + chunk))[1] for c in range(0, n_items, chunk))
+    slot = 50 * max_chunk
+    ring = torch.empty(3 * slot, dtype=torch.uint8, pin_memory=True)
+    got = []
+
+    def cb(ci, first_item, ntri, ptr, user):
+        off = ptr - ring.data_ptr()
+        got.append((ci, ring[off:off + 50 * ntri].numpy().copy()))
+
+    tot = liblm.lm_triangulate_stream(mm.h, k, chunk, ring.data_ptr(), slot, 3, cb)
+    assert tot == n
+    got.sort(key=lambda x: x[0])
+    cat = np.concatenate([x[1] for x in got]).reshape(-1, 50)
+    assert np.array_equal(cat, full)
