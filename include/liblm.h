@@ -216,6 +216,30 @@ lm_status lm_last_error(lm_metamesh* mm, void* stream);
 void lm_metamesh_free(lm_metamesh* mm);
 const char* lm_status_string(lm_status s);
 
+/* Allocation-free variant of lm_tri_count + lm_triangulate for one item
+ * range (the paper has no counterpart: it concerns how this library gets
+ * its scratch memory).  For callers that cannot allocate device memory when
+ * they triangulate -- e.g. code running while a stream is captured into a
+ * CUDA graph, or under an external allocator or memory budget that forbids a
+ * library cudaMalloc.  It calls no cudaMalloc/cudaFree: every scratch buffer
+ * (per-item counts and offsets of the range, scan workspace, FP64 fallback
+ * contexts, work counters) lives in one fixed file-scope device array of
+ * about 7 MB that each GPU loading the library keeps until process exit.
+ *   item range : at most 262,144 items per call, else LM_ERR_CAPACITY;
+ *                chunk larger ranges
+ *   d_out      : records of the range from byte 0 (as lm_triangulate)
+ *   h_ntris    : host, receives the range's triangle count (may be NULL)
+ * Needs only lm_build_metamesh first (no lm_tri_count).  Synchronises the
+ * stream once (to size the kernel's shared memory).  The first call on each
+ * device resolves the array's device address; make that first call before
+ * any stream capture.  All calls share the array and it keeps the last
+ * call's contents (the call clears what must start empty): calls that
+ * overlap on the GPU (other streams, other threads) race and must be
+ * serialised by the caller.  Capacity overflow is reported by lm_last_error
+ * as for lm_triangulate.                                                 */
+lm_status lm_triangulate_noalloc(lm_metamesh* mm, int32_t k, int64_t item_begin, int64_t item_end,
+                                 void* d_out, int64_t capacity_tris, void* stream, int64_t* h_ntris);
+
 /* Utility (no counterpart in the paper): synchronous device-to-host copy of
  * `bytes` bytes, for reading the views of lm_metamesh_export.            */
 lm_status lm_copy_to_host(void* h_dst, const void* d_src, int64_t bytes);

@@ -20,7 +20,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          f"-I{os.path.join(ROOT, 'include')}"]
 UNITS = ["lm_api.cu", "lm_mm_f32.cu", "lm_mm_f64.cu", "lm_tri_f32.cu", "lm_tri_f64.cu",
-         "lm_bwd.cu"]
+         "lm_bwd.cu", "lm_noalloc.cu"]
 
 
 def _nvcc():

@@ -22,7 +22,7 @@ STATUS = {0: "LM_OK", 1: "LM_ERR_INVALID_ARG", 2: "LM_ERR_RADIUS_MISMATCH", 3: "
 EXPORTS = ["lm_build_metamesh", "lm_metamesh_counts", "lm_metamesh_export", "lm_tri_count",
            "lm_tri_range", "lm_triangulate", "lm_triangulate_stream", "lm_stl_header",
            "lm_objective", "lm_metamesh_backward", "lm_last_error", "lm_metamesh_free",
-           "lm_status_string", "lm_copy_to_host", "lm_launch_count"]
+           "lm_status_string", "lm_copy_to_host", "lm_launch_count", "lm_triangulate_noalloc"]
 
 
 class LmError(RuntimeError):
@@ -86,6 +86,7 @@ def load():
         "lm_status_string": ([ctypes.c_int], ctypes.c_char_p),
         "lm_copy_to_host": ([V, V, I64], ctypes.c_int),
         "lm_launch_count": ([], ctypes.c_longlong),
+        "lm_triangulate_noalloc": ([V, I32, I64, I64, V, I64, V, P64], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -162,6 +163,16 @@ def lm_triangulate_stream(h, k, chunk_items, ring_ptr, slot_bytes, n_slots, call
                                      int(slot_bytes), int(n_slots), cb, None, _stream_ptr(stream),
                                      ctypes.byref(tot)), "lm_triangulate_stream")
     return tot.value
+
+
+def lm_triangulate_noalloc(h, k, item_begin, item_end, out_ptr, capacity_tris, stream=None):
+    """Allocation-free triangulation of items [begin, end) (at most 262,144
+    items per call); returns the range's triangle count.  See liblm.h."""
+    n = ctypes.c_int64()
+    _ck(load().lm_triangulate_noalloc(h, int(k), int(item_begin), int(item_end), ctypes.c_void_p(int(out_ptr)),
+                                      int(capacity_tris), _stream_ptr(stream), ctypes.byref(n)),
+        "lm_triangulate_noalloc")
+    return n.value
 
 
 def lm_stl_header(n_tris):
