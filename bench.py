@@ -166,6 +166,10 @@ def bench_gpu(args):
     mm = liblm.MetaMesh(xyz, ends, radii, stream=stream)
     totals = [mm.tri_count(k, stream) for k in ks]
     counts = mm.counts()
+    fb = liblm.lm_fp64_counts(mm.h)
+    fp64 = dict(zip(["pair", "candidate", "position_refine", "dedup", "seam", "loop_angle", "label",
+                     "arc_extent", "tri_segments", "tri_start_angle", "tri_stitch_order", "tri_fan_centre"],
+                    fb[:12]))
     t_build = {"csr": None}
     mm.close()
     out = torch.empty(max(totals) * 50, dtype=torch.uint8, device=dev)
@@ -219,6 +223,7 @@ def bench_gpu(args):
         "write_gbs": {f"k{k}": 50.0 * totals[i] / (phase[f"tri_k{k}_ms"] / 1e3) / 1e9 for i, k in enumerate(ks)},
         "meta_mesh_counts": {"vertices": counts[0], "elliptical_arcs": counts[1], "circular_arcs": counts[2],
                              "holes": counts[3], "degenerate_nodes": counts[5], "max_valence": counts[6]},
+        "fp64_stability_steps": fp64,
         "roofline": roof_tri,
         "gpu_launches": int((l1 - l0) // max(1, args.steps)) * args.steps,
         "clocks": clk.summary(),

@@ -244,6 +244,16 @@ lm_status lm_triangulate_noalloc(lm_metamesh* mm, int32_t k, int64_t item_begin,
  * `bytes` bytes, for reading the views of lm_metamesh_export.            */
 lm_status lm_copy_to_host(void* h_dst, const void* d_src, int64_t bytes);
 
+/* FP64 stability steps (BASELINE's FP32-with-FP64-stability design, no
+ * counterpart in the paper): how many decisions were re-taken in FP64
+ * because their FP32 value lay inside a safety margin of its threshold or
+ * came from an ill-conditioned configuration.  Synchronous.
+ *   out[0] pair classification, [1] candidate vertex re-decision,
+ *   [2] vertex position refinement, [3] deduplication, [4] seam label,
+ *   [5] loop angle order / wrap, [6] arc label, [7] arc extent (build);
+ *   [8..15] reserved for triangulation.                                   */
+lm_status lm_fp64_counts(const lm_metamesh* mm, int64_t out[16]);
+
 /* Utility (no counterpart in the paper): number of CUDA kernels this library
  * has launched in the process so far (host-side counter).                */
 long long lm_launch_count(void);

@@ -502,6 +502,31 @@ NodeOut node_metamesh(const Mesh& M, int64_t n) {
     }
   }
 
+  // ---- arc extent: an elliptical arc must stay within both struts' lengths.
+  // h(phi) = (n0 + n1 cos + n2 sin)/(d0 + d1 cos + d2 sin) on the owner i;
+  // its extrema satisfy P cos + Q sin = W (derivative of the ratio)
+  for (const Arc& a : out.A) {
+    if (a.other < 0) continue;
+    const End& Ei = E[a.owner];
+    const End& Ej = E[a.other];
+    double cij = dot(Ei.u, Ej.u), a1 = dot(Ej.u, Ei.e1), a2 = dot(Ej.u, Ei.e2);
+    double n0 = R * (Ei.s * cij - Ej.s), n1 = R * Ei.co * a1, n2 = R * Ei.co * a2;
+    double d0 = Ej.co - Ei.co * cij, d1 = Ei.s * a1, d2 = Ei.s * a2;
+    double tmax = std::max(hval(Ei, Ej, a.phi0, R), hval(Ei, Ej, a.phi0 + a.dphi, R));
+    double P = n2 * d0 - n0 * d2, Q = n0 * d1 - n1 * d0, W = n1 * d2 - n2 * d1;
+    double rr = std::sqrt(P * P + Q * Q);
+    if (rr > std::fabs(W) && rr > 0.0) {
+      double base = std::atan2(Q, P), off = std::acos(W / rr);
+      for (int sg = -1; sg <= 1; sg += 2) {
+        double ph = base + sg * off;
+        double rel = std::fmod(ph - a.phi0, PI2);
+        if (rel < 0) rel += PI2;
+        if (rel < a.dphi) tmax = std::max(tmax, hval(Ei, Ej, a.phi0 + rel, R));
+      }
+    }
+    if (tmax > std::min(Ei.L * Ei.co, Ej.L * Ej.co)) out.flags |= F_DEGENERATE | F_BEYOND_LENGTH;
+  }
+
   // ---- holes: chain circular arcs (hole on the left seen from outside)
   int na = (int)out.A.size();
   std::vector<char> used(na, 0);

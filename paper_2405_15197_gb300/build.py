@@ -18,6 +18,8 @@ OUT = os.path.join(HERE, "_liblm.so")
 BUILD = os.path.join(ROOT, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
+         # a host-only function called from device code compiles to nothing
+         "--diag-error=20011,20012,20013,20014,20015",
          f"-I{os.path.join(ROOT, 'include')}"]
 UNITS = ["lm_api.cu", "lm_mm_f32.cu", "lm_mm_f64.cu", "lm_tri_f32.cu", "lm_tri_f64.cu",
          "lm_bwd.cu", "lm_noalloc.cu"]

@@ -202,6 +202,8 @@ lm_status build_impl(lm_metamesh* mm, cudaStream_t st) {
   LM_CK(dalloc(&mm->d_queue, 8, st));
   LM_CK(dalloc(&mm->d_misc, 8, st));
   LM_CK(dalloc(&mm->d_acc, 4, st));
+  LM_CK(dalloc(&mm->d_fb, 16, st));
+  LM_CK(cudaMemsetAsync(mm->d_fb, 0, 16 * sizeof(unsigned long long), st));
   LM_CK(cudaMemsetAsync(mm->d_err, 0, 4 * sizeof(int), st));
   LM_CK(cudaMemsetAsync(mm->d_misc, 0, 8 * sizeof(int), st));
   T* node_R = nullptr;
@@ -269,6 +271,7 @@ lm_status build_impl(lm_metamesh* mm, cudaStream_t st) {
   L.node_cnt = node_cnt;
   L.end_cnt = end_cnt;
   L.overflow = overflow;
+  L.fb = mm->d_fb;
   int64_t cap = std::max<int64_t>(N, 1);
   for (int pass = 0; pass < 2; pass++) {
     if (pass == 1) {
@@ -408,6 +411,9 @@ TriLaunch<T> tri_launch(lm_metamesh* mm) {
   L.max_pts = mm->d_misc + 2;
   L.scratch = mm->scratch;
   L.scratch_warps = mm->scratch_warps;
+  L.fb = mm->d_fb;
+  L.redo = mm->redo_bits;
+  L.redo_base = 0;
   return L;
 }
 
@@ -417,6 +423,7 @@ lm_status tri_count_impl(lm_metamesh* mm, int k, cudaStream_t st, int64_t* total
   if (!mm->item_cnt) {
     LM_CK(dalloc(&mm->item_cnt, n_items, st));
     LM_CK(dalloc(&mm->tri_off, n_items + 1, st));
+    LM_CK(dalloc(&mm->redo_bits, mm->E / 32 + 1, st));
   }
   LM_CK(cudaMemsetAsync(mm->d_misc + 2, 0, sizeof(int), st));
   TriLaunch<T> L = tri_launch<T>(mm);
@@ -480,8 +487,8 @@ void lm_metamesh_free(lm_metamesh* mm) {
   void* ptrs[] = {mm->node_R, mm->row_ptr, mm->adj, mm->node_flags, mm->vtx_off, mm->arc_off,
                   mm->hole_off_n, mm->hent_off_n, mm->end_off, mm->vtx_z, mm->vtx_key, mm->vtx_flags,
                   mm->vtx_gen, mm->arc_ends, mm->arc_vtx, mm->arc_phi, mm->loop_ent, mm->hole_off,
-                  mm->hole_ent, mm->item_cnt, mm->tri_off, mm->scratch, mm->d_err, mm->d_queue,
-                  mm->d_misc, mm->d_acc, mm->scan_ws};
+                  mm->hole_ent, mm->item_cnt, mm->tri_off, mm->redo_bits, mm->scratch, mm->d_err, mm->d_queue,
+                  mm->d_misc, mm->d_acc, mm->scan_ws, mm->d_fb};
   for (void* p : ptrs)
     if (p) cudaFreeAsync(p, st);
   cudaStreamSynchronize(st);
@@ -711,6 +718,14 @@ lm_status lm_triangulate_stream(lm_metamesh* mm, int32_t k, int64_t chunk_items,
 }
 
 long long lm_launch_count(void) { return g_launches.load(); }
+
+lm_status lm_fp64_counts(const lm_metamesh* mm, int64_t out[16]) {
+  if (!mm || !out) return LM_ERR_INVALID_ARG;
+  unsigned long long h[16];
+  if (cudaMemcpy(h, mm->d_fb, sizeof(h), cudaMemcpyDeviceToHost) != cudaSuccess) return LM_ERR_CUDA;
+  for (int i = 0; i < 16; i++) out[i] = (int64_t)h[i];
+  return LM_OK;
+}
 
 lm_status lm_copy_to_host(void* h_dst, const void* d_src, int64_t bytes) {
   if (bytes < 0 || (bytes > 0 && (!h_dst || !d_src))) return LM_ERR_INVALID_ARG;

@@ -41,11 +41,17 @@ constexpr double EPS_TAN = 1e-6;    // tangency measure: node exempt from exact 
 // FP32 safety margins: an FP32 quantity closer than this to a decision
 // threshold, or computed from an ill-conditioned configuration, is decided
 // again in FP64 from the inputs.
-constexpr float M_LEN = 1e-3f;   // x R
-constexpr float M_ANG = 1e-4f;   // rad
+constexpr float M_LEN = 1e-4f;   // x R (FP32 candidate error <= ~1e-5 R once conditioned)
+constexpr float M_ANG = 1e-5f;   // rad (loop angles of the meta-mesh)
+constexpr float M_ZIP = 2e-5f;   // rad (stitching order; FP32 angle error <= ~2e-6)
 constexpr float M_COND = 1e-2f;  // conditioning floor of q, |v|^2, |A|, D/R^2, g2
 constexpr float M_CNT = 1e-3f;   // segment-count fraction
-constexpr float M_POS = 1e-1f;   // conditioning floor for keeping an FP32 vertex position
+constexpr float M_POS = 1e-1f;   // conditioning floor for keeping an FP32 circle-point position
+// A triple point keeps its FP32 position when its first-order sensitivity to
+// unit-roundoff perturbations of the strut axes (the dominant FP32 error: the
+// line P_ij n P_ik moves with the plane normals and meets the cone at an
+// angle) stays below M_SENS R per unit roundoff, i.e. about 3e-6 R.
+constexpr float M_SENS = 50.0f;
 
 // node flags (same bits as LM_NODE_* in liblm.h)
 constexpr uint32_t NF_NEAR_TANGENT = 1u, NF_DEGENERATE = 2u, NF_INCONSISTENT = 4u,
@@ -121,28 +127,47 @@ struct EndG {
   int32_t at_lo;
 };
 
-// Frame axis: the coordinate axis of smallest |x_hi - x_lo| (ties -> lowest).
-// FP32 differences decide when strictly ordered; a tie is re-decided on the
-// exact FP64 differences of the inputs.
+// Frame axis: the coordinate axis of smallest |x_hi - x_lo| (ties -> lowest),
+// decided on the exact differences of the inputs.  For FP32 inputs the
+// difference a - b is held exactly as s + e (error-free 2Sum); for FP64 the
+// computed difference is the one the FP64 reference uses.
+struct ExactDiff {
+  float s, e;
+};
+__device__ __forceinline__ ExactDiff exact_abs_diff(float a, float b) {
+  float s = a - b;
+  float bb = s - a;
+  float e = (a - (s - bb)) + (-b - bb);
+  if (s < 0.0f || (s == 0.0f && e < 0.0f)) {
+    s = -s;
+    e = -e;
+  }
+  return ExactDiff{s, e};
+}
+__device__ __forceinline__ bool exact_less(ExactDiff x, ExactDiff y) {
+  return x.s < y.s || (x.s == y.s && x.e < y.e);
+}
 template <typename T>
 __device__ __forceinline__ int frame_axis(const LatDev<T>& L, int32_t lo, int32_t hi) {
-  float a0 = fabsf((float)L.xyz[3 * hi] - (float)L.xyz[3 * lo]);
-  float a1 = fabsf((float)L.xyz[3 * hi + 1] - (float)L.xyz[3 * lo + 1]);
-  float a2 = fabsf((float)L.xyz[3 * hi + 2] - (float)L.xyz[3 * lo + 2]);
-  if (a0 != a1 && a0 != a2 && a1 != a2 && sizeof(T) == 4) {
+  if constexpr (sizeof(T) == 4) {
+    ExactDiff d0 = exact_abs_diff((float)L.xyz[3 * hi], (float)L.xyz[3 * lo]);
+    ExactDiff d1 = exact_abs_diff((float)L.xyz[3 * hi + 1], (float)L.xyz[3 * lo + 1]);
+    ExactDiff d2 = exact_abs_diff((float)L.xyz[3 * hi + 2], (float)L.xyz[3 * lo + 2]);
     int ax = 0;
-    if (a1 < a0) ax = 1;
-    if (a2 < (ax == 0 ? a0 : a1)) ax = 2;
+    ExactDiff best = d0;
+    if (exact_less(d1, best)) { ax = 1; best = d1; }
+    if (exact_less(d2, best)) ax = 2;
+    return ax;
+  } else {
+    double d0 = fabs((double)L.xyz[3 * hi] - (double)L.xyz[3 * lo]);
+    double d1 = fabs((double)L.xyz[3 * hi + 1] - (double)L.xyz[3 * lo + 1]);
+    double d2 = fabs((double)L.xyz[3 * hi + 2] - (double)L.xyz[3 * lo + 2]);
+    int ax = 0;
+    double best = d0;
+    if (d1 < best) { ax = 1; best = d1; }
+    if (d2 < best) ax = 2;
     return ax;
   }
-  double d0 = fabs((double)L.xyz[3 * hi] - (double)L.xyz[3 * lo]);
-  double d1 = fabs((double)L.xyz[3 * hi + 1] - (double)L.xyz[3 * lo + 1]);
-  double d2 = fabs((double)L.xyz[3 * hi + 2] - (double)L.xyz[3 * lo + 2]);
-  int ax = 0;
-  double best = d0;
-  if (d1 < best) { ax = 1; best = d1; }
-  if (d2 < best) ax = 2;
-  return ax;
 }
 
 // Strut end `end_id` at node `node` (Section 4.3.1: strut S_i with ends
@@ -222,6 +247,7 @@ struct GenOut {
   uint8_t tangent[2];
   uint8_t nroot;      // 0 or 2 (roots produced, before screening)
   uint8_t unc;        // whole generator uncertain in this precision
+  uint8_t refine;     // decisions certain, but recompute positions in FP64
   uint32_t nflags;    // node flags raised independent of survival
   uint32_t kflags[2]; // node flags raised if the root is kept as a new vertex
 };
@@ -233,12 +259,14 @@ template <typename U, bool F64>
 __device__ void eval_gen(const EndG<U>* E, int d, U R, uint32_t gcode, GenOut<U>& o) {
   o.nroot = 0;
   o.unc = 0;
+  o.refine = 0;
   o.nflags = 0;
   int type = gcode & 3, i = (gcode >> 3) & 63, j = (gcode >> 9) & 63, k = (gcode >> 15) & 63;
   uint64_t gmask;
   bool sph0;
   U tanq;
-  bool well = true;  // FP32 positions accurate to ~1e-6 R
+  bool well = true;                  // FP32 circle points accurate to ~1e-6 R
+  bool wellr[2] = {true, true};      // FP32 triple points accurate to ~3e-6 R
   if (type == 0) {
     // circle points: unit n with u_i.n = s_i, u_j.n = s_j (two tangency
     // circles on the nodal sphere)
@@ -319,9 +347,6 @@ __device__ void eval_gen(const EndG<U>* E, int d, U R, uint32_t gcode, GenOut<U>
       if (D < U(-1e-3) * mag) return;
       if (D < U(M_COND) * R2 || D < U(1e-3) * mag) { o.unc = 1; return; }
     }
-    if (!F64)
-      well = vv >= U(M_POS) * mm && fabs(A) >= U(M_POS) && D >= U(M_POS) * R2 &&
-             D >= U(M_POS) * (B * B + fabs(A * C) + R2);
     U sq = lm_sqrt(D);
     U lam0, lam1;
     if (B >= U(0)) {
@@ -337,6 +362,21 @@ __device__ void eval_gen(const EndG<U>* E, int d, U R, uint32_t gcode, GenOut<U>
     o.z[1] = z0 + vh * lam1;
     o.t0[0] = G0 + lam0 * G1;
     o.t0[1] = G0 + lam1 * G1;
+    if (!F64) {
+      // z solves (G_i - G_j, G_i - G_k, |z|^2 - R^2 - G_i^2) = 0 with Jacobian
+      // rows mj, mk, nc = z - G_i ico_i u_i; a perturbation of the axes by one
+      // roundoff moves the residuals by about |z| ico (|t| ico for the cone
+      // row), and the Jacobian inverse is adj / (v . nc)
+      U icom = fmax(E[i].ico, fmax(E[j].ico, E[k].ico));
+      U svv = lm_sqrt(vv);
+#pragma unroll
+      for (int r = 0; r < 2; r++) {
+        V3<U> nc = o.z[r] - E[i].u * (o.t0[r] * E[i].ico);
+        U num = norm3(o.z[r]) * (norm3(cross(mk, nc)) + norm3(cross(nc, mj))) +
+                svv * norm3(nc) * fabs(o.t0[r]) * icom;
+        wellr[r] = icom * num <= U(M_SENS) * R * fabs(dot(v, nc));
+      }
+    }
     gmask = (1ull << i) | (1ull << j) | (1ull << k);
     sph0 = false;
     tanq = D - U(EPS_TAN) * R2;
@@ -388,7 +428,7 @@ __device__ void eval_gen(const EndG<U>* E, int d, U R, uint32_t gcode, GenOut<U>
       if (!F64 && fabs(t0 - lim) <= M) unc = true;
       if (t0 > lim) kf |= NF_DEGENERATE | NF_BEYOND;
     }
-    if (unc || !well) {
+    if (unc || !well || !wellr[r]) {
       o.state[r] = 2;
       continue;
     }
@@ -441,6 +481,185 @@ __device__ __forceinline__ T wrap_from(T x, T lo) {
   if (r < lo) r += T(PI2);
   if (r >= lo + T(PI2)) r -= T(PI2);
   return r;
+}
+
+// Largest generator coordinate t of the elliptical arc of plane P_ij on
+// strut end i over angles [phi0, phi0 + dphi]: h = (n0 + n1 c + n2 s) /
+// (d0 + d1 c + d2 s) has its interior extrema where P c + Q s = W.
+template <typename U>
+__device__ U arc_tmax(const EndG<U>& Ei, const EndG<U>& Ej, U R, U phi0, U dphi) {
+  U cij = dot(Ei.u, Ej.u), a1 = dot(Ej.u, Ei.e1), a2 = dot(Ej.u, Ei.e2);
+  U n0 = R * (Ei.s * cij - Ej.s), n1 = R * Ei.co * a1, n2 = R * Ei.co * a2;
+  U d0 = Ej.co - Ei.co * cij, d1 = Ei.s * a1, d2 = Ei.s * a2;
+  U c, s;
+  lm_sincos(phi0, &s, &c);
+  U tmax = hval(Ei, Ej, c, s, R);
+  lm_sincos(phi0 + dphi, &s, &c);
+  U t1 = hval(Ei, Ej, c, s, R);
+  if (t1 > tmax) tmax = t1;
+  U P = n2 * d0 - n0 * d2, Q = n0 * d1 - n1 * d0, W = n1 * d2 - n2 * d1;
+  U rr = lm_sqrt(P * P + Q * Q);
+  if (rr > fabs(W) && rr > U(0)) {
+    U base = lm_atan2(Q, P);
+    U off = acos(W / rr);
+    for (int sg = -1; sg <= 1; sg += 2) {
+      U ph = base + U(sg) * off;
+      U rel = ph - phi0;
+      rel -= U(PI2) * floor(rel * U(1.0 / PI2));
+      if (rel < dphi) {
+        lm_sincos(phi0 + rel, &s, &c);
+        U t = hval(Ei, Ej, c, s, R);
+        if (t > tmax) tmax = t;
+      }
+    }
+  }
+  return tmax;
+}
+
+// FP32 strut-end data promoted to FP64 (for FP64 arithmetic on FP32 inputs)
+__device__ __forceinline__ EndG<double> promote(const EndG<float>& a) {
+  EndG<double> e;
+  e.u = cvt3<double>(a.u);
+  e.e1 = cvt3<double>(a.e1);
+  e.e2 = cvt3<double>(a.e2);
+  e.s = a.s;
+  e.co = a.co;
+  e.ico = 1.0 / (double)a.co;
+  e.L = a.L;
+  e.end_id = a.end_id;
+  e.far = a.far;
+  e.at_lo = a.at_lo;
+  return e;
+}
+__device__ __forceinline__ EndG<double> promote(const EndG<double>& a) { return a; }
+
+// Candidate positions of generator gcode in FP64 arithmetic, without
+// screening (the decisions were certain; only the positions need accuracy).
+template <typename U>
+__device__ __noinline__ void gen_points64(const EndG<U>* E, U R, uint32_t gcode, V3<double> z[2],
+                                          double t0[2]) {
+  int type = gcode & 3, i = (gcode >> 3) & 63, j = (gcode >> 9) & 63, k = (gcode >> 15) & 63;
+  EndG<double> Ei = promote(E[i]), Ej = promote(E[j]);
+  double Rd = (double)R;
+  if (type == 0) {
+    double c = dot(Ei.u, Ej.u), q = 1.0 - c * c, iq = 1.0 / q;
+    double al = (Ei.s - c * Ej.s) * iq, be = (Ej.s - c * Ei.s) * iq;
+    double g2 = 1.0 - (al * al + be * be + 2.0 * al * be * c);
+    V3<double> w = cross(Ei.u, Ej.u);
+    w = w * (1.0 / norm3(w));
+    double g = sqrt(g2 > 0.0 ? g2 : 0.0);
+    V3<double> base = Ei.u * al + Ej.u * be;
+    z[0] = (base - w * g) * Rd;
+    z[1] = (base + w * g) * Rd;
+    t0[0] = t0[1] = 0.0;
+    return;
+  }
+  EndG<double> Ek = promote(E[k]);
+  V3<double> mj = Ei.u * Ei.ico - Ej.u * Ej.ico;
+  V3<double> mk = Ei.u * Ei.ico - Ek.u * Ek.ico;
+  double dj = Rd * (Ei.s * Ei.ico - Ej.s * Ej.ico);
+  double dk = Rd * (Ei.s * Ei.ico - Ek.s * Ek.ico);
+  V3<double> v = cross(mj, mk);
+  double ivv = 1.0 / dot(v, v);
+  V3<double> z0 = (cross(mk, v) * dj - cross(mj, v) * dk) * ivv;
+  V3<double> vh = v * sqrt(ivv);
+  double G0 = (dot(Ei.u, z0) - Rd * Ei.s) * Ei.ico;
+  double G1 = dot(Ei.u, vh) * Ei.ico;
+  double A = 1.0 - G1 * G1, B = -G0 * G1, C = dot(z0, z0) - Rd * Rd - G0 * G0;
+  double D = B * B - A * C;
+  double sq = sqrt(D > 0.0 ? D : 0.0);
+  double lam0, lam1;
+  if (B >= 0.0) {
+    double q = -(B + sq);
+    lam0 = q / A;
+    lam1 = C / q;
+  } else {
+    double q = -B + sq;
+    lam1 = q / A;
+    lam0 = C / q;
+  }
+  z[0] = z0 + vh * lam0;
+  z[1] = z0 + vh * lam1;
+  t0[0] = G0 + lam0 * G1;
+  t0[1] = G0 + lam1 * G1;
+}
+
+// Compact geometry of one arc for point evaluation: owner frame and the
+// plane ratio t(phi) = (n0 + n1 c + n2 s) / (d0 + d1 c + d2 s) (t = 0 on a
+// circular arc).  Point: (R s + t co) u + (R co - t s) rho(phi).
+template <typename T>
+struct ArcGeo {
+  V3<T> u, e1, e2;
+  T Rs, Rco, co, s;
+  T n0, n1, n2, d0, d1, d2;
+};
+
+template <typename T>
+__device__ __forceinline__ ArcGeo<T> arc_geo(const EndG<T>& o, const EndG<T>* ot, T R) {
+  ArcGeo<T> g;
+  g.u = o.u;
+  g.e1 = o.e1;
+  g.e2 = o.e2;
+  g.Rs = R * o.s;
+  g.Rco = R * o.co;
+  g.co = o.co;
+  g.s = o.s;
+  if (ot) {
+    T cij = dot(o.u, ot->u), a1 = dot(ot->u, o.e1), a2 = dot(ot->u, o.e2);
+    g.n0 = R * (o.s * cij - ot->s);
+    g.n1 = R * o.co * a1;
+    g.n2 = R * o.co * a2;
+    g.d0 = ot->co - o.co * cij;
+    g.d1 = o.s * a1;
+    g.d2 = o.s * a2;
+  } else {
+    g.n0 = g.n1 = g.n2 = T(0);
+    g.d0 = T(1);
+    g.d1 = g.d2 = T(0);
+  }
+  return g;
+}
+
+template <typename T>
+__device__ __forceinline__ V3<T> geo_point(const ArcGeo<T>& g, T phi) {
+  T c, s;
+  lm_sincos(phi, &s, &c);
+  T t = (g.n0 + g.n1 * c + g.n2 * s) / (g.d0 + g.d1 * c + g.d2 * s);
+  V3<T> r = g.e1 * c + g.e2 * s;
+  return g.u * (g.Rs + t * g.co) + r * (g.Rco - t * g.s);
+}
+
+// Position of a stored vertex recomputed in FP64 from the inputs, using only
+// the strut ends that generated it (no screening: the vertex is known kept).
+template <typename T>
+__device__ __noinline__ V3<double> vertex_pos64(const LatDev<T>& L, int64_t node, uint32_t gcode) {
+  int64_t b = L.row_ptr[node];
+  int type = gcode & 3, root = (gcode >> 2) & 1;
+  int i = (gcode >> 3) & 63, j = (gcode >> 9) & 63, k = (gcode >> 15) & 63;
+  double R = (double)L.node_R[node];
+  EndG<double> Ei = make_end<T, double>(L, node, L.adj[b + i]);
+  if (type == 2) {
+    bool has = (gcode >> 21) & 1;
+    double t = 0.0;
+    if (has) {
+      EndG<double> Ej = make_end<T, double>(L, node, L.adj[b + j]);
+      t = hval(Ei, Ej, 1.0, 0.0, R);
+    }
+    return surf_point(Ei, 1.0, 0.0, t, R);
+  }
+  EndG<double> Ej = make_end<T, double>(L, node, L.adj[b + j]);
+  EndG<double> E3[3];
+  E3[0] = Ei;
+  E3[1] = Ej;
+  V3<double> z[2];
+  double t0[2];
+  if (type == 0) {
+    gen_points64<double>(E3, R, gen_code(0, 0, 0, 1, 0), z, t0);
+  } else {
+    E3[2] = make_end<T, double>(L, node, L.adj[b + k]);
+    gen_points64<double>(E3, R, gen_code(1, 0, 0, 1, 2), z, t0);
+  }
+  return z[root];
 }
 
 }  // namespace lm

@@ -42,6 +42,7 @@ struct MMLaunch {
   int64_t* hole_off;
   uint32_t* hole_ent;
   int* overflow;
+  unsigned long long* fb;
 };
 
 // persistent meta-mesh launch of one bucket; grid_ctas <= 0: resident CTAs
@@ -78,6 +79,9 @@ struct TriLaunch {
   int* max_pts;
   Node64* scratch;
   int64_t scratch_warps;
+  unsigned long long* fb;
+  uint32_t* redo;     // bitmap of struts deferred to the FP64 pass (bit e - redo_base)
+  int64_t redo_base;
 };
 
 template <typename T>
@@ -124,6 +128,7 @@ struct lm_metamesh {
   int tri_k;
   int32_t* item_cnt;
   int64_t* tri_off;
+  uint32_t* redo_bits;  // [E/32 + 1]: struts deferred to the FP64 stitching pass
   int64_t tri_total;
   int tri_pmax;
   lm::Node64* scratch;
@@ -136,4 +141,6 @@ struct lm_metamesh {
   int64_t scan_ws_n;
   // timing of the last build (device ms): csr, count, emit
   float t_csr, t_count, t_emit;
+  // FP64 stability-step counters: [0..7] meta-mesh build, [8..15] triangulation
+  unsigned long long* d_fb;
 };

@@ -76,7 +76,16 @@ struct MMArgs {
   int64_t* hole_off;
   uint32_t* hole_ent;
   int* overflow;
+  unsigned long long* fb;  // FP64 re-decision counters (see FB_*)
 };
+
+// FP64 stability-step counters
+enum { FB_PAIR = 0, FB_GEN = 1, FB_REFINE = 2, FB_DEDUP = 3, FB_SEAM = 4, FB_ANGLE = 5,
+       FB_LABEL = 6, FB_EXTENT = 7, FB_N = 8 };
+__device__ __forceinline__ void fb_add(unsigned long long* fb, int which, bool pred) {
+  uint32_t m = __ballot_sync(0xffffffffu, pred);
+  if (fb && m && (threadIdx.x & 31) == (__ffs(m) - 1)) atomicAdd(fb + which, (unsigned long long)__popc(m));
+}
 
 // FP64 copies of the node's strut ends, built on first use.
 template <typename T, typename C>
@@ -203,11 +212,18 @@ __device__ void node_metamesh(WarpSmem<T, C>& S, const MMArgs<T>& A, int64_t n, 
               T coin = c < T(0) ? S.E[i].s + S.E[j].s : S.E[i].s - S.E[j].s;
               co = fabs(coin) < T(EPS_TAN);
             }
+          } else if (q < T(0.6 * EPS_PAR)) {
+            // certainly (anti)parallel: q's FP32 error is below 4e-7
+            T coin = c < T(0) ? S.E[i].s + S.E[j].s : S.E[i].s - S.E[j].s;
+            if (fabs(coin) >= T(1.5 * EPS_TAN)) co = false;
+            else if (fabs(coin) <= T(0.5 * EPS_TAN)) co = true;
+            else unc = true;
           } else if (q < T(M_COND)) {
             unc = true;
           }
         }
       }
+      fb_add(A.fb, FB_PAIR, unc);
       if (!IS64 && __any_sync(0xffffffffu, unc)) {
         ensure64(S, L, n, d, lane);
         if (unc) {
@@ -273,6 +289,18 @@ __device__ void node_metamesh(WarpSmem<T, C>& S, const MMArgs<T>& A, int64_t n, 
       }
     }
     bool need64 = !IS64 && (o.unc || (o.nroot == 2 && (o.state[0] == 2 || o.state[1] == 2)));
+    bool needref = !IS64 && !need64 && o.refine && o.nroot == 2 && (o.state[0] == 1 || o.state[1] == 1);
+    fb_add(A.fb, FB_GEN, need64);
+    fb_add(A.fb, FB_REFINE, needref);
+    if (needref) {
+      V3<double> z64[2];
+      double t64[2];
+      gen_points64<T>(S.E, R, code, z64, t64);
+      for (int r = 0; r < 2; r++) {
+        o.z[r] = mk3((T)z64[r].x, (T)z64[r].y, (T)z64[r].z);
+        o.t0[r] = (T)t64[r];
+      }
+    }
     if (!IS64 && __any_sync(0xffffffffu, need64)) {
       ensure64(S, L, n, d, lane);
       if (need64) {
@@ -322,6 +350,7 @@ __device__ void node_metamesh(WarpSmem<T, C>& S, const MMArgs<T>& A, int64_t n, 
           }
         }
         dup = __any_sync(0xffffffffu, dup);
+        fb_add(A.fb, FB_DEDUP, !IS64 && !dup && dunc && lane == 0);
         if (!IS64 && !dup && __any_sync(0xffffffffu, dunc)) {
           ensure64(S, L, n, d, lane);
           V3<double> z64 = vertex_from_gen<double>(ends64(S), d, R64, gc);
@@ -381,6 +410,7 @@ __device__ void node_metamesh(WarpSmem<T, C>& S, const MMArgs<T>& A, int64_t n, 
           if (!IS64 && top - second <= T(M_LEN) * R) unc = true;
         }
       }
+      fb_add(A.fb, FB_SEAM, unc);
       if (!IS64 && __any_sync(0xffffffffu, unc)) {
         ensure64(S, L, n, d, lane);
         if (unc) {
@@ -469,6 +499,7 @@ __device__ void node_metamesh(WarpSmem<T, C>& S, const MMArgs<T>& A, int64_t n, 
           for (int p = 0; p + 1 < nl; p++)
             if (S.le_ang[b0 + p + 1] - S.le_ang[b0 + p] <= T(M_ANG)) unc = true;
       }
+      fb_add(A.fb, FB_ANGLE, unc);
       if (!IS64 && __any_sync(0xffffffffu, unc)) {
         ensure64(S, L, n, d, lane);
         if (unc) {
@@ -524,6 +555,7 @@ __device__ void node_metamesh(WarpSmem<T, C>& S, const MMArgs<T>& A, int64_t n, 
           label = midpoint_label<T>(S.E, i, cm, cs, S.le_ang[b0 + q] + T(0.5) * dph, R, gap);
           if (!IS64 && gap <= T(M_LEN) * R) {
             // exact re-decision (rare; no warp-collective calls here)
+            if (A.fb) atomicAdd(A.fb + FB_LABEL, 1ull);
             if (S.e64_valid != ((d >= 64) ? ~0ull : ((1ull << d) - 1))) {
               for (int li = 0; li < d; li++)
                 if (!((S.e64_valid >> li) & 1ull)) S.E64[li] = make_end<T, double>(L, n, S.E[li].end_id);
@@ -667,6 +699,42 @@ __device__ void node_metamesh(WarpSmem<T, C>& S, const MMArgs<T>& A, int64_t n, 
     }
     na = __shfl_sync(0xffffffffu, na, 0);
     overflow = __shfl_sync(0xffffffffu, (int)overflow, 0);
+  }
+  __syncwarp();
+
+  // ---- arc extent: every elliptical arc within both struts' lengths
+  if (!overflow) {
+    uint32_t f = 0;
+    bool unc = false;
+    for (int a = lane; a < na; a += 32) {
+      if (S.a_other[a] < 0) continue;
+      const EndG<T>& Ei = S.E[S.a_owner[a]];
+      const EndG<T>& Ej = S.E[S.a_other[a]];
+      T tm = arc_tmax(Ei, Ej, R, S.a_phi0[a], S.a_dphi[a]);
+      T lim = fmin(Ei.L * Ei.co, Ej.L * Ej.co);
+      if (!IS64 && fabs(tm - lim) <= T(M_LEN) * R) unc = true;
+      else if (tm > lim) f |= NF_DEGENERATE | NF_BEYOND;
+    }
+    fb_add(A.fb, FB_EXTENT, unc);
+    if (!IS64 && __any_sync(0xffffffffu, unc)) {
+      ensure64(S, L, n, d, lane);
+      const EndG<double>* E = ends64(S);
+      for (int a = lane; a < na; a += 32) {
+        if (S.a_other[a] < 0) continue;
+        const EndG<double>& Ei = E[S.a_owner[a]];
+        const EndG<double>& Ej = E[S.a_other[a]];
+        T lim32 = fmin(S.E[S.a_owner[a]].L * S.E[S.a_owner[a]].co, S.E[S.a_other[a]].L * S.E[S.a_other[a]].co);
+        T tm32 = arc_tmax(S.E[S.a_owner[a]], S.E[S.a_other[a]], R, S.a_phi0[a], S.a_dphi[a]);
+        if (fabs(tm32 - lim32) > T(M_LEN) * R) continue;
+        double p0 = angle64(S, d, R64, S.a_owner[a], S.a_v0[a]);
+        double p1 = angle64(S, d, R64, S.a_owner[a], S.a_v1[a]);
+        double dd = S.a_v0[a] == S.a_v1[a] ? PI2 : p1 - p0;
+        if (dd <= 0.0) dd += PI2;
+        double tm = arc_tmax(Ei, Ej, R64, p0, dd);
+        if (tm > fmin(Ei.L * Ei.co, Ej.L * Ej.co)) f |= NF_DEGENERATE | NF_BEYOND;
+      }
+    }
+    nflags |= __reduce_or_sync(0xffffffffu, f);
   }
   __syncwarp();
 

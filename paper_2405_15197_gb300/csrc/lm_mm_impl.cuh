@@ -71,6 +71,7 @@ cudaError_t launch_metamesh(int bucket, bool emit, const MMLaunch<T>& a, int blo
   A.hole_off = a.hole_off;
   A.hole_ent = a.hole_ent;
   A.overflow = a.overflow;
+  A.fb = a.fb;
   if (A.n_list <= 0) {
     if (used) *used = 0;
     return cudaSuccess;

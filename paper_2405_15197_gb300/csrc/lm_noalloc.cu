@@ -28,6 +28,7 @@ struct NaLayout {
   int32_t cnt[NA_MAX_ITEMS];
   int64_t off[NA_MAX_ITEMS + 1];
   int64_t ws[NA_SCAN_WS];
+  uint32_t redo[NA_MAX_ITEMS / 32 + 2];  // struts deferred to the FP64 pass
   int counters[8];  // [0..1] work queues, [2] max points of one loop
 };
 constexpr size_t NA_CTX_OFFSET = (sizeof(NaLayout) + 255) & ~(size_t)255;
@@ -218,6 +219,8 @@ lm_status run_noalloc(lm_metamesh* mm, int k, int64_t b, int64_t e, void* d_out,
   L.max_pts = nullptr;
   L.scratch = ctx;
   L.scratch_warps = NA_CONTEXTS;
+  L.redo = S->redo;
+  L.redo_base = b;
   return launch_tri_emit<T>(L, st) == cudaSuccess ? LM_OK : LM_ERR_CUDA;
 }
 

@@ -38,7 +38,15 @@ struct TriArgs {
   int pmax;                // points per loop capacity
   int emax;                // loop entries capacity
   int* max_pts;            // count pass: max points of one loop / one node's holes
+  unsigned long long* fb;  // FP64 stability-step counters (8: segments, 9: start angle,
+                           // 10: stitching order, 11: fan centre)
 };
+
+__device__ __forceinline__ void tfb_add(unsigned long long* fb, int which, bool pred,
+                                        unsigned mask = 0xffffffffu) {
+  uint32_t m = __ballot_sync(mask, pred);
+  if (fb && m && (threadIdx.x & 31) == (__ffs(m) - 1)) atomicAdd(fb + which, (unsigned long long)__popc(m));
+}
 
 // ---- segment count (Eq. sampling) with an FP64 recheck flag
 template <typename T>
@@ -197,138 +205,47 @@ __global__ void __launch_bounds__(256) k_tri_count(TriArgs<T> A, Node64* scratch
 
 // ------------------------------------------------------- strut stitching
 // Per-warp shared workspace for one strut (dynamic size from pmax, emax).
-struct StrutHdr {
-  int ne[2], np[2];
-  int64_t node[2];
-  int32_t own_end[2];
-  int own_li[2];
-  int sB;
+template <typename T>
+struct EntryS {
+  ArcGeo<T> g;
+  T phi0, dphi, psi;
+  int N, pre;
+  int64_t ga;
+  uint8_t rev, own;
 };
 
+// node-relative point s of an entry and its angle around the own strut (T);
+// shared by the strut and hole kernels so shared points are bit-identical
 template <typename T>
-struct StrutWs {
-  StrutHdr* h;  // shared scalars of the warp's current strut
-  // entry arrays [2][emax]: global arc, N, prefix, rev, start angle
-  int64_t* e_ga;
-  int* e_n;
-  int* e_pre;
-  uint8_t* e_rev;
-  T* e_psi;
-  // point arrays [2][pmax]
-  T* th;
-  V3<T>* z;
-  double* th64;
-  uint8_t* fl;   // point needs the exact angle
-  T* kB;         // B keys in A's window
-  unsigned char* stage;  // 32 STL records + slack
-};
-
-__host__ __device__ inline size_t strut_ws_bytes(int pmax, int emax, int elt) {
-  size_t b = 64 + 2 * (size_t)emax * (8 + 4 + 4 + 1 + elt) + 2 * (size_t)pmax * (elt + 3 * elt + 8 + 1) +
-             (size_t)pmax * elt + 32 * 50 + 256;
-  return (b + 15) & ~(size_t)15;
-}
-
-template <typename T>
-__device__ StrutWs<T> carve_ws(unsigned char* p, int pmax, int emax) {
-  StrutWs<T> W;
-  W.h = reinterpret_cast<StrutHdr*>(p);
-  size_t o = 64;
-  auto take = [&](size_t bytes) {
-    unsigned char* r = p + o;
-    o += (bytes + 7) & ~(size_t)7;
-    return r;
-  };
-  W.e_ga = (int64_t*)take(2 * emax * 8);
-  W.e_n = (int*)take(2 * emax * 4);
-  W.e_pre = (int*)take(2 * emax * 4);
-  W.e_psi = (T*)take(2 * emax * sizeof(T));
-  W.e_rev = (uint8_t*)take(2 * emax);
-  W.th = (T*)take(2 * pmax * sizeof(T));
-  W.z = (V3<T>*)take(2 * pmax * sizeof(V3<T>));
-  W.th64 = (double*)take(2 * pmax * 8);
-  W.kB = (T*)take(pmax * sizeof(T));
-  W.fl = (uint8_t*)take(2 * pmax);
-  o = (o + 15) & ~(size_t)15;
-  W.stage = p + o;
-  return W;
-}
-
-// node-relative point s of entry q of a loop and its own-frame angle (T)
-template <typename T>
-__device__ void loop_point(const TriArgs<T>& A, int64_t node, const EndG<T>& own, int64_t ga, int N,
-                           int rev, int s, T psi, V3<T>& z, T& th) {
-  const LatDev<T>& L = A.lat;
-  uint32_t av = A.arc_vtx[ga];
-  int v0 = av & 255, v1 = (av >> 8) & 255;
-  int m = rev ? N - s : s;
-  T R = L.node_R[node];
-  if (s == 0) {
-    int64_t vi = A.vtx_off[node] + (rev ? v1 : v0);
+__device__ __forceinline__ void entry_point(const TriArgs<T>& A, int64_t node, const EntryS<T>& e,
+                                            const EndG<T>* own, int s, V3<T>& z, T& th) {
+  int m = e.rev ? e.N - s : s;
+  if (s == 0 || m == 0 || m == e.N) {
+    uint32_t av = A.arc_vtx[e.ga];
+    int64_t vi = A.vtx_off[node] + (m == 0 ? (av & 255) : ((av >> 8) & 255));
     z = mk3(A.vtx_z[3 * vi], A.vtx_z[3 * vi + 1], A.vtx_z[3 * vi + 2]);
-    th = psi;
+    th = e.psi;
+    if (s != 0 && own) th = e.psi + wrap_from(raw_angle(*own, z) - e.psi, T(-ETA_PHI));
     return;
   }
-  int o = (av >> 16) & 255, ot = (int)((av >> 24) & 255) - 1;
-  int64_t b = L.row_ptr[node];
-  EndG<T> Eo = make_end<T, T>(L, node, L.adj[b + o]);
-  T phi0 = A.arc_phi[2 * ga], dphi = A.arc_phi[2 * ga + 1];
-  T phi = phi0 + dphi * (T)m / (T)N;
-  T c, sn;
-  lm_sincos(phi, &sn, &c);
-  T t = T(0);
-  if (ot >= 0) {
-    EndG<T> Et = make_end<T, T>(L, node, L.adj[b + ot]);
-    t = hval(Eo, Et, c, sn, R);
-  }
-  z = surf_point(Eo, c, sn, t, R);
-  if (Eo.end_id == own.end_id) {
-    th = phi;
-  } else {
-    th = psi + wrap_from(raw_angle(own, z) - psi, T(-ETA_PHI));
-  }
+  T phi = e.phi0 + e.dphi * (T)m / (T)e.N;
+  z = geo_point(e.g, phi);
+  if (e.own) th = phi;
+  else if (own) th = e.psi + wrap_from(raw_angle(*own, z) - e.psi, T(-ETA_PHI));
+  else th = T(0);
 }
 
-// exact own-frame angle of the same point (ctx = FP64 context of `node`)
-template <typename T>
-__device__ __noinline__ double loop_theta64(const TriArgs<T>& A, const Node64* ctx, int own_li,
-                                            int64_t ga, int N, int rev, int s) {
-  if (ctx->node < 0 || ctx->d < 1 || ctx->d > 64 || own_li < 0 || own_li >= ctx->d) {
-    atomicCAS(A.err, 0, 6);
-    return 0.0;
-  }
-  uint32_t av = A.arc_vtx[ga];
-  int v0 = av & 255, v1 = (av >> 8) & 255;
-  int o = (av >> 16) & 255, ot = (int)((av >> 24) & 255) - 1;
-  int64_t vo = A.vtx_off[ctx->node];
-  double a0;
-  double dd = arc_dphi64(A, ctx, ga, &a0);
-  const EndG<double>& me = ctx->E[own_li];
-  V3<double> zs = vertex_from_gen<double>(ctx->E, ctx->d, ctx->R, A.vtx_gen[vo + (rev ? v1 : v0)]);
-  double psi = raw_angle(me, zs);
-  if (psi < -ETA_PHI) psi += PI2;
-  if (s == 0) return psi;
-  int m = rev ? N - s : s;
-  double phi = a0 + dd * (double)m / (double)N;
-  if (o == own_li) return phi;
-  double c, sn;
-  sincos(phi, &sn, &c);
-  double t = ot >= 0 ? hval(ctx->E[o], ctx->E[ot], c, sn, ctx->R) : 0.0;
-  V3<double> z = surf_point(ctx->E[o], c, sn, t, ctx->R);
-  return psi + wrap_from(raw_angle(me, z) - psi, -ETA_PHI);
-}
-
-// STL record writer: triangle (a, b, c) given node-relative points and the
-// node centres they belong to; o = the centre the math is relative to.
+// STL record of triangle (a, b, c): relative points (to centre o) for the
+// normal, area and volume; absolute points pa, pb, pc for the record
 template <typename T>
 __device__ __forceinline__ void stl_record(unsigned char* dst, V3<T> o, V3<T> ra, V3<T> rb, V3<T> rc,
                                            V3<T> pa, V3<T> pb, V3<T> pc, double* area, double* vol) {
   V3<T> cr = cross(rb - ra, rc - ra);
   T len = norm3(cr);
   V3<T> nn = len > T(0) ? cr * (T(1) / len) : mk3(T(0), T(0), T(0));
-  float f[12] = {(float)nn.x, (float)nn.y, (float)nn.z, (float)pa.x, (float)pa.y, (float)pa.z,
-                 (float)pb.x, (float)pb.y, (float)pb.z, (float)pc.x, (float)pc.y, (float)pc.z};
   if (dst) {
+    float f[12] = {(float)nn.x, (float)nn.y, (float)nn.z, (float)pa.x, (float)pa.y, (float)pa.z,
+                   (float)pb.x, (float)pb.y, (float)pb.z, (float)pc.x, (float)pc.y, (float)pc.z};
     uint16_t* d16 = reinterpret_cast<uint16_t*>(dst);
     const uint16_t* s16 = reinterpret_cast<const uint16_t*>(f);
 #pragma unroll
@@ -344,16 +261,15 @@ __device__ __forceinline__ void stl_record(unsigned char* dst, V3<T> o, V3<T> ra
 // copy `nbytes` (even) from shared staging to global dst (2-byte aligned):
 // 2-byte head/tail, 16-byte body
 __device__ __forceinline__ void flush_stage(unsigned char* gdst, const unsigned char* st, int nbytes,
-                                            int lane) {
+                                            int lane, int width = 32) {
   uintptr_t ga = (uintptr_t)gdst;
   int head = (int)((16 - (ga & 15)) & 15);
   if (head > nbytes) head = nbytes;
   head &= ~1;
-  for (int q = lane; q < head / 2; q += 32)
+  for (int q = lane; q < head / 2; q += width)
     reinterpret_cast<uint16_t*>(gdst)[q] = reinterpret_cast<const uint16_t*>(st)[q];
   int body = ((nbytes - head) / 16) * 16;
-  // shared source may be misaligned relative to 16: assemble from 2-byte words
-  for (int q = lane; q < body / 16; q += 32) {
+  for (int q = lane; q < body / 16; q += width) {
     const uint16_t* s = reinterpret_cast<const uint16_t*>(st + head + 16 * q);
     uint4 v;
     v.x = (uint32_t)s[0] | ((uint32_t)s[1] << 16);
@@ -363,289 +279,922 @@ __device__ __forceinline__ void flush_stage(unsigned char* gdst, const unsigned 
     reinterpret_cast<uint4*>(gdst + head)[q] = v;
   }
   int tail = nbytes - head - body;
-  for (int q = lane; q < tail / 2; q += 32)
+  for (int q = lane; q < tail / 2; q += width)
     reinterpret_cast<uint16_t*>(gdst + head + body)[q] =
         reinterpret_cast<const uint16_t*>(st + head + body)[q];
 }
 
+// ------------------------------------------- thread-per-strut stitching
+// One thread per strut: the strut's two loops are walked by iterators that
+// compute each subdivision point once, and the zipper runs exactly as the
+// FP64 reference does.  Records are staged per lane in shared memory and
+// leave in aligned groups of 8 (400 bytes = 25 x 16-byte stores).
+
+// FP64 angle of loop point s of arc ga around own end `own_eid` (rare path)
 template <typename T>
-__global__ void __launch_bounds__(256) k_tri_struts(TriArgs<T> A, Node64* scratch,
-                                                     const int64_t* first_ptr) {
+__device__ __noinline__ double theta64_thread(const TriArgs<T>& A, int64_t node, int32_t own_eid, int64_t ga,
+                                              int N, int rev, int s) {
+  const LatDev<T>& L = A.lat;
+  int64_t b = L.row_ptr[node];
+  uint32_t av = A.arc_vtx[ga];
+  int v0 = av & 255, v1 = (av >> 8) & 255;
+  int o = (av >> 16) & 255, ot = (int)((av >> 24) & 255) - 1;
+  int64_t vo = A.vtx_off[node];
+  double R = (double)L.node_R[node];
+  EndG<double> me = make_end<T, double>(L, node, own_eid);
+  EndG<double> Eo = make_end<T, double>(L, node, L.adj[b + o]);
+  V3<double> z0 = vertex_pos64(L, node, A.vtx_gen[vo + v0]);
+  V3<double> z1 = v1 == v0 ? z0 : vertex_pos64(L, node, A.vtx_gen[vo + v1]);
+  double a0 = norm_angle(raw_angle(Eo, z0)), a1 = norm_angle(raw_angle(Eo, z1));
+  double dd = a1 - a0;
+  if (v0 == v1) dd = PI2;
+  else if (dd <= 0.0) dd += PI2;
+  V3<double> zs = rev ? z1 : z0;
+  double psi = norm_angle(raw_angle(me, zs));
+  if (s == 0) return psi;
+  int m = rev ? N - s : s;
+  double phi = a0 + dd * (double)m / (double)N;
+  if (Eo.end_id == own_eid) return phi;
+  double c, sn;
+  sincos(phi, &sn, &c);
+  double t = 0.0;
+  if (ot >= 0) {
+    EndG<double> Et = make_end<T, double>(L, node, L.adj[b + ot]);
+    t = hval(Eo, Et, c, sn, R);
+  }
+  V3<double> z = surf_point(Eo, c, sn, t, R);
+  return psi + wrap_from(raw_angle(me, z) - psi, -ETA_PHI);
+}
+
+// exact segment count of arc ga (rare path)
+template <typename T>
+__device__ __noinline__ int segments64_thread(const TriArgs<T>& A, int64_t node, int64_t ga) {
+  const LatDev<T>& L = A.lat;
+  int64_t b = L.row_ptr[node];
+  uint32_t av = A.arc_vtx[ga];
+  int v0 = av & 255, v1 = (av >> 8) & 255, o = (av >> 16) & 255;
+  int64_t vo = A.vtx_off[node];
+  EndG<double> Eo = make_end<T, double>(L, node, L.adj[b + o]);
+  double dd = PI2;
+  if (v0 != v1) {
+    double a0 = norm_angle(raw_angle(Eo, vertex_pos64(L, node, A.vtx_gen[vo + v0])));
+    double a1 = norm_angle(raw_angle(Eo, vertex_pos64(L, node, A.vtx_gen[vo + v1])));
+    dd = a1 - a0;
+    if (dd <= 0.0) dd += PI2;
+  }
+  bool u;
+  return seg_count<double>(dd, A.k, u);
+}
+
+template <typename T>
+struct LoopIt {
+  int64_t node, q0, ao;
+  int32_t eid;
+  int ne;
+  T R;
+  V3<T> me1, me2;  // own frame
+  // current entry
+  int q, s, N;
+  uint8_t rev, own;
+  int64_t ga;
+  T phi0, dphi, psi;
+  ArcGeo<T>* g;  // per-thread slot in shared memory
+};
+
+template <typename T>
+__device__ __forceinline__ int it_segments(const TriArgs<T>& A, const LoopIt<T>& it, int64_t ga) {
+  bool unc;
+  int N = seg_count<T>(A.arc_phi[2 * ga + 1], A.k, unc);
+  if (unc) N = segments64_thread<T>(A, it.node, ga);
+  return N;
+}
+
+template <typename T>
+__device__ __noinline__ void it_load(const TriArgs<T>& A, LoopIt<T>& it, int q) {
+  const LatDev<T>& L = A.lat;
+  it.q = q;
+  it.s = 0;
+  uint32_t en = A.loop_ent[it.q0 + q];
+  it.ga = it.ao + (en & 0x7fffffffu);
+  it.rev = (uint8_t)(en >> 31);
+  uint32_t av = A.arc_vtx[it.ga];
+  int o = (av >> 16) & 255, ot = (int)((av >> 24) & 255) - 1;
+  it.phi0 = A.arc_phi[2 * it.ga];
+  it.dphi = A.arc_phi[2 * it.ga + 1];
+  it.N = it_segments(A, it, it.ga);
+  int64_t b = L.row_ptr[it.node];
+  int32_t oid = L.adj[b + o];
+  EndG<T> Eo = make_end<T, T>(L, it.node, oid);
+  if (ot >= 0) {
+    EndG<T> Et = make_end<T, T>(L, it.node, L.adj[b + ot]);
+    *it.g = arc_geo(Eo, &Et, it.R);
+  } else {
+    *it.g = arc_geo<T>(Eo, nullptr, it.R);
+  }
+  it.own = (oid == it.eid);
+  if (it.own && !it.rev) {
+    it.psi = it.phi0;
+  } else {
+    int vs = it.rev ? ((av >> 8) & 255) : (av & 255);
+    int64_t vi = A.vtx_off[it.node] + vs;
+    V3<T> zs = mk3(A.vtx_z[3 * vi], A.vtx_z[3 * vi + 1], A.vtx_z[3 * vi + 2]);
+    T a = lm_atan2(dot(zs, it.me2), dot(zs, it.me1));
+    if (sizeof(T) == 4 && fabs(a + T(ETA_PHI)) <= T(M_ANG)) {
+      EndG<double> me = make_end<T, double>(L, it.node, it.eid);
+      a = (T)norm_angle(raw_angle(me, vertex_pos64(L, it.node, A.vtx_gen[vi])));
+    }
+    it.psi = norm_angle(a);
+  }
+}
+
+template <typename T>
+__device__ void it_init(const TriArgs<T>& A, LoopIt<T>& it, int64_t node, int32_t eid, ArcGeo<T>* slot) {
+  const LatDev<T>& L = A.lat;
+  it.g = slot;
+  it.node = node;
+  it.eid = eid;
+  it.q0 = A.end_off[eid];
+  it.ne = (int)(A.end_off[eid + 1] - it.q0);
+  it.ao = A.arc_off[node];
+  it.R = L.node_R[node];
+  EndG<T> me = make_end<T, T>(L, node, eid);
+  it.me1 = me.e1;
+  it.me2 = me.e2;
+  it_load(A, it, 0);
+}
+
+// current point of the iterator (node-relative) and its own-frame angle
+template <typename T>
+__device__ __forceinline__ void it_point(const TriArgs<T>& A, const LoopIt<T>& it, V3<T>& z, T& th) {
+  int m = it.rev ? it.N - it.s : it.s;
+  if (it.s == 0) {
+    uint32_t av = A.arc_vtx[it.ga];
+    int64_t vi = A.vtx_off[it.node] + (m == 0 ? (av & 255) : ((av >> 8) & 255));
+    z = mk3(A.vtx_z[3 * vi], A.vtx_z[3 * vi + 1], A.vtx_z[3 * vi + 2]);
+    th = it.psi;
+    return;
+  }
+  T phi = it.phi0 + it.dphi * (T)m / (T)it.N;
+  z = geo_point(*it.g, phi);
+  if (it.own) th = phi;
+  else th = it.psi + wrap_from(lm_atan2(dot(z, it.me2), dot(z, it.me1)) - it.psi, T(-ETA_PHI));
+}
+
+template <typename T>
+__device__ __forceinline__ void it_next(const TriArgs<T>& A, LoopIt<T>& it) {
+  if (++it.s >= it.N) it_load(A, it, it.q + 1 < it.ne ? it.q + 1 : 0);
+}
+
+template <typename T>
+__device__ __forceinline__ double it_theta64(const TriArgs<T>& A, const LoopIt<T>& it) {
+  return theta64_thread<T>(A, it.node, it.eid, it.ga, it.N, it.rev, it.s);
+}
+
+// 50-byte record into (2-byte aligned) shared memory
+__device__ __forceinline__ void rec_store(unsigned char* dst, const float f[12]) {
+  if (((uintptr_t)dst & 3) == 0) {
+    uint32_t* d32 = reinterpret_cast<uint32_t*>(dst);
+#pragma unroll
+    for (int q = 0; q < 12; q++) d32[q] = __float_as_uint(f[q]);
+    reinterpret_cast<uint16_t*>(dst)[24] = 0;
+  } else {
+    uint16_t* d16 = reinterpret_cast<uint16_t*>(dst);
+#pragma unroll
+    for (int q = 0; q < 12; q++) {
+      uint32_t u = __float_as_uint(f[q]);
+      d16[2 * q] = (uint16_t)(u & 0xffffu);
+      d16[2 * q + 1] = (uint16_t)(u >> 16);
+    }
+    d16[24] = 0;
+  }
+}
+
+constexpr int REC_LANE_STRIDE = 404;  // 8 records + pad (odd word count: no bank conflicts)
+// per-thread shared slot: the two loops' arc geometry (8-byte aligned for
+// FP64), then 8 staged records; the stride is a multiple of 8 bytes with an
+// odd number of 8-byte words
+template <typename T>
+__host__ __device__ constexpr int tri_geo_bytes() {
+  return ((2 * (int)sizeof(ArcGeo<T>) + 15) / 16) * 16;
+}
+template <typename T>
+__host__ __device__ constexpr int tri_lane_stride() {
+  return (((tri_geo_bytes<T>() + 400 + 7) / 8) % 2 == 1) ? ((tri_geo_bytes<T>() + 400 + 7) / 8) * 8
+                                                          : ((tri_geo_bytes<T>() + 400 + 7) / 8) * 8 + 8;
+}
+
+template <typename T, bool OBJ>
+__global__ void __launch_bounds__(128, 3) k_tri_thread(TriArgs<T> A, const int64_t* first_ptr) {
+  extern __shared__ __align__(16) unsigned char stage[];
   const int64_t out_first = first_ptr ? *first_ptr : 0;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const size_t wsb = strut_ws_bytes(A.pmax, A.emax, sizeof(T));
-  StrutWs<T> W = carve_ws<T>(smem_raw + (size_t)w * wsb, A.pmax, A.emax);
-  Node64* ctx = scratch + 2 * gw;
   const LatDev<T>& L = A.lat;
   const int64_t E = L.n_struts;
   const int64_t e_end = A.item_end < E ? A.item_end : E;
-  constexpr bool IS64 = sizeof(T) == 8;
-  while (true) {
-    int64_t e = 0;
-    if (lane == 0) e = A.item_begin + atomicAdd(A.queue, 1);
-    e = __shfl_sync(0xffffffffu, e, 0);
-    if (e >= e_end) break;
+  ArcGeo<T>* gslot = reinterpret_cast<ArcGeo<T>*>(stage + threadIdx.x * tri_lane_stride<T>());
+  unsigned char* my = stage + threadIdx.x * tri_lane_stride<T>() + tri_geo_bytes<T>();
+  const bool vec_ok = A.out && (((uintptr_t)A.out) & 15) == 0;
+  double sa = 0.0, sv = 0.0;
+  for (int64_t e = A.item_begin + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < e_end;
+       e += (int64_t)gridDim.x * blockDim.x) {
     int32_t a = L.ends[2 * e], b = L.ends[2 * e + 1];
     int32_t lo = a < b ? a : b, hi = a < b ? b : a;
     int side_lo = (a == lo) ? 0 : 1;
-    // ---- entries of both loops, segment counts, prefix sums
-    bool ovf = false;
-    for (int X = 0; X < 2; X++) {
-      int64_t node = X == 0 ? lo : hi;
-      int32_t eid = (int32_t)(2 * e + (X == 0 ? side_lo : 1 - side_lo));
-      int64_t q0 = A.end_off[eid], q1 = A.end_off[eid + 1];
-      int ne = (int)(q1 - q0);
-      if (ne > A.emax) { ovf = true; break; }
-      int64_t ao = A.arc_off[node];
-      int cntsum = 0;
-      bool need = false;
-      for (int c0 = 0; c0 < ne; c0 += 32) {
-        int q = c0 + lane;
-        int Nq = 0;
-        bool unc = false;
-        int64_t ga = 0;
-        int rev = 0;
-        if (q < ne) {
-          uint32_t ent = A.loop_ent[q0 + q];
-          ga = ao + (ent & 0x7fffffffu);
-          rev = ent >> 31;
-          Nq = seg_count<T>(A.arc_phi[2 * ga + 1], A.k, unc);
-        }
-        if (__any_sync(0xffffffffu, unc)) {
-          load_node64(L, node, ctx, lane);
-          __syncwarp();
-          if (unc) Nq = arc_segments<T>(A, node, ga, ctx, 0);
-          __syncwarp();
-        }
-        int pre = warp_excl_scan(Nq, lane) + cntsum;
-        if (q < ne) {
-          W.e_ga[X * A.emax + q] = ga;
-          W.e_n[X * A.emax + q] = Nq;
-          W.e_pre[X * A.emax + q] = pre;
-          W.e_rev[X * A.emax + q] = (uint8_t)rev;
-        }
-        cntsum = __shfl_sync(0xffffffffu, pre + Nq, 31);
+    int32_t eA = (int32_t)(2 * e + side_lo), eB = (int32_t)(2 * e + 1 - side_lo);
+    LoopIt<T> IA, IB;
+    it_init(A, IA, lo, eA, gslot);
+    it_init(A, IB, hi, eB, gslot + 1);
+    // loop sizes
+    int nA = 0, nB = 0;
+    for (int q = 0; q < IA.ne; q++) nA += it_segments(A, IA, IA.ao + (A.loop_ent[IA.q0 + q] & 0x7fffffffu));
+    for (int q = 0; q < IB.ne; q++) nB += it_segments(A, IB, IB.ao + (A.loop_ent[IB.q0 + q] & 0x7fffffffu));
+    // A's first point (kept for the wrap)
+    V3<T> a0z;
+    T thA0;
+    it_point(A, IA, a0z, thA0);
+    double thA0_64 = 0.0;
+    bool have_a0_64 = false;
+    auto a0_64 = [&]() {
+      if (!have_a0_64) {
+        uint32_t en = A.loop_ent[IA.q0];
+        int64_t ga0 = IA.ao + (en & 0x7fffffffu);
+        thA0_64 = theta64_thread<T>(A, IA.node, IA.eid, ga0, 1, (int)(en >> 31), 0);
+        have_a0_64 = true;
       }
-      if (cntsum > A.pmax) { ovf = true; break; }
-      if (lane == 0) {
-        W.h->ne[X] = ne;
-        W.h->np[X] = cntsum;
-        W.h->node[X] = node;
-        W.h->own_end[X] = eid;
+      return thA0_64;
+    };
+    // key of a B point in the window [thA0 - ETA_ZIP, thA0 + 2pi - ETA_ZIP)
+    auto keyB = [&](const LoopIt<T>& I, T th, bool& exact, double& k64) -> T {
+      T x = wrap_from(th, thA0 - T(ETA_ZIP));
+      exact = false;
+      if (sizeof(T) == 4 && (x - thA0 <= T(M_ZIP) || thA0 + T(PI2) - x <= T(M_ZIP))) {
+        k64 = wrap_from(it_theta64(A, I), a0_64() - ETA_ZIP);
+        exact = true;
+        x = (T)k64;
       }
-    }
-    if (ovf) {
-      if (lane == 0) atomicCAS(A.err, 0, 4);
-      continue;
-    }
-    __syncwarp();
-    // ---- own ends, start angles of entries, points
-    for (int X = 0; X < 2; X++) {
-      int64_t node = W.h->node[X];
-      int64_t b0 = L.row_ptr[node];
-      int d = (int)(L.row_ptr[node + 1] - b0);
-      int li = 0;
-      for (int q = lane; q < d; q += 32)
-        if (L.adj[b0 + q] == W.h->own_end[X]) li = q + 1;
-      li = __reduce_max_sync(0xffffffffu, li) - 1;
-      if (lane == 0) W.h->own_li[X] = li;
-      EndG<T> own = make_end<T, T>(L, node, W.h->own_end[X]);
-      // start angle of each entry: the stored angle for own arcs; otherwise
-      // the start vertex's angle, re-decided in FP64 next to the wrap point
-      bool pu = false;
-      for (int q = lane; q < W.h->ne[X]; q += 32) {
-        int64_t ga = W.e_ga[X * A.emax + q];
-        uint32_t av = A.arc_vtx[ga];
-        int rev = W.e_rev[X * A.emax + q];
-        if ((int)((av >> 16) & 255) == li && !rev) {
-          W.e_psi[X * A.emax + q] = A.arc_phi[2 * ga];
-          continue;
-        }
-        int64_t vi = A.vtx_off[node] + (rev ? ((av >> 8) & 255) : (av & 255));
-        V3<T> zs = mk3(A.vtx_z[3 * vi], A.vtx_z[3 * vi + 1], A.vtx_z[3 * vi + 2]);
-        T a = raw_angle(own, zs);
-        if (!IS64 && fabs(a + T(ETA_PHI)) <= T(M_ANG)) pu = true;
-        W.e_psi[X * A.emax + q] = norm_angle(a);
-      }
-      if (!IS64 && __any_sync(0xffffffffu, pu)) {
-        load_node64(L, node, ctx + X, lane);
-        __syncwarp();
-        for (int q = lane; q < W.h->ne[X]; q += 32) {
-          int64_t ga = W.e_ga[X * A.emax + q];
-          uint32_t av = A.arc_vtx[ga];
-          int rev = W.e_rev[X * A.emax + q];
-          if ((int)((av >> 16) & 255) == li && !rev) continue;
-          int64_t vi = A.vtx_off[node] + (rev ? ((av >> 8) & 255) : (av & 255));
-          V3<double> z64 = vertex_from_gen<double>(ctx[X].E, ctx[X].d, ctx[X].R, A.vtx_gen[vi]);
-          W.e_psi[X * A.emax + q] = (T)norm_angle(raw_angle(ctx[X].E[li], z64));
-        }
-      }
-      __syncwarp();
-      int np = W.h->np[X], ne = W.h->ne[X];
-      for (int p = lane; p < np; p += 32) {
-        // entry containing point p
-        int lo_q = 0, hi_q = ne - 1;
-        while (lo_q < hi_q) {
-          int mid = (lo_q + hi_q + 1) >> 1;
-          if (W.e_pre[X * A.emax + mid] <= p) lo_q = mid;
-          else hi_q = mid - 1;
-        }
-        int q = lo_q;
+      return x;
+    };
+    // rotation of B: first point after the single drop of its keys
+    V3<T> bprev = mk3(T(0), T(0), T(0));
+    int sB = 0;
+    {
+      T kprev = T(0);
+      bool found = false;
+      for (int j = 0; j < nB; j++) {
         V3<T> z;
         T th;
-        loop_point<T>(A, node, own, W.e_ga[X * A.emax + q], W.e_n[X * A.emax + q],
-                      W.e_rev[X * A.emax + q], p - W.e_pre[X * A.emax + q],
-                      W.e_psi[X * A.emax + q], z, th);
-        W.z[X * A.pmax + p] = z;
-        W.th[X * A.pmax + p] = th;
-        W.fl[X * A.pmax + p] = 0;
-      }
-    }
-    __syncwarp();
-    const int nA = W.h->np[0], nB = W.h->np[1];
-    T* thA = W.th;
-    T* thB = W.th + A.pmax;
-    // ---- exact angles where an A point and a B point are too close to order
-    if (!IS64) {
-      bool any = false;
-      for (int i = lane; i < nA; i += 32) {
-        for (int j = 0; j < nB; j++) {
-          T dd = thA[i] - thB[j];
-          dd -= T(PI2) * rint(dd * T(1.0 / PI2));
-          if (fabs(dd) <= T(M_ANG)) {
-            W.fl[i] = 1;
-            W.fl[A.pmax + j] = 1;
-            any = true;
-          }
+        it_point(A, IB, z, th);
+        bool ex;
+        double k64;
+        T kj = keyB(IB, th, ex, k64);
+        if (j > 0 && kj < kprev) {
+          sB = j;
+          found = true;
+          break;
         }
+        bprev = z;
+        kprev = kj;
+        it_next(A, IB);
       }
-      if (__any_sync(0xffffffffu, any)) {
-        __syncwarp();
-        for (int X = 0; X < 2; X++) {
-          load_node64(L, W.h->node[X], ctx + X, lane);
-        }
-        __syncwarp();
-        for (int X = 0; X < 2; X++) {
-          int np = W.h->np[X], ne = W.h->ne[X];
-          for (int p = lane; p < np; p += 32) {
-            if (!W.fl[X * A.pmax + p]) continue;
-            int lo_q = 0, hi_q = ne - 1;
-            while (lo_q < hi_q) {
-              int mid = (lo_q + hi_q + 1) >> 1;
-              if (W.e_pre[X * A.emax + mid] <= p) lo_q = mid;
-              else hi_q = mid - 1;
-            }
-            int q = lo_q;
-            W.th64[X * A.pmax + p] =
-                loop_theta64<T>(A, ctx + X, W.h->own_li[X], W.e_ga[X * A.emax + q], W.e_n[X * A.emax + q],
-                                W.e_rev[X * A.emax + q], p - W.e_pre[X * A.emax + q]);
-          }
-        }
-        __syncwarp();
+      if (!found) {
+        // no drop: rotation 0; B's last point is the one before it
+        sB = 0;
+        it_load(A, IB, 0);
       }
     }
-    // ---- B keys in the window [thA0 - ETA_ZIP, thA0 + 2pi - ETA_ZIP) that
-    // starts at A's first point; exact keys for flagged B points
-    const T thA0 = thA[0];
-    for (int j = lane; j < nB; j += 32) {
-      T x = wrap_from(thB[j], thA0 - T(ETA_ZIP));
-      if (!IS64 && W.fl[A.pmax + j]) {
-        double a0 = W.fl[0] ? W.th64[0] : (double)thA0;
-        double x64 = wrap_from(W.th64[A.pmax + j], a0 - ETA_ZIP);
-        W.th64[A.pmax + j] = x64;
-        x = (T)x64;
-      }
-      W.kB[j] = x;
-    }
-    __syncwarp();
-    {
-      // rotation: first index of the smallest key
-      T mn = T(1e30);
-      for (int j = lane; j < nB; j += 32) mn = fmin(mn, W.kB[j]);
-      for (int o = 16; o > 0; o >>= 1) mn = fmin(mn, __shfl_xor_sync(0xffffffffu, mn, o));
-      int first = 0x7fffffff;
-      for (int j = lane; j < nB; j += 32)
-        if (W.kB[j] == mn) first = min(first, j);
-      first = __reduce_min_sync(0xffffffffu, first);
-      if (lane == 0) W.h->sB = first == 0x7fffffff ? 0 : first;
-    }
-    __syncwarp();
-    const int sB = W.h->sB;
-    // A event i (1..nA) precedes B event j (0..nB-1) iff thA(i) <= kB(j) + ETA_ZIP
-    auto a_before_b = [&](int i, int j) -> bool {
-      int ia = i < nA ? i : 0;
-      int jb = (sB + j) % nB;
-      if (!IS64 && W.fl[ia] && W.fl[A.pmax + jb]) {
-        double x = W.th64[ia] + (i < nA ? 0.0 : PI2);
-        return x <= W.th64[A.pmax + jb] + ETA_ZIP;
-      }
-      T x = i < nA ? thA[i] : thA0 + T(PI2);
-      return x <= W.kB[jb] + T(ETA_ZIP);
-    };
-    // ---- triangles: merged sequence of nA + nB events; each lane takes one
-    // output position and finds its event by merge-path search
-    const int ntri = nA + nB;
+    // zipper (ties advance A)
     const int64_t t0 = A.tri_off[e] - out_first;
-    double sa = 0.0, sv = 0.0;
+    const int ntri = nA + nB;
     V3<T> cA = node_xyz<T, T>(L, lo), cB = node_xyz<T, T>(L, hi);
     V3<T> dAB = cB - cA;
-    for (int c0 = 0; c0 < ntri; c0 += 32) {
-      int p = c0 + lane;
-      if (p < ntri) {
-        int lo_i = p - nB > 0 ? p - nB : 0, hi_i = p < nA ? p : nA;
-        while (lo_i < hi_i) {
-          int mid = (lo_i + hi_i) >> 1;
-          bool more = (mid < nA) && (p - mid - 1 >= 0) && a_before_b(mid + 1, p - mid - 1);
-          if (more) lo_i = mid + 1;
-          else hi_i = mid;
-        }
-        int i = lo_i, jn = p - i;
-        bool isA = (i < nA) && (jn == nB || a_before_b(i + 1, jn));
-        V3<T> ra, rb, rc, pa, pb, pc;
-        if (isA) {
-          int jb = ((sB + jn - 1) % nB + nB) % nB;
-          V3<T> zb = W.z[A.pmax + jb];
-          ra = W.z[i];
-          rb = W.z[(i + 1) % nA];
-          rc = dAB + zb;
-          pa = cA + ra;
-          pb = cA + rb;
-          pc = cB + zb;
+    V3<T> acur = a0z, bcur = bprev;
+    it_next(A, IA);
+    V3<T> anext;
+    T thAn;
+    if (nA > 1) it_point(A, IA, anext, thAn);
+    else { anext = a0z; thAn = thA0 + T(PI2); }
+    int ia = 0, ib = -1;
+    V3<T> bnext;
+    T thBn;
+    it_point(A, IB, bnext, thBn);
+    bool exB;
+    double kB64;
+    T kBn = keyB(IB, thBn, exB, kB64);
+    for (int t = 0; t < ntri; t++) {
+      bool takeA;
+      if (ib == nB - 1) takeA = true;
+      else if (ia >= nA) takeA = false;
+      else {
+        T xa = ia + 1 < nA ? thAn : thA0 + T(PI2);
+        if (sizeof(T) == 4 && fabs(xa - kBn) <= T(M_ZIP)) {
+          double xa64 = ia + 1 < nA ? it_theta64(A, IA) : a0_64() + PI2;
+          double kb = exB ? kB64 : wrap_from(it_theta64(A, IB), a0_64() - ETA_ZIP);
+          takeA = xa64 <= kb + ETA_ZIP;
         } else {
-          int jb = (sB + jn) % nB, jp = ((sB + jn - 1) % nB + nB) % nB;
-          V3<T> za = W.z[i % nA];
-          ra = za;
-          rb = dAB + W.z[A.pmax + jb];
-          rc = dAB + W.z[A.pmax + jp];
-          pa = cA + za;
-          pb = cB + W.z[A.pmax + jb];
-          pc = cB + W.z[A.pmax + jp];
+          takeA = xa <= kBn + T(ETA_ZIP);
         }
-        double ar, vo;
-        stl_record<T>(A.out ? W.stage + 50 * lane : nullptr, cA, ra, rb, rc, pa, pb, pc, &ar, &vo);
-        sa += ar;
-        sv += vo;
       }
-      __syncwarp();
+      V3<T> ra, rb, rc, pa, pb, pc;
+      if (takeA) {
+        ra = acur;
+        rb = anext;
+        rc = dAB + bcur;
+        pa = cA + acur;
+        pb = cA + anext;
+        pc = cB + bcur;
+        acur = anext;
+        ia++;
+        if (ia < nA) {
+          it_next(A, IA);
+          if (ia + 1 < nA) it_point(A, IA, anext, thAn);
+          else { anext = a0z; thAn = thA0 + T(PI2); }
+        }
+      } else {
+        ra = acur;
+        rb = dAB + bnext;
+        rc = dAB + bcur;
+        pa = cA + acur;
+        pb = cB + bnext;
+        pc = cB + bcur;
+        bcur = bnext;
+        ib++;
+        if (ib < nB - 1) {
+          it_next(A, IB);
+          it_point(A, IB, bnext, thBn);
+          kBn = keyB(IB, thBn, exB, kB64);
+        }
+      }
+      // record
+      V3<T> cr = cross(rb - ra, rc - ra);
+      T len = norm3(cr);
+      V3<T> nn = len > T(0) ? cr * (T(1) / len) : mk3(T(0), T(0), T(0));
+      if (OBJ) {
+        sa += 0.5 * (double)len;
+        sv += ((double)dot(ra, cross(rb, rc)) +
+               dot(mk3((double)cA.x, (double)cA.y, (double)cA.z), mk3((double)cr.x, (double)cr.y, (double)cr.z))) *
+              (1.0 / 6.0);
+      }
       if (A.out) {
-        int nrec = ntri - c0 < 32 ? ntri - c0 : 32;
-        int64_t gt = t0 + c0;
-        if (gt + nrec <= A.capacity) flush_stage(A.out + 50 * gt, W.stage, 50 * nrec, lane);
-        else if (lane == 0) atomicCAS(A.err, 0, 4);
+        int64_t u = t0 + t;
+        int slot = (int)(u & 7);
+        float f[12] = {(float)nn.x, (float)nn.y, (float)nn.z, (float)pa.x, (float)pa.y, (float)pa.z,
+                       (float)pb.x, (float)pb.y, (float)pb.z, (float)pc.x, (float)pc.y, (float)pc.z};
+        rec_store(my + 50 * slot, f);
+        if (slot == 7 || t == ntri - 1) {
+          int first_slot = (int)((u - (int64_t)(t < slot ? t : slot)) & 7);
+          int nrec = slot - first_slot + 1;
+          int64_t ustart = u - (nrec - 1);
+          if (ustart + nrec > A.capacity) {
+            atomicCAS(A.err, 0, 4);
+          } else if (vec_ok && nrec == 8) {
+            uint4* dst = reinterpret_cast<uint4*>(A.out + 50 * ustart);
+            const uint32_t* src = reinterpret_cast<const uint32_t*>(my);
+#pragma unroll 5
+            for (int c = 0; c < 25; c++) dst[c] = make_uint4(src[4 * c], src[4 * c + 1], src[4 * c + 2], src[4 * c + 3]);
+          } else {
+            uint16_t* dst = reinterpret_cast<uint16_t*>(A.out + 50 * ustart);
+            const uint16_t* src = reinterpret_cast<const uint16_t*>(my + 50 * first_slot);
+            for (int c = 0; c < 25 * nrec; c++) dst[c] = src[c];
+          }
+        }
       }
-      __syncwarp();
     }
-    if (A.acc) {
-      for (int o = 16; o > 0; o >>= 1) {
-        sa += __shfl_xor_sync(0xffffffffu, sa, o);
-        sv += __shfl_xor_sync(0xffffffffu, sv, o);
+  }
+  if (OBJ && A.acc) {
+    for (int o = 16; o > 0; o >>= 1) {
+      sa += __shfl_xor_sync(0xffffffffu, sa, o);
+      sv += __shfl_xor_sync(0xffffffffu, sv, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+      atomicAdd(A.acc, sa);
+      atomicAdd(A.acc + 1, sv);
+    }
+  }
+}
+
+// ------------------------------------------------ tile-per-strut stitching
+// A tile of TL lanes (16: two struts per warp) stitches one strut.  The
+// entries of both loops are set up lane-parallel (their arc geometry goes to
+// shared memory), the loop points are evaluated lane-parallel, B's angles are
+// moved into A's window and B is rotated to its smallest key, and then each
+// lane emits one triangle per round, finding its place in the zipper by a
+// merge-path search.  Records are staged per tile and stored with 16-byte
+// vector stores.  Angle decisions that FP32 cannot take safely (keys within
+// M_ZIP of each other or of the window edges) are retaken in FP64 from the
+// exact vertex generators, recomputed per comparison (they are rare).
+template <typename T>
+struct TileEntry {
+  ArcGeo<T> g;
+  T phi0, dphi, psi;
+  int N, pre;
+  int64_t ga;
+  uint8_t rev, own, pad0, pad1;
+};
+
+struct TileHdr {
+  int np[2], ne[2];
+  int pad[4];
+  double a0_64;  // FP64 angle of A's first point (when some key was flagged)
+};
+
+// per-tile shared memory: header, entries of both loops, point angles and
+// positions of both loops, B keys, FP64 flags, staging of TL records
+template <typename T, int TL>
+struct TileLayout {
+  __host__ __device__ static constexpr size_t r16c(size_t b) { return (b + 15) & ~(size_t)15; }
+  int pmax, emax;
+  bool exact;  // the FP64 pass also holds FP64 arc data per entry and angles per point
+  __host__ __device__ size_t ent() const { return r16c(sizeof(TileHdr)); }
+  __host__ __device__ size_t th() const { return ent() + r16c(2 * (size_t)emax * sizeof(TileEntry<T>)); }
+  __host__ __device__ size_t z() const { return th() + r16c(2 * (size_t)pmax * sizeof(T)); }
+  __host__ __device__ size_t kb() const { return z() + r16c(2 * (size_t)pmax * sizeof(V3<T>)); }
+  __host__ __device__ size_t fl() const { return kb() + r16c((size_t)pmax * sizeof(T)); }
+  __host__ __device__ size_t stage() const { return fl() + r16c(2 * (size_t)pmax); }
+  __host__ __device__ size_t ea64() const { return stage() + r16c(TL * 50); }
+  __host__ __device__ size_t th64() const { return ea64() + (exact ? r16c(2 * (size_t)emax * 32) : 0); }
+  __host__ __device__ size_t bytes() const { return th64() + (exact ? r16c(2 * (size_t)pmax * 8) : 0); }
+};
+
+// FP64 data of one loop entry: start angle of its arc in the owner's frame,
+// angular extent, and the angle of the entry's first point in the loop's frame
+struct Arc64 {
+  double a0, dd, psi, pad;
+};
+
+template <int TL>
+__device__ __forceinline__ unsigned tile_mask(int lane) {
+  return TL == 32 ? 0xffffffffu : (((1u << TL) - 1u) << (lane & ~(TL - 1)));
+}
+template <int TL>
+__device__ __forceinline__ int tile_excl_scan(int x, int tl, unsigned m) {
+  int v = x;
+#pragma unroll
+  for (int o = 1; o < TL; o <<= 1) {
+    int t = __shfl_up_sync(m, v, o, TL);
+    if (tl >= o) v += t;
+  }
+  return v - x;
+}
+
+// entry of point p of a loop (entries hold the exclusive prefix of points)
+template <typename T>
+__device__ __forceinline__ int tile_entry_of(const TileEntry<T>* ents, int ne, int p) {
+  int lq = 0, hq = ne - 1;
+  while (lq < hq) {
+    int mid = (lq + hq + 1) >> 1;
+    if (ents[mid].pre <= p) lq = mid;
+    else hq = mid - 1;
+  }
+  return lq;
+}
+
+// FP64 arc data of entry (ga, rev) of the loop of `own_eid` (rare path)
+template <typename T>
+__device__ __noinline__ Arc64 arc64_data(const TriArgs<T>& A, int64_t node, int32_t own_eid, int64_t ga, int rev) {
+  const LatDev<T>& L = A.lat;
+  int64_t b = L.row_ptr[node];
+  uint32_t av = A.arc_vtx[ga];
+  int v0 = av & 255, v1 = (av >> 8) & 255, o = (av >> 16) & 255;
+  int64_t vo = A.vtx_off[node];
+  EndG<double> me = make_end<T, double>(L, node, own_eid);
+  EndG<double> Eo = make_end<T, double>(L, node, L.adj[b + o]);
+  V3<double> z0 = vertex_pos64(L, node, A.vtx_gen[vo + v0]);
+  V3<double> z1 = v1 == v0 ? z0 : vertex_pos64(L, node, A.vtx_gen[vo + v1]);
+  Arc64 r;
+  r.a0 = norm_angle(raw_angle(Eo, z0));
+  double a1 = norm_angle(raw_angle(Eo, z1));
+  r.dd = a1 - r.a0;
+  if (v0 == v1) r.dd = PI2;
+  else if (r.dd <= 0.0) r.dd += PI2;
+  r.psi = norm_angle(raw_angle(me, rev ? z1 : z0));
+  r.pad = 0.0;
+  return r;
+}
+
+// FP64 angle of point s of an entry from its FP64 arc data (rare path)
+template <typename T>
+__device__ __noinline__ double point64_theta(const TriArgs<T>& A, int64_t node, int32_t own_eid, int64_t ga,
+                                             const Arc64& d, int N, int rev, int s) {
+  if (s == 0) return d.psi;
+  const LatDev<T>& L = A.lat;
+  int64_t b = L.row_ptr[node];
+  uint32_t av = A.arc_vtx[ga];
+  int o = (av >> 16) & 255, ot = (int)((av >> 24) & 255) - 1;
+  int m = rev ? N - s : s;
+  double phi = d.a0 + d.dd * (double)m / (double)N;
+  int32_t oid = L.adj[b + o];
+  if (oid == own_eid) return phi;
+  double R = (double)L.node_R[node];
+  EndG<double> Eo = make_end<T, double>(L, node, oid);
+  EndG<double> me = make_end<T, double>(L, node, own_eid);
+  double c, sn;
+  sincos(phi, &sn, &c);
+  double t = 0.0;
+  if (ot >= 0) {
+    EndG<double> Et = make_end<T, double>(L, node, L.adj[b + ot]);
+    t = hval(Eo, Et, c, sn, R);
+  }
+  V3<double> z = surf_point(Eo, c, sn, t, R);
+  return d.psi + wrap_from(raw_angle(me, z) - d.psi, -ETA_PHI);
+}
+
+// Set up one loop entry (arc geometry, start angle, segment count) in shared
+// memory.  EXACT: decisions that FP32 cannot take safely are retaken in FP64;
+// otherwise such an entry returns -1 and its strut is deferred.
+template <typename T, bool EXACT>
+__device__ __forceinline__ int tile_entry_setup_impl(const TriArgs<T>& A, int64_t node, int32_t eid, int64_t qi,
+                                                     TileEntry<T>* dst) {
+  const LatDev<T>& L = A.lat;
+  const int64_t ao = A.arc_off[node], rb = L.row_ptr[node], vo = A.vtx_off[node];
+  const T R = L.node_R[node];
+  constexpr bool IS64 = sizeof(T) == 8;
+  TileEntry<T> en;
+  uint32_t ent = A.loop_ent[qi];
+  en.ga = ao + (ent & 0x7fffffffu);
+  en.rev = (uint8_t)(ent >> 31);
+  en.pad0 = en.pad1 = 0;
+  uint32_t av = A.arc_vtx[en.ga];
+  int o = (av >> 16) & 255, ot = (int)((av >> 24) & 255) - 1;
+  en.phi0 = A.arc_phi[2 * en.ga];
+  en.dphi = A.arc_phi[2 * en.ga + 1];
+  bool unc;
+  int Nq = seg_count<T>(en.dphi, A.k, unc);
+  if (unc) {
+    if (!EXACT) return -1;
+    Nq = segments64_thread<T>(A, node, en.ga);
+  }
+  int32_t oid = L.adj[rb + o];
+  EndG<T> Eo = make_end<T, T>(L, node, oid);
+  if (ot >= 0) {
+    EndG<T> Et = make_end<T, T>(L, node, L.adj[rb + ot]);
+    en.g = arc_geo(Eo, &Et, R);
+  } else {
+    en.g = arc_geo<T>(Eo, nullptr, R);
+  }
+  en.own = (oid == eid);
+  if (en.own && !en.rev) {
+    en.psi = en.phi0;
+  } else {
+    int64_t vi = vo + (en.rev ? ((av >> 8) & 255) : (av & 255));
+    V3<T> zs = mk3(A.vtx_z[3 * vi], A.vtx_z[3 * vi + 1], A.vtx_z[3 * vi + 2]);
+    EndG<T> own = make_end<T, T>(L, node, eid);
+    T ang = raw_angle(own, zs);
+    if (!IS64 && fabs(ang + T(ETA_PHI)) <= T(M_ANG)) {
+      if (!EXACT) return -1;
+      EndG<double> me = make_end<T, double>(L, node, eid);
+      ang = (T)norm_angle(raw_angle(me, vertex_pos64(L, node, A.vtx_gen[vi])));
+    }
+    en.psi = norm_angle(ang);
+  }
+  en.N = Nq;
+  en.pre = 0;
+  *dst = en;
+  return Nq;
+}
+
+template <typename T>
+__device__ __noinline__ int tile_entry_setup_exact(const TriArgs<T>& A, int64_t node, int32_t eid, int64_t qi,
+                                                   TileEntry<T>* dst) {
+  return tile_entry_setup_impl<T, true>(A, node, eid, qi, dst);
+}
+
+template <typename T, int TL>
+struct TileSmem {
+  TileHdr* H;
+  TileEntry<T>* ENT;
+  T* TH;
+  V3<T>* Z;
+  T* KB;
+  uint8_t* FL;
+  unsigned char* STG;
+  Arc64* EA64;
+  double* TH64;
+  __device__ TileSmem(unsigned char* base, const TileLayout<T, TL>& Lay)
+      : H(reinterpret_cast<TileHdr*>(base)),
+        ENT(reinterpret_cast<TileEntry<T>*>(base + Lay.ent())),
+        TH(reinterpret_cast<T*>(base + Lay.th())),
+        Z(reinterpret_cast<V3<T>*>(base + Lay.z())),
+        KB(reinterpret_cast<T*>(base + Lay.kb())),
+        FL(reinterpret_cast<uint8_t*>(base + Lay.fl())),
+        STG(base + Lay.stage()),
+        EA64(reinterpret_cast<Arc64*>(base + Lay.ea64())),
+        TH64(reinterpret_cast<double*>(base + Lay.th64())) {}
+};
+
+// Stitch strut e with one tile.  Returns true (uniformly over the tile) when
+// the strut needs FP64 decisions and EXACT is off: nothing was written then.
+template <typename T, int TL, bool OBJ, bool EXACT>
+__device__ __forceinline__ bool tile_strut(const TriArgs<T>& A, const TileSmem<T, TL>& S, int64_t e,
+                                           int64_t out_first, int tl, unsigned m, bool vec_ok, double& sa,
+                                           double& sv) {
+  constexpr bool IS64 = sizeof(T) == 8;
+  constexpr bool FP64_STEPS = EXACT && !IS64;
+  const LatDev<T>& L = A.lat;
+  TileHdr* H = S.H;
+  TileEntry<T>* ENT = S.ENT;
+  T* TH = S.TH;
+  V3<T>* Z = S.Z;
+  T* KB = S.KB;
+  uint8_t* FL = S.FL;
+  int32_t a = L.ends[2 * e], b = L.ends[2 * e + 1];
+  int32_t lo = a < b ? a : b, hi = a < b ? b : a;
+  int side_lo = (a == lo) ? 0 : 1;
+  const int32_t eA = (int32_t)(2 * e + side_lo), eB = (int32_t)(2 * e + 1 - side_lo);
+  bool ok = true, defer = false;
+  // ---- entries of both loops
+  for (int X = 0; X < 2 && ok && !defer; X++) {
+    int64_t node = X == 0 ? lo : hi;
+    int32_t eid = X == 0 ? eA : eB;
+    int64_t q0 = A.end_off[eid];
+    int ne = (int)(A.end_off[eid + 1] - q0);
+    if (ne < 1 || ne > A.emax) {
+      ok = false;
+      break;
+    }
+    int cnt = 0;
+    for (int c0 = 0; c0 < ne; c0 += TL) {
+      int q = c0 + tl;
+      int Nq = 0;
+      if (q < ne) {
+        if (FP64_STEPS) Nq = tile_entry_setup_exact<T>(A, node, eid, q0 + q, ENT + X * A.emax + q);
+        else Nq = tile_entry_setup_impl<T, false>(A, node, eid, q0 + q, ENT + X * A.emax + q);
       }
-      if (lane == 0) {
-        atomicAdd(A.acc, sa);
-        atomicAdd(A.acc + 1, sv);
+      if (__any_sync(m, Nq < 0)) {
+        defer = true;
+        break;
       }
+      int pre = tile_excl_scan<TL>(Nq, tl, m) + cnt;
+      if (q < ne) ENT[X * A.emax + q].pre = pre;
+      cnt = __shfl_sync(m, pre + Nq, TL - 1, TL);
+    }
+    if (cnt > A.pmax) ok = false;
+    if (tl == 0) {
+      H->ne[X] = ne;
+      H->np[X] = cnt;
+    }
+  }
+  if (defer) return true;
+  __syncwarp(m);
+  if (!ok) {
+    if (tl == 0) atomicCAS(A.err, 0, 4);
+    return false;
+  }
+  const int nA = H->np[0], nB = H->np[1];
+  const int neA = H->ne[0], neB = H->ne[1];
+  // ---- points of both loops
+  for (int X = 0; X < 2; X++) {
+    int64_t node = X == 0 ? lo : hi;
+    int32_t eid = X == 0 ? eA : eB;
+    EndG<T> own = make_end<T, T>(L, node, eid);
+    int np = X == 0 ? nA : nB, ne = X == 0 ? neA : neB;
+    const TileEntry<T>* ents = ENT + X * A.emax;
+    for (int p = tl; p < np; p += TL) {
+      const TileEntry<T>& en = ents[tile_entry_of(ents, ne, p)];
+      int sidx = p - en.pre;
+      int mm = en.rev ? en.N - sidx : sidx;
+      V3<T> zz;
+      T th;
+      if (sidx == 0) {
+        uint32_t av = A.arc_vtx[en.ga];
+        int64_t vi = A.vtx_off[node] + (mm == 0 ? (av & 255) : ((av >> 8) & 255));
+        zz = mk3(A.vtx_z[3 * vi], A.vtx_z[3 * vi + 1], A.vtx_z[3 * vi + 2]);
+        th = en.psi;
+      } else {
+        T phi = en.phi0 + en.dphi * (T)mm / (T)en.N;
+        zz = geo_point(en.g, phi);
+        th = en.own ? phi : en.psi + wrap_from(raw_angle(own, zz) - en.psi, T(-ETA_PHI));
+      }
+      Z[X * A.pmax + p] = zz;
+      TH[X * A.pmax + p] = th;
+      if (FP64_STEPS) FL[X * A.pmax + p] = 0;
+    }
+  }
+  __syncwarp(m);
+  const T thA0 = TH[0];
+  // ---- B keys in A's window [thA0 - ETA_ZIP, thA0 + 2pi - ETA_ZIP)
+  bool any = false;
+  for (int j = tl; j < nB; j += TL) {
+    T x = wrap_from(TH[A.pmax + j], thA0 - T(ETA_ZIP));
+    KB[j] = x;
+    if (!IS64 && (x - thA0 <= T(M_ZIP) || thA0 + T(PI2) - x <= T(M_ZIP))) {
+      if (FP64_STEPS) FL[A.pmax + j] = 2;  // window edge: key retaken in FP64
+      any = true;
+    }
+  }
+  if (!IS64 && !EXACT && __any_sync(m, any)) return true;
+  __syncwarp(m);
+  auto rotation = [&]() {
+    T mn = T(1e30);
+    for (int j = tl; j < nB; j += TL) mn = fmin(mn, KB[j]);
+#pragma unroll
+    for (int o = TL / 2; o > 0; o >>= 1) mn = fmin(mn, __shfl_xor_sync(m, mn, o, TL));
+    int first = 0x7fffffff;
+    for (int j = tl; j < nB; j += TL)
+      if (KB[j] == mn) first = min(first, j);
+#pragma unroll
+    for (int o = TL / 2; o > 0; o >>= 1) first = min(first, __shfl_xor_sync(m, first, o, TL));
+    return first == 0x7fffffff ? 0 : first;
+  };
+  int sB = rotation();
+  if (!IS64) {
+    // A points whose angle lies within M_ZIP of some B key: every such pair
+    // is decided in FP64 (B keys are sorted after the rotation up to FP32
+    // rounding, so each scan stops at the first key clearly out of range)
+    for (int i = tl; i <= nA; i += TL) {
+      if (i == 0) continue;
+      T x = i < nA ? TH[i] : thA0 + T(PI2);
+      int lj = 0, hj = nB;
+      while (lj < hj) {
+        int mid = (lj + hj) >> 1;
+        if (KB[(sB + mid) % nB] < x) lj = mid + 1;
+        else hj = mid;
+      }
+      bool hit = false;
+      for (int jj = lj - 1; jj >= lj - nB; jj--) {
+        int jr = (jj % nB + nB) % nB;
+        T kv = KB[(sB + jr) % nB] - (jj < 0 ? T(PI2) : T(0));
+        if (kv < x - T(2 * M_ZIP)) break;
+        if (fabs(kv - x) <= T(M_ZIP)) {
+          if (FP64_STEPS) FL[A.pmax + (sB + jr) % nB] |= 1;
+          hit = true;
+        }
+      }
+      for (int jj = lj; jj < lj + nB; jj++) {
+        int jr = jj % nB;
+        T kv = KB[(sB + jr) % nB] + (jj >= nB ? T(PI2) : T(0));
+        if (kv > x + T(2 * M_ZIP)) break;
+        if (fabs(kv - x) <= T(M_ZIP)) {
+          if (FP64_STEPS) FL[A.pmax + (sB + jr) % nB] |= 1;
+          hit = true;
+        }
+      }
+      if (hit) {
+        if (FP64_STEPS) FL[i < nA ? i : 0] |= 1;
+        any = true;
+      }
+    }
+  }
+  const bool anyt = !IS64 && __any_sync(m, any);
+  if (!EXACT && anyt) return true;
+  if (FP64_STEPS) tfb_add(A.fb, 10, anyt && tl == 0, m);
+  if (FP64_STEPS && anyt) {
+    // A's first point fixes the window: always taken in FP64 here
+    if (tl == 0) FL[0] |= 4;
+    __syncwarp(m);
+    // FP64 arc data of every entry that holds a flagged point, then the FP64
+    // angle of every flagged point, each computed once
+    for (int X = 0; X < 2; X++) {
+      int64_t node = X == 0 ? lo : hi;
+      int32_t eid = X == 0 ? eA : eB;
+      int ne = X == 0 ? neA : neB;
+      const TileEntry<T>* ents = ENT + X * A.emax;
+      for (int q = tl; q < ne; q += TL) {
+        bool need = false;
+        for (int p = ents[q].pre; p < ents[q].pre + ents[q].N && !need; p++) need = FL[X * A.pmax + p] != 0;
+        if (need) S.EA64[X * A.emax + q] = arc64_data<T>(A, node, eid, ents[q].ga, ents[q].rev);
+      }
+    }
+    __syncwarp(m);
+    for (int X = 0; X < 2; X++) {
+      int64_t node = X == 0 ? lo : hi;
+      int32_t eid = X == 0 ? eA : eB;
+      int np = X == 0 ? nA : nB, ne = X == 0 ? neA : neB;
+      const TileEntry<T>* ents = ENT + X * A.emax;
+      for (int p = tl; p < np; p += TL) {
+        if (!FL[X * A.pmax + p]) continue;
+        int q = tile_entry_of(ents, ne, p);
+        S.TH64[X * A.pmax + p] = point64_theta<T>(A, node, eid, ents[q].ga, S.EA64[X * A.emax + q], ents[q].N,
+                                                  ents[q].rev, p - ents[q].pre);
+      }
+    }
+    __syncwarp(m);
+    const double a0 = S.TH64[0];
+    // B keys of flagged points in FP64; window-edge keys replace the FP32
+    // ones, then B is rotated again
+    for (int j = tl; j < nB; j += TL) {
+      uint8_t f = FL[A.pmax + j];
+      if (!f) continue;
+      double x64 = wrap_from(S.TH64[A.pmax + j], a0 - ETA_ZIP);
+      S.TH64[A.pmax + j] = x64;
+      if (f & 2) KB[j] = (T)x64;
+    }
+    __syncwarp(m);
+    sB = rotation();
+  }
+  const double a0_64 = FP64_STEPS && anyt ? S.TH64[0] : 0.0;
+  auto a_before_b = [&](int i, int j) -> bool {
+    int jb = (sB + j) % nB;
+    if (FP64_STEPS && anyt && FL[i < nA ? i : 0] && FL[A.pmax + jb]) {
+      double x = i < nA ? S.TH64[i] : a0_64 + PI2;
+      return x <= S.TH64[A.pmax + jb] + ETA_ZIP;
+    }
+    T x = i < nA ? TH[i] : thA0 + T(PI2);
+    return x <= KB[jb] + T(ETA_ZIP);
+  };
+  // ---- triangles by merge-path; TL records per round
+  const int ntri = nA + nB;
+  const int64_t t0 = A.tri_off[e] - out_first;
+  V3<T> cA = node_xyz<T, T>(L, lo), cB = node_xyz<T, T>(L, hi);
+  V3<T> dAB = cB - cA;
+  for (int c0 = 0; c0 < ntri; c0 += TL) {
+    int p = c0 + tl;
+    if (p < ntri) {
+      // i = A events among the first p (ties -> A first)
+      int li_ = p - nB > 0 ? p - nB : 0, hi_ = p < nA ? p : nA;
+      while (li_ < hi_) {
+        int mid = (li_ + hi_) >> 1;
+        if (a_before_b(mid + 1, p - mid - 1)) li_ = mid + 1;
+        else hi_ = mid;
+      }
+      int i = li_, jn = p - i;
+      bool isA = (i < nA) && (jn == nB || a_before_b(i + 1, jn));
+      int jp = (sB + jn + nB - 1) % nB;
+      V3<T> za = Z[i < nA ? i : 0];
+      V3<T> zp = Z[A.pmax + jp];
+      V3<T> q1 = isA ? Z[(i + 1) % nA] : Z[A.pmax + (sB + jn) % nB];
+      V3<T> ra = za, rb = isA ? q1 : dAB + q1, rc = dAB + zp;
+      V3<T> pa = cA + za, pb = isA ? cA + q1 : cB + q1, pc = cB + zp;
+      V3<T> cr = cross(rb - ra, rc - ra);
+      T len = norm3(cr);
+      V3<T> nn = len > T(0) ? cr * (T(1) / len) : mk3(T(0), T(0), T(0));
+      if (OBJ) {
+        sa += 0.5 * (double)len;
+        sv += ((double)dot(ra, cross(rb, rc)) +
+               dot(mk3((double)cA.x, (double)cA.y, (double)cA.z), mk3((double)cr.x, (double)cr.y, (double)cr.z))) *
+              (1.0 / 6.0);
+      }
+      if (A.out) {
+        float f[12] = {(float)nn.x, (float)nn.y, (float)nn.z, (float)pa.x, (float)pa.y, (float)pa.z,
+                       (float)pb.x, (float)pb.y, (float)pb.z, (float)pc.x, (float)pc.y, (float)pc.z};
+        rec_store(S.STG + 50 * tl, f);
+      }
+    }
+    __syncwarp(m);
+    if (A.out) {
+      int nrec = ntri - c0 < TL ? ntri - c0 : TL;
+      int64_t gt = t0 + c0;
+      if (gt + nrec <= A.capacity) {
+        if (vec_ok) flush_stage(A.out + 50 * gt, S.STG, 50 * nrec, tl, TL);
+        else {
+          uint16_t* d16 = reinterpret_cast<uint16_t*>(A.out + 50 * gt);
+          const uint16_t* s16 = reinterpret_cast<const uint16_t*>(S.STG);
+          for (int q = tl; q < 25 * nrec; q += TL) d16[q] = s16[q];
+        }
+      } else if (tl == 0) {
+        atomicCAS(A.err, 0, 4);
+      }
+    }
+    __syncwarp(m);
+  }
+  return false;
+}
+
+// Strut pass.  EXACT off: every strut of [item_begin, min(item_end, E)) is
+// stitched in the kernel's precision, and a strut that needs an FP64 stability
+// step is marked in `redo` (bit e - redo_base) instead.  EXACT on: only the
+// marked struts are stitched, with the FP64 steps.
+template <typename T, int TL, bool OBJ, bool EXACT>
+__global__ void __launch_bounds__(256, EXACT ? 1 : 2)
+    k_tri_tiles(TriArgs<T> A, const int64_t* first_ptr, uint32_t* redo, int64_t redo_base) {
+  const int64_t out_first = first_ptr ? *first_ptr : 0;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int lane = threadIdx.x & 31;
+  const int tl = lane & (TL - 1);
+  const unsigned m = tile_mask<TL>(lane);
+  const int tile_in_block = threadIdx.x / TL;
+  const int64_t gtile = (int64_t)blockIdx.x * (blockDim.x / TL) + tile_in_block;
+  const int64_t ntiles = (int64_t)gridDim.x * (blockDim.x / TL);
+  TileLayout<T, TL> Lay{A.pmax, A.emax, EXACT};
+  TileSmem<T, TL> S(smem_raw + (size_t)tile_in_block * Lay.bytes(), Lay);
+  const int64_t E = A.lat.n_struts;
+  const int64_t e_end = A.item_end < E ? A.item_end : E;
+  const bool vec_ok = A.out && (((uintptr_t)A.out) & 15) == 0;
+  double sa = 0.0, sv = 0.0;
+  if (!EXACT) {
+    for (int64_t e = A.item_begin + gtile; e < e_end; e += ntiles) {
+      bool d = tile_strut<T, TL, OBJ, false>(A, S, e, out_first, tl, m, vec_ok, sa, sv);
+      if (d && tl == 0) atomicOr(redo + ((e - redo_base) >> 5), 1u << ((e - redo_base) & 31));
+    }
+  } else {
+    const int64_t w0 = (A.item_begin - redo_base) >> 5, w1 = (e_end - redo_base + 31) >> 5;
+    for (int64_t w = w0 + gtile; w < w1; w += ntiles) {
+      uint32_t bits = redo[w];
+      while (bits) {
+        int bit = __ffs(bits) - 1;
+        bits &= bits - 1;
+        int64_t e = redo_base + 32 * w + bit;
+        if (e < A.item_begin || e >= e_end) continue;
+        tile_strut<T, TL, OBJ, true>(A, S, e, out_first, tl, m, vec_ok, sa, sv);
+      }
+    }
+  }
+  if (OBJ && A.acc) {
+    for (int o = 16; o > 0; o >>= 1) {
+      sa += __shfl_xor_sync(0xffffffffu, sa, o);
+      sv += __shfl_xor_sync(0xffffffffu, sv, o);
+    }
+    if (lane == 0) {
+      atomicAdd(A.acc, sa);
+      atomicAdd(A.acc + 1, sv);
     }
   }
 }
@@ -703,12 +1252,22 @@ __global__ void __launch_bounds__(256) k_tri_holes(TriArgs<T> A, Node64* scratch
           }
           Nq = arc_segments<T>(A, nd, ga, ctx, 0);
         }
-        EndG<T> own = make_end<T, T>(L, nd, L.adj[rb + ((A.arc_vtx[ga] >> 16) & 255)]);
+        EndG<T> Eo = make_end<T, T>(L, nd, L.adj[rb + ((A.arc_vtx[ga] >> 16) & 255)]);
+        EntryS<T> en;
+        en.g = arc_geo<T>(Eo, nullptr, R);
+        en.phi0 = A.arc_phi[2 * ga];
+        en.dphi = A.arc_phi[2 * ga + 1];
+        en.psi = T(0);
+        en.N = Nq;
+        en.pre = M;
+        en.ga = ga;
+        en.rev = (uint8_t)rev;
+        en.own = 1;
         for (int s = lane; s < Nq; s += 32) {
           V3<T> z;
           T th;
           if (M + s < A.pmax) {
-            loop_point<T>(A, nd, own, ga, Nq, rev, s, T(0), z, th);
+            entry_point<T>(A, nd, en, nullptr, s, z, th);
             Q[M + s] = z;
           }
         }
@@ -752,6 +1311,7 @@ __global__ void __launch_bounds__(256) k_tri_holes(TriArgs<T> A, Node64* scratch
         else if (bl > T(0)) dir = b * (T(1) / bl);
         else dir = make_end<T, T>(L, nd, L.adj[rb]).u * T(-1);
       }
+      tfb_add(A.fb, 11, unc && lane == 0);
       if (!IS64 && unc) {
         // exact: contour in FP64 from the inputs
         if (ctx->node != nd) load_node64(L, nd, ctx, lane);

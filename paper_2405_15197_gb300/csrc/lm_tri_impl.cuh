@@ -40,6 +40,7 @@ TriArgs<T> tri_args(const TriLaunch<T>& a) {
   A.pmax = a.pmax;
   A.emax = a.emax;
   A.max_pts = a.max_pts;
+  A.fb = a.fb;
   return A;
 }
 
@@ -69,25 +70,81 @@ cudaError_t launch_tri_emit(const TriLaunch<T>& a, cudaStream_t st) {
   TriArgs<T> A = tri_args(a);
   const int warps = 8, threads = warps * 32;
   int sms = sm_count();
+  (void)threads;
   cudaError_t e;
-  // struts
+  // struts: one 16-lane tile per strut (two per warp) while the per-tile
+  // shared memory fits; otherwise (very fine resolutions) one thread per
+  // strut that streams its points
   if (a.item_begin < a.n_struts) {
-    size_t smem = warps * strut_ws_bytes(a.pmax, a.emax, sizeof(T));
-    e = cudaFuncSetAttribute(k_tri_struts<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tri_struts<T>, threads, smem);
-    if (per_sm < 1) per_sm = 1;
-    int64_t grid = (int64_t)per_sm * sms;
-    int64_t gmax = a.scratch_warps / (2 * warps);
-    if (grid > gmax) grid = gmax;
-    int64_t n = (a.item_end < a.n_struts ? a.item_end : a.n_struts) - a.item_begin;
-    int64_t gneed = (n + warps - 1) / warps;
-    if (grid > gneed) grid = gneed;
-    if (grid < 1) grid = 1;
-    A.queue = a.queue;
-    count_launch();
-    k_tri_struts<T><<<(unsigned)grid, threads, smem, st>>>(A, a.scratch, a.first_ptr);
+    constexpr int TL = 16;
+    const int64_t n = (a.item_end < a.n_struts ? a.item_end : a.n_struts) - a.item_begin;
+    TileLayout<T, TL> Lay{a.pmax, a.emax, false}, LayX{a.pmax, a.emax, true};
+    const size_t smem_cap = 200 * 1024;
+    auto tiles_for = [&](size_t bytes) {
+      int t = 16;
+      while (t > 2 && (size_t)t * bytes > smem_cap) t >>= 1;
+      return (size_t)t * bytes <= smem_cap ? t : 0;
+    };
+    const int tiles = tiles_for(Lay.bytes()), tilesx = tiles_for(LayX.bytes());
+    if (tiles > 0 && tilesx > 0) {
+      constexpr bool F32 = sizeof(T) == 4;
+      const int64_t e_end = a.item_end < a.n_struts ? a.item_end : a.n_struts;
+      const int64_t w0 = (a.item_begin - a.redo_base) >> 5, w1 = (e_end - a.redo_base + 31) >> 5;
+      if (F32) {
+        if (!a.redo) return cudaErrorInvalidValue;
+        e = cudaMemsetAsync(a.redo + w0, 0, (size_t)(w1 - w0) * sizeof(uint32_t), st);
+        if (e != cudaSuccess) return e;
+      }
+      {
+        const int tpb = tiles * TL;
+        size_t smem = (size_t)tiles * Lay.bytes();
+        auto kern = a.acc ? k_tri_tiles<T, TL, true, false> : k_tri_tiles<T, TL, false, false>;
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        int per_sm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, tpb, smem);
+        if (per_sm < 1) per_sm = 1;
+        int64_t grid = (n + tiles - 1) / tiles;
+        int64_t gmax = (int64_t)per_sm * sms * 8;
+        if (grid > gmax) grid = gmax;
+        if (grid < 1) grid = 1;
+        count_launch();
+        kern<<<(unsigned)grid, tpb, smem, st>>>(A, a.first_ptr, a.redo, a.redo_base);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+      }
+      if (F32) {
+        // the deferred struts, with the FP64 stability steps
+        const int tpb = tilesx * TL;
+        size_t smem = (size_t)tilesx * LayX.bytes();
+        auto kx = a.acc ? k_tri_tiles<T, TL, true, true> : k_tri_tiles<T, TL, false, true>;
+        e = cudaFuncSetAttribute(kx, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        int per_sm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kx, tpb, smem);
+        if (per_sm < 1) per_sm = 1;
+        int64_t gx = (w1 - w0 + tilesx - 1) / tilesx;
+        if (gx > (int64_t)per_sm * sms) gx = (int64_t)per_sm * sms;
+        if (gx < 1) gx = 1;
+        count_launch();
+        kx<<<(unsigned)gx, tpb, smem, st>>>(A, a.first_ptr, a.redo, a.redo_base);
+      }
+    } else {
+      const int tpb = 128;
+      size_t smem = (size_t)tpb * tri_lane_stride<T>();
+      auto kern = a.acc ? k_tri_thread<T, true> : k_tri_thread<T, false>;
+      e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      int per_sm = 0;
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, tpb, smem);
+      if (per_sm < 1) per_sm = 1;
+      int64_t grid = (n + tpb - 1) / tpb;
+      int64_t gmax = (int64_t)per_sm * sms * 8;
+      if (grid > gmax) grid = gmax;
+      if (grid < 1) grid = 1;
+      count_launch();
+      kern<<<(unsigned)grid, tpb, smem, st>>>(A, a.first_ptr);
+    }
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }

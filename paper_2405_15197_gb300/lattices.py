@@ -106,11 +106,11 @@ def octet(n: int, radius_range=(0.04, 0.08), seed: int = SEED, ncells=None):
     return _pack(pts.astype(np.float64) * 0.5, ends, node_r, f"octet{nx}x{ny}x{nz}")
 
 
-def irregular(n_nodes: int, kmin=4, kmax=16, sigma=0.25, seed: int = SEED):
+def irregular(n_nodes: int, kmin=4, kmax=16, sigma=0.25, seed: int = SEED, r_scale=0.3):
     """Irregular lattice: i.i.d. uniform points in the unit cube, each joined
     to its k_v nearest neighbours with k_v uniform in {kmin..kmax}; the
     directed kNN graph is symmetrised.  Node radius is lognormal with median
-    0.3 x mean strut length and log-sd sigma, clipped to 0.45 x the node's
+    r_scale (0.3) x mean strut length and log-sd sigma, clipped to 0.45 x the node's
     shortest incident strut so that adjacent spheres never overlap.  Struts
     are listed by (lower id, higher id)."""
     from scipy.spatial import cKDTree
@@ -128,7 +128,7 @@ def irregular(n_nodes: int, kmin=4, kmax=16, sigma=0.25, seed: int = SEED):
     key = np.unique(lo.astype(np.int64) * n_nodes + hi)
     ends = np.stack([key // n_nodes, key % n_nodes], 1)
     L = np.linalg.norm(pts[ends[:, 0]] - pts[ends[:, 1]], axis=1)
-    r = np.exp(rng.normal(np.log(0.3 * L.mean()), sigma, size=n_nodes))
+    r = np.exp(rng.normal(np.log(r_scale * L.mean()), sigma, size=n_nodes))
     minL = np.full(n_nodes, np.inf)
     np.minimum.at(minL, ends[:, 0], L)
     np.minimum.at(minL, ends[:, 1], L)

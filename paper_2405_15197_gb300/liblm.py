@@ -22,7 +22,8 @@ STATUS = {0: "LM_OK", 1: "LM_ERR_INVALID_ARG", 2: "LM_ERR_RADIUS_MISMATCH", 3: "
 EXPORTS = ["lm_build_metamesh", "lm_metamesh_counts", "lm_metamesh_export", "lm_tri_count",
            "lm_tri_range", "lm_triangulate", "lm_triangulate_stream", "lm_stl_header",
            "lm_objective", "lm_metamesh_backward", "lm_last_error", "lm_metamesh_free",
-           "lm_status_string", "lm_copy_to_host", "lm_launch_count", "lm_triangulate_noalloc"]
+           "lm_status_string", "lm_copy_to_host", "lm_launch_count", "lm_triangulate_noalloc",
+           "lm_fp64_counts"]
 
 
 class LmError(RuntimeError):
@@ -86,6 +87,7 @@ def load():
         "lm_status_string": ([ctypes.c_int], ctypes.c_char_p),
         "lm_copy_to_host": ([V, V, I64], ctypes.c_int),
         "lm_launch_count": ([], ctypes.c_longlong),
+        "lm_fp64_counts": ([V, P64], ctypes.c_int),
         "lm_triangulate_noalloc": ([V, I32, I64, I64, V, I64, V, P64], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
@@ -206,6 +208,12 @@ def lm_metamesh_free(h):
 
 def lm_status_string(s):
     return load().lm_status_string(int(s)).decode()
+
+
+def lm_fp64_counts(h):
+    out = (ctypes.c_int64 * 16)()
+    _ck(load().lm_fp64_counts(h, out), "lm_fp64_counts")
+    return list(out)
 
 
 def lm_launch_count():

@@ -138,7 +138,8 @@ def parse_stl(records):
 def compare_triangles(gn, gv, otris, R_max, tol=2e-5):
     """Per-triangle comparison of the GPU STL records with the oracle's
     triangles (same order): vertices within tol relative (magnitude + R);
-    normals within a bound scaled by the triangle's conditioning."""
+    normals within the bound that the vertex tolerance implies for the
+    triangle's conditioning."""
     ov = otris[:, 1:]
     on = otris[:, 0]
     if gv.shape[0] != ov.shape[0]:
@@ -149,7 +150,10 @@ def compare_triangles(gn, gv, otris, R_max, tol=2e-5):
     emax = np.max([np.linalg.norm(x, axis=1) for x in e], axis=0)
     area2 = np.linalg.norm(np.cross(e[0], -e[2]), axis=1)
     cond = np.where(area2 > 0, R_max * emax / np.maximum(area2, 1e-300), np.inf)
-    ntol = 1e-4 + 2e-6 * cond
+    # a vertex error of d R moves the normal by about d R / height, and the
+    # height of a triangle is area2 / emax = R_max / cond: the FP32 vertex
+    # tolerance of 2e-5 R therefore allows normal errors up to 2e-5 cond
+    ntol = 1e-4 + 2e-5 * cond
     dn = np.linalg.norm(gn.astype(np.float64) - on, axis=1)
     good = np.isfinite(cond)
     errs = []

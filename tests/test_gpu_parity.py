@@ -23,7 +23,7 @@ LATTICES = {
     "bcc3": lambda: L.bcc(3, radius=0.1),
     "octet3": lambda: L.octet(3),
     "bccjit4": lambda: L.bcc(4, jitter=0.05, radius_range=(0.05, 0.09)),
-    "irregular": lambda: L.irregular(1500, seed=9),
+    "irregular": lambda: L.irregular(1500, seed=9, r_scale=0.06),
     "strut": lambda: L.single_strut((0.1, 0.2, 0.3), (1.0, 0.7, 0.5), 0.1, 0.1),
     "cone": lambda: L.single_strut((0.1, 0.2, 0.3), (1.0, 0.7, 0.5), 0.12, 0.05),
     "star5": lambda: L.star([(1, 0, 0), (0, 1, 0.2), (-1, 0.3, 0), (0.2, -1, 0.5), (0, 0, 1)],
@@ -53,10 +53,10 @@ def test_metamesh_parity(name, dtype):
     rep = P.compare_metamesh(g, o, z_tol=tol, phi_tol=tol)
     assert rep.ok(), "\n".join(rep.errors[:8])
     if name == "irregular":
-        # kNN lattice with radii up to 0.45 x the shortest strut: most nodes
-        # violate the lattice model (reported as the degenerate fraction)
+        # kNN lattice: acute strut pairs whose sections run past a short
+        # strut's end are degenerate (reported as the degenerate fraction)
         print(f"irregular: {rep.exempt_nodes}/{o.N} nodes exempt (flags {getattr(rep, 'exempt_flags', 0)})")
-        assert rep.checked_nodes >= 0.2 * o.N
+        assert rep.checked_nodes >= 0.4 * o.N
     else:
         assert rep.exempt_nodes == 0 and rep.checked_nodes == o.N
     cnt = mm.counts()

@@ -166,6 +166,29 @@ def test_equal_cylinder_ellipse(theta_deg):
     assert np.allclose(P @ (u1 - u2), 0, atol=1e-14)
 
 
+@pytest.mark.parametrize("theta_deg,beyond", [(8.0, True), (10.0, True), (13.0, False), (16.0, False)])
+def test_section_past_strut_length(theta_deg, beyond):
+    """Lattice model (Section 4.1): a plane section must stay within the
+    struts it joins.  For two equal cylinders of radius r at angle theta the
+    section reaches the generator coordinate r cot(theta/2) (the end of the
+    ellipse's major axis); the node is flagged degenerate (past a strut's
+    length) exactly when that exceeds the strut length."""
+    th = math.radians(theta_deg)
+    r, length = 0.1, 1.0
+    u1 = np.array([1.0, 0, 0])
+    u2 = np.array([math.cos(th), math.sin(th), 0])
+    lat = L.star([u1, u2], radius=r, length=length)
+    o = oracle.Oracle(lat)
+    tmax = r / math.tan(th / 2)
+    # the envelope on strut 0 peaks at the closed form (dense sampling)
+    phi = np.linspace(0, 2 * np.pi, 20001)
+    t, lab = o.envelope(0, 0, phi)
+    assert abs(t.max() - tmax) < 1e-6 * tmax
+    fl = o.node(0)["flags"]
+    assert bool(fl & 8) == beyond and bool(fl & 2) == beyond
+    assert (tmax > length) == beyond
+
+
 def _rot(axis, ang, v):
     axis = axis / np.linalg.norm(axis)
     return v * math.cos(ang) + np.cross(axis, v) * math.sin(ang) + axis * (axis @ v) * (1 - math.cos(ang))
@@ -257,7 +280,7 @@ def test_envelope_dense_sampling(name):
     label and span; the loops cover exactly 2 pi."""
     lat = {"bccjit2": lambda: L.bcc(2, jitter=0.05, radius_range=(0.05, 0.09)),
            "octet1": lambda: L.octet(1),
-           "irregular": lambda: L.irregular(60, seed=3)}[name]()
+           "irregular": lambda: L.irregular(120, seed=3, r_scale=0.06)}[name]()
     o = oracle.Oracle(lat)
     row, adj, _ = o.csr()
     sizes = o.node_sizes()
