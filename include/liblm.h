@@ -244,14 +244,19 @@ lm_status lm_triangulate_noalloc(lm_metamesh* mm, int32_t k, int64_t item_begin,
  * `bytes` bytes, for reading the views of lm_metamesh_export.            */
 lm_status lm_copy_to_host(void* h_dst, const void* d_src, int64_t bytes);
 
-/* FP64 stability steps (BASELINE's FP32-with-FP64-stability design, no
- * counterpart in the paper): how many decisions were re-taken in FP64
- * because their FP32 value lay inside a safety margin of its threshold or
- * came from an ill-conditioned configuration.  Synchronous.
+/* FP64 stability steps (of the FP32 path; no counterpart in the paper): how
+ * many decisions were re-taken in FP64 because their FP32 value lay inside
+ * a safety margin of its threshold or came from an ill-conditioned
+ * configuration.  Synchronous.  Cumulative over the handle's lifetime.
  *   out[0] pair classification, [1] candidate vertex re-decision,
  *   [2] vertex position refinement, [3] deduplication, [4] seam label,
  *   [5] loop angle order / wrap, [6] arc label, [7] arc extent (build);
- *   [8..15] reserved for triangulation.                                   */
+ *   [8] segment count, [9] start angle, [10] struts stitched with FP64
+ *   angles, [11] fan centre (triangulation); struts deferred from the FP32
+ *   stitching pass because of [12] an entry's segment count or start
+ *   angle, [13] a key at the edge of the angular window, [14] a pair of
+ *   keys within the zipper margin; [15] pairs of zipper keys decided in
+ *   FP64.                                                                  */
 lm_status lm_fp64_counts(const lm_metamesh* mm, int64_t out[16]);
 
 /* Utility (no counterpart in the paper): number of CUDA kernels this library

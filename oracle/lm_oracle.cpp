@@ -57,8 +57,16 @@ const double PI2 = 6.283185307179586476925286766559;
 const double ETA_SIGMA = 1e-9;   // x R: a strut passes through a vertex
 const double ETA_DEDUP = 1e-3;   // x R: two candidates with one key are one vertex
 const double ETA_PHI = 1e-9;     // rad: loop angles normalised to [-ETA_PHI, 2pi-ETA_PHI)
-const double ETA_ZIP = 1e-9;     // rad: zipper tie
-const double TAU_COUNT = 1e-6;   // segment-count offset
+// rad: zipper tie band.  A point of loop A advances before a point of loop B
+// whose angle it exceeds by at most ETA_ZIP.  Points of the two loops of a
+// (near-)symmetric strut line up to within far less than this, so they all
+// take the same branch.
+const double ETA_ZIP = 0.0009765625;  // 2^-10
+// segment-count offset: an arc whose ratio dphi k / 2pi exceeds an integer n
+// by at most TAU_COUNT gets n segments (exact multiples, as on symmetric
+// lattices, keep the minimal count; the chord error may exceed its target
+// by a relative 2^-10 / n at most)
+const double TAU_COUNT = 0.0009765625;  // 2^-10
 const double ETA_BARY = 1e-4;    // x R: hole barycentre too close to the centre
 const double EPS_PAR = 1e-6;     // 1 - c^2 below this: (anti)parallel pair
 const double EPS_TAN = 1e-6;     // tangency measure below this: node exempt

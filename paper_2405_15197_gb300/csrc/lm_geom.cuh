@@ -32,8 +32,8 @@ constexpr double PI2 = 6.283185307179586476925286766559;
 constexpr double ETA_SIGMA = 1e-9;  // x R: a strut passes through a vertex
 constexpr double ETA_DEDUP = 1e-3;  // x R: candidates with one key are one vertex
 constexpr double ETA_PHI = 1e-9;    // rad: angles normalised to [-ETA_PHI, 2pi - ETA_PHI)
-constexpr double ETA_ZIP = 1e-9;    // rad: stitching tie
-constexpr double TAU_COUNT = 1e-6;  // segment count offset
+constexpr double ETA_ZIP = 0.0009765625;  // rad (2^-10): stitching tie band
+constexpr double TAU_COUNT = 0.0009765625;  // segment count offset (2^-10)
 constexpr double ETA_BARY = 1e-4;   // x R: hole barycentre at the centre
 constexpr double EPS_PAR = 1e-6;    // 1 - c^2 below this: (anti)parallel pair
 constexpr double EPS_TAN = 1e-6;    // tangency measure: node exempt from exact parity
@@ -43,9 +43,9 @@ constexpr double EPS_TAN = 1e-6;    // tangency measure: node exempt from exact 
 // again in FP64 from the inputs.
 constexpr float M_LEN = 1e-4f;   // x R (FP32 candidate error <= ~1e-5 R once conditioned)
 constexpr float M_ANG = 1e-5f;   // rad (loop angles of the meta-mesh)
-constexpr float M_ZIP = 2e-5f;   // rad (stitching order; FP32 angle error <= ~2e-6)
+constexpr float M_ZIP = 2e-5f;   // rad (stitching order, about ETA_ZIP; FP32 angle error <= ~2e-6)
 constexpr float M_COND = 1e-2f;  // conditioning floor of q, |v|^2, |A|, D/R^2, g2
-constexpr float M_CNT = 1e-3f;   // segment-count fraction
+constexpr float M_CNT = 2e-5f;   // rad: arc extent, for the segment count (x k / 2pi)
 constexpr float M_POS = 1e-1f;   // conditioning floor for keeping an FP32 circle-point position
 // A triple point keeps its FP32 position when its first-order sensitivity to
 // unit-roundoff perturbations of the strut axes (the dominant FP32 error: the

@@ -53,7 +53,7 @@ template <typename T>
 __device__ __forceinline__ int seg_count(T dphi, int k, bool& unc) {
   T y = dphi * (T)k * T(1.0 / PI2) - T(TAU_COUNT);
   T c = ceil(y);
-  unc = sizeof(T) == 4 && fabs(y - rint(y)) <= T(M_CNT);
+  unc = sizeof(T) == 4 && fabs(y - rint(y)) <= T(M_CNT) * (T)k * T(1.0 / PI2);
   int n = (int)c;
   return n < 1 ? 1 : n;
 }
@@ -526,7 +526,7 @@ __global__ void __launch_bounds__(128, 3) k_tri_thread(TriArgs<T> A, const int64
     auto keyB = [&](const LoopIt<T>& I, T th, bool& exact, double& k64) -> T {
       T x = wrap_from(th, thA0 - T(ETA_ZIP));
       exact = false;
-      if (sizeof(T) == 4 && (x - thA0 <= T(M_ZIP) || thA0 + T(PI2) - x <= T(M_ZIP))) {
+      if (sizeof(T) == 4 && (x - (thA0 - T(ETA_ZIP)) <= T(M_ZIP) || thA0 + T(PI2 - ETA_ZIP) - x <= T(M_ZIP))) {
         k64 = wrap_from(it_theta64(A, I), a0_64() - ETA_ZIP);
         exact = true;
         x = (T)k64;
@@ -585,7 +585,7 @@ __global__ void __launch_bounds__(128, 3) k_tri_thread(TriArgs<T> A, const int64
       else if (ia >= nA) takeA = false;
       else {
         T xa = ia + 1 < nA ? thAn : thA0 + T(PI2);
-        if (sizeof(T) == 4 && fabs(xa - kBn) <= T(M_ZIP)) {
+        if (sizeof(T) == 4 && fabs(xa - kBn - T(ETA_ZIP)) <= T(M_ZIP)) {
           double xa64 = ia + 1 < nA ? it_theta64(A, IA) : a0_64() + PI2;
           double kb = exB ? kB64 : wrap_from(it_theta64(A, IB), a0_64() - ETA_ZIP);
           takeA = xa64 <= kb + ETA_ZIP;
@@ -919,6 +919,7 @@ __device__ __forceinline__ bool tile_strut(const TriArgs<T>& A, const TileSmem<T
         else Nq = tile_entry_setup_impl<T, false>(A, node, eid, q0 + q, ENT + X * A.emax + q);
       }
       if (__any_sync(m, Nq < 0)) {
+        tfb_add(A.fb, 12, tl == 0, m);
         defer = true;
         break;
       }
@@ -975,12 +976,15 @@ __device__ __forceinline__ bool tile_strut(const TriArgs<T>& A, const TileSmem<T
   for (int j = tl; j < nB; j += TL) {
     T x = wrap_from(TH[A.pmax + j], thA0 - T(ETA_ZIP));
     KB[j] = x;
-    if (!IS64 && (x - thA0 <= T(M_ZIP) || thA0 + T(PI2) - x <= T(M_ZIP))) {
+    if (!IS64 && (x - (thA0 - T(ETA_ZIP)) <= T(M_ZIP) || thA0 + T(PI2 - ETA_ZIP) - x <= T(M_ZIP))) {
       if (FP64_STEPS) FL[A.pmax + j] = 2;  // window edge: key retaken in FP64
       any = true;
     }
   }
-  if (!IS64 && !EXACT && __any_sync(m, any)) return true;
+  if (!IS64 && !EXACT && __any_sync(m, any)) {
+    tfb_add(A.fb, 13, tl == 0, m);
+    return true;
+  }
   __syncwarp(m);
   auto rotation = [&]() {
     T mn = T(1e30);
@@ -996,12 +1000,13 @@ __device__ __forceinline__ bool tile_strut(const TriArgs<T>& A, const TileSmem<T
   };
   int sB = rotation();
   if (!IS64) {
-    // A points whose angle lies within M_ZIP of some B key: every such pair
-    // is decided in FP64 (B keys are sorted after the rotation up to FP32
-    // rounding, so each scan stops at the first key clearly out of range)
+    // A points whose angle lies within M_ZIP of some B key + ETA_ZIP: every
+    // such pair is decided in FP64 (B keys are sorted after the rotation up
+    // to FP32 rounding, so each scan stops at the first key clearly out of
+    // range)
     for (int i = tl; i <= nA; i += TL) {
       if (i == 0) continue;
-      T x = i < nA ? TH[i] : thA0 + T(PI2);
+      T x = (i < nA ? TH[i] : thA0 + T(PI2)) - T(ETA_ZIP);
       int lj = 0, hj = nB;
       while (lj < hj) {
         int mid = (lj + hj) >> 1;
@@ -1034,7 +1039,10 @@ __device__ __forceinline__ bool tile_strut(const TriArgs<T>& A, const TileSmem<T
     }
   }
   const bool anyt = !IS64 && __any_sync(m, any);
-  if (!EXACT && anyt) return true;
+  if (!EXACT && anyt) {
+    tfb_add(A.fb, 14, tl == 0, m);
+    return true;
+  }
   if (FP64_STEPS) tfb_add(A.fb, 10, anyt && tl == 0, m);
   if (FP64_STEPS && anyt) {
     // A's first point fixes the window: always taken in FP64 here
@@ -1076,6 +1084,18 @@ __device__ __forceinline__ bool tile_strut(const TriArgs<T>& A, const TileSmem<T
       double x64 = wrap_from(S.TH64[A.pmax + j], a0 - ETA_ZIP);
       S.TH64[A.pmax + j] = x64;
       if (f & 2) KB[j] = (T)x64;
+    }
+    __syncwarp(m);
+    if (A.fb) {
+      // pairs of keys decided in FP64 (within M_ZIP of the tie band's edge)
+      int pairs = 0;
+      for (int i = tl + 1; i <= nA; i += TL) {
+        if (!FL[i < nA ? i : 0]) continue;
+        double x = (i < nA ? S.TH64[i] : a0 + PI2) - ETA_ZIP;
+        for (int j = 0; j < nB; j++)
+          if (FL[A.pmax + j] && fabs(S.TH64[A.pmax + j] - x) <= M_ZIP) pairs++;
+      }
+      if (pairs) atomicAdd(A.fb + 15, (unsigned long long)pairs);
     }
     __syncwarp(m);
     sB = rotation();
