@@ -245,9 +245,11 @@ lm_status lm_triangulate_noalloc(lm_metamesh* mm, int32_t k, int64_t item_begin,
 lm_status lm_copy_to_host(void* h_dst, const void* d_src, int64_t bytes);
 
 /* FP64 stability steps (of the FP32 path; no counterpart in the paper): how
- * many decisions were re-taken in FP64 because their FP32 value lay inside
- * a safety margin of its threshold or came from an ill-conditioned
- * configuration.  Synchronous.  Cumulative over the handle's lifetime.
+ * many decisions were re-taken in higher precision because their FP32 value
+ * lay inside a safety margin of its threshold or came from an
+ * ill-conditioned configuration.  Candidate re-decisions ([1]) run in
+ * double-float arithmetic (about 48 bits), the others in FP64.
+ * Synchronous.  Cumulative over the handle's lifetime.
  *   out[0] pair classification, [1] candidate vertex re-decision,
  *   [2] vertex position refinement, [3] deduplication, [4] seam label,
  *   [5] loop angle order / wrap, [6] arc label, [7] arc extent (build);

@@ -56,7 +56,12 @@ const double PI2 = 6.283185307179586476925286766559;
 // Tolerances (readings; the CUDA path decides with the same values).
 const double ETA_SIGMA = 1e-9;   // x R: a strut passes through a vertex
 const double ETA_DEDUP = 1e-3;   // x R: two candidates with one key are one vertex
-const double ETA_PHI = 1e-9;     // rad: loop angles normalised to [-ETA_PHI, 2pi-ETA_PHI)
+const double ETA_PHI = 1e-9;     // rad: angle ties; relative angles wrap to [-ETA_PHI, 2pi-ETA_PHI)
+// rad: absolute angles around a strut end are normalised to
+// [-PHI_CUT, 2pi - PHI_CUT).  The cut sits away from angle 0, where
+// symmetric lattices put vertices, so which end of the range they land on is
+// never a rounding question.
+const double PHI_CUT = 0.0009765625;  // 2^-10
 // rad: zipper tie band.  A point of loop A advances before a point of loop B
 // whose angle it exceeds by at most ETA_ZIP.  Points of the two loops of a
 // (near-)symmetric strut line up to within far less than this, so they all
@@ -199,10 +204,10 @@ inline double G(const End& e, V3 z, double R) { return (dot(e.u, z) - R * e.s) /
 inline double hval(const End& i, const End& j, double phi, double R) {
   return R * (dot(j.u, wdir(i, phi)) - j.s) / (j.co - dot(j.u, gdir(i, phi)));
 }
-// angle of a node-relative point around strut end e, in [-ETA_PHI, 2pi-ETA_PHI)
+// angle of a node-relative point around strut end e, in [-PHI_CUT, 2pi-PHI_CUT)
 inline double angle(const End& e, V3 z) {
   double p = std::atan2(dot(z, e.e2), dot(z, e.e1));
-  if (p < -ETA_PHI) p += PI2;
+  if (p < -PHI_CUT) p += PI2;
   return p;
 }
 

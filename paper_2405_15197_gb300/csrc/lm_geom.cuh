@@ -24,6 +24,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "lm_df.cuh"
+
 namespace lm {
 
 constexpr double PI2 = 6.283185307179586476925286766559;
@@ -31,7 +33,8 @@ constexpr double PI2 = 6.283185307179586476925286766559;
 // Decision thresholds (readings of ties the paper is silent on).
 constexpr double ETA_SIGMA = 1e-9;  // x R: a strut passes through a vertex
 constexpr double ETA_DEDUP = 1e-3;  // x R: candidates with one key are one vertex
-constexpr double ETA_PHI = 1e-9;    // rad: angles normalised to [-ETA_PHI, 2pi - ETA_PHI)
+constexpr double ETA_PHI = 1e-9;    // rad: angle ties; relative angles wrap to [-ETA_PHI, 2pi - ETA_PHI)
+constexpr double PHI_CUT = 0.0009765625;  // rad (2^-10): absolute angles in [-PHI_CUT, 2pi - PHI_CUT)
 constexpr double ETA_ZIP = 0.0009765625;  // rad (2^-10): stitching tie band
 constexpr double TAU_COUNT = 0.0009765625;  // segment count offset (2^-10)
 constexpr double ETA_BARY = 1e-4;   // x R: hole barycentre at the centre
@@ -93,6 +96,7 @@ __device__ __forceinline__ V3<U> cvt3(V3<S> a) {
 }
 __device__ __forceinline__ float lm_sqrt(float x) { return sqrtf(x); }
 __device__ __forceinline__ double lm_sqrt(double x) { return sqrt(x); }
+__device__ __forceinline__ df lm_sqrt(df x) { return df_sqrt(x); }
 __device__ __forceinline__ float lm_atan2(float y, float x) { return atan2f(y, x); }
 __device__ __forceinline__ double lm_atan2(double y, double x) { return atan2(y, x); }
 __device__ __forceinline__ void lm_sincos(float a, float* s, float* c) { sincosf(a, s, c); }
@@ -292,7 +296,7 @@ __device__ void eval_gen(const EndG<U>* E, int d, U R, uint32_t gcode, GenOut<U>
       if (g2 < U(-1e-3) * mag) return;
       if (g2 < U(M_COND) * mag) { o.unc = 1; return; }
     }
-    if (!F64) well = q >= U(M_POS) && g2 >= U(M_POS) * (U(1) + al * al + be * be);
+    if constexpr (!F64) well = q >= U(M_POS) && g2 >= U(M_POS) * (U(1) + al * al + be * be);
     V3<U> w = cross(E[i].u, E[j].u);
     w = w * (U(1) / norm3(w));
     U g = lm_sqrt(g2);
@@ -327,7 +331,7 @@ __device__ void eval_gen(const EndG<U>* E, int d, U R, uint32_t gcode, GenOut<U>
     U B = -G0 * G1;
     U C = dot(z0, z0) - R * R - G0 * G0;
     if (F64) {
-      if (fabs((double)A) < 1e-12) {
+      if (fabs(A) < U(1e-12)) {
         o.nflags |= NF_DEGENERATE | NF_ALONG;
         return;
       }
@@ -362,7 +366,7 @@ __device__ void eval_gen(const EndG<U>* E, int d, U R, uint32_t gcode, GenOut<U>
     o.z[1] = z0 + vh * lam1;
     o.t0[0] = G0 + lam0 * G1;
     o.t0[1] = G0 + lam1 * G1;
-    if (!F64) {
+    if constexpr (!F64) {
       // z solves (G_i - G_j, G_i - G_k, |z|^2 - R^2 - G_i^2) = 0 with Jacobian
       // rows mj, mk, nc = z - G_i ico_i u_i; a perturbation of the axes by one
       // roundoff moves the residuals by about |z| ico (|t| ico for the cone
@@ -471,7 +475,7 @@ __device__ __forceinline__ int warp_excl_scan(int x, int lane) {
 
 template <typename T>
 __device__ __forceinline__ T norm_angle(T a) {
-  return a < T(-ETA_PHI) ? a + T(PI2) : a;
+  return a < T(-PHI_CUT) ? a + T(PI2) : a;
 }
 
 // x moved by a multiple of 2pi into [lo, lo + 2pi) (one floor, no loop)

@@ -27,7 +27,8 @@ template <typename T, typename C>
 struct WarpSmem {
   EndG<T> E[C::D];
   EndG<double> E64[sizeof(T) == 4 ? C::D : 1];
-  uint64_t e64_valid;
+  EndG<df> EDF[sizeof(T) == 4 ? C::D : 1];
+  uint64_t e64_valid, edf_valid;
   uint64_t tan_small[C::D], tan_neg[C::D], coinc[C::D];
   V3<T> vz[C::V];
   uint64_t vkey[C::V];
@@ -98,6 +99,20 @@ __device__ void ensure64(WarpSmem<T, C>& S, const LatDev<T>& L, int64_t n, int d
     if (miss >> li & 1ull) S.E64[li] = make_end<T, double>(L, n, S.E[li].end_id);
   __syncwarp();
   if (lane == 0) S.e64_valid |= miss;
+  __syncwarp();
+}
+// Double-float copies of the node's strut ends (candidate re-decisions),
+// built on first use.
+template <typename T, typename C>
+__device__ void ensure_df(WarpSmem<T, C>& S, const LatDev<T>& L, int64_t n, int d, int lane) {
+  if (sizeof(T) == 8) return;
+  uint64_t all = d >= 64 ? ~0ull : ((1ull << d) - 1);
+  uint64_t miss = all & ~S.edf_valid;
+  if (!miss) return;
+  for (int li = lane; li < d; li += 32)
+    if (miss >> li & 1ull) S.EDF[li] = make_end<T, df>(L, n, S.E[li].end_id);
+  __syncwarp();
+  if (lane == 0) S.edf_valid |= miss;
   __syncwarp();
 }
 template <typename T, typename C>
@@ -183,6 +198,7 @@ __device__ void node_metamesh(WarpSmem<T, C>& S, const MMArgs<T>& A, int64_t n, 
     S.nv = 0;
     S.nflags = 0;
     S.e64_valid = 0;
+    S.edf_valid = 0;
   }
   __syncwarp();
 
@@ -301,22 +317,25 @@ __device__ void node_metamesh(WarpSmem<T, C>& S, const MMArgs<T>& A, int64_t n, 
         o.t0[r] = (T)t64[r];
       }
     }
-    if (!IS64 && __any_sync(0xffffffffu, need64)) {
-      ensure64(S, L, n, d, lane);
-      if (need64) {
-        GenOut<double> o64;
-        eval_gen<double, true>(ends64(S), d, R64, code, o64);
-        o.nroot = o64.nroot;
-        o.unc = 0;
-        o.nflags = o64.nflags;
-        for (int r = 0; r < 2; r++) {
-          o.z[r] = mk3((T)o64.z[r].x, (T)o64.z[r].y, (T)o64.z[r].z);
-          o.t0[r] = (T)o64.t0[r];
-          o.key[r] = o64.key[r];
-          o.sphere[r] = o64.sphere[r];
-          o.state[r] = o64.state[r];
-          o.tangent[r] = o64.tangent[r];
-          o.kflags[r] = o64.kflags[r];
+    if constexpr (!IS64) {
+      if (__any_sync(0xffffffffu, need64)) {
+        // re-decision in double-float (about 48 bits; see lm_df.cuh)
+        ensure_df(S, L, n, d, lane);
+        if (need64) {
+          GenOut<df> o64;
+          eval_gen<df, true>(S.EDF, d, df(R), code, o64);
+          o.nroot = o64.nroot;
+          o.unc = 0;
+          o.nflags = o64.nflags;
+          for (int r = 0; r < 2; r++) {
+            o.z[r] = mk3((T)(float)o64.z[r].x, (T)(float)o64.z[r].y, (T)(float)o64.z[r].z);
+            o.t0[r] = (T)(float)o64.t0[r];
+            o.key[r] = o64.key[r];
+            o.sphere[r] = o64.sphere[r];
+            o.state[r] = o64.state[r];
+            o.tangent[r] = o64.tangent[r];
+            o.kflags[r] = o64.kflags[r];
+          }
         }
       }
     }
@@ -482,7 +501,7 @@ __device__ void node_metamesh(WarpSmem<T, C>& S, const MMArgs<T>& A, int64_t n, 
         for (int v = 0; v < S.nv; v++) {
           if (!((S.vkey[v] >> i) & 1ull)) continue;
           T a = raw_angle(S.E[i], S.vz[v]);
-          if (!IS64 && fabs(a + T(ETA_PHI)) <= T(M_ANG)) unc = true;
+          if (!IS64 && fabs(a + T(PHI_CUT)) <= T(M_ANG)) unc = true;
           a = norm_angle(a);
           // stable insertion by angle
           int p = q;

@@ -95,8 +95,8 @@ __device__ __noinline__ double arc_dphi64(const TriArgs<T>& A, const Node64* ctx
   V3<double> z0 = vertex_from_gen<double>(ctx->E, ctx->d, ctx->R, A.vtx_gen[vo + v0]);
   V3<double> z1 = vertex_from_gen<double>(ctx->E, ctx->d, ctx->R, A.vtx_gen[vo + v1]);
   double a0 = raw_angle(ctx->E[o], z0), a1 = raw_angle(ctx->E[o], z1);
-  if (a0 < -ETA_PHI) a0 += PI2;
-  if (a1 < -ETA_PHI) a1 += PI2;
+  if (a0 < -PHI_CUT) a0 += PI2;
+  if (a1 < -PHI_CUT) a1 += PI2;
   double dd = a1 - a0;
   if (v0 == v1) dd = PI2;
   else if (dd <= 0.0) dd += PI2;
@@ -399,7 +399,7 @@ __device__ __noinline__ void it_load(const TriArgs<T>& A, LoopIt<T>& it, int q) 
     int64_t vi = A.vtx_off[it.node] + vs;
     V3<T> zs = mk3(A.vtx_z[3 * vi], A.vtx_z[3 * vi + 1], A.vtx_z[3 * vi + 2]);
     T a = lm_atan2(dot(zs, it.me2), dot(zs, it.me1));
-    if (sizeof(T) == 4 && fabs(a + T(ETA_PHI)) <= T(M_ANG)) {
+    if (sizeof(T) == 4 && fabs(a + T(PHI_CUT)) <= T(M_ANG)) {
       EndG<double> me = make_end<T, double>(L, it.node, it.eid);
       a = (T)norm_angle(raw_angle(me, vertex_pos64(L, it.node, A.vtx_gen[vi])));
     }
@@ -838,7 +838,7 @@ __device__ __forceinline__ int tile_entry_setup_impl(const TriArgs<T>& A, int64_
     V3<T> zs = mk3(A.vtx_z[3 * vi], A.vtx_z[3 * vi + 1], A.vtx_z[3 * vi + 2]);
     EndG<T> own = make_end<T, T>(L, node, eid);
     T ang = raw_angle(own, zs);
-    if (!IS64 && fabs(ang + T(ETA_PHI)) <= T(M_ANG)) {
+    if (!IS64 && fabs(ang + T(PHI_CUT)) <= T(M_ANG)) {
       if (!EXACT) return -1;
       EndG<double> me = make_end<T, double>(L, node, eid);
       ang = (T)norm_angle(raw_angle(me, vertex_pos64(L, node, A.vtx_gen[vi])));
