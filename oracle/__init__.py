@@ -65,6 +65,12 @@ def _load():
                                        ctypes.c_int, c_dp]
         lib.lmo_envelope.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int,
                                      ctypes.c_int64, c_dp, c_dp, c_i32p]
+        lib.lmo_frozen_record.restype = ctypes.c_void_p
+        lib.lmo_frozen_record.argtypes = [ctypes.c_void_p, ctypes.c_int]
+        lib.lmo_frozen_free.argtypes = [ctypes.c_void_p]
+        lib.lmo_frozen_objective.argtypes = [ctypes.c_void_p, ctypes.c_void_p, c_dp, c_dp, c_dp]
+        lib.lmo_frozen_fd.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double, c_i64p,
+                                      ctypes.c_int64, c_dp]
         _lib = lib
     return _lib
 
@@ -197,3 +203,36 @@ class Oracle:
                                       _p(tris, c_dp) if want_tris else None, _p(acc, c_dp))
         assert got == T, (got, T)
         return (tris.reshape(T, 4, 3) if want_tris else None), float(acc[0]), float(acc[1])
+
+
+class Frozen:
+    """The discrete structure of an oracle triangulation at resolution k
+    (vertex generators, arcs, loops, holes, segment counts, stitching order,
+    fan-centre rule), re-evaluated at perturbed node positions and radii:
+    the function whose derivative the adjoint computes."""
+
+    def __init__(self, o, k):
+        self.o = o
+        self.k = int(k)
+        self.h = _load().lmo_frozen_record(o.h, self.k)
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            _load().lmo_frozen_free(self.h)
+            self.h = None
+
+    def objective(self, xyz, node_R):
+        """(area, volume) at node positions xyz [N,3] and node radii [N]."""
+        xyz = np.ascontiguousarray(xyz, dtype=np.float64)
+        node_R = np.ascontiguousarray(node_R, dtype=np.float64)
+        out = np.zeros(2)
+        _load().lmo_frozen_objective(self.o.h, self.h, _p(xyz, c_dp), _p(node_R, c_dp), _p(out, c_dp))
+        return float(out[0]), float(out[1])
+
+    def fd(self, step, nodes):
+        """Central differences: arrays (d_area, d_volume), each [len(nodes), 4]
+        with columns d/dx, d/dy, d/dz, d/dR of the listed nodes."""
+        nodes = np.ascontiguousarray(nodes, dtype=np.int64)
+        g = np.zeros((nodes.size, 8))
+        _load().lmo_frozen_fd(self.o.h, self.h, float(step), _p(nodes, c_i64p), nodes.size, _p(g, c_dp))
+        return g[:, :4].copy(), g[:, 4:].copy()

@@ -615,13 +615,14 @@ struct LoopPts {
   std::vector<double> th;  // unwrapped angle around the strut
 };
 
-LoopPts loop_points(const NodeGeo& g, const NodeOut& no, int li, int k) {
+// Nf: recorded segment counts per node-local arc (frozen topology), or NULL
+LoopPts loop_points(const NodeGeo& g, const NodeOut& no, int li, int k, const std::vector<int>* Nf = nullptr) {
   LoopPts P;
   const End& me = g.E[li];
   const std::vector<Entry>& L = no.loops[li];
   for (const Entry& en : L) {
     const Arc& a = no.A[en.arc];
-    int N = seg_count(a.dphi, k);
+    int N = Nf ? (*Nf)[en.arc] : seg_count(a.dphi, k);
     int vs = en.rev ? a.v1 : a.v0;
     double psi = angle(me, no.V[vs].z);
     for (int s = 0; s < N; s++) {
@@ -651,6 +652,15 @@ struct Tri {
   double area, vol;
 };
 
+// Discrete structure of a triangulation at k, recorded once and replayed
+// with perturbed geometry (the adjoint's reference: topology held fixed).
+struct Frozen {
+  int k = 0;
+  std::vector<std::vector<int>> N;        // [node][arc] segment count
+  std::vector<std::vector<uint8_t>> zip;  // [strut] stitching steps, 1 = A advances
+  std::vector<std::vector<uint8_t>> fan;  // [node][hole] centre rule (see hole_tris)
+};
+
 // a, b, c relative to o (an exact node centre) give the STL normal, the area
 // and the volume term det(a,b,c) + o.(2 x area vector); pa, pb, pc are the
 // absolute coordinates, always formed as (own node centre) + (relative point)
@@ -669,7 +679,10 @@ void emit(std::vector<Tri>& T, V3 o, V3 a, V3 b, V3 c, V3 pa, V3 pb, V3 pc) {
 
 // lateral band of strut e: zipper between its loop at the lo node (A) and at
 // the hi node (B), both in the strut's angle; ties advance A.
-void strut_tris(const Mesh& M, int64_t e, int k, std::vector<Tri>& T) {
+// fz: record the stitching steps into fz (replay = false) or replay them
+// and the recorded segment counts (replay = true); NULL: plain evaluation
+void strut_tris(const Mesh& M, int64_t e, int k, std::vector<Tri>& T, Frozen* fz = nullptr,
+                bool replay = false) {
   int32_t a = M.lat.ends[2 * e], b = M.lat.ends[2 * e + 1];
   int32_t lo = std::min(a, b), hi = std::max(a, b);
   int side_lo = (a == lo) ? 0 : 1;
@@ -680,8 +693,10 @@ void strut_tris(const Mesh& M, int64_t e, int k, std::vector<Tri>& T) {
     if (M.adj[q] == endA) liA = (int)(q - M.row_ptr[lo]);
   for (int64_t q = M.row_ptr[hi]; q < M.row_ptr[hi + 1]; q++)
     if (M.adj[q] == endB) liB = (int)(q - M.row_ptr[hi]);
-  LoopPts PA = loop_points(gA, M.nodes[lo], liA, k);
-  LoopPts PB = loop_points(gB, M.nodes[hi], liB, k);
+  const std::vector<int>* NA = replay ? &fz->N[lo] : nullptr;
+  const std::vector<int>* NB = replay ? &fz->N[hi] : nullptr;
+  LoopPts PA = loop_points(gA, M.nodes[lo], liA, k, NA);
+  LoopPts PB = loop_points(gB, M.nodes[hi], liB, k, NB);
   int nA = (int)PA.z.size(), nB = (int)PB.z.size();
   V3 dAB = sub(gB.c, gA.c);
   // B's angles moved into the window [thA0 - ETA_ZIP, thA0 + 2pi - ETA_ZIP)
@@ -706,8 +721,13 @@ void strut_tris(const Mesh& M, int64_t e, int k, std::vector<Tri>& T) {
   // state: current A point ia (0..nA), current B point ib (-1..nB-1);
   // events a_1..a_nA and b_0..b_{nB-1} in key order, ties -> A first
   int ia = 0, ib = -1;
+  size_t step = 0;
+  if (fz && !replay) fz->zip[e].clear();
   while (ia < nA || ib < nB - 1) {
     bool takeA = (ib == nB - 1) || (ia < nA && thA(ia + 1) <= thB(ib + 1) + ETA_ZIP);
+    if (fz && replay) takeA = step < fz->zip[e].size() ? fz->zip[e][step] != 0 : (ia < nA);
+    if (fz && !replay) fz->zip[e].push_back(takeA ? 1 : 0);
+    step++;
     if (takeA) {
       emit(T, gA.c, pA(ia), pA(ia + 1), pB(ib), aA(ia), aA(ia + 1), aB(ib));
       ia++;
@@ -719,15 +739,20 @@ void strut_tris(const Mesh& M, int64_t e, int k, std::vector<Tri>& T) {
 }
 
 // hole fans of node n (Section 5 hole filling)
-void hole_tris(const Mesh& M, int64_t n, int k, std::vector<Tri>& T) {
+// fz: record (replay = false) or replay (replay = true) the centre rule of
+// every hole and the segment counts; NULL: plain evaluation
+void hole_tris(const Mesh& M, int64_t n, int k, std::vector<Tri>& T, Frozen* fz = nullptr,
+               bool replay = false) {
   const NodeOut& no = M.nodes[n];
   if (no.holes.empty()) return;
   NodeGeo g = node_geo(M, n);
-  for (const auto& hole : no.holes) {
+  if (fz && !replay) fz->fan[n].assign(no.holes.size(), 0);
+  for (size_t hh = 0; hh < no.holes.size(); hh++) {
+    const auto& hole = no.holes[hh];
     std::vector<V3> q;
     for (const Entry& en : hole) {
       const Arc& a = no.A[en.arc];
-      int N = seg_count(a.dphi, k);
+      int N = replay ? fz->N[n][en.arc] : seg_count(a.dphi, k);
       for (int s = 0; s < N; s++) q.push_back(arc_point(g, no, a, en.rev ? N - s : s, N));
     }
     int Mq = (int)q.size();
@@ -741,26 +766,142 @@ void hole_tris(const Mesh& M, int64_t n, int k, std::vector<Tri>& T) {
         if (dot(e.u, dir) > e.s) return false;
       return true;
     };
+    // rule: 0 barycentre direction, 1 -sum u, 2 barycentre (no -sum u), 3 -u_0
     V3 dir = mk(0, 0, 0);
-    bool ok = false;
     double bl = norm(b);
-    if (bl > ETA_BARY * g.R) {
-      dir = mul(b, 1.0 / bl);
-      ok = in_hole(dir);
+    V3 su = mk(0, 0, 0);
+    for (const End& e : g.E) su = sub(su, e.u);
+    double sl = norm(su);
+    int rule;
+    if (replay) {
+      rule = fz->fan[n][hh];
+    } else {
+      rule = -1;
+      if (bl > ETA_BARY * g.R && in_hole(mul(b, 1.0 / bl))) rule = 0;
+      else if (sl > ETA_BARY) rule = 1;
+      else if (bl > 0.0) rule = 2;
+      else rule = 3;
+      if (fz) fz->fan[n][hh] = (uint8_t)rule;
     }
-    if (!ok) {
-      V3 su = mk(0, 0, 0);
-      for (const End& e : g.E) su = sub(su, e.u);
-      double sl = norm(su);
-      if (sl > ETA_BARY) dir = mul(su, 1.0 / sl);
-      else if (bl > 0.0) dir = mul(b, 1.0 / bl);
-      else dir = mul(g.E[0].u, -1.0);
-    }
+    if (rule == 0 || rule == 2) dir = mul(b, 1.0 / bl);
+    else if (rule == 1) dir = mul(su, 1.0 / sl);
+    else dir = mul(g.E[0].u, -1.0);
     V3 bp = mul(dir, g.R);
     for (int m = 0; m < Mq; m++) {
       V3 q1 = q[(m + 1) % Mq];
       emit(T, g.c, bp, q[m], q1, add(g.c, bp), add(g.c, q[m]), add(g.c, q1));
     }
+  }
+}
+
+// ----------------------------------------------- frozen-topology objective
+// Reference of the adjoint: d(area, volume)/d(node positions, radii) with the
+// discrete structure held fixed (vertex generators, arcs, loops, holes,
+// segment counts, stitching order, fan-centre rule).  Geometry is recomputed
+// from perturbed parameters: each vertex from its generator (the formulas of
+// node_metamesh: circle point, triple point with the same root, seam), each
+// arc's angles from its end vertices (followed continuously from the recorded
+// values), then points and triangles as in strut_tris / hole_tris.
+
+// node-relative vertex of generator `gen` from the node's strut ends
+V3 vertex_from_gen(const std::vector<End>& E, double R, uint32_t gen) {
+  int type = gen & 3, root = (gen >> 2) & 1;
+  int i = (gen >> 3) & 63, j = (gen >> 9) & 63, k = (gen >> 15) & 63;
+  if (type == 0) {
+    double c = dot(E[i].u, E[j].u);
+    double q = 1.0 - c * c;
+    double al = (E[i].s - c * E[j].s) / q;
+    double be = (E[j].s - c * E[i].s) / q;
+    double g2 = 1.0 - (al * al + be * be + 2.0 * al * be * c);
+    V3 w = cross(E[i].u, E[j].u);
+    w = mul(w, 1.0 / norm(w));
+    double g = std::sqrt(std::max(g2, 0.0));
+    return mul(add(add(mul(E[i].u, al), mul(E[j].u, be)), mul(w, root == 0 ? -g : g)), R);
+  }
+  if (type == 1) {
+    V3 mj = sub(mul(E[i].u, 1.0 / E[i].co), mul(E[j].u, 1.0 / E[j].co));
+    V3 mk_ = sub(mul(E[i].u, 1.0 / E[i].co), mul(E[k].u, 1.0 / E[k].co));
+    double dj = R * (E[i].s / E[i].co - E[j].s / E[j].co);
+    double dk = R * (E[i].s / E[i].co - E[k].s / E[k].co);
+    V3 v = cross(mj, mk_);
+    double vv = dot(v, v);
+    V3 z0 = mul(sub(mul(cross(mk_, v), dj), mul(cross(mj, v), dk)), 1.0 / vv);
+    V3 vh = mul(v, 1.0 / std::sqrt(vv));
+    double G0 = (dot(E[i].u, z0) - R * E[i].s) / E[i].co;
+    double G1 = dot(E[i].u, vh) / E[i].co;
+    double A = 1.0 - G1 * G1;
+    double B = -G0 * G1;
+    double C = dot(z0, z0) - R * R - G0 * G0;
+    double sq = std::sqrt(std::max(B * B - A * C, 0.0));
+    // roots (-B - sq)/A and (-B + sq)/A, in the stable form
+    double lam;
+    if (B >= 0.0) {
+      double q = -(B + sq);
+      lam = root == 0 ? q / A : C / q;
+    } else {
+      double q = -B + sq;
+      lam = root == 1 ? q / A : C / q;
+    }
+    return add(z0, mul(vh, lam));
+  }
+  // seam at angle 0 of strut end i, on plane P_ij when labelled
+  double t = (gen >> 21) & 1 ? hval(E[i], E[j], 0.0, R) : 0.0;
+  return add(mul(wdir(E[i], 0.0), R), mul(gdir(E[i], 0.0), t));
+}
+
+inline double wrap_pi(double x) { return x - PI2 * std::nearbyint(x / PI2); }
+
+// geometry of node n recomputed from the (perturbed) lattice of M2, with the
+// discrete structure of `base`
+void refresh_node(const Mesh& M2, const NodeOut& base, NodeOut& out, int64_t n) {
+  if (base.V.empty() && base.A.empty()) return;
+  NodeGeo g = node_geo(M2, n);
+  for (size_t v = 0; v < base.V.size(); v++) out.V[v].z = vertex_from_gen(g.E, g.R, base.V[v].gen);
+  for (size_t a = 0; a < base.A.size(); a++) {
+    const Arc& b = base.A[a];
+    const End& o = g.E[b.owner];
+    auto ang = [&](V3 z) { return std::atan2(dot(z, o.e2), dot(z, o.e1)); };
+    double p0 = b.phi0 + wrap_pi(ang(out.V[b.v0].z) - b.phi0);
+    double dp = PI2;
+    if (b.v0 != b.v1) {
+      double e1 = b.phi0 + b.dphi;
+      dp = e1 + wrap_pi(ang(out.V[b.v1].z) - e1) - p0;
+    }
+    out.A[a].phi0 = p0;
+    out.A[a].dphi = dp;
+  }
+}
+
+// items (strut bands, then node holes) whose triangles depend on node v
+void items_of(const Mesh& M, int64_t v, std::vector<int64_t>& struts, std::vector<int64_t>& nodes) {
+  nodes.clear();
+  struts.clear();
+  nodes.push_back(v);
+  for (int64_t q = M.row_ptr[v]; q < M.row_ptr[v + 1]; q++) {
+    int32_t e = M.adj[q] >> 1;
+    int32_t a = M.lat.ends[2 * e], b = M.lat.ends[2 * e + 1];
+    nodes.push_back(a == v ? b : a);
+  }
+  for (int64_t w : nodes)
+    for (int64_t q = M.row_ptr[w]; q < M.row_ptr[w + 1]; q++) struts.push_back(M.adj[q] >> 1);
+  std::sort(struts.begin(), struts.end());
+  struts.erase(std::unique(struts.begin(), struts.end()), struts.end());
+  std::sort(nodes.begin(), nodes.end());
+  nodes.erase(std::unique(nodes.begin(), nodes.end()), nodes.end());
+}
+
+void sum_items(const Mesh& M2, Frozen* fz, const std::vector<int64_t>& struts,
+               const std::vector<int64_t>& nodes, double* acc) {
+  std::vector<Tri> T;
+  for (int64_t e : struts) {
+    T.clear();
+    strut_tris(M2, e, fz->k, T, fz, true);
+    for (auto& t : T) { acc[0] += t.area; acc[1] += t.vol; }
+  }
+  for (int64_t n : nodes) {
+    T.clear();
+    hole_tris(M2, n, fz->k, T, fz, true);
+    for (auto& t : T) { acc[0] += t.area; acc[1] += t.vol; }
   }
 }
 
@@ -998,6 +1139,85 @@ void lmo_end_frame(void* h, int64_t n, int li, double* out) {
   End e = make_end(*M, n, M->adj[M->row_ptr[n] + li]);
   double v[11] = {e.u.x, e.u.y, e.u.z, e.e1.x, e.e1.y, e.e1.z, e.e2.x, e.e2.y, e.e2.z, e.s, e.co};
   std::memcpy(out, v, sizeof(v));
+}
+
+// ---- frozen-topology objective (adjoint reference)
+// record the discrete structure of the triangulation at k (meta-mesh of all
+// nodes must be built)
+void* lmo_frozen_record(void* h, int k) {
+  Mesh* M = (Mesh*)h;
+  Frozen* fz = new Frozen();
+  fz->k = k;
+  int64_t N = M->lat.n_nodes, E = M->lat.n_struts;
+  fz->N.resize(N);
+  fz->zip.resize(E);
+  fz->fan.resize(N);
+  for (int64_t n = 0; n < N; n++)
+    for (const Arc& a : M->nodes[n].A) fz->N[n].push_back(seg_count(a.dphi, k));
+  std::vector<Tri> T;
+  for (int64_t e = 0; e < E; e++) { T.clear(); strut_tris(*M, e, k, T, fz, false); }
+  for (int64_t n = 0; n < N; n++) { T.clear(); hole_tris(*M, n, k, T, fz, false); }
+  return fz;
+}
+
+void lmo_frozen_free(void* fz) { delete (Frozen*)fz; }
+
+// area and volume (out[0], out[1]) of the recorded structure evaluated at
+// node positions xyz [N][3] and node radii node_R [N]
+void lmo_frozen_objective(void* h, void* f, const double* xyz, const double* node_R, double* out) {
+  Mesh* M = (Mesh*)h;
+  Frozen* fz = (Frozen*)f;
+  Mesh M2;
+  M2.lat = M->lat;
+  M2.lat.xyz = xyz;
+  M2.node_R.assign(node_R, node_R + M->lat.n_nodes);
+  M2.row_ptr = M->row_ptr;
+  M2.adj = M->adj;
+  M2.nodes = M->nodes;
+  for (int64_t n = 0; n < M->lat.n_nodes; n++) refresh_node(M2, M->nodes[n], M2.nodes[n], n);
+  std::vector<int64_t> struts(M->lat.n_struts), nodes(M->lat.n_nodes);
+  for (int64_t e = 0; e < M->lat.n_struts; e++) struts[e] = e;
+  for (int64_t n = 0; n < M->lat.n_nodes; n++) nodes[n] = n;
+  out[0] = out[1] = 0.0;
+  sum_items(M2, fz, struts, nodes, out);
+}
+
+// central differences with step `step` of the recorded structure's area and
+// volume for the nodes in `list`: g[8 q + 0..3] = d area / d(x, y, z, R) of
+// node list[q], g[8 q + 4..7] the same for the volume.  Only the items that
+// depend on the perturbed node are re-evaluated.
+void lmo_frozen_fd(void* h, void* f, double step, const int64_t* list, int64_t n_list, double* g) {
+  Mesh* M = (Mesh*)h;
+  Frozen* fz = (Frozen*)f;
+  int64_t N = M->lat.n_nodes;
+  std::vector<double> xyz(M->lat.xyz, M->lat.xyz + 3 * N);
+  Mesh M2;
+  M2.lat = M->lat;
+  M2.lat.xyz = xyz.data();
+  M2.node_R = M->node_R;
+  M2.row_ptr = M->row_ptr;
+  M2.adj = M->adj;
+  M2.nodes = M->nodes;
+  std::vector<int64_t> struts, nodes;
+  for (int64_t q = 0; q < n_list; q++) {
+    int64_t v = list[q];
+    items_of(*M, v, struts, nodes);
+    for (int p = 0; p < 4; p++) {
+      double acc[2][2] = {{0, 0}, {0, 0}};
+      for (int sg = 0; sg < 2; sg++) {
+        double d = sg == 0 ? step : -step;
+        if (p < 3) xyz[3 * v + p] = M->lat.xyz[3 * v + p] + d;
+        else M2.node_R[v] = M->node_R[v] + d;
+        for (int64_t w : nodes) refresh_node(M2, M->nodes[w], M2.nodes[w], w);
+        sum_items(M2, fz, struts, nodes, acc[sg]);
+      }
+      if (p < 3) xyz[3 * v + p] = M->lat.xyz[3 * v + p];
+      else M2.node_R[v] = M->node_R[v];
+      g[8 * q + p] = (acc[0][0] - acc[1][0]) / (2.0 * step);
+      g[8 * q + 4 + p] = (acc[0][1] - acc[1][1]) / (2.0 * step);
+    }
+    for (int64_t w : nodes) M2.nodes[w] = M->nodes[w];
+  }
 }
 
 }  // extern "C"

@@ -735,9 +735,20 @@ lm_status lm_copy_to_host(void* h_dst, const void* d_src, int64_t bytes) {
 
 lm_status lm_metamesh_backward(lm_metamesh* mm, int32_t k, double w_area, double w_vol, void* d_grad_xyz,
                                void* d_grad_r, void* stream, double* h_area, double* h_volume) {
-  (void)mm; (void)k; (void)w_area; (void)w_vol; (void)d_grad_xyz; (void)d_grad_r; (void)stream;
-  (void)h_area; (void)h_volume;
-  return LM_ERR_STATE;
+  if (!mm || !valid_k(k)) return LM_ERR_INVALID_ARG;
+  lm_status s = LM_OK;
+  if (mm->tri_k != k) {
+    s = lm_tri_count(mm, k, stream, nullptr);
+    if (s != LM_OK) return s;
+  }
+  s = lm_objective(mm, k, stream, h_area, h_volume);
+  if (s != LM_OK) return s;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = mm->dtype == LM_F32
+                      ? lm::metamesh_backward<float>(mm, k, w_area, w_vol, d_grad_xyz, d_grad_r, st)
+                      : lm::metamesh_backward<double>(mm, k, w_area, w_vol, d_grad_xyz, d_grad_r, st);
+  if (e != cudaSuccess) return st_cuda(e);
+  return lm_last_error(mm, stream);
 }
 
 }  // extern "C"

@@ -6,6 +6,8 @@
 
 #include "../../include/liblm.h"
 
+struct lm_metamesh;
+
 namespace lm {
 
 struct Node64;
@@ -88,6 +90,11 @@ template <typename T>
 cudaError_t launch_tri_count(const TriLaunch<T>& a, cudaStream_t st);
 template <typename T>
 cudaError_t launch_tri_emit(const TriLaunch<T>& a, cudaStream_t st);
+// adjoint (lm_bwd.cu): gradients of w_area area + w_vol volume at k added
+// into gxyz [N][3] and gr [N] (lattice dtype); requires the counts at k
+template <typename T>
+cudaError_t metamesh_backward(lm_metamesh* mm, int k, double w_area, double w_vol, void* gxyz, void* gr,
+                              cudaStream_t st);
 size_t node64_bytes();
 int64_t tri_scratch_warps();
 // host-side count of kernels this library launched (all threads)

@@ -40,6 +40,11 @@ struct TriArgs {
   int* max_pts;            // count pass: max points of one loop / one node's holes
   unsigned long long* fb;  // FP64 stability-step counters (8: segments, 9: start angle,
                            // 10: stitching order, 11: fan centre)
+  // adjoint (point adjoints instead of records)
+  float* adj;                 // [n_vtx + interior arc points][3]
+  const int64_t* arc_pt_off;  // [A + 1] first interior point of each arc
+  int64_t n_vtx;
+  float w_area, w_vol;
 };
 
 __device__ __forceinline__ void tfb_add(unsigned long long* fb, int which, bool pred,
@@ -703,6 +708,7 @@ struct TileLayout {
   __host__ __device__ static constexpr size_t r16c(size_t b) { return (b + 15) & ~(size_t)15; }
   int pmax, emax;
   bool exact;  // the FP64 pass also holds FP64 arc data per entry and angles per point
+  bool adjm;   // adjoint mode: point ids of both loops
   __host__ __device__ size_t ent() const { return r16c(sizeof(TileHdr)); }
   __host__ __device__ size_t th() const { return ent() + r16c(2 * (size_t)emax * sizeof(TileEntry<T>)); }
   __host__ __device__ size_t z() const { return th() + r16c(2 * (size_t)pmax * sizeof(T)); }
@@ -711,7 +717,8 @@ struct TileLayout {
   __host__ __device__ size_t stage() const { return fl() + r16c(2 * (size_t)pmax); }
   __host__ __device__ size_t ea64() const { return stage() + r16c(TL * 50); }
   __host__ __device__ size_t th64() const { return ea64() + (exact ? r16c(2 * (size_t)emax * 32) : 0); }
-  __host__ __device__ size_t bytes() const { return th64() + (exact ? r16c(2 * (size_t)pmax * 8) : 0); }
+  __host__ __device__ size_t pid() const { return th64() + (exact ? r16c(2 * (size_t)pmax * 8) : 0); }
+  __host__ __device__ size_t bytes() const { return pid() + (adjm ? r16c(2 * (size_t)pmax * 8) : 0); }
 };
 
 // FP64 data of one loop entry: start angle of its arc in the owner's frame,
@@ -868,6 +875,7 @@ struct TileSmem {
   unsigned char* STG;
   Arc64* EA64;
   double* TH64;
+  int64_t* PID;
   __device__ TileSmem(unsigned char* base, const TileLayout<T, TL>& Lay)
       : H(reinterpret_cast<TileHdr*>(base)),
         ENT(reinterpret_cast<TileEntry<T>*>(base + Lay.ent())),
@@ -877,12 +885,34 @@ struct TileSmem {
         FL(reinterpret_cast<uint8_t*>(base + Lay.fl())),
         STG(base + Lay.stage()),
         EA64(reinterpret_cast<Arc64*>(base + Lay.ea64())),
-        TH64(reinterpret_cast<double*>(base + Lay.th64())) {}
+        TH64(reinterpret_cast<double*>(base + Lay.th64())),
+        PID(reinterpret_cast<int64_t*>(base + Lay.pid())) {}
 };
+
+// Point adjoints of one triangle (a, b, c relative to any common origin; n =
+// (b - a) x (c - a), nh = n / |n|): each corner p gets
+// w_area dA/dp + w_vol n / 6 with dA/da = (b - c) x nh / 2 (cyclically).
+template <typename T>
+__device__ __forceinline__ void tri_point_adjoints(const TriArgs<T>& A, V3<T> a, V3<T> b, V3<T> c, V3<T> nh,
+                                                   V3<T> n, int64_t pa, int64_t pb, int64_t pc) {
+  const float wa = 0.5f * A.w_area, wv = A.w_vol / 6.0f;
+  V3<float> nf = mk3((float)n.x, (float)n.y, (float)n.z), hf = mk3((float)nh.x, (float)nh.y, (float)nh.z);
+  V3<float> af = mk3((float)a.x, (float)a.y, (float)a.z), bf = mk3((float)b.x, (float)b.y, (float)b.z),
+            cf = mk3((float)c.x, (float)c.y, (float)c.z);
+  V3<float> g[3] = {cross(bf - cf, hf) * wa + nf * wv, cross(cf - af, hf) * wa + nf * wv,
+                    cross(af - bf, hf) * wa + nf * wv};
+  int64_t id[3] = {pa, pb, pc};
+#pragma unroll
+  for (int q = 0; q < 3; q++) {
+    atomicAdd(A.adj + 3 * id[q], g[q].x);
+    atomicAdd(A.adj + 3 * id[q] + 1, g[q].y);
+    atomicAdd(A.adj + 3 * id[q] + 2, g[q].z);
+  }
+}
 
 // Stitch strut e with one tile.  Returns true (uniformly over the tile) when
 // the strut needs FP64 decisions and EXACT is off: nothing was written then.
-template <typename T, int TL, bool OBJ, bool EXACT>
+template <typename T, int TL, bool OBJ, bool EXACT, bool ADJ = false>
 __device__ __forceinline__ bool tile_strut(const TriArgs<T>& A, const TileSmem<T, TL>& S, int64_t e,
                                            int64_t out_first, int tl, unsigned m, bool vec_ok, double& sa,
                                            double& sv) {
@@ -967,6 +997,11 @@ __device__ __forceinline__ bool tile_strut(const TriArgs<T>& A, const TileSmem<T
       Z[X * A.pmax + p] = zz;
       TH[X * A.pmax + p] = th;
       if (FP64_STEPS) FL[X * A.pmax + p] = 0;
+      if constexpr (ADJ) {
+        uint32_t av = A.arc_vtx[en.ga];
+        S.PID[X * A.pmax + p] = sidx == 0 ? A.vtx_off[node] + (mm == 0 ? (av & 255) : ((av >> 8) & 255))
+                                          : A.n_vtx + A.arc_pt_off[en.ga] + mm - 1;
+      }
     }
   }
   __syncwarp(m);
@@ -1136,20 +1171,27 @@ __device__ __forceinline__ bool tile_strut(const TriArgs<T>& A, const TileSmem<T
       V3<T> cr = cross(rb - ra, rc - ra);
       T len = norm3(cr);
       V3<T> nn = len > T(0) ? cr * (T(1) / len) : mk3(T(0), T(0), T(0));
-      if (OBJ) {
-        sa += 0.5 * (double)len;
-        sv += ((double)dot(ra, cross(rb, rc)) +
-               dot(mk3((double)cA.x, (double)cA.y, (double)cA.z), mk3((double)cr.x, (double)cr.y, (double)cr.z))) *
-              (1.0 / 6.0);
-      }
-      if (A.out) {
-        float f[12] = {(float)nn.x, (float)nn.y, (float)nn.z, (float)pa.x, (float)pa.y, (float)pa.z,
-                       (float)pb.x, (float)pb.y, (float)pb.z, (float)pc.x, (float)pc.y, (float)pc.z};
-        rec_store(S.STG + 50 * tl, f);
+      if constexpr (ADJ) {
+        int64_t ia_ = S.PID[i < nA ? i : 0];
+        int64_t ib_ = isA ? S.PID[(i + 1) % nA] : S.PID[A.pmax + (sB + jn) % nB];
+        int64_t ic_ = S.PID[A.pmax + jp];
+        tri_point_adjoints<T>(A, ra, rb, rc, nn, cr, ia_, ib_, ic_);
+      } else {
+        if (OBJ) {
+          sa += 0.5 * (double)len;
+          sv += ((double)dot(ra, cross(rb, rc)) +
+                 dot(mk3((double)cA.x, (double)cA.y, (double)cA.z), mk3((double)cr.x, (double)cr.y, (double)cr.z))) *
+                (1.0 / 6.0);
+        }
+        if (A.out) {
+          float f[12] = {(float)nn.x, (float)nn.y, (float)nn.z, (float)pa.x, (float)pa.y, (float)pa.z,
+                         (float)pb.x, (float)pb.y, (float)pb.z, (float)pc.x, (float)pc.y, (float)pc.z};
+          rec_store(S.STG + 50 * tl, f);
+        }
       }
     }
     __syncwarp(m);
-    if (A.out) {
+    if (!ADJ && A.out) {
       int nrec = ntri - c0 < TL ? ntri - c0 : TL;
       int64_t gt = t0 + c0;
       if (gt + nrec <= A.capacity) {
@@ -1172,7 +1214,7 @@ __device__ __forceinline__ bool tile_strut(const TriArgs<T>& A, const TileSmem<T
 // stitched in the kernel's precision, and a strut that needs an FP64 stability
 // step is marked in `redo` (bit e - redo_base) instead.  EXACT on: only the
 // marked struts are stitched, with the FP64 steps.
-template <typename T, int TL, bool OBJ, bool EXACT>
+template <typename T, int TL, bool OBJ, bool EXACT, bool ADJ = false>
 __global__ void __launch_bounds__(256, EXACT ? 1 : 2)
     k_tri_tiles(TriArgs<T> A, const int64_t* first_ptr, uint32_t* redo, int64_t redo_base) {
   const int64_t out_first = first_ptr ? *first_ptr : 0;
@@ -1183,7 +1225,7 @@ __global__ void __launch_bounds__(256, EXACT ? 1 : 2)
   const int tile_in_block = threadIdx.x / TL;
   const int64_t gtile = (int64_t)blockIdx.x * (blockDim.x / TL) + tile_in_block;
   const int64_t ntiles = (int64_t)gridDim.x * (blockDim.x / TL);
-  TileLayout<T, TL> Lay{A.pmax, A.emax, EXACT};
+  TileLayout<T, TL> Lay{A.pmax, A.emax, EXACT, ADJ};
   TileSmem<T, TL> S(smem_raw + (size_t)tile_in_block * Lay.bytes(), Lay);
   const int64_t E = A.lat.n_struts;
   const int64_t e_end = A.item_end < E ? A.item_end : E;
@@ -1191,7 +1233,7 @@ __global__ void __launch_bounds__(256, EXACT ? 1 : 2)
   double sa = 0.0, sv = 0.0;
   if (!EXACT) {
     for (int64_t e = A.item_begin + gtile; e < e_end; e += ntiles) {
-      bool d = tile_strut<T, TL, OBJ, false>(A, S, e, out_first, tl, m, vec_ok, sa, sv);
+      bool d = tile_strut<T, TL, OBJ, false, ADJ>(A, S, e, out_first, tl, m, vec_ok, sa, sv);
       if (d && tl == 0) atomicOr(redo + ((e - redo_base) >> 5), 1u << ((e - redo_base) & 31));
     }
   } else {
@@ -1203,7 +1245,7 @@ __global__ void __launch_bounds__(256, EXACT ? 1 : 2)
         bits &= bits - 1;
         int64_t e = redo_base + 32 * w + bit;
         if (e < A.item_begin || e >= e_end) continue;
-        tile_strut<T, TL, OBJ, true>(A, S, e, out_first, tl, m, vec_ok, sa, sv);
+        tile_strut<T, TL, OBJ, true, ADJ>(A, S, e, out_first, tl, m, vec_ok, sa, sv);
       }
     }
   }

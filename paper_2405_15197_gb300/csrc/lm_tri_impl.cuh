@@ -78,7 +78,7 @@ cudaError_t launch_tri_emit(const TriLaunch<T>& a, cudaStream_t st) {
   if (a.item_begin < a.n_struts) {
     constexpr int TL = 16;
     const int64_t n = (a.item_end < a.n_struts ? a.item_end : a.n_struts) - a.item_begin;
-    TileLayout<T, TL> Lay{a.pmax, a.emax, false}, LayX{a.pmax, a.emax, true};
+    TileLayout<T, TL> Lay{a.pmax, a.emax, false, false}, LayX{a.pmax, a.emax, true, false};
     const size_t smem_cap = 200 * 1024;
     auto tiles_for = [&](size_t bytes) {
       int t = 16;

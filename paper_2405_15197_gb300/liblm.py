@@ -268,6 +268,16 @@ class MetaMesh:
     def objective(self, k, stream=None):
         return lm_objective(self.h, k, stream)
 
+    def backward(self, k, w_area=1.0, w_vol=0.0, stream=None):
+        """Adjoint at k: (d/d node xyz [N,3], d/d node radius [N], area,
+        volume) of w_area*area + w_vol*volume, as CUDA tensors of the
+        lattice dtype."""
+        import torch
+        gx = torch.zeros((self.n_nodes, 3), dtype=self.dtype, device="cuda")
+        gr = torch.zeros((self.n_nodes,), dtype=self.dtype, device="cuda")
+        a, v = lm_metamesh_backward(self.h, k, w_area, w_vol, gx.data_ptr(), gr.data_ptr(), stream)
+        return gx, gr, a, v
+
     def download(self):
         """Host copies of every meta-mesh array (numpy)."""
         v = lm_metamesh_export(self.h)

@@ -1,0 +1,67 @@
+"""Adjoint (lm_metamesh_backward) against central finite differences of the
+FP64 oracle with the discrete structure frozen, on a jittered BCC 4^3
+lattice (189 nodes, 512 struts, 756 parameters) at k = 32."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import oracle  # noqa: E402
+from paper_2405_15197_gb300 import lattices as L  # noqa: E402
+from paper_2405_15197_gb300 import liblm  # noqa: E402
+from paper_2405_15197_gb300.adjoint import lattice_objective  # noqa: E402
+from tests import parity as P  # noqa: E402
+
+K = 32
+_cache = {}
+
+
+def setup(dtype):
+    if dtype not in _cache:
+        lat = P.lattice_as(L.bcc(4, jitter=0.05, radius_range=(0.05, 0.09)), dtype)
+        o = oracle.Oracle(lat)
+        fz = oracle.Frozen(o, K)
+        ga, gv = fz.fd(1e-4, np.arange(o.N))
+        _cache[dtype] = (lat, o, ga, gv)
+    return _cache[dtype]
+
+
+def rel_err(g, ref):
+    return np.abs(g - ref).max() / np.abs(ref).max()
+
+
+@pytest.mark.parametrize("dtype", [np.float32, np.float64])
+def test_adjoint_vs_frozen_fd(dtype):
+    lat, o, ga, gv = setup(dtype)
+    xyz, ends, radii = P.to_device(lat, dtype)
+    mm = liblm.MetaMesh(xyz, ends, radii)
+    _, oa, ov = o.triangulate(K, want_tris=False)
+    for w, ref in (((1.0, 0.0), ga), ((0.0, 1.0), gv)):
+        gx, gr, a, v = mm.backward(K, *w)
+        assert a == pytest.approx(oa, rel=1e-5) and v == pytest.approx(ov, rel=1e-5)
+        g = np.concatenate([gx.cpu().numpy(), gr.cpu().numpy()[:, None]], 1).astype(np.float64)
+        e = rel_err(g, ref)
+        print(f"w={w}: max |adjoint - FD| / max |FD| = {e:.2e}")
+        assert e < 1e-3
+
+
+def test_adjoint_accumulates_and_autograd():
+    lat, o, ga, gv = setup(np.float32)
+    xyz, ends, radii = P.to_device(lat, np.float32)
+    node_R = torch.tensor(o.csr()[2], dtype=torch.float32, device="cuda")
+    x = xyz.clone().requires_grad_(True)
+    r = node_R.clone().requires_grad_(True)
+    J = lattice_objective(x, r, ends, K, 0.5, 2.0)
+    _, oa, ov = o.triangulate(K, want_tris=False)
+    assert J.item() == pytest.approx(0.5 * oa + 2.0 * ov, rel=1e-5)
+    gx, gr = torch.autograd.grad(J * 3.0, (x, r))
+    ref = 3.0 * (0.5 * ga + 2.0 * gv)
+    g = np.concatenate([gx.cpu().numpy(), gr.cpu().numpy()[:, None]], 1).astype(np.float64)
+    assert rel_err(g, ref) < 1e-3
+    # gradients are added into the caller's buffers
+    mm = liblm.MetaMesh(xyz, ends, radii)
+    g1 = torch.ones((o.N, 3), device="cuda")
+    g2 = torch.ones((o.N,), device="cuda")
+    liblm.lm_metamesh_backward(mm.h, K, 1.0, 0.0, g1.data_ptr(), g2.data_ptr())
+    assert np.allclose(g1.cpu().numpy() - 1.0, ga[:, :3], rtol=0, atol=1e-3 * np.abs(ga).max())

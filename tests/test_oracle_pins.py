@@ -378,3 +378,83 @@ def test_lateral_band_is_local(k):
             cosang = np.clip(np.einsum("ij,ij->i", P[:, a_], P[:, b_]), -1, 1)
             worst = max(worst, float(np.arccos(cosang).max()))
     assert worst < 2 * (2 * math.pi / k) + 1e-9
+
+
+# ------------------------------------------- P7: adjoint reference (oracle)
+def _node_R(o):
+    return o.csr()[2]
+
+
+def test_frozen_objective_matches_triangulation():
+    """The recorded structure re-evaluated at the unperturbed parameters gives
+    the triangulation's own area and volume (objective of Section 5's mesh)."""
+    lat = L.bcc(3, jitter=0.05, radius_range=(0.05, 0.09), seed=5)
+    o = oracle.Oracle(lat)
+    for k in (8, 32):
+        _, a, v = o.triangulate(k, want_tris=False)
+        fz = oracle.Frozen(o, k)
+        a2, v2 = fz.objective(o.xyz, _node_R(o))
+        assert a2 == pytest.approx(a, rel=1e-13) and v2 == pytest.approx(v, rel=1e-13)
+
+
+@pytest.mark.parametrize("k", [8, 13])
+def test_frozen_gradient_straight_strut(k):
+    """Isolated cylinder of radius r and length L (both ends valence 1): the
+    lateral band is N rectangles and each cap an N-triangle fan to the point
+    at distance r along -u, so area = 2 N r L sin(pi/N) + 2 N r^2 sin(pi/N)
+    sqrt(1 + cos^2(pi/N)) and volume = (N/2) r^2 sin(2 pi/N) (L + 2r/3).
+    Central differences of the frozen objective give d/dL along the axis,
+    zero across it, and half of d/dr for each node radius."""
+    p0, p1 = np.array([0.1, 0.2, 0.3]), np.array([1.0, 0.7, 0.5])
+    r = 0.1
+    lat = L.single_strut(p0, p1, r, r)
+    o = oracle.Oracle(lat)
+    fz = oracle.Frozen(o, k)
+    N = k
+    Ls = np.linalg.norm(p1 - p0)
+    u = (p1 - p0) / Ls
+    sn, cs = math.sin(math.pi / N), math.cos(math.pi / N)
+    area = 2 * N * r * Ls * sn + 2 * N * r * r * sn * math.sqrt(1 + cs * cs)
+    vol = 0.5 * N * r * r * math.sin(2 * math.pi / N) * (Ls + 2 * r / 3)
+    a0, v0 = fz.objective(o.xyz, _node_R(o))
+    assert a0 == pytest.approx(area, rel=1e-12) and v0 == pytest.approx(vol, rel=1e-12)
+    dA_dL = 2 * N * r * sn
+    dA_dr = 2 * N * Ls * sn + 4 * N * r * sn * math.sqrt(1 + cs * cs)
+    dV_dL = 0.5 * N * r * r * math.sin(2 * math.pi / N)
+    dV_dr = N * r * math.sin(2 * math.pi / N) * (Ls + 2 * r / 3) + N * r * r * math.sin(2 * math.pi / N) / 3
+    ga, gv = fz.fd(1e-5, [0, 1])
+    for q, sgn in ((0, -1.0), (1, 1.0)):
+        assert np.allclose(ga[q, :3], sgn * dA_dL * u, rtol=1e-7, atol=1e-8)
+        assert np.allclose(gv[q, :3], sgn * dV_dL * u, rtol=1e-7, atol=1e-8)
+        assert ga[q, 3] == pytest.approx(dA_dr / 2, rel=1e-7)
+        assert gv[q, 3] == pytest.approx(dV_dr / 2, rel=1e-7)
+
+
+def test_frozen_gradient_smooth_and_local():
+    """With the structure frozen the objective is smooth: central differences
+    at h and h/2 agree to O(h^2) (Richardson), and the locally re-evaluated
+    difference equals the difference of whole-lattice evaluations."""
+    lat = L.bcc(2, jitter=0.05, radius_range=(0.05, 0.09), seed=11)
+    o = oracle.Oracle(lat)
+    fz = oracle.Frozen(o, 16)
+    nodes = np.arange(o.N)
+    ga1, gv1 = fz.fd(1e-4, nodes)
+    ga2, gv2 = fz.fd(5e-5, nodes)
+    sa, sv = np.abs(ga1).max(), np.abs(gv1).max()
+    assert np.abs(ga1 - ga2).max() < 1e-6 * sa and np.abs(gv1 - gv2).max() < 1e-6 * sv
+    # whole-lattice central difference for a few parameters
+    R = _node_R(o)
+    for v, p in ((3, 0), (9, 2), (13, 3)):
+        xp, xm = o.xyz.copy(), o.xyz.copy()
+        Rp, Rm = R.copy(), R.copy()
+        if p < 3:
+            xp[v, p] += 1e-4
+            xm[v, p] -= 1e-4
+        else:
+            Rp[v] += 1e-4
+            Rm[v] -= 1e-4
+        ap, vp = fz.objective(xp, Rp)
+        am, vm = fz.objective(xm, Rm)
+        # whole sums of ~1 differenced at 1e-4: rounding near 1e-11
+        assert (ap - am) / 2e-4 == pytest.approx(ga1[v, p], rel=1e-7, abs=1e-9)
+        assert (vp - vm) / 2e-4 == pytest.approx(gv1[v, p], rel=1e-7, abs=1e-9)
