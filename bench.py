@@ -34,6 +34,8 @@ WORKLOADS = {
                  "desc": "octet-truss 100^3 cells, radii U[0.04,0.08] per node (cones), k=8 and k=32 from one meta-mesh"},
     "octet40": {"kind": "octet", "n": 40, "ks": (8, 32),
                 "desc": "octet-truss 40^3 cells (smaller case), k=8 and k=32"},
+    "octet24": {"kind": "octet", "n": 24, "ks": (8, 32),
+                "desc": "octet-truss 24^3 cells (profiling case), k=8 and k=32"},
     "bcc500": {"kind": "bcc", "n": 500, "ks": (8, 32), "R": 0.05,
                "desc": "BCC 500^3 cells, 1.0e9 struts, R=0.05, k=8 and k=32"},
 }
@@ -206,9 +208,11 @@ def bench_gpu(args):
     tri_bytes = 50.0 * totals[ks.index(k_big)]
     roof_tri = {"bound": "hbm", "achieved": tri_bytes / (tri_ms / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
                 "frac": tri_bytes / (tri_ms / 1e3) / 1e9 / hbm, "traffic": None,
-                "kernel": f"k_tri_struts+k_tri_holes (k={k_big})", "peak_kind": f"{peak_kind} hbm_gbs"}
+                "kernel": f"triangulation emit at k={k_big} (k_tri_tiles FP32 pass + FP64 pass + k_tri_holes)",
+                "algorithmic_bytes": "50 B written per triangle", "peak_kind": f"{peak_kind} hbm_gbs"}
     # end-to-end: pinned host inputs -> device -> meta-mesh -> triangles streamed to a pinned ring
     e2e = bench_e2e(torch, liblm, xyz, ends, radii, ks, stream, dev, args) if not args.no_e2e else None
+    adjoint = bench_adjoint(torch, liblm, dev, stream) if not args.no_adjoint else None
     res = {
         "metric": "meta-mesh struts/s; triangles/s & write GB/s vs HBM peak; adjoint struts/s",
         "value": value, "unit": "struts/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -228,6 +232,7 @@ def bench_gpu(args):
         "gpu_launches": int((l1 - l0) // max(1, args.steps)) * args.steps,
         "clocks": clk.summary(),
         "e2e": e2e,
+        "adjoint": adjoint,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         res["cpu_baseline"] = cpu_baseline(args, quick=True)
@@ -279,6 +284,36 @@ def bench_e2e(torch, liblm, xyz, ends, radii, ks, stream, dev, args):
                                       + hr.numel() * hr.element_size()),
             "d2h_bytes_per_step": int(50 * tot), "steps": steps,
             "path": "pinned host lattice -> lm_build_metamesh -> lm_triangulate_stream (pinned ring)"}
+
+
+def bench_adjoint(torch, liblm, dev, stream):
+    """Adjoint throughput on the differentiation workload: BCC 64^3 cells with
+    Gaussian node jitter 0.05 and node radii U[0.05, 0.09], objective area +
+    volume at k = 32 (lm_metamesh_backward, device-resident lattice)."""
+    from paper_2405_15197_gb300 import lattices as L
+    lat = L.bcc(64, jitter=0.05, radius_range=(0.05, 0.09))
+    xyz = torch.tensor(lat["xyz"], dtype=torch.float32, device=dev)
+    ends = torch.tensor(lat["ends"], dtype=torch.int32, device=dev)
+    radii = torch.tensor(lat["radii"], dtype=torch.float32, device=dev)
+    mm = liblm.MetaMesh(xyz, ends, radii, stream=stream)
+    mm.tri_count(32, stream)
+    gx = torch.zeros((xyz.shape[0], 3), dtype=torch.float32, device=dev)
+    gr = torch.zeros((xyz.shape[0],), dtype=torch.float32, device=dev)
+    liblm.lm_metamesh_backward(mm.h, 32, 1.0, 1.0, gx.data_ptr(), gr.data_ptr(), stream)
+    ts = []
+    for _ in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        liblm.lm_metamesh_backward(mm.h, 32, 1.0, 1.0, gx.data_ptr(), gr.data_ptr(), stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    mm.close()
+    ms = statistics.median(ts)
+    E = int(ends.shape[0])
+    return {"struts_per_s": E / (ms / 1e3), "ms": ms, "n_struts": E, "k": 32,
+            "workload": "BCC 64^3 cells, node jitter N(0, 0.05), radii U[0.05, 0.09], d(area + volume)/d(xyz, R)",
+            "includes": "objective evaluation + point adjoints + per-node forward-mode pass"}
 
 
 def cpu_baseline(args, quick=False):
@@ -339,6 +374,7 @@ def main():
     ap.add_argument("--workload", default="octet100", choices=sorted(WORKLOADS))
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         bench_reference(args)
