@@ -408,6 +408,7 @@ TriLaunch<T> tri_launch(lm_metamesh* mm) {
   L.err = mm->d_err;
   L.emax = std::max(mm->max_loop_entries, 1);
   L.pmax = std::max(mm->tri_pmax, 1);
+  L.dmax = std::max(mm->max_valence, 1);
   L.max_pts = mm->d_misc + 2;
   L.scratch = mm->scratch;
   L.scratch_warps = mm->scratch_warps;

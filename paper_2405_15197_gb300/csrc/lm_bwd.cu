@@ -40,6 +40,7 @@ TriArgs<T> bwd_args(lm_metamesh* mm, int k) {
   A.err = mm->d_err;
   A.pmax = mm->tri_pmax > 0 ? mm->tri_pmax : 1;
   A.emax = mm->max_loop_entries > 0 ? mm->max_loop_entries : 1;
+  A.dmax = mm->max_valence > 0 ? mm->max_valence : 1;
   A.n_vtx = mm->V;
   return A;
 }
@@ -430,13 +431,14 @@ cudaError_t metamesh_backward(lm_metamesh* mm, int k, double w_area, double w_vo
   //    stitching, so every stitching decision is the forward's)
   if (mm->E > 0) {
     constexpr int TL = 16;
-    TileLayout<T, TL> Lay{A.pmax, A.emax, false, true}, LayX{A.pmax, A.emax, true, true};
+    TileLayout<T, TL> Lay{A.pmax, A.emax, false, true, A.dmax}, LayX{A.pmax, A.emax, true, true, A.dmax};
     auto tiles_for = [&](size_t bytes) {
       int t = 16;
       while (t > 2 && (size_t)t * bytes > 200 * 1024) t >>= 1;
       return (size_t)t * bytes <= 200 * 1024 ? t : 0;
     };
-    const int tiles = tiles_for(Lay.bytes()), tilesx = tiles_for(LayX.bytes());
+    const int tiles = tiles_for(Lay.bytes());
+    const int tilesx = tiles_for(LayX.bytes()) < 4 ? tiles_for(LayX.bytes()) : 4;
     if (tiles == 0 || tilesx == 0) { status = cudaErrorInvalidValue; goto done; }
     const int64_t words = mm->E / 32 + 1;
     BK(cudaMallocAsync((void**)&redo, sizeof(uint32_t) * (size_t)words, st));
@@ -456,8 +458,9 @@ cudaError_t metamesh_backward(lm_metamesh* mm, int k, double w_area, double w_vo
       size_t smem = (size_t)tilesx * LayX.bytes();
       auto kx = k_tri_tiles<T, TL, false, true, true>;
       BK(cudaFuncSetAttribute(kx, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      int64_t gx = (words + tilesx - 1) / tilesx;
-      if (gx > (int64_t)sms * 2) gx = (int64_t)sms * 2;
+      int per_sm = 0;
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kx, tilesx * TL, smem);
+      int64_t gx = (int64_t)(per_sm > 0 ? per_sm : 1) * sms;
       count_launch();
       kx<<<(unsigned)gx, tilesx * TL, smem, st>>>(A, nullptr, redo, 0);
       BK(cudaGetLastError());

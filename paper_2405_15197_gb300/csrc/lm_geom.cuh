@@ -633,6 +633,55 @@ __device__ __forceinline__ V3<T> geo_point(const ArcGeo<T>& g, T phi) {
   return g.u * (g.Rs + t * g.co) + r * (g.Rco - t * g.s);
 }
 
+// Node-relative point of vertex generator `gcode` from the node's strut ends
+// (no screening: the vertex is known to be kept).  Circle point: unit n with
+// u_i.n = s_i and u_j.n = s_j, times R.  Triple point: line P_ij n P_ik cut
+// with cone i, root (-B -/+ sqrt(B^2 - A C))/A in the stable form.  Seam:
+// generator at angle 0 of strut end i, cut by plane P_ij when labelled.
+template <typename U>
+__device__ V3<U> gen_point(const EndG<U>* E, U R, uint32_t gcode) {
+  int type = gcode & 3, root = (gcode >> 2) & 1;
+  int i = (gcode >> 3) & 63, j = (gcode >> 9) & 63, k = (gcode >> 15) & 63;
+  if (type == 0) {
+    U c = dot(E[i].u, E[j].u);
+    U q = U(1) - c * c;
+    U al = (E[i].s - c * E[j].s) / q;
+    U be = (E[j].s - c * E[i].s) / q;
+    U g2 = U(1) - (al * al + be * be + U(2) * al * be * c);
+    V3<U> w = cross(E[i].u, E[j].u);
+    w = w * (U(1) / norm3(w));
+    U g = lm_sqrt(g2);
+    V3<U> base = E[i].u * al + E[j].u * be;
+    return (root == 0 ? base - w * g : base + w * g) * R;
+  }
+  if (type == 1) {
+    V3<U> mj = E[i].u * E[i].ico - E[j].u * E[j].ico;
+    V3<U> mk = E[i].u * E[i].ico - E[k].u * E[k].ico;
+    U dj = R * (E[i].s * E[i].ico - E[j].s * E[j].ico);
+    U dk = R * (E[i].s * E[i].ico - E[k].s * E[k].ico);
+    V3<U> v = cross(mj, mk);
+    U ivv = U(1) / dot(v, v);
+    V3<U> z0 = (cross(mk, v) * dj - cross(mj, v) * dk) * ivv;
+    V3<U> vh = v * lm_sqrt(ivv);
+    U G0 = (dot(E[i].u, z0) - R * E[i].s) * E[i].ico;
+    U G1 = dot(E[i].u, vh) * E[i].ico;
+    U A = U(1) - G1 * G1, B = -(G0 * G1), C = dot(z0, z0) - R * R - G0 * G0;
+    U sq = lm_sqrt(B * B - A * C);
+    U lam;
+    if ((float)B >= 0.0f) {
+      U q = -(B + sq);
+      lam = root == 0 ? q / A : C / q;
+    } else {
+      U q = sq - B;
+      lam = root == 1 ? q / A : C / q;
+    }
+    return z0 + vh * lam;
+  }
+  U t = U(0);
+  if ((gcode >> 21) & 1) t = hval(E[i], E[j], U(1), U(0), R);
+  return surf_point(E[i], U(1), U(0), t, R);
+}
+
 // Position of a stored vertex recomputed in FP64 from the inputs, using only
 // the strut ends that generated it (no screening: the vertex is known kept).
 template <typename T>

@@ -78,6 +78,7 @@ struct TriLaunch {
   int* queue;  // 2 counters
   int* err;
   int pmax, emax;
+  int dmax;  // largest node valence
   int* max_pts;
   Node64* scratch;
   int64_t scratch_warps;

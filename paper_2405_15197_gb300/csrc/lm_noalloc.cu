@@ -216,6 +216,7 @@ lm_status run_noalloc(lm_metamesh* mm, int k, int64_t b, int64_t e, void* d_out,
   L.err = mm->d_err;
   L.emax = mm->max_loop_entries > 0 ? mm->max_loop_entries : 1;
   L.pmax = maxp + 1;
+  L.dmax = mm->max_valence > 0 ? mm->max_valence : 1;
   L.max_pts = nullptr;
   L.scratch = ctx;
   L.scratch_warps = NA_CONTEXTS;

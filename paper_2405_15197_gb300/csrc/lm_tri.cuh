@@ -37,6 +37,7 @@ struct TriArgs {
   int* err;
   int pmax;                // points per loop capacity
   int emax;                // loop entries capacity
+  int dmax;                // largest node valence
   int* max_pts;            // count pass: max points of one loop / one node's holes
   unsigned long long* fb;  // FP64 stability-step counters (8: segments, 9: start angle,
                            // 10: stitching order, 11: fan centre)
@@ -697,7 +698,8 @@ struct TileEntry {
 
 struct TileHdr {
   int np[2], ne[2];
-  int pad[4];
+  int li[2];     // local index of the strut's end at its lo / hi node (FP64 pass)
+  int pad[2];
   double a0_64;  // FP64 angle of A's first point (when some key was flagged)
 };
 
@@ -707,8 +709,10 @@ template <typename T, int TL>
 struct TileLayout {
   __host__ __device__ static constexpr size_t r16c(size_t b) { return (b + 15) & ~(size_t)15; }
   int pmax, emax;
-  bool exact;  // the FP64 pass also holds FP64 arc data per entry and angles per point
+  bool exact;  // the FP64 pass also holds FP64 strut ends of both nodes, FP64 arc
+               // data per entry and angles per point
   bool adjm;   // adjoint mode: point ids of both loops
+  int dmax;    // largest node valence (FP64 strut ends)
   __host__ __device__ size_t ent() const { return r16c(sizeof(TileHdr)); }
   __host__ __device__ size_t th() const { return ent() + r16c(2 * (size_t)emax * sizeof(TileEntry<T>)); }
   __host__ __device__ size_t z() const { return th() + r16c(2 * (size_t)pmax * sizeof(T)); }
@@ -717,7 +721,10 @@ struct TileLayout {
   __host__ __device__ size_t stage() const { return fl() + r16c(2 * (size_t)pmax); }
   __host__ __device__ size_t ea64() const { return stage() + r16c(TL * 50); }
   __host__ __device__ size_t th64() const { return ea64() + (exact ? r16c(2 * (size_t)emax * 32) : 0); }
-  __host__ __device__ size_t pid() const { return th64() + (exact ? r16c(2 * (size_t)pmax * 8) : 0); }
+  __host__ __device__ size_t e64() const { return th64() + (exact ? r16c(2 * (size_t)pmax * 8) : 0); }
+  __host__ __device__ size_t pid() const {
+    return e64() + (exact ? r16c(2 * (size_t)dmax * sizeof(EndG<double>)) : 0);
+  }
   __host__ __device__ size_t bytes() const { return pid() + (adjm ? r16c(2 * (size_t)pmax * 8) : 0); }
 };
 
@@ -754,54 +761,63 @@ __device__ __forceinline__ int tile_entry_of(const TileEntry<T>* ents, int ne, i
   return lq;
 }
 
-// FP64 arc data of entry (ga, rev) of the loop of `own_eid` (rare path)
+// FP64 arc data of entry (ga, rev) of the loop of local end `li` (rare
+// path); E: the node's strut ends in FP64 (shared memory)
 template <typename T>
-__device__ __noinline__ Arc64 arc64_data(const TriArgs<T>& A, int64_t node, int32_t own_eid, int64_t ga, int rev) {
-  const LatDev<T>& L = A.lat;
-  int64_t b = L.row_ptr[node];
+__device__ __noinline__ Arc64 arc64_data(const TriArgs<T>& A, const EndG<double>* E, int64_t node, int li,
+                                         int64_t ga, int rev) {
   uint32_t av = A.arc_vtx[ga];
   int v0 = av & 255, v1 = (av >> 8) & 255, o = (av >> 16) & 255;
   int64_t vo = A.vtx_off[node];
-  EndG<double> me = make_end<T, double>(L, node, own_eid);
-  EndG<double> Eo = make_end<T, double>(L, node, L.adj[b + o]);
-  V3<double> z0 = vertex_pos64(L, node, A.vtx_gen[vo + v0]);
-  V3<double> z1 = v1 == v0 ? z0 : vertex_pos64(L, node, A.vtx_gen[vo + v1]);
+  double R = (double)A.lat.node_R[node];
+  V3<double> z0 = gen_point<double>(E, R, A.vtx_gen[vo + v0]);
+  V3<double> z1 = v1 == v0 ? z0 : gen_point<double>(E, R, A.vtx_gen[vo + v1]);
   Arc64 r;
-  r.a0 = norm_angle(raw_angle(Eo, z0));
-  double a1 = norm_angle(raw_angle(Eo, z1));
+  r.a0 = norm_angle(raw_angle(E[o], z0));
+  double a1 = norm_angle(raw_angle(E[o], z1));
   r.dd = a1 - r.a0;
   if (v0 == v1) r.dd = PI2;
   else if (r.dd <= 0.0) r.dd += PI2;
-  r.psi = norm_angle(raw_angle(me, rev ? z1 : z0));
+  r.psi = norm_angle(raw_angle(E[li], rev ? z1 : z0));
   r.pad = 0.0;
   return r;
 }
 
 // FP64 angle of point s of an entry from its FP64 arc data (rare path)
 template <typename T>
-__device__ __noinline__ double point64_theta(const TriArgs<T>& A, int64_t node, int32_t own_eid, int64_t ga,
-                                             const Arc64& d, int N, int rev, int s) {
+__device__ __noinline__ double point64_theta(const TriArgs<T>& A, const EndG<double>* E, int64_t node, int li,
+                                             int64_t ga, const Arc64& d, int N, int rev, int s) {
   if (s == 0) return d.psi;
-  const LatDev<T>& L = A.lat;
-  int64_t b = L.row_ptr[node];
   uint32_t av = A.arc_vtx[ga];
   int o = (av >> 16) & 255, ot = (int)((av >> 24) & 255) - 1;
   int m = rev ? N - s : s;
   double phi = d.a0 + d.dd * (double)m / (double)N;
-  int32_t oid = L.adj[b + o];
-  if (oid == own_eid) return phi;
-  double R = (double)L.node_R[node];
-  EndG<double> Eo = make_end<T, double>(L, node, oid);
-  EndG<double> me = make_end<T, double>(L, node, own_eid);
+  if (o == li) return phi;
+  double R = (double)A.lat.node_R[node];
   double c, sn;
   sincos(phi, &sn, &c);
-  double t = 0.0;
-  if (ot >= 0) {
-    EndG<double> Et = make_end<T, double>(L, node, L.adj[b + ot]);
-    t = hval(Eo, Et, c, sn, R);
+  double t = ot >= 0 ? hval(E[o], E[ot], c, sn, R) : 0.0;
+  V3<double> z = surf_point(E[o], c, sn, t, R);
+  return d.psi + wrap_from(raw_angle(E[li], z) - d.psi, -ETA_PHI);
+}
+
+// exact segment count of arc ga (rare path; E as above)
+template <typename T>
+__device__ __noinline__ int segments64_cached(const TriArgs<T>& A, const EndG<double>* E, int64_t node,
+                                              int64_t ga) {
+  uint32_t av = A.arc_vtx[ga];
+  int v0 = av & 255, v1 = (av >> 8) & 255, o = (av >> 16) & 255;
+  int64_t vo = A.vtx_off[node];
+  double R = (double)A.lat.node_R[node];
+  double dd = PI2;
+  if (v0 != v1) {
+    double a0 = norm_angle(raw_angle(E[o], gen_point<double>(E, R, A.vtx_gen[vo + v0])));
+    double a1 = norm_angle(raw_angle(E[o], gen_point<double>(E, R, A.vtx_gen[vo + v1])));
+    dd = a1 - a0;
+    if (dd <= 0.0) dd += PI2;
   }
-  V3<double> z = surf_point(Eo, c, sn, t, R);
-  return d.psi + wrap_from(raw_angle(me, z) - d.psi, -ETA_PHI);
+  bool u;
+  return seg_count<double>(dd, A.k, u);
 }
 
 // Set up one loop entry (arc geometry, start angle, segment count) in shared
@@ -809,7 +825,8 @@ __device__ __noinline__ double point64_theta(const TriArgs<T>& A, int64_t node, 
 // otherwise such an entry returns -1 and its strut is deferred.
 template <typename T, bool EXACT>
 __device__ __forceinline__ int tile_entry_setup_impl(const TriArgs<T>& A, int64_t node, int32_t eid, int64_t qi,
-                                                     TileEntry<T>* dst) {
+                                                     TileEntry<T>* dst, const EndG<double>* E64 = nullptr,
+                                                     int li = 0) {
   const LatDev<T>& L = A.lat;
   const int64_t ao = A.arc_off[node], rb = L.row_ptr[node], vo = A.vtx_off[node];
   const T R = L.node_R[node];
@@ -827,7 +844,7 @@ __device__ __forceinline__ int tile_entry_setup_impl(const TriArgs<T>& A, int64_
   int Nq = seg_count<T>(en.dphi, A.k, unc);
   if (unc) {
     if (!EXACT) return -1;
-    Nq = segments64_thread<T>(A, node, en.ga);
+    Nq = segments64_cached<T>(A, E64, node, en.ga);
   }
   int32_t oid = L.adj[rb + o];
   EndG<T> Eo = make_end<T, T>(L, node, oid);
@@ -847,8 +864,7 @@ __device__ __forceinline__ int tile_entry_setup_impl(const TriArgs<T>& A, int64_
     T ang = raw_angle(own, zs);
     if (!IS64 && fabs(ang + T(PHI_CUT)) <= T(M_ANG)) {
       if (!EXACT) return -1;
-      EndG<double> me = make_end<T, double>(L, node, eid);
-      ang = (T)norm_angle(raw_angle(me, vertex_pos64(L, node, A.vtx_gen[vi])));
+      ang = (T)norm_angle(raw_angle(E64[li], gen_point<double>(E64, (double)R, A.vtx_gen[vi])));
     }
     en.psi = norm_angle(ang);
   }
@@ -860,8 +876,8 @@ __device__ __forceinline__ int tile_entry_setup_impl(const TriArgs<T>& A, int64_
 
 template <typename T>
 __device__ __noinline__ int tile_entry_setup_exact(const TriArgs<T>& A, int64_t node, int32_t eid, int64_t qi,
-                                                   TileEntry<T>* dst) {
-  return tile_entry_setup_impl<T, true>(A, node, eid, qi, dst);
+                                                   TileEntry<T>* dst, const EndG<double>* E64, int li) {
+  return tile_entry_setup_impl<T, true>(A, node, eid, qi, dst, E64, li);
 }
 
 template <typename T, int TL>
@@ -875,6 +891,7 @@ struct TileSmem {
   unsigned char* STG;
   Arc64* EA64;
   double* TH64;
+  EndG<double>* E64;
   int64_t* PID;
   __device__ TileSmem(unsigned char* base, const TileLayout<T, TL>& Lay)
       : H(reinterpret_cast<TileHdr*>(base)),
@@ -886,6 +903,7 @@ struct TileSmem {
         STG(base + Lay.stage()),
         EA64(reinterpret_cast<Arc64*>(base + Lay.ea64())),
         TH64(reinterpret_cast<double*>(base + Lay.th64())),
+        E64(reinterpret_cast<EndG<double>*>(base + Lay.e64())),
         PID(reinterpret_cast<int64_t*>(base + Lay.pid())) {}
 };
 
@@ -930,6 +948,24 @@ __device__ __forceinline__ bool tile_strut(const TriArgs<T>& A, const TileSmem<T
   int side_lo = (a == lo) ? 0 : 1;
   const int32_t eA = (int32_t)(2 * e + side_lo), eB = (int32_t)(2 * e + 1 - side_lo);
   bool ok = true, defer = false;
+  if constexpr (FP64_STEPS) {
+    // FP64 strut ends of both nodes, once per strut (every FP64 step below
+    // reads them), and the local index of the strut's end at each node
+    const int64_t rb0 = L.row_ptr[lo], rb1 = L.row_ptr[hi];
+    const int d0 = (int)(L.row_ptr[lo + 1] - rb0), d1 = (int)(L.row_ptr[hi + 1] - rb1);
+    if (d0 > A.dmax || d1 > A.dmax) {
+      if (tl == 0) atomicCAS(A.err, 0, 4);
+      return false;
+    }
+    for (int q = tl; q < d0 + d1; q += TL) {
+      int X = q < d0 ? 0 : 1, li = X == 0 ? q : q - d0;
+      int64_t node = X == 0 ? lo : hi;
+      int32_t eid = L.adj[(X == 0 ? rb0 : rb1) + li];
+      S.E64[X * A.dmax + li] = make_end<T, double>(L, node, eid);
+      if (eid == (X == 0 ? eA : eB)) H->li[X] = li;
+    }
+    __syncwarp(m);
+  }
   // ---- entries of both loops
   for (int X = 0; X < 2 && ok && !defer; X++) {
     int64_t node = X == 0 ? lo : hi;
@@ -945,7 +981,8 @@ __device__ __forceinline__ bool tile_strut(const TriArgs<T>& A, const TileSmem<T
       int q = c0 + tl;
       int Nq = 0;
       if (q < ne) {
-        if (FP64_STEPS) Nq = tile_entry_setup_exact<T>(A, node, eid, q0 + q, ENT + X * A.emax + q);
+        if (FP64_STEPS)
+          Nq = tile_entry_setup_exact<T>(A, node, eid, q0 + q, ENT + X * A.emax + q, S.E64 + X * A.dmax, H->li[X]);
         else Nq = tile_entry_setup_impl<T, false>(A, node, eid, q0 + q, ENT + X * A.emax + q);
       }
       if (__any_sync(m, Nq < 0)) {
@@ -1093,7 +1130,8 @@ __device__ __forceinline__ bool tile_strut(const TriArgs<T>& A, const TileSmem<T
       for (int q = tl; q < ne; q += TL) {
         bool need = false;
         for (int p = ents[q].pre; p < ents[q].pre + ents[q].N && !need; p++) need = FL[X * A.pmax + p] != 0;
-        if (need) S.EA64[X * A.emax + q] = arc64_data<T>(A, node, eid, ents[q].ga, ents[q].rev);
+        if (need)
+          S.EA64[X * A.emax + q] = arc64_data<T>(A, S.E64 + X * A.dmax, node, H->li[X], ents[q].ga, ents[q].rev);
       }
     }
     __syncwarp(m);
@@ -1105,7 +1143,8 @@ __device__ __forceinline__ bool tile_strut(const TriArgs<T>& A, const TileSmem<T
       for (int p = tl; p < np; p += TL) {
         if (!FL[X * A.pmax + p]) continue;
         int q = tile_entry_of(ents, ne, p);
-        S.TH64[X * A.pmax + p] = point64_theta<T>(A, node, eid, ents[q].ga, S.EA64[X * A.emax + q], ents[q].N,
+        S.TH64[X * A.pmax + p] = point64_theta<T>(A, S.E64 + X * A.dmax, node, H->li[X], ents[q].ga,
+                                                  S.EA64[X * A.emax + q], ents[q].N,
                                                   ents[q].rev, p - ents[q].pre);
       }
     }
@@ -1215,7 +1254,7 @@ __device__ __forceinline__ bool tile_strut(const TriArgs<T>& A, const TileSmem<T
 // step is marked in `redo` (bit e - redo_base) instead.  EXACT on: only the
 // marked struts are stitched, with the FP64 steps.
 template <typename T, int TL, bool OBJ, bool EXACT, bool ADJ = false>
-__global__ void __launch_bounds__(256, EXACT ? 1 : 2)
+__global__ void __launch_bounds__(EXACT ? 64 : 256, EXACT ? 4 : 2)
     k_tri_tiles(TriArgs<T> A, const int64_t* first_ptr, uint32_t* redo, int64_t redo_base) {
   const int64_t out_first = first_ptr ? *first_ptr : 0;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1225,7 +1264,7 @@ __global__ void __launch_bounds__(256, EXACT ? 1 : 2)
   const int tile_in_block = threadIdx.x / TL;
   const int64_t gtile = (int64_t)blockIdx.x * (blockDim.x / TL) + tile_in_block;
   const int64_t ntiles = (int64_t)gridDim.x * (blockDim.x / TL);
-  TileLayout<T, TL> Lay{A.pmax, A.emax, EXACT, ADJ};
+  TileLayout<T, TL> Lay{A.pmax, A.emax, EXACT, ADJ, A.dmax};
   TileSmem<T, TL> S(smem_raw + (size_t)tile_in_block * Lay.bytes(), Lay);
   const int64_t E = A.lat.n_struts;
   const int64_t e_end = A.item_end < E ? A.item_end : E;
@@ -1237,16 +1276,10 @@ __global__ void __launch_bounds__(256, EXACT ? 1 : 2)
       if (d && tl == 0) atomicOr(redo + ((e - redo_base) >> 5), 1u << ((e - redo_base) & 31));
     }
   } else {
-    const int64_t w0 = (A.item_begin - redo_base) >> 5, w1 = (e_end - redo_base + 31) >> 5;
-    for (int64_t w = w0 + gtile; w < w1; w += ntiles) {
-      uint32_t bits = redo[w];
-      while (bits) {
-        int bit = __ffs(bits) - 1;
-        bits &= bits - 1;
-        int64_t e = redo_base + 32 * w + bit;
-        if (e < A.item_begin || e >= e_end) continue;
-        tile_strut<T, TL, OBJ, true, ADJ>(A, S, e, out_first, tl, m, vec_ok, sa, sv);
-      }
+    // marked struts dealt round-robin over the tiles (marks cluster in space)
+    for (int64_t e = A.item_begin + gtile; e < e_end; e += ntiles) {
+      if (!((redo[(e - redo_base) >> 5] >> ((e - redo_base) & 31)) & 1u)) continue;
+      tile_strut<T, TL, OBJ, true, ADJ>(A, S, e, out_first, tl, m, vec_ok, sa, sv);
     }
   }
   if (OBJ && A.acc) {

@@ -39,6 +39,7 @@ TriArgs<T> tri_args(const TriLaunch<T>& a) {
   A.err = a.err;
   A.pmax = a.pmax;
   A.emax = a.emax;
+  A.dmax = a.dmax > 0 ? a.dmax : 1;
   A.max_pts = a.max_pts;
   A.fb = a.fb;
   return A;
@@ -78,14 +79,15 @@ cudaError_t launch_tri_emit(const TriLaunch<T>& a, cudaStream_t st) {
   if (a.item_begin < a.n_struts) {
     constexpr int TL = 16;
     const int64_t n = (a.item_end < a.n_struts ? a.item_end : a.n_struts) - a.item_begin;
-    TileLayout<T, TL> Lay{a.pmax, a.emax, false, false}, LayX{a.pmax, a.emax, true, false};
+    TileLayout<T, TL> Lay{a.pmax, a.emax, false, false, a.dmax}, LayX{a.pmax, a.emax, true, false, a.dmax};
     const size_t smem_cap = 200 * 1024;
     auto tiles_for = [&](size_t bytes) {
       int t = 16;
       while (t > 2 && (size_t)t * bytes > smem_cap) t >>= 1;
       return (size_t)t * bytes <= smem_cap ? t : 0;
     };
-    const int tiles = tiles_for(Lay.bytes()), tilesx = tiles_for(LayX.bytes());
+    const int tiles = tiles_for(Lay.bytes());
+    const int tilesx = tiles_for(LayX.bytes()) < 4 ? tiles_for(LayX.bytes()) : 4;
     if (tiles > 0 && tilesx > 0) {
       constexpr bool F32 = sizeof(T) == 4;
       const int64_t e_end = a.item_end < a.n_struts ? a.item_end : a.n_struts;
@@ -123,8 +125,7 @@ cudaError_t launch_tri_emit(const TriLaunch<T>& a, cudaStream_t st) {
         int per_sm = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kx, tpb, smem);
         if (per_sm < 1) per_sm = 1;
-        int64_t gx = (w1 - w0 + tilesx - 1) / tilesx;
-        if (gx > (int64_t)per_sm * sms) gx = (int64_t)per_sm * sms;
+        int64_t gx = (int64_t)per_sm * sms;
         if (gx < 1) gx = 1;
         count_launch();
         kx<<<(unsigned)gx, tpb, smem, st>>>(A, a.first_ptr, a.redo, a.redo_base);
