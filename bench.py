@@ -116,12 +116,19 @@ def make_lattice_device(wl, device, torch):
             torch.tensor(lat["radii"], dtype=torch.float32, device=device))
 
 
+def tuned_options(liblm):
+    """Build options with the launch-shape autotuner on (cached per process)."""
+    opt = liblm.lm_options()
+    opt.autotune = 1
+    return opt
+
+
 def run_step(torch, liblm, xyz, ends, radii, ks, out, stream, want_times=False):
     """One full step on device-resident inputs.  Returns (struts, tris per k,
     per-phase times in ms) ."""
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 + 2 * len(ks))]
     ev[0].record(stream)
-    mm = liblm.MetaMesh(xyz, ends, radii, stream=stream)
+    mm = liblm.MetaMesh(xyz, ends, radii, options=tuned_options(liblm), stream=stream)
     ev[1].record(stream)
     tris = []
     for q, k in enumerate(ks):
@@ -164,10 +171,12 @@ def bench_gpu(args):
     xyz, ends, radii = make_lattice_device(wl, dev, torch)
     torch.cuda.synchronize()
     stream = torch.cuda.current_stream()
-    # output buffer sized for the larger k
-    mm = liblm.MetaMesh(xyz, ends, radii, stream=stream)
+    # output buffer sized for the larger k (this first build also runs the
+    # launch-shape autotuner; later builds reuse its choice)
+    mm = liblm.MetaMesh(xyz, ends, radii, options=tuned_options(liblm), stream=stream)
     totals = [mm.tri_count(k, stream) for k in ks]
     counts = mm.counts()
+    launch_shape = liblm.lm_metamesh_launch_shape(mm.h)
     fb = liblm.lm_fp64_counts(mm.h)
     fp64 = dict(zip(["pair", "candidate", "position_refine", "dedup", "seam", "loop_angle", "label",
                      "arc_extent", "tri_segments", "tri_start_angle", "tri_stitch_order", "tri_fan_centre"],
@@ -228,6 +237,8 @@ def bench_gpu(args):
         "meta_mesh_counts": {"vertices": counts[0], "elliptical_arcs": counts[1], "circular_arcs": counts[2],
                              "holes": counts[3], "degenerate_nodes": counts[5], "max_valence": counts[6]},
         "fp64_stability_steps": fp64,
+        "metamesh_launch_shape": {"buckets": ["d<=16", "d<=32", "d<=64"],
+                                  "warps_per_block_nodes_per_pop": launch_shape, "autotuned": True},
         "roofline": roof_tri,
         "gpu_launches": int((l1 - l0) // max(1, args.steps)) * args.steps,
         "clocks": clk.summary(),
@@ -259,7 +270,7 @@ def bench_e2e(torch, liblm, xyz, ends, radii, ks, stream, dev, args):
         dx = hx.to(dev, non_blocking=True)
         de = he.to(dev, non_blocking=True)
         dr = hr.to(dev, non_blocking=True)
-        mm = liblm.MetaMesh(dx, de, dr, stream=stream)
+        mm = liblm.MetaMesh(dx, de, dr, options=tuned_options(liblm), stream=stream)
         tot = 0
         for k in ks:
             mm.tri_count(k, stream)

@@ -209,6 +209,13 @@ lm_status lm_metamesh_backward(lm_metamesh* mm, int32_t k, double w_area, double
                                void* d_grad_xyz, void* d_grad_r, void* stream, double* h_area,
                                double* h_volume);
 
+/* Launch shape the build used for the persistent meta-mesh kernel, per
+ * valence bucket (d <= 16, d <= 32, d <= 64): out[2b] = warps per block,
+ * out[2b+1] = nodes a warp takes per work-queue access.  With
+ * lm_options.autotune these are the autotuner's choices (Section 4.3.3's
+ * workload balancing, done by measurement); 0 for buckets without nodes. */
+lm_status lm_metamesh_launch_shape(const lm_metamesh* mm, int32_t out[6]);
+
 /* First asynchronous error recorded on the handle by a device-side check
  * (capacity, timeout); synchronises `stream`, then clears it.            */
 lm_status lm_last_error(lm_metamesh* mm, void* stream);

@@ -7,6 +7,9 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <vector>
 
 #include "lm_internal.h"
@@ -188,6 +191,61 @@ lm_status read_err(lm_metamesh* mm, cudaStream_t st) {
   return (lm_status)e;
 }
 
+// ---- autotuner of the persistent meta-mesh launch (block shape and nodes
+// popped per queue access), per device, lattice dtype and valence bucket:
+// each candidate runs the count pass on a sample of the bucket's nodes and
+// the fastest is cached for the process.
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int>, std::pair<int, int>> g_tune;
+
+template <typename T>
+lm_status tune_bucket(lm_metamesh* mm, MMLaunch<T> L, int b, int n_list, cudaStream_t st, int* bw, int* npt) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  auto key = std::make_tuple(dev, (int)mm->dtype, b);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune.find(key);
+    if (it != g_tune.end()) {
+      *bw = it->second.first;
+      *npt = it->second.second;
+      return LM_OK;
+    }
+  }
+  const int cand_bw[3] = {1, 2, 4}, cand_npt[4] = {1, 2, 4, 8};
+  L.n_list = std::min(n_list, 8192);
+  L.queue = mm->d_queue + 3;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float best = 1e30f;
+  int bbw = 4, bnpt = 1;
+  for (int rep = 0; rep < 2; rep++)  // first round warms up
+    for (int i = 0; i < 3; i++)
+      for (int j = 0; j < 4; j++) {
+        L.nodes_per_task = cand_npt[j];
+        LM_CK(cudaMemsetAsync(L.queue, 0, sizeof(int), st));
+        cudaEventRecord(e0, st);
+        LM_CK(launch_metamesh<T>(b, false, L, cand_bw[i], 0, st, nullptr));
+        cudaEventRecord(e1, st);
+        LM_CK(cudaEventSynchronize(e1));
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (rep == 1 && ms < best) {
+          best = ms;
+          bbw = cand_bw[i];
+          bnpt = cand_npt[j];
+        }
+      }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  *bw = bbw;
+  *npt = bnpt;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune[key] = std::make_pair(bbw, bnpt);
+  return LM_OK;
+}
+
 template <typename T>
 lm_status build_impl(lm_metamesh* mm, cudaStream_t st) {
   const int64_t N = mm->N, E = mm->E;
@@ -338,14 +396,35 @@ lm_status build_impl(lm_metamesh* mm, cudaStream_t st) {
       L.hole_off = mm->hole_off;
       L.hole_ent = mm->hole_ent;
     }
+    if (pass == 0 && mm->opt.autotune) {
+      for (int b = 0; b < NB_BUCKETS; b++) {
+        if (hb[b] == 0) continue;
+        L.nodes = lists + b * cap;
+        int bw = 0, npt = 0;
+        lm_status ts = tune_bucket<T>(mm, L, b, hb[b], st, &bw, &npt);
+        if (ts != LM_OK) return ts;
+        mm->tuned[b][0] = bw;
+        mm->tuned[b][1] = npt;
+      }
+      // the sample runs counted their FP64 steps too
+      LM_CK(cudaMemsetAsync(mm->d_fb, 0, 16 * sizeof(unsigned long long), st));
+    }
     for (int b = NB_BUCKETS - 1; b >= 0; b--) {
       if (hb[b] == 0) continue;
       L.nodes = lists + b * cap;
       L.n_list = hb[b];
       L.queue = mm->d_queue + b;
+      int bw = mm->opt.block_warps, npt = mm->opt.nodes_per_task;
+      if (mm->opt.autotune) {
+        if (bw <= 0) bw = mm->tuned[b][0];
+        if (npt <= 0) npt = mm->tuned[b][1];
+      }
+      L.nodes_per_task = npt > 0 ? npt : 1;
+      mm->tuned[b][0] = bw > 0 ? bw : 4;
+      mm->tuned[b][1] = L.nodes_per_task;
       LM_CK(cudaMemsetAsync(mm->d_queue + b, 0, sizeof(int), st));
       int used = 0;
-      LM_CK(launch_metamesh<T>(b, pass == 1, L, mm->opt.block_warps, mm->opt.grid_ctas, st, &used));
+      LM_CK(launch_metamesh<T>(b, pass == 1, L, bw, mm->opt.grid_ctas, st, &used));
     }
   }
   cudaEventRecord(ev[3], st);
@@ -614,6 +693,15 @@ lm_status lm_objective(lm_metamesh* mm, int32_t k, void* stream, double* h_area,
   LM_CK(cudaStreamSynchronize(st));
   if (h_area) *h_area = h[0];
   if (h_volume) *h_volume = h[1];
+  return LM_OK;
+}
+
+lm_status lm_metamesh_launch_shape(const lm_metamesh* mm, int32_t out[6]) {
+  if (!mm || !out) return LM_ERR_INVALID_ARG;
+  for (int b = 0; b < 3; b++) {
+    out[2 * b] = mm->tuned[b][0];
+    out[2 * b + 1] = mm->tuned[b][1];
+  }
   return LM_OK;
 }
 

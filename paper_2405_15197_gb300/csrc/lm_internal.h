@@ -151,4 +151,7 @@ struct lm_metamesh {
   float t_csr, t_count, t_emit;
   // FP64 stability-step counters: [0..7] meta-mesh build, [8..15] triangulation
   unsigned long long* d_fb;
+  // launch shape of the meta-mesh kernel per valence bucket (block warps,
+  // nodes per queue access), as used by the last build
+  int tuned[3][2];
 };

@@ -23,7 +23,7 @@ EXPORTS = ["lm_build_metamesh", "lm_metamesh_counts", "lm_metamesh_export", "lm_
            "lm_tri_range", "lm_triangulate", "lm_triangulate_stream", "lm_stl_header",
            "lm_objective", "lm_metamesh_backward", "lm_last_error", "lm_metamesh_free",
            "lm_status_string", "lm_copy_to_host", "lm_launch_count", "lm_triangulate_noalloc",
-           "lm_fp64_counts"]
+           "lm_fp64_counts", "lm_metamesh_launch_shape"]
 
 
 class LmError(RuntimeError):
@@ -89,6 +89,7 @@ def load():
         "lm_launch_count": ([], ctypes.c_longlong),
         "lm_fp64_counts": ([V, P64], ctypes.c_int),
         "lm_triangulate_noalloc": ([V, I32, I64, I64, V, I64, V, P64], ctypes.c_int),
+        "lm_metamesh_launch_shape": ([V, ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -302,3 +303,10 @@ class MetaMesh:
             "hole_off": g(v.hole_off, 8 * (v.n_holes + 1), np.int64),
             "hole_ent": g(v.hole_ent, 4 * v.n_hole_ent, np.uint32),
         }
+
+
+def lm_metamesh_launch_shape(h):
+    """[(warps per block, nodes per queue access)] per valence bucket."""
+    out = (ctypes.c_int32 * 6)()
+    _ck(load().lm_metamesh_launch_shape(h, out), "lm_metamesh_launch_shape")
+    return [(out[2 * b], out[2 * b + 1]) for b in range(3)]

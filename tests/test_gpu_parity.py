@@ -213,3 +213,22 @@ def test_streaming_matches_direct():
     got.sort(key=lambda x: x[0])
     cat = np.concatenate([x[1] for x in got]).reshape(-1, 50)
     assert np.array_equal(cat, full)
+
+
+def test_autotuned_build_is_identical():
+    """The autotuner (lm_options.autotune) only changes the launch shape of the
+    persistent meta-mesh kernel: the meta-mesh is the same array for array."""
+    lat = P.lattice_as(LATTICES["irregular"](), np.float32)
+    xyz, ends, radii = P.to_device(lat, np.float32)
+    ref = liblm.MetaMesh(xyz, ends, radii)
+    opt = liblm.lm_options()
+    opt.autotune = 1
+    tuned = liblm.MetaMesh(xyz, ends, radii, options=opt)
+    a, b = ref.download(), tuned.download()
+    for key in a:
+        assert np.array_equal(a[key], b[key]), key
+    shape = liblm.lm_metamesh_launch_shape(tuned.h)
+    for bw, npt in shape:
+        assert (bw, npt) == (0, 0) or (bw in (1, 2, 4) and npt in (1, 2, 4, 8))
+    assert shape[0][0] > 0
+    assert liblm.lm_fp64_counts(tuned.h)[:8] == liblm.lm_fp64_counts(ref.h)[:8]
