@@ -65,8 +65,9 @@ const double PHI_CUT = 0.0009765625;  // 2^-10
 // rad: zipper tie band.  A point of loop A advances before a point of loop B
 // whose angle it exceeds by at most ETA_ZIP.  Points of the two loops of a
 // (near-)symmetric strut line up to within far less than this, so they all
-// take the same branch.
-const double ETA_ZIP = 0.0009765625;  // 2^-10
+// take the same branch; the band is also far from the structural angle
+// differences of symmetric lattices (multiples of the point spacing).
+const double ETA_ZIP = 0.015625;  // 2^-6
 // segment-count offset: an arc whose ratio dphi k / 2pi exceeds an integer n
 // by at most TAU_COUNT gets n segments (exact multiples, as on symmetric
 // lattices, keep the minimal count; the chord error may exceed its target

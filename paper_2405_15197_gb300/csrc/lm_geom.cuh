@@ -35,7 +35,7 @@ constexpr double ETA_SIGMA = 1e-9;  // x R: a strut passes through a vertex
 constexpr double ETA_DEDUP = 1e-3;  // x R: candidates with one key are one vertex
 constexpr double ETA_PHI = 1e-9;    // rad: angle ties; relative angles wrap to [-ETA_PHI, 2pi - ETA_PHI)
 constexpr double PHI_CUT = 0.0009765625;  // rad (2^-10): absolute angles in [-PHI_CUT, 2pi - PHI_CUT)
-constexpr double ETA_ZIP = 0.0009765625;  // rad (2^-10): stitching tie band
+constexpr double ETA_ZIP = 0.015625;  // rad (2^-6): stitching tie band
 constexpr double TAU_COUNT = 0.0009765625;  // segment count offset (2^-10)
 constexpr double ETA_BARY = 1e-4;   // x R: hole barycentre at the centre
 constexpr double EPS_PAR = 1e-6;    // 1 - c^2 below this: (anti)parallel pair
