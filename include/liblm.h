@@ -183,7 +183,11 @@ lm_status lm_triangulate(lm_metamesh* mm, int32_t k, int64_t item_begin, int64_t
  * Items are processed in chunks of chunk_items; chunk c is copied to
  * h_ring + (c % n_slots) * slot_bytes.  After each chunk's copy completes,
  * the callback (may be NULL) is invoked on a host thread with (chunk index,
- * first item, triangle count, slot pointer, user).  Synchronising.       */
+ * first item, triangle count, slot pointer, user).  Synchronising.
+ * The per-chunk device work (range set-up, deferral-bitmap reset, strut and
+ * fan kernels) is captured once into two CUDA graphs, one per device
+ * buffer, whose first node reads the next chunk from a device cursor; each
+ * chunk is then one graph launch plus one copy.                          */
 typedef void (*lm_chunk_cb)(int64_t chunk, int64_t first_item, int64_t n_tris, void* h_slot,
                             void* user);
 lm_status lm_triangulate_stream(lm_metamesh* mm, int32_t k, int64_t chunk_items, void* h_ring,

@@ -538,6 +538,49 @@ lm_status tri_emit_impl(lm_metamesh* mm, int k, int64_t b, int64_t e, void* out,
   return LM_OK;
 }
 
+// Two CUDA graphs for the chunk sequence of lm_triangulate_stream: graph q
+// emits chunks q, q + 2, q + 4, ... into dbuf[q].  Its first node takes the
+// next chunk of its sequence from a device cursor and writes the item range
+// that the emit kernels read, so one instantiated graph replays every chunk
+// of its parity with no host work besides the launch.
+//   dev: device int64 [6] = cursor[2], range[2][2]
+template <typename T>
+lm_status chunk_graphs(lm_metamesh* mm, int k, int64_t chunk, int64_t n_items, uint8_t* dbuf[2], int64_t cap,
+                       int64_t* dev, cudaGraphExec_t ex[2], long long* kernels_per_launch) {
+  cudaStream_t cs;
+  LM_CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  lm_status s = LM_OK;
+  for (int q = 0; q < 2 && s == LM_OK; q++) {
+    TriLaunch<T> L = tri_launch<T>(mm);
+    L.k = k;
+    L.item_begin = 0;
+    L.item_end = n_items;  // host-side sizing only; the kernels read the range
+    L.capacity = cap;
+    L.first_ptr = nullptr;
+    L.out = dbuf[q];
+    L.acc = nullptr;
+    L.range = dev + 2 + 2 * q;
+    long long n0 = g_launches.load();
+    cudaGraph_t g = nullptr;
+    if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed) != cudaSuccess) { s = LM_ERR_CUDA; break; }
+    cudaError_t e0 = launch_chunk_begin(dev + q, 2, chunk, n_items, dev + 2 + 2 * q, cs);
+    cudaError_t e1 = cudaMemsetAsync(mm->d_queue, 0, 2 * sizeof(int), cs);
+    cudaError_t e2 = launch_tri_emit<T>(L, cs);
+    cudaError_t e3 = cudaStreamEndCapture(cs, &g);
+    long long n1 = g_launches.load();
+    count_launch((int)-(n1 - n0));  // capture is not execution
+    *kernels_per_launch = n1 - n0;
+    if (e0 != cudaSuccess || e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess || !g) {
+      s = LM_ERR_CUDA;
+      break;
+    }
+    if (cudaGraphInstantiate(&ex[q], g, 0) != cudaSuccess) s = LM_ERR_CUDA;
+    cudaGraphDestroy(g);
+  }
+  cudaStreamDestroy(cs);
+  return s;
+}
+
 bool valid_k(int k) { return k >= 1 && k <= 4096; }
 
 }  // namespace
@@ -760,12 +803,27 @@ lm_status lm_triangulate_stream(lm_metamesh* mm, int32_t k, int64_t chunk_items,
     cudaEventCreateWithFlags(&done_copy[q], cudaEventDisableTiming);
   }
   std::vector<cudaEvent_t> copied(n_chunks);
+  // chunk graphs: cursors start at chunks 0 and 1
+  int64_t* gdev = nullptr;
+  cudaGraphExec_t gex[2] = {nullptr, nullptr};
+  long long kpl = 0;
+  LM_CK(cudaMallocAsync((void**)&gdev, 6 * sizeof(int64_t), st));
+  {
+    const int64_t init[6] = {0, 1, 0, 0, 0, 0};
+    LM_CK(cudaMemcpyAsync(gdev, init, sizeof(init), cudaMemcpyHostToDevice, st));
+    LM_CK(cudaStreamSynchronize(st));
+    s = mm->dtype == LM_F32 ? chunk_graphs<float>(mm, k, chunk_items, n_items, dbuf, max_tris, gdev, gex, &kpl)
+                            : chunk_graphs<double>(mm, k, chunk_items, n_items, dbuf, max_tris, gdev, gex, &kpl);
+  }
   for (int64_t c = 0; c < n_chunks && s == LM_OK; c++) {
     int q = (int)(c & 1);
-    int64_t b = c * chunk_items, e = std::min(n_items, b + chunk_items);
     if (c >= 2) cudaStreamWaitEvent(st, done_copy[q], 0);
-    s = lm_triangulate(mm, k, b, e, dbuf[q], max_tris, stream);
-    if (s != LM_OK) break;
+    cudaError_t ge = cudaGraphLaunch(gex[q], st);
+    if (ge != cudaSuccess) {
+      s = st_cuda(ge);
+      break;
+    }
+    count_launch((int)kpl);
     cudaEventRecord(done_comp[q], st);
     // the host slot of chunk c was last used by chunk c - n_slots: wait for
     // its copy and hand it to the caller first
@@ -794,6 +852,9 @@ lm_status lm_triangulate_stream(lm_metamesh* mm, int32_t k, int64_t chunk_items,
     if (cb && s == LM_OK) cb(c, c * chunk_items, bnd[c + 1] - bnd[c], (uint8_t*)h_ring + (c % n_slots) * slot_bytes, user);
   }
   cudaStreamSynchronize(cs);
+  for (int q = 0; q < 2; q++)
+    if (gex[q]) cudaGraphExecDestroy(gex[q]);
+  cudaFreeAsync(gdev, st);
   for (int q = 0; q < 2; q++) {
     cudaFreeAsync(dbuf[q], st);
     cudaEventDestroy(done_comp[q]);

@@ -85,6 +85,7 @@ struct TriLaunch {
   unsigned long long* fb;
   uint32_t* redo;     // bitmap of struts deferred to the FP64 pass (bit e - redo_base)
   int64_t redo_base;
+  const int64_t* range;  // device-side [begin, end) overriding item_begin/end, or NULL
 };
 
 template <typename T>
@@ -96,6 +97,9 @@ cudaError_t launch_tri_emit(const TriLaunch<T>& a, cudaStream_t st);
 template <typename T>
 cudaError_t metamesh_backward(lm_metamesh* mm, int k, double w_area, double w_vol, void* gxyz, void* gr,
                               cudaStream_t st);
+// first node of a chunk graph (see lm_triangulate_stream)
+cudaError_t launch_chunk_begin(int64_t* cursor, int64_t stride, int64_t chunk, int64_t n_items, int64_t* range,
+                               cudaStream_t st);
 size_t node64_bytes();
 int64_t tri_scratch_warps();
 // host-side count of kernels this library launched (all threads)

@@ -41,6 +41,9 @@ struct TriArgs {
   int* max_pts;            // count pass: max points of one loop / one node's holes
   unsigned long long* fb;  // FP64 stability-step counters (8: segments, 9: start angle,
                            // 10: stitching order, 11: fan centre)
+  // device-side item range [2] (chunks replayed from one CUDA graph), or NULL:
+  // item_begin / item_end and first_ptr then apply
+  const int64_t* range;
   // adjoint (point adjoints instead of records)
   float* adj;                 // [n_vtx + interior arc points][3]
   const int64_t* arc_pt_off;  // [A + 1] first interior point of each arc
@@ -1256,7 +1259,11 @@ __device__ __forceinline__ bool tile_strut(const TriArgs<T>& A, const TileSmem<T
 template <typename T, int TL, bool OBJ, bool EXACT, bool ADJ = false>
 __global__ void __launch_bounds__(EXACT ? 64 : 256, EXACT ? 4 : 2)
     k_tri_tiles(TriArgs<T> A, const int64_t* first_ptr, uint32_t* redo, int64_t redo_base) {
-  const int64_t out_first = first_ptr ? *first_ptr : 0;
+  if (A.range) {
+    A.item_begin = A.range[0];
+    A.item_end = A.range[1];
+  }
+  const int64_t out_first = A.range ? A.tri_off[A.item_begin] : (first_ptr ? *first_ptr : 0);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31;
   const int tl = lane & (TL - 1);
@@ -1294,6 +1301,28 @@ __global__ void __launch_bounds__(EXACT ? 64 : 256, EXACT ? 4 : 2)
   }
 }
 
+// ------------------------------------------------ chunks replayed by graph
+// First node of a chunk graph: the next chunk of this graph's sequence
+// (cursor[0], stepped by `stride`) as a device-side item range.
+static __global__ void k_chunk_begin(int64_t* cursor, int64_t stride, int64_t chunk, int64_t n_items, int64_t* range) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    int64_t c = cursor[0];
+    int64_t b = c * chunk, e = b + chunk;
+    range[0] = b < n_items ? b : n_items;
+    range[1] = e < n_items ? e : n_items;
+    cursor[0] = c + stride;
+  }
+}
+
+// Clear the deferral bitmap words of the struts of a device-side range.
+static __global__ void k_redo_clear(const int64_t* range, uint32_t* redo, int64_t base, int64_t n_struts) {
+  int64_t b = range[0], e = range[1] < n_struts ? range[1] : n_struts;
+  if (e <= b) return;
+  int64_t w0 = (b - base) >> 5, w1 = (e - base + 31) >> 5;
+  for (int64_t w = w0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; w < w1; w += (int64_t)gridDim.x * blockDim.x)
+    redo[w] = 0u;
+}
+
 // ---------------------------------------------------------- hole fans
 // One warp per node: for each hole, the contour points (circular arcs in
 // hole order), their barycentre b, b_project = o + R (b - o)/|b - o| (Section
@@ -1302,7 +1331,11 @@ __global__ void __launch_bounds__(EXACT ? 64 : 256, EXACT ? 4 : 2)
 template <typename T>
 __global__ void __launch_bounds__(256) k_tri_holes(TriArgs<T> A, Node64* scratch,
                                                     const int64_t* first_ptr) {
-  const int64_t out_first = first_ptr ? *first_ptr : 0;
+  if (A.range) {
+    A.item_begin = A.range[0];
+    A.item_end = A.range[1];
+  }
+  const int64_t out_first = A.range ? A.tri_off[A.item_begin] : (first_ptr ? *first_ptr : 0);
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;

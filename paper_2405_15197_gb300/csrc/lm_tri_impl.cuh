@@ -41,6 +41,7 @@ TriArgs<T> tri_args(const TriLaunch<T>& a) {
   A.emax = a.emax;
   A.dmax = a.dmax > 0 ? a.dmax : 1;
   A.max_pts = a.max_pts;
+  A.range = a.range;
   A.fb = a.fb;
   return A;
 }
@@ -94,7 +95,16 @@ cudaError_t launch_tri_emit(const TriLaunch<T>& a, cudaStream_t st) {
       const int64_t w0 = (a.item_begin - a.redo_base) >> 5, w1 = (e_end - a.redo_base + 31) >> 5;
       if (F32) {
         if (!a.redo) return cudaErrorInvalidValue;
-        e = cudaMemsetAsync(a.redo + w0, 0, (size_t)(w1 - w0) * sizeof(uint32_t), st);
+        if (a.range) {
+          int64_t gw = (w1 - w0 + 255) / 256;
+          if (gw > (int64_t)sms * 4) gw = (int64_t)sms * 4;
+          if (gw < 1) gw = 1;
+          count_launch();
+          k_redo_clear<<<(unsigned)gw, 256, 0, st>>>(a.range, a.redo, a.redo_base, a.n_struts);
+          e = cudaGetLastError();
+        } else {
+          e = cudaMemsetAsync(a.redo + w0, 0, (size_t)(w1 - w0) * sizeof(uint32_t), st);
+        }
         if (e != cudaSuccess) return e;
       }
       {

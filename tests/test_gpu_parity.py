@@ -190,14 +190,15 @@ def test_empty_and_invalid_inputs():
         liblm.lm_triangulate(mm.h, 9, 0, 1, 0, 0, None)                       # k without count
 
 
-def test_streaming_matches_direct():
+@pytest.mark.parametrize("name,dtype,k,chunk", [("octet3", np.float32, 32, 97), ("irregular", np.float32, 16, 1000),
+                                                ("octet3", np.float64, 8, 61)])
+def test_streaming_matches_direct(name, dtype, k, chunk):
     """Chunked triangulation streamed to pinned host slots (overlapped
-    device-to-host copies) reproduces the direct output."""
-    lat, mm, g, o = build("octet3", np.float32)
-    k = 32
+    device-to-host copies; the per-chunk work replayed from two CUDA graphs)
+    reproduces the direct output, including struts stitched by the FP64 pass."""
+    lat, mm, g, o = build(name, dtype)
     n = mm.tri_count(k)
     full = mm.triangulate(k).cpu().numpy()
-    chunk = 97
     n_items = mm.n_struts + mm.n_nodes
     max_chunk = max(liblm.lm_tri_range(mm.h, c, min(n_items, c + chunk))[1] for c in range(0, n_items, chunk))
     slot = 50 * max_chunk
