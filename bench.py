@@ -116,6 +116,32 @@ def make_lattice_device(wl, device, torch):
             torch.tensor(lat["radii"], dtype=torch.float32, device=device))
 
 
+_chunk_cache = {}
+
+
+def emit_chunks(liblm, mm, k, cap_tris):
+    """Item ranges whose records fit the device output buffer (one range when
+    the whole triangulation fits; the 1e9-strut lattice reuses a bounded
+    buffer chunk after chunk).  Sized once per (lattice, k) from the counts."""
+    n_items = mm.n_struts + mm.n_nodes
+    key = (mm.n_struts, mm.n_nodes, k, cap_tris)
+    if key not in _chunk_cache:
+        _, total = liblm.lm_tri_range(mm.h, 0, n_items)
+        if total <= cap_tris:
+            _chunk_cache[key] = [(0, n_items)]
+        else:
+            step = max(1, int(0.5 * cap_tris * n_items / total))
+            ranges, b = [], 0
+            while b < n_items:
+                e = min(n_items, b + step)
+                while liblm.lm_tri_range(mm.h, b, e)[1] > cap_tris:
+                    e = b + max(1, (e - b) // 2)
+                ranges.append((b, e))
+                b = e
+            _chunk_cache[key] = ranges
+    return _chunk_cache[key]
+
+
 def tuned_options(liblm):
     """Build options with the launch-shape autotuner on (cached per process)."""
     opt = liblm.lm_options()
@@ -134,7 +160,8 @@ def run_step(torch, liblm, xyz, ends, radii, ks, out, stream, want_times=False):
     for q, k in enumerate(ks):
         n = mm.tri_count(k, stream)
         ev[2 + 2 * q].record(stream)
-        liblm.lm_triangulate(mm.h, k, 0, mm.n_struts + mm.n_nodes, out.data_ptr(), out.numel() // 50, stream)
+        for b, e in emit_chunks(liblm, mm, k, out.numel() // 50):
+            liblm.lm_triangulate(mm.h, k, b, e, out.data_ptr(), out.numel() // 50, stream)
         ev[3 + 2 * q].record(stream)
         tris.append(n)
     err = liblm.lm_last_error(mm.h, stream)
@@ -183,7 +210,12 @@ def bench_gpu(args):
                     fb[:12]))
     t_build = {"csr": None}
     mm.close()
-    out = torch.empty(max(totals) * 50, dtype=torch.uint8, device=dev)
+    # device output buffer: the whole triangulation when it fits in 64 GB,
+    # else a reused 16 GB chunk buffer
+    out_bytes = max(totals) * 50
+    if out_bytes > (64 << 30):
+        out_bytes = 16 << 30
+    out = torch.empty(out_bytes, dtype=torch.uint8, device=dev)
     for _ in range(args.warmup):
         run_step(torch, liblm, xyz, ends, radii, ks, out, stream)
     torch.cuda.synchronize()
