@@ -681,7 +681,7 @@ __global__ void __launch_bounds__(128, 3) k_tri_thread(TriArgs<T> A, const int64
 }
 
 // ------------------------------------------------ tile-per-strut stitching
-// A tile of TL lanes (16: two struts per warp) stitches one strut.  The
+// A tile of TL lanes (8 on the forward path: four struts per warp) stitches one strut.  The
 // entries of both loops are set up lane-parallel (their arc geometry goes to
 // shared memory), the loop points are evaluated lane-parallel, B's angles are
 // moved into A's window and B is rotated to its smallest key, and then each

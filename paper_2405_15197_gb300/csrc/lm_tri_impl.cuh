@@ -74,21 +74,22 @@ cudaError_t launch_tri_emit(const TriLaunch<T>& a, cudaStream_t st) {
   int sms = sm_count();
   (void)threads;
   cudaError_t e;
-  // struts: one 16-lane tile per strut (two per warp) while the per-tile
-  // shared memory fits; otherwise (very fine resolutions) one thread per
-  // strut that streams its points
+  // struts: one 8-lane tile per strut (four per warp; measured faster than
+  // 4, 16 or 32 lanes on octet and BCC lattices at k = 8 and 32) while the
+  // per-tile shared memory fits; otherwise (very fine resolutions) one thread
+  // per strut that streams its points
   if (a.item_begin < a.n_struts) {
-    constexpr int TL = 16;
+    constexpr int TL = 8;
     const int64_t n = (a.item_end < a.n_struts ? a.item_end : a.n_struts) - a.item_begin;
     TileLayout<T, TL> Lay{a.pmax, a.emax, false, false, a.dmax}, LayX{a.pmax, a.emax, true, false, a.dmax};
     const size_t smem_cap = 200 * 1024;
     auto tiles_for = [&](size_t bytes) {
-      int t = 16;
+      int t = 256 / TL;
       while (t > 2 && (size_t)t * bytes > smem_cap) t >>= 1;
       return (size_t)t * bytes <= smem_cap ? t : 0;
     };
     const int tiles = tiles_for(Lay.bytes());
-    const int tilesx = tiles_for(LayX.bytes()) < 4 ? tiles_for(LayX.bytes()) : 4;
+    const int tilesx = tiles_for(LayX.bytes()) < 64 / TL ? tiles_for(LayX.bytes()) : 64 / TL;
     if (tiles > 0 && tilesx > 0) {
       constexpr bool F32 = sizeof(T) == 4;
       const int64_t e_end = a.item_end < a.n_struts ? a.item_end : a.n_struts;
