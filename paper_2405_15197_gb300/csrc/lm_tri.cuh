@@ -690,6 +690,9 @@ __global__ void __launch_bounds__(128, 3) k_tri_thread(TriArgs<T> A, const int64
 // vector stores.  Angle decisions that FP32 cannot take safely (keys within
 // M_ZIP of each other or of the window edges) are retaken in FP64 from the
 // exact vertex generators, recomputed per comparison (they are rare).
+// x in [-n, 2n) moved into [0, n) (no integer division)
+__device__ __forceinline__ int wrap_idx(int x, int n) { return x < 0 ? x + n : (x >= n ? x - n : x); }
+
 template <typename T>
 struct TileEntry {
   ArcGeo<T> g;
@@ -1085,25 +1088,25 @@ __device__ __forceinline__ bool tile_strut(const TriArgs<T>& A, const TileSmem<T
       int lj = 0, hj = nB;
       while (lj < hj) {
         int mid = (lj + hj) >> 1;
-        if (KB[(sB + mid) % nB] < x) lj = mid + 1;
+        if (KB[wrap_idx(sB + mid, nB)] < x) lj = mid + 1;
         else hj = mid;
       }
       bool hit = false;
       for (int jj = lj - 1; jj >= lj - nB; jj--) {
-        int jr = (jj % nB + nB) % nB;
-        T kv = KB[(sB + jr) % nB] - (jj < 0 ? T(PI2) : T(0));
+        int jr = wrap_idx(jj, nB);
+        T kv = KB[wrap_idx(sB + jr, nB)] - (jj < 0 ? T(PI2) : T(0));
         if (kv < x - T(2 * M_ZIP)) break;
         if (fabs(kv - x) <= T(M_ZIP)) {
-          if (FP64_STEPS) FL[A.pmax + (sB + jr) % nB] |= 1;
+          if (FP64_STEPS) FL[A.pmax + wrap_idx(sB + jr, nB)] |= 1;
           hit = true;
         }
       }
       for (int jj = lj; jj < lj + nB; jj++) {
-        int jr = jj % nB;
-        T kv = KB[(sB + jr) % nB] + (jj >= nB ? T(PI2) : T(0));
+        int jr = wrap_idx(jj, nB);
+        T kv = KB[wrap_idx(sB + jr, nB)] + (jj >= nB ? T(PI2) : T(0));
         if (kv > x + T(2 * M_ZIP)) break;
         if (fabs(kv - x) <= T(M_ZIP)) {
-          if (FP64_STEPS) FL[A.pmax + (sB + jr) % nB] |= 1;
+          if (FP64_STEPS) FL[A.pmax + wrap_idx(sB + jr, nB)] |= 1;
           hit = true;
         }
       }
@@ -1179,7 +1182,7 @@ __device__ __forceinline__ bool tile_strut(const TriArgs<T>& A, const TileSmem<T
   }
   const double a0_64 = FP64_STEPS && anyt ? S.TH64[0] : 0.0;
   auto a_before_b = [&](int i, int j) -> bool {
-    int jb = (sB + j) % nB;
+    int jb = wrap_idx(sB + j, nB);
     if (FP64_STEPS && anyt && FL[i < nA ? i : 0] && FL[A.pmax + jb]) {
       double x = i < nA ? S.TH64[i] : a0_64 + PI2;
       return x <= S.TH64[A.pmax + jb] + ETA_ZIP;
@@ -1204,10 +1207,10 @@ __device__ __forceinline__ bool tile_strut(const TriArgs<T>& A, const TileSmem<T
       }
       int i = li_, jn = p - i;
       bool isA = (i < nA) && (jn == nB || a_before_b(i + 1, jn));
-      int jp = (sB + jn + nB - 1) % nB;
+      int jp = wrap_idx(sB + jn - 1, nB);
       V3<T> za = Z[i < nA ? i : 0];
       V3<T> zp = Z[A.pmax + jp];
-      V3<T> q1 = isA ? Z[(i + 1) % nA] : Z[A.pmax + (sB + jn) % nB];
+      V3<T> q1 = isA ? Z[i + 1 < nA ? i + 1 : 0] : Z[A.pmax + wrap_idx(sB + jn, nB)];
       V3<T> ra = za, rb = isA ? q1 : dAB + q1, rc = dAB + zp;
       V3<T> pa = cA + za, pb = isA ? cA + q1 : cB + q1, pc = cB + zp;
       V3<T> cr = cross(rb - ra, rc - ra);
@@ -1215,7 +1218,7 @@ __device__ __forceinline__ bool tile_strut(const TriArgs<T>& A, const TileSmem<T
       V3<T> nn = len > T(0) ? cr * (T(1) / len) : mk3(T(0), T(0), T(0));
       if constexpr (ADJ) {
         int64_t ia_ = S.PID[i < nA ? i : 0];
-        int64_t ib_ = isA ? S.PID[(i + 1) % nA] : S.PID[A.pmax + (sB + jn) % nB];
+        int64_t ib_ = isA ? S.PID[i + 1 < nA ? i + 1 : 0] : S.PID[A.pmax + wrap_idx(sB + jn, nB)];
         int64_t ic_ = S.PID[A.pmax + jp];
         tri_point_adjoints<T>(A, ra, rb, rc, nn, cr, ia_, ib_, ic_);
       } else {
