@@ -433,12 +433,12 @@ cudaError_t metamesh_backward(lm_metamesh* mm, int k, double w_area, double w_vo
     constexpr int TL = 16;
     TileLayout<T, TL> Lay{A.pmax, A.emax, false, true, A.dmax}, LayX{A.pmax, A.emax, true, true, A.dmax};
     auto tiles_for = [&](size_t bytes) {
-      int t = 16;
+      int t = 128 / TL;  // the stitching kernel's block bound
       while (t > 2 && (size_t)t * bytes > 200 * 1024) t >>= 1;
       return (size_t)t * bytes <= 200 * 1024 ? t : 0;
     };
     const int tiles = tiles_for(Lay.bytes());
-    const int tilesx = tiles_for(LayX.bytes()) < 4 ? tiles_for(LayX.bytes()) : 4;
+    const int tilesx = tiles_for(LayX.bytes()) < 64 / TL ? tiles_for(LayX.bytes()) : 64 / TL;
     if (tiles == 0 || tilesx == 0) { status = cudaErrorInvalidValue; goto done; }
     const int64_t words = mm->E / 32 + 1;
     BK(cudaMallocAsync((void**)&redo, sizeof(uint32_t) * (size_t)words, st));

@@ -1260,7 +1260,7 @@ __device__ __forceinline__ bool tile_strut(const TriArgs<T>& A, const TileSmem<T
 // step is marked in `redo` (bit e - redo_base) instead.  EXACT on: only the
 // marked struts are stitched, with the FP64 steps.
 template <typename T, int TL, bool OBJ, bool EXACT, bool ADJ = false>
-__global__ void __launch_bounds__(EXACT ? 64 : 256, EXACT ? 4 : 2)
+__global__ void __launch_bounds__(EXACT ? 64 : 128, EXACT ? 4 : 6)
     k_tri_tiles(TriArgs<T> A, const int64_t* first_ptr, uint32_t* redo, int64_t redo_base) {
   if (A.range) {
     A.item_begin = A.range[0];

@@ -84,7 +84,7 @@ cudaError_t launch_tri_emit(const TriLaunch<T>& a, cudaStream_t st) {
     TileLayout<T, TL> Lay{a.pmax, a.emax, false, false, a.dmax}, LayX{a.pmax, a.emax, true, false, a.dmax};
     const size_t smem_cap = 200 * 1024;
     auto tiles_for = [&](size_t bytes) {
-      int t = 256 / TL;
+      int t = 128 / TL;
       while (t > 2 && (size_t)t * bytes > smem_cap) t >>= 1;
       return (size_t)t * bytes <= smem_cap ? t : 0;
     };
