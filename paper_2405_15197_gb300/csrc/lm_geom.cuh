@@ -284,13 +284,25 @@ struct GenOut {
   uint8_t refine;     // decisions certain, but recompute positions in FP64
   uint32_t nflags;    // node flags raised independent of survival
   uint32_t kflags[2]; // node flags raised if the root is kept as a new vertex
+  uint64_t umask[2];  // FP32: strut ends whose screening decision was uncertain
+};
+
+// What an FP32 evaluation already decided, for a higher-precision
+// re-decision of the same generator: per root its FP32 state (0 rejected,
+// 1 kept, 2 uncertain, 3 duplicate of a vertex found earlier) and the strut
+// ends whose screening was uncertain.  Every other screening decision was
+// certain (beyond its margin) and is not repeated.
+struct GenHint {
+  uint8_t st[2];
+  uint64_t umask[2];
 };
 
 // Candidates of one generator with screening (trimming) against every strut
 // end of the node.  F64 = true: all decisions exact (thresholds only).
 // F64 = false: decisions within the FP32 margins are reported uncertain.
 template <typename U, bool F64>
-__device__ void eval_gen(const EndG<U>* E, int d, U R, uint32_t gcode, GenOut<U>& o) {
+__device__ void eval_gen(const EndG<U>* E, int d, U R, uint32_t gcode, GenOut<U>& o,
+                         const GenHint* hint = nullptr) {
   o.nroot = 0;
   o.unc = 0;
   o.refine = 0;
@@ -424,6 +436,11 @@ __device__ void eval_gen(const EndG<U>* E, int d, U R, uint32_t gcode, GenOut<U>
     o.sphere[r] = sph0;
     o.tangent[r] = tanq < U(0);
     o.kflags[r] = 0;
+    o.umask[r] = 0;
+    if (hint && (hint->st[r] == 0 || hint->st[r] == 3)) {
+      o.state[r] = hint->st[r];
+      continue;
+    }
     U t0 = o.t0[r];
     V3<U> z = o.z[r];
     // certain rejections first (inside the sphere side, wrong nappe, inside
@@ -433,12 +450,16 @@ __device__ void eval_gen(const EndG<U>* E, int d, U R, uint32_t gcode, GenOut<U>
     if (t0 < -eta - M) rej = true;
     else if (t0 < -eta + M && !F64) unc = true;
     for (int l = 0; l < d && !rej; l++) {
+      if (hint && !((hint->umask[r] >> l) & 1ull)) continue;  // certain in FP32
       if (gmask >> l & 1ull) {
         U np = R - E[l].s * dot(E[l].u, z);
         if (np <= -M) rej = true;
         else if (np <= M) {
           if (F64) rej = true;
-          else unc = true;
+          else {
+            unc = true;
+            o.umask[r] |= 1ull << l;
+          }
         }
         continue;
       }
@@ -446,7 +467,10 @@ __device__ void eval_gen(const EndG<U>* E, int d, U R, uint32_t gcode, GenOut<U>
       if (sg > eta + M) rej = true;
       else if (sg >= -eta - M) {
         if (F64) key |= 1ull << l;
-        else unc = true;
+        else {
+          unc = true;
+          o.umask[r] |= 1ull << l;
+        }
       }
     }
     if (rej) continue;

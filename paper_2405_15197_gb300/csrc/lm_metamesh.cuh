@@ -322,8 +322,15 @@ __device__ void node_metamesh(WarpSmem<T, C>& S, const MMArgs<T>& A, int64_t n, 
         // re-decision in double-float (about 48 bits; see lm_df.cuh)
         ensure_df(S, L, n, d, lane);
         if (need64) {
+          // a generator uncertain as a whole is redone in full; otherwise only
+          // the uncertain screening decisions of its roots are retaken
+          GenHint hint;
+          for (int r = 0; r < 2; r++) {
+            hint.st[r] = o.state[r];
+            hint.umask[r] = o.umask[r];
+          }
           GenOut<df> o64;
-          eval_gen<df, true>(S.EDF, d, df(R), code, o64);
+          eval_gen<df, true>(S.EDF, d, df(R), code, o64, o.unc ? nullptr : &hint);
           o.nroot = o64.nroot;
           o.unc = 0;
           o.nflags = o64.nflags;
