@@ -252,6 +252,8 @@ def bench_gpu(args):
                 "kernel": f"triangulation emit at k={k_big} (k_tri_tiles FP32 pass + FP64 pass + k_tri_holes)",
                 "algorithmic_bytes": "50 B written per triangle", "peak_kind": f"{peak_kind} hbm_gbs"}
     # end-to-end: pinned host inputs -> device -> meta-mesh -> triangles streamed to a pinned ring
+    del out
+    torch.cuda.empty_cache()
     e2e = bench_e2e(torch, liblm, xyz, ends, radii, ks, stream, dev, args) if not args.no_e2e else None
     adjoint = bench_adjoint(torch, liblm, dev, stream) if not args.no_adjoint else None
     res = {
