@@ -1195,18 +1195,24 @@ __device__ __forceinline__ bool tile_strut(const TriArgs<T>& A, const TileSmem<T
   const int64_t t0 = A.tri_off[e] - out_first;
   V3<T> cA = node_xyz<T, T>(L, lo), cB = node_xyz<T, T>(L, hi);
   V3<T> dAB = cB - cA;
+  int ibase = 0;  // A events before position c0 (carried from round to round)
   for (int c0 = 0; c0 < ntri; c0 += TL) {
     int p = c0 + tl;
+    int i = ibase;
+    bool isA = false;
     if (p < ntri) {
-      // i = A events among the first p (ties -> A first)
-      int li_ = p - nB > 0 ? p - nB : 0, hi_ = p < nA ? p : nA;
+      // i = A events among the first p (ties -> A first); i(p) - i(c0) is
+      // between 0 and p - c0, so the search spans at most TL + 1 values
+      int li_ = p - nB > ibase ? p - nB : ibase, hi_ = ibase + tl;
+      if (hi_ > nA) hi_ = nA;
       while (li_ < hi_) {
         int mid = (li_ + hi_) >> 1;
         if (a_before_b(mid + 1, p - mid - 1)) li_ = mid + 1;
         else hi_ = mid;
       }
-      int i = li_, jn = p - i;
-      bool isA = (i < nA) && (jn == nB || a_before_b(i + 1, jn));
+      i = li_;
+      int jn = p - i;
+      isA = (i < nA) && (jn == nB || a_before_b(i + 1, jn));
       int jp = wrap_idx(sB + jn - 1, nB);
       V3<T> za = Z[i < nA ? i : 0];
       V3<T> zp = Z[A.pmax + jp];
@@ -1234,6 +1240,12 @@ __device__ __forceinline__ bool tile_strut(const TriArgs<T>& A, const TileSmem<T
           rec_store(S.STG + 50 * tl, f);
         }
       }
+    }
+    {
+      // the last position of this round fixes the next round's base
+      int lastl = ntri - c0 < TL ? ntri - c0 - 1 : TL - 1;
+      int nxt = __shfl_sync(m, i + (isA ? 1 : 0), lastl, TL);
+      ibase = nxt;
     }
     __syncwarp(m);
     if (!ADJ && A.out) {
