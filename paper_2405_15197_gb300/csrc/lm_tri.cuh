@@ -972,38 +972,48 @@ __device__ __forceinline__ bool tile_strut(const TriArgs<T>& A, const TileSmem<T
     }
     __syncwarp(m);
   }
-  // ---- entries of both loops
-  for (int X = 0; X < 2 && ok && !defer; X++) {
-    int64_t node = X == 0 ? lo : hi;
-    int32_t eid = X == 0 ? eA : eB;
-    int64_t q0 = A.end_off[eid];
-    int ne = (int)(A.end_off[eid + 1] - q0);
-    if (ne < 1 || ne > A.emax) {
-      ok = false;
-      break;
-    }
-    int cnt = 0;
-    for (int c0 = 0; c0 < ne; c0 += TL) {
+  // ---- entries of both loops, set up together (lanes over the entries of
+  // loop A, then of loop B, so the dependent loads of both overlap)
+  {
+    const int64_t qa = A.end_off[eA], qb = A.end_off[eB];
+    const int neA0 = (int)(A.end_off[eA + 1] - qa), neB0 = (int)(A.end_off[eB + 1] - qb);
+    if (neA0 < 1 || neA0 > A.emax || neB0 < 1 || neB0 > A.emax) ok = false;
+    int cnt[2] = {0, 0};
+    const int net = neA0 + neB0;
+    for (int c0 = 0; c0 < net && ok; c0 += TL) {
       int q = c0 + tl;
-      int Nq = 0;
-      if (q < ne) {
+      int Nq = 0, X = 0, qq = q;
+      if (q >= neA0) {
+        X = 1;
+        qq = q - neA0;
+      }
+      if (q < net) {
+        int64_t node = X == 0 ? lo : hi;
+        int32_t eid = X == 0 ? eA : eB;
+        int64_t qi = (X == 0 ? qa : qb) + qq;
         if (FP64_STEPS)
-          Nq = tile_entry_setup_exact<T>(A, node, eid, q0 + q, ENT + X * A.emax + q, S.E64 + X * A.dmax, H->li[X]);
-        else Nq = tile_entry_setup_impl<T, false>(A, node, eid, q0 + q, ENT + X * A.emax + q);
+          Nq = tile_entry_setup_exact<T>(A, node, eid, qi, ENT + X * A.emax + qq, S.E64 + X * A.dmax, H->li[X]);
+        else Nq = tile_entry_setup_impl<T, false>(A, node, eid, qi, ENT + X * A.emax + qq);
       }
       if (__any_sync(m, Nq < 0)) {
         tfb_add(A.fb, 12, tl == 0, m);
         defer = true;
         break;
       }
-      int pre = tile_excl_scan<TL>(Nq, tl, m) + cnt;
-      if (q < ne) ENT[X * A.emax + q].pre = pre;
-      cnt = __shfl_sync(m, pre + Nq, TL - 1, TL);
+      // per-loop exclusive prefix: scan the round's loop-A and loop-B counts
+      // separately (loop B's entries follow loop A's in lane order)
+      int nA_ = X == 0 ? Nq : 0, nB_ = X == 1 ? Nq : 0;
+      int pa = tile_excl_scan<TL>(nA_, tl, m), pb = tile_excl_scan<TL>(nB_, tl, m);
+      if (q < net) ENT[X * A.emax + qq].pre = X == 0 ? cnt[0] + pa : cnt[1] + pb;
+      cnt[0] += __shfl_sync(m, pa + nA_, TL - 1, TL);
+      cnt[1] += __shfl_sync(m, pb + nB_, TL - 1, TL);
     }
-    if (cnt > A.pmax) ok = false;
+    if (cnt[0] > A.pmax || cnt[1] > A.pmax) ok = false;
     if (tl == 0) {
-      H->ne[X] = ne;
-      H->np[X] = cnt;
+      H->ne[0] = neA0;
+      H->ne[1] = neB0;
+      H->np[0] = cnt[0];
+      H->np[1] = cnt[1];
     }
   }
   if (defer) return true;
