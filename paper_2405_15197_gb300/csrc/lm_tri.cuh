@@ -1024,14 +1024,15 @@ __device__ __forceinline__ bool tile_strut(const TriArgs<T>& A, const TileSmem<T
   }
   const int nA = H->np[0], nB = H->np[1];
   const int neA = H->ne[0], neB = H->ne[1];
-  // ---- points of both loops
-  for (int X = 0; X < 2; X++) {
-    int64_t node = X == 0 ? lo : hi;
-    int32_t eid = X == 0 ? eA : eB;
-    EndG<T> own = make_end<T, T>(L, node, eid);
-    int np = X == 0 ? nA : nB, ne = X == 0 ? neA : neB;
-    const TileEntry<T>* ents = ENT + X * A.emax;
-    for (int p = tl; p < np; p += TL) {
+  // ---- points of both loops, lanes over the points of A then of B (the
+  // strut frame e1, e2 -- all raw_angle reads -- is the same at both ends)
+  {
+    const EndG<T> own = make_end<T, T>(L, lo, eA);
+    for (int q = tl; q < nA + nB; q += TL) {
+      const int X = q < nA ? 0 : 1, p = X == 0 ? q : q - nA;
+      const int64_t node = X == 0 ? lo : hi;
+      const int ne = X == 0 ? neA : neB;
+      const TileEntry<T>* ents = ENT + X * A.emax;
       const TileEntry<T>& en = ents[tile_entry_of(ents, ne, p)];
       int sidx = p - en.pre;
       int mm = en.rev ? en.N - sidx : sidx;
