@@ -494,6 +494,8 @@ TriLaunch<T> tri_launch(lm_metamesh* mm) {
   L.fb = mm->d_fb;
   L.redo = mm->redo_bits;
   L.redo_base = 0;
+  L.rlist = mm->redo_list;
+  L.rcap = mm->redo_cap;
   return L;
 }
 
@@ -504,6 +506,10 @@ lm_status tri_count_impl(lm_metamesh* mm, int k, cudaStream_t st, int64_t* total
     LM_CK(dalloc(&mm->item_cnt, n_items, st));
     LM_CK(dalloc(&mm->tri_off, n_items + 1, st));
     LM_CK(dalloc(&mm->redo_bits, mm->E / 32 + 1, st));
+    // the deferred struts are rare (about 1 % on cone-strut lattices); more
+    // than redo_cap in one call fall back to scanning the bitmap
+    mm->redo_cap = std::min<int64_t>(std::max<int64_t>(mm->E / 32, 65536), (int64_t)1 << 24);
+    LM_CK(dalloc(&mm->redo_list, mm->redo_cap + 1, st));
   }
   LM_CK(cudaMemsetAsync(mm->d_misc + 2, 0, sizeof(int), st));
   TriLaunch<T> L = tri_launch<T>(mm);
@@ -610,7 +616,7 @@ void lm_metamesh_free(lm_metamesh* mm) {
   void* ptrs[] = {mm->node_R, mm->row_ptr, mm->adj, mm->node_flags, mm->vtx_off, mm->arc_off,
                   mm->hole_off_n, mm->hent_off_n, mm->end_off, mm->vtx_z, mm->vtx_key, mm->vtx_flags,
                   mm->vtx_gen, mm->arc_ends, mm->arc_vtx, mm->arc_phi, mm->loop_ent, mm->hole_off,
-                  mm->hole_ent, mm->item_cnt, mm->tri_off, mm->redo_bits, mm->scratch, mm->d_err, mm->d_queue,
+                  mm->hole_ent, mm->item_cnt, mm->tri_off, mm->redo_bits, mm->redo_list, mm->scratch, mm->d_err, mm->d_queue,
                   mm->d_misc, mm->d_acc, mm->scan_ws, mm->d_fb};
   for (void* p : ptrs)
     if (p) cudaFreeAsync(p, st);

@@ -85,6 +85,8 @@ struct TriLaunch {
   unsigned long long* fb;
   uint32_t* redo;     // bitmap of struts deferred to the FP64 pass (bit e - redo_base)
   int64_t redo_base;
+  unsigned long long* rlist;  // [1 + rcap]: count, then the deferred struts (NULL: bitmap only)
+  int64_t rcap;
   const int64_t* range;  // device-side [begin, end) overriding item_begin/end, or NULL
 };
 
@@ -141,6 +143,8 @@ struct lm_metamesh {
   int32_t* item_cnt;
   int64_t* tri_off;
   uint32_t* redo_bits;  // [E/32 + 1]: struts deferred to the FP64 stitching pass
+  unsigned long long* redo_list;  // [1 + redo_cap]: the same struts, listed
+  int64_t redo_cap;
   int64_t tri_total;
   int tri_pmax;
   lm::Node64* scratch;

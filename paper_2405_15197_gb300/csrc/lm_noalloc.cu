@@ -29,6 +29,7 @@ struct NaLayout {
   int64_t off[NA_MAX_ITEMS + 1];
   int64_t ws[NA_SCAN_WS];
   uint32_t redo[NA_MAX_ITEMS / 32 + 2];  // struts deferred to the FP64 pass
+  unsigned long long rlist[NA_MAX_ITEMS / 16 + 1];  // the same, listed (count first)
   int counters[8];  // [0..1] work queues, [2] max points of one loop
 };
 constexpr size_t NA_CTX_OFFSET = (sizeof(NaLayout) + 255) & ~(size_t)255;
@@ -222,6 +223,8 @@ lm_status run_noalloc(lm_metamesh* mm, int k, int64_t b, int64_t e, void* d_out,
   L.scratch_warps = NA_CONTEXTS;
   L.redo = S->redo;
   L.redo_base = b;
+  L.rlist = S->rlist;
+  L.rcap = NA_MAX_ITEMS / 16;
   return launch_tri_emit<T>(L, st) == cudaSuccess ? LM_OK : LM_ERR_CUDA;
 }
 

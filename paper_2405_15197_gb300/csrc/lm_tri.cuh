@@ -44,6 +44,11 @@ struct TriArgs {
   // device-side item range [2] (chunks replayed from one CUDA graph), or NULL:
   // item_begin / item_end and first_ptr then apply
   const int64_t* range;
+  // struts deferred to the FP64 stitching pass, listed: [0] count, then up to
+  // rcap strut ids (NULL: the pass scans the deferral bitmap instead; so it
+  // does when the count exceeds rcap)
+  unsigned long long* rlist;
+  int64_t rcap;
   // adjoint (point adjoints instead of records)
   float* adj;                 // [n_vtx + interior arc points][3]
   const int64_t* arc_pt_off;  // [A + 1] first interior point of each arc
@@ -827,8 +832,11 @@ __device__ __noinline__ int segments64_cached(const TriArgs<T>& A, const EndG<do
 }
 
 // Set up one loop entry (arc geometry, start angle, segment count) in shared
-// memory.  EXACT: decisions that FP32 cannot take safely are retaken in FP64;
-// otherwise such an entry returns -1 and its strut is deferred.
+// memory.  EXACT: decisions that FP32 cannot take safely are retaken in FP64.
+// Otherwise an uncertain start angle returns -1 (the strut is deferred) and an
+// uncertain segment count returns the FP32 count with SEG_UNC set (the caller
+// settles it from the strut's exact triangle count, or defers the strut).
+constexpr int SEG_UNC = 1 << 29;
 template <typename T, bool EXACT>
 __device__ __forceinline__ int tile_entry_setup_impl(const TriArgs<T>& A, int64_t node, int32_t eid, int64_t qi,
                                                      TileEntry<T>* dst, const EndG<double>* E64 = nullptr,
@@ -848,10 +856,7 @@ __device__ __forceinline__ int tile_entry_setup_impl(const TriArgs<T>& A, int64_
   en.dphi = A.arc_phi[2 * en.ga + 1];
   bool unc;
   int Nq = seg_count<T>(en.dphi, A.k, unc);
-  if (unc) {
-    if (!EXACT) return -1;
-    Nq = segments64_cached<T>(A, E64, node, en.ga);
-  }
+  if (EXACT && unc) Nq = segments64_cached<T>(A, E64, node, en.ga);
   int32_t oid = L.adj[rb + o];
   EndG<T> Eo = make_end<T, T>(L, node, oid);
   if (ot >= 0) {
@@ -877,7 +882,7 @@ __device__ __forceinline__ int tile_entry_setup_impl(const TriArgs<T>& A, int64_
   en.N = Nq;
   en.pre = 0;
   *dst = en;
-  return Nq;
+  return (!EXACT && unc) ? (Nq | SEG_UNC) : Nq;
 }
 
 template <typename T>
@@ -979,6 +984,7 @@ __device__ __forceinline__ bool tile_strut(const TriArgs<T>& A, const TileSmem<T
     const int neA0 = (int)(A.end_off[eA + 1] - qa), neB0 = (int)(A.end_off[eB + 1] - qb);
     if (neA0 < 1 || neA0 > A.emax || neB0 < 1 || neB0 > A.emax) ok = false;
     int cnt[2] = {0, 0};
+    int nunc = 0, uncX = 0, uncQ = 0;  // entries with an uncertain segment count
     const int net = neA0 + neB0;
     for (int c0 = 0; c0 < net && ok; c0 += TL) {
       int q = c0 + tl;
@@ -1000,6 +1006,16 @@ __device__ __forceinline__ bool tile_strut(const TriArgs<T>& A, const TileSmem<T
         defer = true;
         break;
       }
+      if (!EXACT) {
+        const unsigned ub = __ballot_sync(m, (Nq & SEG_UNC) != 0) >> (TL == 32 ? 0 : (threadIdx.x & 31 & ~(TL - 1)));
+        if (ub) {
+          nunc += __popc(ub);
+          const int qu = c0 + __ffs(ub) - 1;
+          uncX = qu < neA0 ? 0 : 1;
+          uncQ = qu < neA0 ? qu : qu - neA0;
+        }
+        Nq &= ~SEG_UNC;
+      }
       // per-loop exclusive prefix: scan the round's loop-A and loop-B counts
       // separately (loop B's entries follow loop A's in lane order)
       int nA_ = X == 0 ? Nq : 0, nB_ = X == 1 ? Nq : 0;
@@ -1007,6 +1023,23 @@ __device__ __forceinline__ bool tile_strut(const TriArgs<T>& A, const TileSmem<T
       if (q < net) ENT[X * A.emax + qq].pre = X == 0 ? cnt[0] + pa : cnt[1] + pb;
       cnt[0] += __shfl_sync(m, pa + nA_, TL - 1, TL);
       cnt[1] += __shfl_sync(m, pb + nB_, TL - 1, TL);
+    }
+    if (!EXACT && !defer && ok && nunc > 0) {
+      // the count pass decided every segment count exactly: with one
+      // uncertain entry, the strut's triangle count (points of both loops)
+      // fixes it; with more the strut is deferred
+      const int diff = (int)(A.tri_off[e + 1] - A.tri_off[e]) - (cnt[0] + cnt[1]);
+      __syncwarp(m);
+      TileEntry<T>* eu = ENT + uncX * A.emax + uncQ;
+      if (nunc > 1 || diff < -1 || diff > 1 || eu->N + diff < 1) {
+        tfb_add(A.fb, 12, tl == 0, m);
+        defer = true;
+      } else if (diff != 0) {
+        const int neX = uncX == 0 ? neA0 : neB0;
+        for (int q = uncQ + 1 + tl; q < neX; q += TL) ENT[uncX * A.emax + q].pre += diff;
+        if (tl == 0) eu->N += diff;
+        cnt[uncX] += diff;
+      }
     }
     if (cnt[0] > A.pmax || cnt[1] > A.pmax) ok = false;
     if (tl == 0) {
@@ -1306,13 +1339,26 @@ __global__ void __launch_bounds__(EXACT ? 64 : 128, EXACT ? 4 : 6)
   if (!EXACT) {
     for (int64_t e = A.item_begin + gtile; e < e_end; e += ntiles) {
       bool d = tile_strut<T, TL, OBJ, false, ADJ>(A, S, e, out_first, tl, m, vec_ok, sa, sv);
-      if (d && tl == 0) atomicOr(redo + ((e - redo_base) >> 5), 1u << ((e - redo_base) & 31));
+      if (d && tl == 0) {
+        atomicOr(redo + ((e - redo_base) >> 5), 1u << ((e - redo_base) & 31));
+        if (A.rlist) {
+          unsigned long long q = atomicAdd(A.rlist, 1ull);
+          if (q < (unsigned long long)A.rcap) A.rlist[1 + q] = (unsigned long long)e;
+        }
+      }
     }
   } else {
-    // marked struts dealt round-robin over the tiles (marks cluster in space)
-    for (int64_t e = A.item_begin + gtile; e < e_end; e += ntiles) {
-      if (!((redo[(e - redo_base) >> 5] >> ((e - redo_base) & 31)) & 1u)) continue;
-      tile_strut<T, TL, OBJ, true, ADJ>(A, S, e, out_first, tl, m, vec_ok, sa, sv);
+    const unsigned long long nl = A.rlist ? A.rlist[0] : 0ull;
+    if (A.rlist && nl <= (unsigned long long)A.rcap) {
+      // the listed struts, dealt round-robin over the tiles
+      for (int64_t i = gtile; i < (int64_t)nl; i += ntiles)
+        tile_strut<T, TL, OBJ, true, ADJ>(A, S, (int64_t)A.rlist[1 + i], out_first, tl, m, vec_ok, sa, sv);
+    } else {
+      // marked struts dealt round-robin over the tiles (marks cluster in space)
+      for (int64_t e = A.item_begin + gtile; e < e_end; e += ntiles) {
+        if (!((redo[(e - redo_base) >> 5] >> ((e - redo_base) & 31)) & 1u)) continue;
+        tile_strut<T, TL, OBJ, true, ADJ>(A, S, e, out_first, tl, m, vec_ok, sa, sv);
+      }
     }
   }
   if (OBJ && A.acc) {
@@ -1340,8 +1386,11 @@ static __global__ void k_chunk_begin(int64_t* cursor, int64_t stride, int64_t ch
   }
 }
 
-// Clear the deferral bitmap words of the struts of a device-side range.
-static __global__ void k_redo_clear(const int64_t* range, uint32_t* redo, int64_t base, int64_t n_struts) {
+// Clear the deferral bitmap words of the struts of a device-side range, and
+// the deferral list.
+static __global__ void k_redo_clear(const int64_t* range, uint32_t* redo, int64_t base, int64_t n_struts,
+                                    unsigned long long* rlist) {
+  if (rlist && blockIdx.x == 0 && threadIdx.x == 0) rlist[0] = 0ull;
   int64_t b = range[0], e = range[1] < n_struts ? range[1] : n_struts;
   if (e <= b) return;
   int64_t w0 = (b - base) >> 5, w1 = (e - base + 31) >> 5;
@@ -1350,7 +1399,7 @@ static __global__ void k_redo_clear(const int64_t* range, uint32_t* redo, int64_
 }
 
 // ---------------------------------------------------------- hole fans
-// One warp per node: for each hole, the contour points (circular arcs in
+// One warp per node with holes: for each hole, the contour points (circular arcs in
 // hole order), their barycentre b, b_project = o + R (b - o)/|b - o| (Section
 // 5), falling back to the direction away from the struts when b sits at the
 // centre or outside the hole region; fan triangles (b_project, q_m, q_m+1).
@@ -1375,13 +1424,25 @@ __global__ void __launch_bounds__(256) k_tri_holes(TriArgs<T> A, Node64* scratch
   constexpr bool IS64 = sizeof(T) == 8;
   const int64_t n0 = (A.item_begin > E ? A.item_begin : E) - E;
   const int64_t n1 = A.item_end - E;
+  // nodes are taken from the queue 32 at a time (most have no hole: one
+  // atomic per node would bound the kernel by the counter's throughput); a
+  // group is 32 nodes `stride` apart, so that runs of consecutive nodes with
+  // holes (a face of the lattice) spread over many groups
+  const int64_t stride = (n1 - n0 + 31) / 32;
+  unsigned todo = 0;
+  int64_t g0 = 0;
   while (true) {
-    int64_t nd = 0;
-    if (lane == 0) nd = n0 + atomicAdd(A.queue, 1);
-    nd = __shfl_sync(0xffffffffu, nd, 0);
-    if (nd >= n1) break;
+    if (!todo) {
+      if (lane == 0) g0 = atomicAdd(A.queue, 1);
+      g0 = __shfl_sync(0xffffffffu, g0, 0);
+      if (g0 >= stride) break;
+      const int64_t mine = n0 + g0 + lane * stride;
+      todo = __ballot_sync(0xffffffffu, mine < n1 && A.node_hole_off[mine] != A.node_hole_off[mine + 1]);
+      if (!todo) continue;
+    }
+    const int64_t nd = n0 + g0 + (__ffs(todo) - 1) * stride;
+    todo &= todo - 1;
     int64_t h0 = A.node_hole_off[nd], h1 = A.node_hole_off[nd + 1];
-    if (h0 == h1) continue;
     int64_t ao = A.arc_off[nd];
     int64_t rb = L.row_ptr[nd];
     int d = (int)(L.row_ptr[nd + 1] - rb);

@@ -1,5 +1,6 @@
 // Launchers of the triangulation kernels.
 #pragma once
+#include <algorithm>
 #include "lm_internal.h"
 #include "lm_tri.cuh"
 
@@ -7,7 +8,7 @@ namespace lm {
 
 template <typename T>
 TriArgs<T> tri_args(const TriLaunch<T>& a) {
-  TriArgs<T> A;
+  TriArgs<T> A{};
   A.lat.xyz = a.xyz;
   A.lat.ends = a.ends;
   A.lat.node_R = a.node_R;
@@ -42,6 +43,8 @@ TriArgs<T> tri_args(const TriLaunch<T>& a) {
   A.dmax = a.dmax > 0 ? a.dmax : 1;
   A.max_pts = a.max_pts;
   A.range = a.range;
+  A.rlist = a.rlist;
+  A.rcap = a.rlist ? a.rcap : 0;
   A.fb = a.fb;
   return A;
 }
@@ -79,17 +82,20 @@ cudaError_t launch_tri_emit(const TriLaunch<T>& a, cudaStream_t st) {
   // per-tile shared memory fits; otherwise (very fine resolutions) one thread
   // per strut that streams its points
   if (a.item_begin < a.n_struts) {
-    constexpr int TL = 8;
+    // the FP64 pass (about 1 % of the struts, FP64 at 1/64 of the FP32 rate)
+    // gives each deferred strut a whole warp
+    constexpr int TL = 8, TLX = 32;
     const int64_t n = (a.item_end < a.n_struts ? a.item_end : a.n_struts) - a.item_begin;
-    TileLayout<T, TL> Lay{a.pmax, a.emax, false, false, a.dmax}, LayX{a.pmax, a.emax, true, false, a.dmax};
+    TileLayout<T, TL> Lay{a.pmax, a.emax, false, false, a.dmax};
+    TileLayout<T, TLX> LayX{a.pmax, a.emax, true, false, a.dmax};
     const size_t smem_cap = 200 * 1024;
-    auto tiles_for = [&](size_t bytes) {
-      int t = 128 / TL;
+    auto tiles_for = [&](size_t bytes, int tl) {
+      int t = 128 / tl;
       while (t > 2 && (size_t)t * bytes > smem_cap) t >>= 1;
       return (size_t)t * bytes <= smem_cap ? t : 0;
     };
-    const int tiles = tiles_for(Lay.bytes());
-    const int tilesx = tiles_for(LayX.bytes()) < 64 / TL ? tiles_for(LayX.bytes()) : 64 / TL;
+    const int tiles = tiles_for(Lay.bytes(), TL);
+    const int tilesx = std::min(tiles_for(LayX.bytes(), TLX), 64 / TLX);
     if (tiles > 0 && tilesx > 0) {
       constexpr bool F32 = sizeof(T) == 4;
       const int64_t e_end = a.item_end < a.n_struts ? a.item_end : a.n_struts;
@@ -101,10 +107,11 @@ cudaError_t launch_tri_emit(const TriLaunch<T>& a, cudaStream_t st) {
           if (gw > (int64_t)sms * 4) gw = (int64_t)sms * 4;
           if (gw < 1) gw = 1;
           count_launch();
-          k_redo_clear<<<(unsigned)gw, 256, 0, st>>>(a.range, a.redo, a.redo_base, a.n_struts);
+          k_redo_clear<<<(unsigned)gw, 256, 0, st>>>(a.range, a.redo, a.redo_base, a.n_struts, a.rlist);
           e = cudaGetLastError();
         } else {
           e = cudaMemsetAsync(a.redo + w0, 0, (size_t)(w1 - w0) * sizeof(uint32_t), st);
+          if (e == cudaSuccess && a.rlist) e = cudaMemsetAsync(a.rlist, 0, sizeof(unsigned long long), st);
         }
         if (e != cudaSuccess) return e;
       }
@@ -128,9 +135,9 @@ cudaError_t launch_tri_emit(const TriLaunch<T>& a, cudaStream_t st) {
       }
       if (F32) {
         // the deferred struts, with the FP64 stability steps
-        const int tpb = tilesx * TL;
+        const int tpb = tilesx * TLX;
         size_t smem = (size_t)tilesx * LayX.bytes();
-        auto kx = a.acc ? k_tri_tiles<T, TL, true, true> : k_tri_tiles<T, TL, false, true>;
+        auto kx = a.acc ? k_tri_tiles<T, TLX, true, true> : k_tri_tiles<T, TLX, false, true>;
         e = cudaFuncSetAttribute(kx, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         int per_sm = 0;
@@ -175,7 +182,7 @@ cudaError_t launch_tri_emit(const TriLaunch<T>& a, cudaStream_t st) {
     if (grid > gmax) grid = gmax;
     int64_t nb = a.item_begin > a.n_struts ? a.item_begin : a.n_struts;
     int64_t n = a.item_end - nb;
-    int64_t gneed = (n + warps - 1) / warps;
+    int64_t gneed = ((n + 31) / 32 + warps - 1) / warps;  // groups of 32 nodes
     if (grid > gneed) grid = gneed;
     if (grid < 1) grid = 1;
     A.queue = a.queue + 1;
