@@ -714,8 +714,11 @@ struct TileHdr {
   double a0_64;  // FP64 angle of A's first point (when some key was flagged)
 };
 
-// per-tile shared memory: header, entries of both loops, point angles and
-// positions of both loops, B keys, FP64 flags, staging of TL records
+// per-tile shared memory: header, entries of both loops (the staging of TL
+// records reuses them: they are dead once the points are evaluated), point
+// angles of both loops (B's angles are overwritten by B's keys), point
+// positions of both loops; the FP64 pass adds flags per point and its FP64
+// data.  Smaller tiles mean more struts in flight per SM.
 template <typename T, int TL>
 struct TileLayout {
   __host__ __device__ static constexpr size_t r16c(size_t b) { return (b + 15) & ~(size_t)15; }
@@ -725,12 +728,16 @@ struct TileLayout {
   bool adjm;   // adjoint mode: point ids of both loops
   int dmax;    // largest node valence (FP64 strut ends)
   __host__ __device__ size_t ent() const { return r16c(sizeof(TileHdr)); }
-  __host__ __device__ size_t th() const { return ent() + r16c(2 * (size_t)emax * sizeof(TileEntry<T>)); }
+  __host__ __device__ size_t ent_bytes() const {
+    size_t e = 2 * (size_t)emax * sizeof(TileEntry<T>), st = (size_t)TL * 50;
+    return r16c(e > st ? e : st);
+  }
+  __host__ __device__ size_t th() const { return ent() + ent_bytes(); }
+  __host__ __device__ size_t kb() const { return th() + (size_t)pmax * sizeof(T); }
   __host__ __device__ size_t z() const { return th() + r16c(2 * (size_t)pmax * sizeof(T)); }
-  __host__ __device__ size_t kb() const { return z() + r16c(2 * (size_t)pmax * sizeof(V3<T>)); }
-  __host__ __device__ size_t fl() const { return kb() + r16c((size_t)pmax * sizeof(T)); }
-  __host__ __device__ size_t stage() const { return fl() + r16c(2 * (size_t)pmax); }
-  __host__ __device__ size_t ea64() const { return stage() + r16c(TL * 50); }
+  __host__ __device__ size_t fl() const { return z() + r16c(2 * (size_t)pmax * sizeof(V3<T>)); }
+  __host__ __device__ size_t stage() const { return ent(); }
+  __host__ __device__ size_t ea64() const { return fl() + (exact ? r16c(2 * (size_t)pmax) : 0); }
   __host__ __device__ size_t th64() const { return ea64() + (exact ? r16c(2 * (size_t)emax * 32) : 0); }
   __host__ __device__ size_t e64() const { return th64() + (exact ? r16c(2 * (size_t)pmax * 8) : 0); }
   __host__ __device__ size_t pid() const {
@@ -1316,7 +1323,7 @@ __device__ __forceinline__ bool tile_strut(const TriArgs<T>& A, const TileSmem<T
 // step is marked in `redo` (bit e - redo_base) instead.  EXACT on: only the
 // marked struts are stitched, with the FP64 steps.
 template <typename T, int TL, bool OBJ, bool EXACT, bool ADJ = false>
-__global__ void __launch_bounds__(EXACT ? 64 : 128, EXACT ? 4 : 6)
+__global__ void __launch_bounds__(EXACT ? 64 : 128, EXACT ? 4 : 7)
     k_tri_tiles(TriArgs<T> A, const int64_t* first_ptr, uint32_t* redo, int64_t redo_base) {
   if (A.range) {
     A.item_begin = A.range[0];
