@@ -483,6 +483,41 @@ __device__ __forceinline__ void rec_store(unsigned char* dst, const float f[12])
   }
 }
 
+// one record at any 2-byte aligned dst with 13 stores (12 words + 1
+// halfword) whatever dst mod 4: at dst = 2 mod 4 the words pair the high half
+// of value q with the low half of value q + 1
+__device__ __forceinline__ void rec_store_any(unsigned char* dst, const float f[12]) {
+  const bool odd = ((uintptr_t)dst & 2) != 0;
+  uint32_t* w = reinterpret_cast<uint32_t*>(dst + (odd ? 2 : 0));
+#pragma unroll
+  for (int q = 0; q < 12; q++) {
+    const uint32_t u = __float_as_uint(f[q]), un = q < 11 ? __float_as_uint(f[q + 1]) : 0u;
+    w[q] = odd ? __byte_perm(u, un, 0x5432) : u;
+  }
+  *reinterpret_cast<uint16_t*>(odd ? dst : dst + 48) = odd ? (uint16_t)(__float_as_uint(f[0]) & 0xffffu) : (uint16_t)0;
+}
+
+// copy `nbytes` (even) staged at offset sh (even, < 16) of a 16-byte aligned
+// shared buffer to global gdst, where gdst = sh mod 16: 16-byte loads and
+// stores for the body, halfwords for the head and tail
+__device__ __forceinline__ void flush_congruent(unsigned char* gdst, const unsigned char* st, int sh, int nbytes,
+                                                int lane, int width) {
+  const int end = sh + nbytes;
+  const int cf = (sh + 15) >> 4, ce = end >> 4;  // full 16-byte chunks [cf, ce)
+  if (cf >= ce) {
+    for (int q = lane; q < nbytes / 2; q += width)
+      reinterpret_cast<uint16_t*>(gdst)[q] = reinterpret_cast<const uint16_t*>(st + sh)[q];
+    return;
+  }
+  for (int c = cf + lane; c < ce; c += width)
+    *reinterpret_cast<uint4*>(gdst + 16 * c - sh) = *reinterpret_cast<const uint4*>(st + 16 * c);
+  const int hh = (16 * cf - sh) >> 1, th = (end - 16 * ce) >> 1;
+  for (int q = lane; q < hh + th; q += width) {
+    const int off = q < hh ? sh + 2 * q : 16 * ce + 2 * (q - hh);
+    *reinterpret_cast<uint16_t*>(gdst + off - sh) = *reinterpret_cast<const uint16_t*>(st + off);
+  }
+}
+
 constexpr int REC_LANE_STRIDE = 404;  // 8 records + pad (odd word count: no bank conflicts)
 // per-thread shared slot: the two loops' arc geometry (8-byte aligned for
 // FP64), then 8 staged records; the stride is a multiple of 8 bytes with an
@@ -729,7 +764,7 @@ struct TileLayout {
   int dmax;    // largest node valence (FP64 strut ends)
   __host__ __device__ size_t ent() const { return r16c(sizeof(TileHdr)); }
   __host__ __device__ size_t ent_bytes() const {
-    size_t e = 2 * (size_t)emax * sizeof(TileEntry<T>), st = (size_t)TL * 50;
+    size_t e = 2 * (size_t)emax * sizeof(TileEntry<T>), st = (size_t)TL * 50 + 16;
     return r16c(e > st ? e : st);
   }
   __host__ __device__ size_t th() const { return ent() + ent_bytes(); }
@@ -1249,6 +1284,9 @@ __device__ __forceinline__ bool tile_strut(const TriArgs<T>& A, const TileSmem<T
   int ibase = 0;  // A events before position c0 (carried from round to round)
   for (int c0 = 0; c0 < ntri; c0 += TL) {
     int p = c0 + tl;
+    // records staged at the global destination's offset mod 16 (out is
+    // 16-byte aligned: 50 t = 2 t mod 16)
+    const int sh = vec_ok ? (int)((2 * (t0 + c0)) & 15) : 0;
     int i = ibase;
     bool isA = false;
     if (p < ntri) {
@@ -1288,7 +1326,7 @@ __device__ __forceinline__ bool tile_strut(const TriArgs<T>& A, const TileSmem<T
         if (A.out) {
           float f[12] = {(float)nn.x, (float)nn.y, (float)nn.z, (float)pa.x, (float)pa.y, (float)pa.z,
                          (float)pb.x, (float)pb.y, (float)pb.z, (float)pc.x, (float)pc.y, (float)pc.z};
-          rec_store(S.STG + 50 * tl, f);
+          rec_store_any(S.STG + sh + 50 * tl, f);
         }
       }
     }
@@ -1303,7 +1341,7 @@ __device__ __forceinline__ bool tile_strut(const TriArgs<T>& A, const TileSmem<T
       int nrec = ntri - c0 < TL ? ntri - c0 : TL;
       int64_t gt = t0 + c0;
       if (gt + nrec <= A.capacity) {
-        if (vec_ok) flush_stage(A.out + 50 * gt, S.STG, 50 * nrec, tl, TL);
+        if (vec_ok) flush_congruent(A.out + 50 * gt, S.STG, sh, 50 * nrec, tl, TL);
         else {
           uint16_t* d16 = reinterpret_cast<uint16_t*>(A.out + 50 * gt);
           const uint16_t* s16 = reinterpret_cast<const uint16_t*>(S.STG);
