@@ -749,8 +749,12 @@ struct TileHdr {
   double a0_64;  // FP64 angle of A's first point (when some key was flagged)
 };
 
-// per-tile shared memory: header, entries of both loops (the staging of TL
-// records reuses them: they are dead once the points are evaluated), point
+// consecutive triangles per lane and round of the zipper (one merge-path
+// search per lane and round, then single comparisons)
+constexpr int TILE_RPL = 2;
+
+// per-tile shared memory: header, entries of both loops (the staging of
+// TL * TILE_RPL records reuses them: they are dead once the points are evaluated), point
 // angles of both loops (B's angles are overwritten by B's keys), point
 // positions of both loops; the FP64 pass adds flags per point and its FP64
 // data.  Smaller tiles mean more struts in flight per SM.
@@ -764,7 +768,7 @@ struct TileLayout {
   int dmax;    // largest node valence (FP64 strut ends)
   __host__ __device__ size_t ent() const { return r16c(sizeof(TileHdr)); }
   __host__ __device__ size_t ent_bytes() const {
-    size_t e = 2 * (size_t)emax * sizeof(TileEntry<T>), st = (size_t)TL * 50 + 16;
+    size_t e = 2 * (size_t)emax * sizeof(TileEntry<T>), st = (size_t)TL * TILE_RPL * 50 + 16;
     return r16c(e > st ? e : st);
   }
   __host__ __device__ size_t th() const { return ent() + ent_bytes(); }
@@ -1276,23 +1280,23 @@ __device__ __forceinline__ bool tile_strut(const TriArgs<T>& A, const TileSmem<T
     T x = i < nA ? TH[i] : thA0 + T(PI2);
     return x <= KB[jb] + T(ETA_ZIP);
   };
-  // ---- triangles by merge-path; TL records per round
+  // ---- triangles by merge-path; TL * RPL records per round
+  constexpr int RPL = TILE_RPL;
   const int ntri = nA + nB;
   const int64_t t0 = A.tri_off[e] - out_first;
   V3<T> cA = node_xyz<T, T>(L, lo), cB = node_xyz<T, T>(L, hi);
   V3<T> dAB = cB - cA;
   int ibase = 0;  // A events before position c0 (carried from round to round)
-  for (int c0 = 0; c0 < ntri; c0 += TL) {
-    int p = c0 + tl;
+  for (int c0 = 0; c0 < ntri; c0 += TL * RPL) {
+    const int p = c0 + RPL * tl;  // this lane's first position
     // records staged at the global destination's offset mod 16 (out is
     // 16-byte aligned: 50 t = 2 t mod 16)
     const int sh = vec_ok ? (int)((2 * (t0 + c0)) & 15) : 0;
     int i = ibase;
-    bool isA = false;
     if (p < ntri) {
       // i = A events among the first p (ties -> A first); i(p) - i(c0) is
-      // between 0 and p - c0, so the search spans at most TL + 1 values
-      int li_ = p - nB > ibase ? p - nB : ibase, hi_ = ibase + tl;
+      // between 0 and p - c0, so the search spans at most RPL TL + 1 values
+      int li_ = p - nB > ibase ? p - nB : ibase, hi_ = ibase + RPL * tl;
       if (hi_ > nA) hi_ = nA;
       while (li_ < hi_) {
         int mid = (li_ + hi_) >> 1;
@@ -1300,45 +1304,47 @@ __device__ __forceinline__ bool tile_strut(const TriArgs<T>& A, const TileSmem<T
         else hi_ = mid;
       }
       i = li_;
-      int jn = p - i;
-      isA = (i < nA) && (jn == nB || a_before_b(i + 1, jn));
-      int jp = wrap_idx(sB + jn - 1, nB);
-      V3<T> za = Z[i < nA ? i : 0];
-      V3<T> zp = Z[A.pmax + jp];
-      V3<T> q1 = isA ? Z[i + 1 < nA ? i + 1 : 0] : Z[A.pmax + wrap_idx(sB + jn, nB)];
-      V3<T> ra = za, rb = isA ? q1 : dAB + q1, rc = dAB + zp;
-      V3<T> pa = cA + za, pb = isA ? cA + q1 : cB + q1, pc = cB + zp;
-      V3<T> cr = cross(rb - ra, rc - ra);
-      T len = norm3(cr);
-      V3<T> nn = len > T(0) ? cr * (T(1) / len) : mk3(T(0), T(0), T(0));
-      if constexpr (ADJ) {
-        int64_t ia_ = S.PID[i < nA ? i : 0];
-        int64_t ib_ = isA ? S.PID[i + 1 < nA ? i + 1 : 0] : S.PID[A.pmax + wrap_idx(sB + jn, nB)];
-        int64_t ic_ = S.PID[A.pmax + jp];
-        tri_point_adjoints<T>(A, ra, rb, rc, nn, cr, ia_, ib_, ic_);
-      } else {
-        if (OBJ) {
-          sa += 0.5 * (double)len;
-          sv += ((double)dot(ra, cross(rb, rc)) +
-                 dot(mk3((double)cA.x, (double)cA.y, (double)cA.z), mk3((double)cr.x, (double)cr.y, (double)cr.z))) *
-                (1.0 / 6.0);
+#pragma unroll
+      for (int r = 0; r < RPL; r++) {
+        if (p + r >= ntri) break;
+        const int jn = p + r - i;
+        const bool isA = (i < nA) && (jn == nB || a_before_b(i + 1, jn));
+        int jp = wrap_idx(sB + jn - 1, nB);
+        V3<T> za = Z[i < nA ? i : 0];
+        V3<T> zp = Z[A.pmax + jp];
+        V3<T> q1 = isA ? Z[i + 1 < nA ? i + 1 : 0] : Z[A.pmax + wrap_idx(sB + jn, nB)];
+        V3<T> ra = za, rb = isA ? q1 : dAB + q1, rc = dAB + zp;
+        V3<T> pa = cA + za, pb = isA ? cA + q1 : cB + q1, pc = cB + zp;
+        V3<T> cr = cross(rb - ra, rc - ra);
+        T len = norm3(cr);
+        V3<T> nn = len > T(0) ? cr * (T(1) / len) : mk3(T(0), T(0), T(0));
+        if constexpr (ADJ) {
+          int64_t ia_ = S.PID[i < nA ? i : 0];
+          int64_t ib_ = isA ? S.PID[i + 1 < nA ? i + 1 : 0] : S.PID[A.pmax + wrap_idx(sB + jn, nB)];
+          int64_t ic_ = S.PID[A.pmax + jp];
+          tri_point_adjoints<T>(A, ra, rb, rc, nn, cr, ia_, ib_, ic_);
+        } else {
+          if (OBJ) {
+            sa += 0.5 * (double)len;
+            sv += ((double)dot(ra, cross(rb, rc)) +
+                   dot(mk3((double)cA.x, (double)cA.y, (double)cA.z), mk3((double)cr.x, (double)cr.y, (double)cr.z))) *
+                  (1.0 / 6.0);
+          }
+          if (A.out) {
+            float f[12] = {(float)nn.x, (float)nn.y, (float)nn.z, (float)pa.x, (float)pa.y, (float)pa.z,
+                           (float)pb.x, (float)pb.y, (float)pb.z, (float)pc.x, (float)pc.y, (float)pc.z};
+            rec_store_any(S.STG + sh + 50 * (RPL * tl + r), f);
+          }
         }
-        if (A.out) {
-          float f[12] = {(float)nn.x, (float)nn.y, (float)nn.z, (float)pa.x, (float)pa.y, (float)pa.z,
-                         (float)pb.x, (float)pb.y, (float)pb.z, (float)pc.x, (float)pc.y, (float)pc.z};
-          rec_store_any(S.STG + sh + 50 * tl, f);
-        }
+        i += isA ? 1 : 0;
       }
     }
-    {
-      // the last position of this round fixes the next round's base
-      int lastl = ntri - c0 < TL ? ntri - c0 - 1 : TL - 1;
-      int nxt = __shfl_sync(m, i + (isA ? 1 : 0), lastl, TL);
-      ibase = nxt;
-    }
+    const int npos = ntri - c0 < TL * RPL ? ntri - c0 : TL * RPL;
+    // the lane holding this round's last position fixes the next round's base
+    ibase = __shfl_sync(m, i, (npos - 1) / RPL, TL);
     __syncwarp(m);
     if (!ADJ && A.out) {
-      int nrec = ntri - c0 < TL ? ntri - c0 : TL;
+      const int nrec = npos;
       int64_t gt = t0 + c0;
       if (gt + nrec <= A.capacity) {
         if (vec_ok) flush_congruent(A.out + 50 * gt, S.STG, sh, 50 * nrec, tl, TL);
