@@ -331,6 +331,24 @@ lm_status build_impl(lm_metamesh* mm, cudaStream_t st) {
   L.overflow = overflow;
   L.fb = mm->d_fb;
   int64_t cap = std::max<int64_t>(N, 1);
+  // candidate outcomes recorded by the count pass for the emit pass (about
+  // 24 B per node of valence 8, 72 B at valence 12); without room for them
+  // the emit pass evaluates every candidate again
+  uint32_t* smask = nullptr;
+  int64_t smask_off[NB_BUCKETS] = {0}, smask_w[NB_BUCKETS] = {0};
+  {
+    int64_t tot = 0;
+    for (int b = 0; b < NB_BUCKETS; b++) {
+      const int dcap = b == 0 ? 16 : (b == 1 ? 32 : 64);
+      smask_w[b] = smask_words_for(std::min(dcap, std::max(maxdeg, 1)));
+      smask_off[b] = tot;
+      tot += (int64_t)hb[b] * smask_w[b];
+    }
+    if (tot > 0 && cudaMallocAsync((void**)&smask, sizeof(uint32_t) * (size_t)tot, st) != cudaSuccess) {
+      (void)cudaGetLastError();
+      smask = nullptr;
+    }
+  }
   for (int pass = 0; pass < 2; pass++) {
     if (pass == 1) {
       cudaEventRecord(ev[2], st);
@@ -355,6 +373,7 @@ lm_status build_impl(lm_metamesh* mm, cudaStream_t st) {
       LM_CK(cudaMemcpyAsync(&ovf, overflow, sizeof(int), cudaMemcpyDeviceToHost, st));
       LM_CK(cudaStreamSynchronize(st));
       if (ovf) {
+        dfree(smask, st);
         dfree(node_cnt, st);
         dfree(end_cnt, st);
         dfree(lists, st);
@@ -423,11 +442,15 @@ lm_status build_impl(lm_metamesh* mm, cudaStream_t st) {
       mm->tuned[b][0] = bw > 0 ? bw : 4;
       mm->tuned[b][1] = L.nodes_per_task;
       LM_CK(cudaMemsetAsync(mm->d_queue + b, 0, sizeof(int), st));
+      L.smask = smask ? smask + smask_off[b] : nullptr;
+      L.smask_words = smask_w[b];
       int used = 0;
       LM_CK(launch_metamesh<T>(b, pass == 1, L, bw, mm->opt.grid_ctas, st, &used));
+      L.smask = nullptr;
     }
   }
   cudaEventRecord(ev[3], st);
+  dfree(smask, st);
   // statistics
   unsigned long long* dstat = nullptr;
   LM_CK(dalloc(&dstat, 4, st));

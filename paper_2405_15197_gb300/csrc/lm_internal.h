@@ -45,7 +45,16 @@ struct MMLaunch {
   uint32_t* hole_ent;
   int* overflow;
   unsigned long long* fb;
+  uint32_t* smask;  // count-pass candidate outcomes, smask_words per listed node (NULL: none)
+  int64_t smask_words;
 };
+
+// per round of 32 candidate generators: 4 words of candidate outcomes for a
+// node of valence up to d (circle points d(d-1)/2, triple points d(d-1)(d-2)/6)
+__host__ __device__ inline int64_t smask_words_for(int d) {
+  const int64_t ng = (int64_t)d * (d - 1) / 2 + (int64_t)d * (d - 1) * (d - 2) / 6;
+  return 4 * ((ng + 31) / 32);
+}
 
 // persistent meta-mesh launch of one bucket; grid_ctas <= 0: resident CTAs
 // x SM count.  Returns the CTAs launched in *used_ctas.

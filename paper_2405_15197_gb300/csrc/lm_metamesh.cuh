@@ -78,6 +78,14 @@ struct MMArgs {
   uint32_t* hole_ent;
   int* overflow;
   unsigned long long* fb;  // FP64 re-decision counters (see FB_*)
+  // candidate outcomes of the count pass, smask_words per node of the list:
+  // per round of 32 generators, two words of kept-root bits (2 per
+  // generator, lanes 0-15 then 16-31) and two words holding bit 0 and bit 1
+  // of how the positions were taken (0 FP32, 1 FP64 refinement, 2
+  // double-float re-decision); the emit pass replays only the kept roots.
+  // NULL: the emit pass evaluates every candidate again.
+  uint32_t* smask;
+  int64_t smask_words;
 };
 
 // FP64 stability-step counters
@@ -177,7 +185,7 @@ __device__ int midpoint_label(const EndG<U>* E, int li, uint64_t cm, bool cs, U 
 }
 
 template <typename T, typename C, bool EMIT>
-__device__ void node_metamesh(WarpSmem<T, C>& S, const MMArgs<T>& A, int64_t n, int lane) {
+__device__ void node_metamesh(WarpSmem<T, C>& S, const MMArgs<T>& A, int64_t n, int64_t t, int lane) {
   const LatDev<T>& L = A.lat;
   constexpr bool IS64 = sizeof(T) == 8;
   const int64_t base = L.row_ptr[n];
@@ -271,7 +279,83 @@ __device__ void node_metamesh(WarpSmem<T, C>& S, const MMArgs<T>& A, int64_t n, 
   const int ng = np + nt;
   bool overflow = false;
   uint32_t nflags = 0;
-  for (int c0 = 0; c0 < ng && !overflow; c0 += 32) {
+  const bool replay = EMIT && A.smask != nullptr;
+  if (replay) {
+    // the kept roots recorded by the count pass, compacted into a list (the
+    // loop arrays are free until the loops are built), then evaluated 32
+    // generators at a time along the path the count pass took, and appended
+    // in canonical order (they survived screening and deduplication there)
+    const uint32_t* mk = A.smask + t * A.smask_words;
+    uint32_t* SL = reinterpret_cast<uint32_t*>(S.le_ang);
+    int ns = 0;
+    for (int c0 = 0; c0 < ng; c0 += 32) {
+      const uint32_t* w = mk + 4 * (c0 >> 5);
+      const int kb = (int)((w[lane >> 4] >> (2 * (lane & 15))) & 3u);
+      const int path = (int)(((w[2] >> lane) & 1u) | (((w[3] >> lane) & 1u) << 1));
+      const uint32_t bal = __ballot_sync(0xffffffffu, kb != 0);
+      if (kb) SL[ns + __popc(bal & ((1u << lane) - 1u))] = (uint32_t)(c0 + lane) | ((uint32_t)kb << 16) | ((uint32_t)path << 18);
+      ns += __popc(bal);
+    }
+    __syncwarp();
+    for (int s0 = 0; s0 < ns; s0 += 32) {
+      const uint32_t ent = s0 + lane < ns ? SL[s0 + lane] : 0u;
+      const int kb = (int)((ent >> 16) & 3u), path = (int)((ent >> 18) & 3u);
+      GenOut<T> o;
+      o.nroot = 0;
+      o.unc = 0;
+      o.nflags = 0;
+      uint32_t code = 0;
+      if (kb) {
+        code = decode_gen((int)(ent & 0xffffu), d, np);
+        eval_gen<T, IS64>(S.E, d, R, code, o);
+      }
+      if (!IS64 && path == 1) {
+        V3<double> z64[2];
+        double t64[2];
+        gen_points64<T>(S.E, R, code, z64, t64);
+        for (int r = 0; r < 2; r++) o.z[r] = mk3((T)z64[r].x, (T)z64[r].y, (T)z64[r].z);
+      }
+      if constexpr (!IS64) {
+        if (__any_sync(0xffffffffu, path == 2)) {
+          ensure_df(S, L, n, d, lane);
+          if (path == 2) {
+            GenOut<df> o64;
+            eval_gen<df, true>(S.EDF, d, df(R), code, o64);
+            for (int r = 0; r < 2; r++) {
+              o.z[r] = mk3((T)(float)o64.z[r].x, (T)(float)o64.z[r].y, (T)(float)o64.z[r].z);
+              o.key[r] = o64.key[r];
+              o.sphere[r] = o64.sphere[r];
+            }
+          }
+        }
+      }
+      const uint32_t k0 = __ballot_sync(0xffffffffu, kb & 1), k1 = __ballot_sync(0xffffffffu, kb & 2);
+      uint32_t any = k0 | k1;
+      while (any) {
+        const int src = __ffs(any) - 1;
+        any &= any - 1;
+        for (int r = 0; r < 2; r++) {
+          if (!(((r == 0 ? k0 : k1) >> src) & 1u)) continue;
+          V3<T> z = mk3(__shfl_sync(0xffffffffu, o.z[r].x, src), __shfl_sync(0xffffffffu, o.z[r].y, src),
+                        __shfl_sync(0xffffffffu, o.z[r].z, src));
+          uint64_t key = __shfl_sync(0xffffffffu, (unsigned long long)o.key[r], src);
+          int sph = __shfl_sync(0xffffffffu, (int)o.sphere[r], src);
+          uint32_t gc = __shfl_sync(0xffffffffu, code, src) | ((uint32_t)r << 2);
+          if (lane == 0) {
+            const int nvc = S.nv;
+            S.vz[nvc] = z;
+            S.vkey[nvc] = key;
+            S.vfl[nvc] = sph ? VF_SPHERE : 0;
+            S.vgen[nvc] = gc;
+            S.nv = nvc + 1;
+          }
+          __syncwarp();
+        }
+      }
+    }
+    __syncwarp();
+  }
+  for (int c0 = 0; c0 < (replay ? 0 : ng) && !overflow; c0 += 32) {
     int g = c0 + lane;
     GenOut<T> o;
     uint32_t code = 0;
@@ -306,6 +390,7 @@ __device__ void node_metamesh(WarpSmem<T, C>& S, const MMArgs<T>& A, int64_t n, 
     }
     bool need64 = !IS64 && (o.unc || (o.nroot == 2 && (o.state[0] == 2 || o.state[1] == 2)));
     bool needref = !IS64 && !need64 && o.refine && o.nroot == 2 && (o.state[0] == 1 || o.state[1] == 1);
+    uint32_t kept[2] = {0u, 0u};  // roots appended this round (count-pass record)
     fb_add(A.fb, FB_GEN, need64);
     fb_add(A.fb, FB_REFINE, needref);
     if (needref) {
@@ -400,10 +485,22 @@ __device__ void node_metamesh(WarpSmem<T, C>& S, const MMArgs<T>& A, int64_t n, 
           S.vgen[nvc] = gc;
           S.nv = nvc + 1;
         }
+        kept[src >> 4] |= 1u << (2 * (src & 15) + r);
         nflags |= kf;
         __syncwarp();
       }
       if (overflow) break;
+    }
+    if (!EMIT && A.smask) {
+      const int path = need64 ? 2 : (needref ? 1 : 0);
+      const uint32_t p0 = __ballot_sync(0xffffffffu, path & 1), p1 = __ballot_sync(0xffffffffu, path & 2);
+      if (lane == 0) {
+        uint32_t* w = A.smask + t * A.smask_words + 4 * (c0 >> 5);
+        w[0] = kept[0];
+        w[1] = kept[1];
+        w[2] = p0;
+        w[3] = p1;
+      }
     }
     __syncwarp();
   }
@@ -878,7 +975,7 @@ __global__ void __launch_bounds__(128) k_metamesh(MMArgs<T> A) {
     if (first >= A.n_list) break;
     int64_t last = first + npt < A.n_list ? first + npt : A.n_list;
     for (int64_t t = first; t < last; t++) {
-      node_metamesh<T, C, EMIT>(S, A, A.nodes[t], lane);
+      node_metamesh<T, C, EMIT>(S, A, A.nodes[t], t, lane);
       __syncwarp();
     }
   }

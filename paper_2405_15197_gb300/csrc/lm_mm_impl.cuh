@@ -40,7 +40,7 @@ cudaError_t go_metamesh(bool emit, const MMArgs<T>& A, int block_warps, int grid
 template <typename T>
 cudaError_t launch_metamesh(int bucket, bool emit, const MMLaunch<T>& a, int block_warps,
                             int grid_ctas, cudaStream_t st, int* used) {
-  MMArgs<T> A;
+  MMArgs<T> A{};
   A.lat.xyz = a.xyz;
   A.lat.ends = a.ends;
   A.lat.node_R = a.node_R;
@@ -72,6 +72,8 @@ cudaError_t launch_metamesh(int bucket, bool emit, const MMLaunch<T>& a, int blo
   A.hole_ent = a.hole_ent;
   A.overflow = a.overflow;
   A.fb = a.fb;
+  A.smask = a.smask;
+  A.smask_words = a.smask ? a.smask_words : 0;
   if (A.n_list <= 0) {
     if (used) *used = 0;
     return cudaSuccess;
