@@ -7,7 +7,9 @@
 // built one strut end per lane, and per-node counts feed warp-aggregated
 // prefix sums.  The same code runs twice: a count pass (sizes only) and an
 // emit pass that writes the structure-of-arrays layout at scanned offsets
-// (Section 4.3.2's index region + data region, here CSR offsets + SoA).
+// (Section 4.3.2's index region + data region, here CSR offsets + SoA).  The
+// count pass also records each candidate's outcome, so that the emit pass
+// evaluates only the kept roots instead of screening every candidate again.
 //
 // Arithmetic is T (float for FP32 lattices, double for FP64 lattices).  For
 // FP32 every decision whose FP32 value lies inside a safety margin of its

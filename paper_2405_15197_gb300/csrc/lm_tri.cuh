@@ -725,9 +725,9 @@ __global__ void __launch_bounds__(128, 3) k_tri_thread(TriArgs<T> A, const int64
 // entries of both loops are set up lane-parallel (their arc geometry goes to
 // shared memory), the loop points are evaluated lane-parallel, B's angles are
 // moved into A's window and B is rotated to its smallest key, and then each
-// lane emits one triangle per round, finding its place in the zipper by a
-// merge-path search.  Records are staged per tile and stored with 16-byte
-// vector stores.  Angle decisions that FP32 cannot take safely (keys within
+// lane emits two consecutive triangles per round, finding its place in the
+// zipper by a merge-path search.  Records are staged per tile at their
+// destination's offset mod 16 and stored with 16-byte vector stores.  Angle decisions that FP32 cannot take safely (keys within
 // M_ZIP of each other or of the window edges) are retaken in FP64 from the
 // exact vertex generators, recomputed per comparison (they are rare).
 // x in [-n, 2n) moved into [0, n) (no integer division)
