@@ -90,13 +90,19 @@ typedef struct {
  *                   the winner (host memory) and use it
  *   block_warps   : warps per block of the meta-mesh kernel (0 = default)
  *   grid_ctas     : persistent grid size (0 = resident CTAs x SM count)
- *   nodes_per_task: nodes a warp pops from the work queue at once (0 = 1)  */
+ *   nodes_per_task: nodes a warp pops from the work queue at once (0 = 1)
+ *   arena_bytes   : device memory for the count pass to keep each node's
+ *                   meta-mesh, so that a gather into the CSR layout replaces
+ *                   the emit pass for the nodes it holds (0 = up to 30 % of
+ *                   the free memory; < 0 = none: every node is emitted);
+ *                   the result is the same either way                       */
 typedef struct {
   int32_t autotune;
   int32_t block_warps;
   int32_t grid_ctas;
   int32_t nodes_per_task;
-  int64_t reserved[4];
+  int64_t arena_bytes;
+  int64_t reserved[3];
 } lm_options;
 
 typedef struct lm_metamesh lm_metamesh;

@@ -331,24 +331,66 @@ lm_status build_impl(lm_metamesh* mm, cudaStream_t st) {
   L.overflow = overflow;
   L.fb = mm->d_fb;
   int64_t cap = std::max<int64_t>(N, 1);
-  // candidate outcomes recorded by the count pass for the emit pass (about
-  // 24 B per node of valence 8, 72 B at valence 12); without room for them
-  // the emit pass evaluates every candidate again
-  uint32_t* smask = nullptr;
-  int64_t smask_off[NB_BUCKETS] = {0}, smask_w[NB_BUCKETS] = {0};
+  // arena of the count pass (replaces the emit pass for the nodes it holds):
+  // room for about 4 vertices, 6 arcs and 12 loop entries per strut, scaled
+  // down to 30 % of the free memory (the CSR arrays are allocated beside it)
+  MMArena<T> arena{};
+  void* arena_buf = nullptr;
   {
-    int64_t tot = 0;
-    for (int b = 0; b < NB_BUCKETS; b++) {
-      const int dcap = b == 0 ? 16 : (b == 1 ? 32 : 64);
-      smask_w[b] = smask_words_for(std::min(dcap, std::max(maxdeg, 1)));
-      smask_off[b] = tot;
-      tot += (int64_t)hb[b] * smask_w[b];
-    }
-    if (tot > 0 && cudaMallocAsync((void**)&smask, sizeof(uint32_t) * (size_t)tot, st) != cudaSuccess) {
-      (void)cudaGetLastError();
-      smask = nullptr;
+    int64_t cap[5] = {4 * E + 2 * N + 1024, 6 * E + 2 * N + 1024, 12 * E + 4 * N + 1024, N + 1024, 4 * N + 1024};
+    const size_t per[5] = {3 * sizeof(T) + 16, 8 + 4 + 2 * sizeof(T), 4, 4, 4};
+    size_t fixed = 40 * (size_t)std::max<int64_t>(N, 1) + 5 * 8 + 4096, var = 0;
+    for (int q = 0; q < 5; q++) var += per[q] * (size_t)cap[q];
+    size_t fr = 0, tot = 0;
+    cudaMemGetInfo(&fr, &tot);
+    double budget = 0.3 * (double)fr;
+    if (mm->opt.arena_bytes > 0) budget = std::min(budget, (double)mm->opt.arena_bytes);
+    double f = (budget - (double)fixed) / (double)var;
+    if (f > 1.0) f = 1.0;
+    if (mm->opt.arena_bytes >= 0 && f > 0.0) {
+      for (int q = 0; q < 5; q++) cap[q] = (int64_t)((double)cap[q] * f) + 64;
+      size_t off[12], o = 0;
+      auto take = [&](size_t bytes) {
+        size_t at = o;
+        o += (bytes + 255) & ~(size_t)255;
+        return at;
+      };
+      off[0] = take(3 * sizeof(T) * (size_t)cap[0]);
+      off[1] = take(8 * (size_t)cap[0]);
+      off[2] = take(4 * (size_t)cap[0]);
+      off[3] = take(4 * (size_t)cap[0]);
+      off[4] = take(8 * (size_t)cap[1]);
+      off[5] = take(4 * (size_t)cap[1]);
+      off[6] = take(2 * sizeof(T) * (size_t)cap[1]);
+      off[7] = take(4 * (size_t)cap[2]);
+      off[8] = take(4 * (size_t)cap[3]);
+      off[9] = take(4 * (size_t)cap[4]);
+      off[10] = take(5 * 8 * (size_t)std::max<int64_t>(N, 1));
+      off[11] = take(64);
+      if (cudaMallocAsync(&arena_buf, o, st) == cudaSuccess) {
+        unsigned char* b = (unsigned char*)arena_buf;
+        arena.vz = (T*)(b + off[0]);
+        arena.vkey = (uint64_t*)(b + off[1]);
+        arena.vfl = (uint32_t*)(b + off[2]);
+        arena.vgen = (uint32_t*)(b + off[3]);
+        arena.aends = (int32_t*)(b + off[4]);
+        arena.avtx = (uint32_t*)(b + off[5]);
+        arena.aphi = (T*)(b + off[6]);
+        arena.le = (uint32_t*)(b + off[7]);
+        arena.ho = (uint32_t*)(b + off[8]);
+        arena.he = (uint32_t*)(b + off[9]);
+        arena.start = (int64_t*)(b + off[10]);
+        arena.cnt = (unsigned long long*)(b + off[11]);
+        arena.miss = (int*)(b + off[11] + 40);
+        for (int q = 0; q < 5; q++) arena.cap[q] = cap[q];
+        LM_CK(cudaMemsetAsync(b + off[11], 0, 64, st));
+      } else {
+        (void)cudaGetLastError();
+        arena_buf = nullptr;
+      }
     }
   }
+  int arena_miss = 0;
   for (int pass = 0; pass < 2; pass++) {
     if (pass == 1) {
       cudaEventRecord(ev[2], st);
@@ -371,9 +413,10 @@ lm_status build_impl(lm_metamesh* mm, cudaStream_t st) {
       LM_CK(cudaMemcpyAsync(&tot[4], mm->end_off + 2 * E, 8, cudaMemcpyDeviceToHost, st));
       int ovf = 0;
       LM_CK(cudaMemcpyAsync(&ovf, overflow, sizeof(int), cudaMemcpyDeviceToHost, st));
+      if (arena_buf) LM_CK(cudaMemcpyAsync(&arena_miss, arena.miss, sizeof(int), cudaMemcpyDeviceToHost, st));
       LM_CK(cudaStreamSynchronize(st));
       if (ovf) {
-        dfree(smask, st);
+        if (arena_buf) cudaFreeAsync(arena_buf, st);
         dfree(node_cnt, st);
         dfree(end_cnt, st);
         dfree(lists, st);
@@ -414,6 +457,12 @@ lm_status build_impl(lm_metamesh* mm, cudaStream_t st) {
       L.loop_ent = mm->loop_ent;
       L.hole_off = mm->hole_off;
       L.hole_ent = mm->hole_ent;
+      if (arena_buf) {
+        // nodes held by the arena go to their CSR ranges; the emit pass below
+        // computes only the others
+        L.arena = arena;
+        LM_CK(launch_mm_gather<T>(L, st));
+      }
     }
     if (pass == 0 && mm->opt.autotune) {
       for (int b = 0; b < NB_BUCKETS; b++) {
@@ -428,6 +477,8 @@ lm_status build_impl(lm_metamesh* mm, cudaStream_t st) {
       // the sample runs counted their FP64 steps too
       LM_CK(cudaMemsetAsync(mm->d_fb, 0, 16 * sizeof(unsigned long long), st));
     }
+    if (arena_buf) L.arena = arena;
+    if (pass == 1 && arena_buf && arena_miss == 0) break;
     for (int b = NB_BUCKETS - 1; b >= 0; b--) {
       if (hb[b] == 0) continue;
       L.nodes = lists + b * cap;
@@ -442,15 +493,12 @@ lm_status build_impl(lm_metamesh* mm, cudaStream_t st) {
       mm->tuned[b][0] = bw > 0 ? bw : 4;
       mm->tuned[b][1] = L.nodes_per_task;
       LM_CK(cudaMemsetAsync(mm->d_queue + b, 0, sizeof(int), st));
-      L.smask = smask ? smask + smask_off[b] : nullptr;
-      L.smask_words = smask_w[b];
       int used = 0;
       LM_CK(launch_metamesh<T>(b, pass == 1, L, bw, mm->opt.grid_ctas, st, &used));
-      L.smask = nullptr;
     }
   }
   cudaEventRecord(ev[3], st);
-  dfree(smask, st);
+  if (arena_buf) cudaFreeAsync(arena_buf, st);
   // statistics
   unsigned long long* dstat = nullptr;
   LM_CK(dalloc(&dstat, 4, st));

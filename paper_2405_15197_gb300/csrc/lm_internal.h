@@ -16,6 +16,27 @@ struct Node64;
 enum { NB_BUCKETS = 3 };
 __host__ __device__ inline int bucket_of(int d) { return d <= 16 ? 0 : (d <= 32 ? 1 : 2); }
 
+// Arena of the meta-mesh count pass: each node's output, stashed at
+// atomically reserved positions, so that a gather into the CSR layout
+// replaces the emit pass (nodes that do not fit go through the emit pass).
+template <typename T>
+struct MMArena {
+  T* vz;               // [cap[0]][3]
+  uint64_t* vkey;      // [cap[0]]
+  uint32_t* vfl;       // [cap[0]]
+  uint32_t* vgen;      // [cap[0]]
+  int32_t* aends;      // [cap[1]][2]
+  uint32_t* avtx;      // [cap[1]]
+  T* aphi;             // [cap[1]][2]
+  uint32_t* le;        // [cap[2]] loop entries of the node's ends, in adjacency order
+  uint32_t* ho;        // [cap[3]] hole starts, relative to the node's first hole entry
+  uint32_t* he;        // [cap[4]]
+  unsigned long long* cnt;  // [5] reserved so far
+  int64_t cap[5];
+  int64_t* start;      // [N][5] arena positions of each node's data; start[5n] < 0: not stored
+  int* miss;           // nodes not stored
+};
+
 template <typename T>
 struct MMLaunch {
   // inputs
@@ -45,22 +66,18 @@ struct MMLaunch {
   uint32_t* hole_ent;
   int* overflow;
   unsigned long long* fb;
-  uint32_t* smask;  // count-pass candidate outcomes, smask_words per listed node (NULL: none)
-  int64_t smask_words;
+  MMArena<T> arena;  // arena.start NULL: none
 };
-
-// per round of 32 candidate generators: 4 words of candidate outcomes for a
-// node of valence up to d (circle points d(d-1)/2, triple points d(d-1)(d-2)/6)
-__host__ __device__ inline int64_t smask_words_for(int d) {
-  const int64_t ng = (int64_t)d * (d - 1) / 2 + (int64_t)d * (d - 1) * (d - 2) / 6;
-  return 4 * ((ng + 31) / 32);
-}
 
 // persistent meta-mesh launch of one bucket; grid_ctas <= 0: resident CTAs
 // x SM count.  Returns the CTAs launched in *used_ctas.
 template <typename T>
 cudaError_t launch_metamesh(int bucket, bool emit, const MMLaunch<T>& a, int block_warps,
                             int grid_ctas, cudaStream_t st, int* used_ctas);
+// copy the arena-stored nodes into the CSR layout (the launch's output arrays
+// and offsets)
+template <typename T>
+cudaError_t launch_mm_gather(const MMLaunch<T>& a, cudaStream_t st);
 
 template <typename T>
 struct TriLaunch {

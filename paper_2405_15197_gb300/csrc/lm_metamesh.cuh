@@ -8,8 +8,9 @@
 // prefix sums.  The same code runs twice: a count pass (sizes only) and an
 // emit pass that writes the structure-of-arrays layout at scanned offsets
 // (Section 4.3.2's index region + data region, here CSR offsets + SoA).  The
-// count pass also records each candidate's outcome, so that the emit pass
-// evaluates only the kept roots instead of screening every candidate again.
+// count pass also keeps each node's output in an arena when it has room; a
+// gather then moves those nodes to their CSR ranges and the emit pass
+// computes only the others.
 //
 // Arithmetic is T (float for FP32 lattices, double for FP64 lattices).  For
 // FP32 every decision whose FP32 value lies inside a safety margin of its
@@ -80,14 +81,12 @@ struct MMArgs {
   uint32_t* hole_ent;
   int* overflow;
   unsigned long long* fb;  // FP64 re-decision counters (see FB_*)
-  // candidate outcomes of the count pass, smask_words per node of the list:
-  // per round of 32 generators, two words of kept-root bits (2 per
-  // generator, lanes 0-15 then 16-31) and two words holding bit 0 and bit 1
-  // of how the positions were taken (0 FP32, 1 FP64 refinement, 2
-  // double-float re-decision); the emit pass replays only the kept roots.
-  // NULL: the emit pass evaluates every candidate again.
-  uint32_t* smask;
-  int64_t smask_words;
+  // 0: count pass (sizes, and each node's output stashed in `ar` when it
+  // has room); 1: emit pass (CSR outputs of the nodes `ar` does not hold).
+  // One kernel instantiation serves both, so both write the same bits.
+  int emit;
+  // count pass: each node's output stashed in an arena (start NULL: none)
+  MMArena<T> ar;
 };
 
 // FP64 stability-step counters
@@ -186,10 +185,13 @@ __device__ int midpoint_label(const EndG<U>* E, int li, uint64_t cm, bool cs, U 
   return label;
 }
 
-template <typename T, typename C, bool EMIT>
-__device__ void node_metamesh(WarpSmem<T, C>& S, const MMArgs<T>& A, int64_t n, int64_t t, int lane) {
+template <typename T, typename C>
+__device__ void node_metamesh(WarpSmem<T, C>& S, const MMArgs<T>& A, int64_t n, int lane) {
   const LatDev<T>& L = A.lat;
+  const bool EMIT = A.emit != 0;
   constexpr bool IS64 = sizeof(T) == 8;
+  // stored in the arena by the count pass: gathered, not emitted
+  if (EMIT && A.ar.start && A.ar.start[5 * n] >= 0) return;
   const int64_t base = L.row_ptr[n];
   const int d = (int)(L.row_ptr[n + 1] - base);
   const T R = L.node_R[n];
@@ -198,6 +200,8 @@ __device__ void node_metamesh(WarpSmem<T, C>& S, const MMArgs<T>& A, int64_t n, 
     if (!EMIT && lane == 0) {
       A.node_flags[n] = 0;
       for (int q = 0; q < 4; q++) A.node_cnt[4 * n + q] = 0;
+      if (A.ar.start)
+        for (int q = 0; q < 5; q++) A.ar.start[5 * n + q] = 0;
     }
     return;
   }
@@ -281,83 +285,7 @@ __device__ void node_metamesh(WarpSmem<T, C>& S, const MMArgs<T>& A, int64_t n, 
   const int ng = np + nt;
   bool overflow = false;
   uint32_t nflags = 0;
-  const bool replay = EMIT && A.smask != nullptr;
-  if (replay) {
-    // the kept roots recorded by the count pass, compacted into a list (the
-    // loop arrays are free until the loops are built), then evaluated 32
-    // generators at a time along the path the count pass took, and appended
-    // in canonical order (they survived screening and deduplication there)
-    const uint32_t* mk = A.smask + t * A.smask_words;
-    uint32_t* SL = reinterpret_cast<uint32_t*>(S.le_ang);
-    int ns = 0;
-    for (int c0 = 0; c0 < ng; c0 += 32) {
-      const uint32_t* w = mk + 4 * (c0 >> 5);
-      const int kb = (int)((w[lane >> 4] >> (2 * (lane & 15))) & 3u);
-      const int path = (int)(((w[2] >> lane) & 1u) | (((w[3] >> lane) & 1u) << 1));
-      const uint32_t bal = __ballot_sync(0xffffffffu, kb != 0);
-      if (kb) SL[ns + __popc(bal & ((1u << lane) - 1u))] = (uint32_t)(c0 + lane) | ((uint32_t)kb << 16) | ((uint32_t)path << 18);
-      ns += __popc(bal);
-    }
-    __syncwarp();
-    for (int s0 = 0; s0 < ns; s0 += 32) {
-      const uint32_t ent = s0 + lane < ns ? SL[s0 + lane] : 0u;
-      const int kb = (int)((ent >> 16) & 3u), path = (int)((ent >> 18) & 3u);
-      GenOut<T> o;
-      o.nroot = 0;
-      o.unc = 0;
-      o.nflags = 0;
-      uint32_t code = 0;
-      if (kb) {
-        code = decode_gen((int)(ent & 0xffffu), d, np);
-        eval_gen<T, IS64>(S.E, d, R, code, o);
-      }
-      if (!IS64 && path == 1) {
-        V3<double> z64[2];
-        double t64[2];
-        gen_points64<T>(S.E, R, code, z64, t64);
-        for (int r = 0; r < 2; r++) o.z[r] = mk3((T)z64[r].x, (T)z64[r].y, (T)z64[r].z);
-      }
-      if constexpr (!IS64) {
-        if (__any_sync(0xffffffffu, path == 2)) {
-          ensure_df(S, L, n, d, lane);
-          if (path == 2) {
-            GenOut<df> o64;
-            eval_gen<df, true>(S.EDF, d, df(R), code, o64);
-            for (int r = 0; r < 2; r++) {
-              o.z[r] = mk3((T)(float)o64.z[r].x, (T)(float)o64.z[r].y, (T)(float)o64.z[r].z);
-              o.key[r] = o64.key[r];
-              o.sphere[r] = o64.sphere[r];
-            }
-          }
-        }
-      }
-      const uint32_t k0 = __ballot_sync(0xffffffffu, kb & 1), k1 = __ballot_sync(0xffffffffu, kb & 2);
-      uint32_t any = k0 | k1;
-      while (any) {
-        const int src = __ffs(any) - 1;
-        any &= any - 1;
-        for (int r = 0; r < 2; r++) {
-          if (!(((r == 0 ? k0 : k1) >> src) & 1u)) continue;
-          V3<T> z = mk3(__shfl_sync(0xffffffffu, o.z[r].x, src), __shfl_sync(0xffffffffu, o.z[r].y, src),
-                        __shfl_sync(0xffffffffu, o.z[r].z, src));
-          uint64_t key = __shfl_sync(0xffffffffu, (unsigned long long)o.key[r], src);
-          int sph = __shfl_sync(0xffffffffu, (int)o.sphere[r], src);
-          uint32_t gc = __shfl_sync(0xffffffffu, code, src) | ((uint32_t)r << 2);
-          if (lane == 0) {
-            const int nvc = S.nv;
-            S.vz[nvc] = z;
-            S.vkey[nvc] = key;
-            S.vfl[nvc] = sph ? VF_SPHERE : 0;
-            S.vgen[nvc] = gc;
-            S.nv = nvc + 1;
-          }
-          __syncwarp();
-        }
-      }
-    }
-    __syncwarp();
-  }
-  for (int c0 = 0; c0 < (replay ? 0 : ng) && !overflow; c0 += 32) {
+  for (int c0 = 0; c0 < ng && !overflow; c0 += 32) {
     int g = c0 + lane;
     GenOut<T> o;
     uint32_t code = 0;
@@ -392,7 +320,6 @@ __device__ void node_metamesh(WarpSmem<T, C>& S, const MMArgs<T>& A, int64_t n, 
     }
     bool need64 = !IS64 && (o.unc || (o.nroot == 2 && (o.state[0] == 2 || o.state[1] == 2)));
     bool needref = !IS64 && !need64 && o.refine && o.nroot == 2 && (o.state[0] == 1 || o.state[1] == 1);
-    uint32_t kept[2] = {0u, 0u};  // roots appended this round (count-pass record)
     fb_add(A.fb, FB_GEN, need64);
     fb_add(A.fb, FB_REFINE, needref);
     if (needref) {
@@ -487,22 +414,10 @@ __device__ void node_metamesh(WarpSmem<T, C>& S, const MMArgs<T>& A, int64_t n, 
           S.vgen[nvc] = gc;
           S.nv = nvc + 1;
         }
-        kept[src >> 4] |= 1u << (2 * (src & 15) + r);
         nflags |= kf;
         __syncwarp();
       }
       if (overflow) break;
-    }
-    if (!EMIT && A.smask) {
-      const int path = need64 ? 2 : (needref ? 1 : 0);
-      const uint32_t p0 = __ballot_sync(0xffffffffu, path & 1), p1 = __ballot_sync(0xffffffffu, path & 2);
-      if (lane == 0) {
-        uint32_t* w = A.smask + t * A.smask_words + 4 * (c0 >> 5);
-        w[0] = kept[0];
-        w[1] = kept[1];
-        w[2] = p0;
-        w[3] = p1;
-      }
     }
     __syncwarp();
   }
@@ -913,6 +828,7 @@ __device__ void node_metamesh(WarpSmem<T, C>& S, const MMArgs<T>& A, int64_t n, 
         A.node_flags[n] = nflags | NF_OVERFLOW;
         for (int q = 0; q < 4; q++) A.node_cnt[4 * n + q] = 0;
         atomicAdd(A.overflow, 1);
+        if (A.ar.start) A.ar.start[5 * n] = -1;
       }
       for (int li = lane; li < d; li += 32) A.end_cnt[L.adj[base + li]] = 0;
       return;
@@ -926,6 +842,48 @@ __device__ void node_metamesh(WarpSmem<T, C>& S, const MMArgs<T>& A, int64_t n, 
     }
     for (int li = lane; li < d; li += 32)
       A.end_cnt[L.adj[base + li]] = S.loop_off[li + 1] - S.loop_off[li];
+    if (A.ar.start) {
+      // stash the node's output in the arena (all five parts, or none)
+      const int nle = S.loop_off[d];
+      const long long want[5] = {S.nv, na, nle, nh, nhe};
+      long long at[5] = {0, 0, 0, 0, 0};
+      int ok = 1;
+      if (lane == 0) {
+        for (int q = 0; q < 5; q++) {
+          at[q] = want[q] ? (long long)atomicAdd(A.ar.cnt + q, (unsigned long long)want[q]) : 0;
+          if (at[q] + want[q] > A.ar.cap[q]) ok = 0;
+        }
+        for (int q = 0; q < 5; q++) A.ar.start[5 * n + q] = ok ? at[q] : -1;
+        if (!ok) atomicAdd(A.ar.miss, 1);
+      }
+      ok = __shfl_sync(0xffffffffu, ok, 0);
+      for (int q = 0; q < 5; q++) at[q] = __shfl_sync(0xffffffffu, at[q], 0);
+      if (ok) {
+        for (int v = lane; v < S.nv; v += 32) {
+          A.ar.vz[3 * (at[0] + v)] = S.vz[v].x;
+          A.ar.vz[3 * (at[0] + v) + 1] = S.vz[v].y;
+          A.ar.vz[3 * (at[0] + v) + 2] = S.vz[v].z;
+          A.ar.vkey[at[0] + v] = S.vkey[v];
+          A.ar.vfl[at[0] + v] = S.vfl[v];
+          A.ar.vgen[at[0] + v] = S.vgen[v];
+        }
+        for (int a = lane; a < na; a += 32) {
+          A.ar.aends[2 * (at[1] + a)] = S.E[S.a_owner[a]].end_id;
+          A.ar.aends[2 * (at[1] + a) + 1] = S.a_other[a] < 0 ? -1 : S.E[S.a_other[a]].end_id;
+          A.ar.avtx[at[1] + a] = (uint32_t)S.a_v0[a] | ((uint32_t)S.a_v1[a] << 8) |
+                                 ((uint32_t)S.a_owner[a] << 16) | ((uint32_t)(S.a_other[a] + 1) << 24);
+          A.ar.aphi[2 * (at[1] + a)] = S.a_phi0[a];
+          A.ar.aphi[2 * (at[1] + a) + 1] = S.a_dphi[a];
+        }
+        for (int q = lane; q < nle; q += 32)
+          A.ar.le[at[2] + q] = (uint32_t)S.le_arc[q] | ((uint32_t)S.le_rev[q] << 31);
+        for (int h = lane; h < nh; h += 32) A.ar.ho[at[3] + h] = S.h_off[h];
+        for (int q = lane; q < nhe; q += 32) {
+          uint32_t e = S.h_ent[q];
+          A.ar.he[at[4] + q] = (e & 0x7fffu) | ((e & 0x8000u) ? 0x80000000u : 0u);
+        }
+      }
+    }
     return;
   }
   if (overflow) return;
@@ -963,7 +921,7 @@ __device__ void node_metamesh(WarpSmem<T, C>& S, const MMArgs<T>& A, int64_t n, 
 
 // Persistent work-stealing launch: each warp pops tasks of nodes_per_task
 // consecutive entries of the bucket's node list from an atomic counter.
-template <typename T, typename C, bool EMIT>
+template <typename T, typename C>
 __global__ void __launch_bounds__(128) k_metamesh(MMArgs<T> A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -977,7 +935,7 @@ __global__ void __launch_bounds__(128) k_metamesh(MMArgs<T> A) {
     if (first >= A.n_list) break;
     int64_t last = first + npt < A.n_list ? first + npt : A.n_list;
     for (int64_t t = first; t < last; t++) {
-      node_metamesh<T, C, EMIT>(S, A, A.nodes[t], t, lane);
+      node_metamesh<T, C>(S, A, A.nodes[t], lane);
       __syncwarp();
     }
   }

@@ -2,4 +2,5 @@
 #include "lm_mm_impl.cuh"
 namespace lm {
 template cudaError_t launch_metamesh<float>(int, bool, const MMLaunch<float>&, int, int, cudaStream_t, int*);
+template cudaError_t launch_mm_gather<float>(const MMLaunch<float>&, cudaStream_t);
 }

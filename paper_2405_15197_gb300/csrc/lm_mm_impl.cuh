@@ -17,7 +17,7 @@ cudaError_t go_metamesh(bool emit, const MMArgs<T>& A, int block_warps, int grid
   if (block_warps <= 0) block_warps = 4;
   while (block_warps > 1 && per * block_warps > 200 * 1024) block_warps >>= 1;
   size_t smem = per * block_warps;
-  auto kern = emit ? k_metamesh<T, C, true> : k_metamesh<T, C, false>;
+  auto kern = k_metamesh<T, C>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int dev = 0, sms = 0, per_sm = 0;
@@ -72,8 +72,8 @@ cudaError_t launch_metamesh(int bucket, bool emit, const MMLaunch<T>& a, int blo
   A.hole_ent = a.hole_ent;
   A.overflow = a.overflow;
   A.fb = a.fb;
-  A.smask = a.smask;
-  A.smask_words = a.smask ? a.smask_words : 0;
+  A.emit = emit ? 1 : 0;
+  A.ar = a.arena;
   if (A.n_list <= 0) {
     if (used) *used = 0;
     return cudaSuccess;
@@ -83,6 +83,63 @@ cudaError_t launch_metamesh(int bucket, bool emit, const MMLaunch<T>& a, int blo
     case 1: return go_metamesh<T, Cap32>(emit, A, block_warps, grid_ctas, st, used);
     default: return go_metamesh<T, Cap64>(emit, A, block_warps, grid_ctas, st, used);
   }
+}
+
+// One warp per node stored in the arena: its vertices, arcs, holes and hole
+// entries move to the node's CSR ranges, its loop entries to the CSR ranges of
+// its ends (adjacency order), hole starts become absolute.
+template <typename T>
+__global__ void __launch_bounds__(256) k_mm_gather(MMLaunch<T> a) {
+  const int lane = threadIdx.x & 31;
+  const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const MMArena<T>& R = a.arena;
+  for (int64_t n = w0; n < a.n_nodes; n += nw) {
+    const int64_t* st = R.start + 5 * n;
+    if (st[0] < 0) continue;
+    const int64_t vo = a.vtx_off[n], nv = a.vtx_off[n + 1] - vo;
+    for (int64_t v = lane; v < nv; v += 32) {
+      a.vtx_z[3 * (vo + v)] = R.vz[3 * (st[0] + v)];
+      a.vtx_z[3 * (vo + v) + 1] = R.vz[3 * (st[0] + v) + 1];
+      a.vtx_z[3 * (vo + v) + 2] = R.vz[3 * (st[0] + v) + 2];
+      a.vtx_key[vo + v] = R.vkey[st[0] + v];
+      a.vtx_flags[vo + v] = R.vfl[st[0] + v];
+      a.vtx_gen[vo + v] = R.vgen[st[0] + v];
+    }
+    const int64_t ao = a.arc_off[n], na = a.arc_off[n + 1] - ao;
+    for (int64_t q = lane; q < na; q += 32) {
+      a.arc_ends[2 * (ao + q)] = R.aends[2 * (st[1] + q)];
+      a.arc_ends[2 * (ao + q) + 1] = R.aends[2 * (st[1] + q) + 1];
+      a.arc_vtx[ao + q] = R.avtx[st[1] + q];
+      a.arc_phi[2 * (ao + q)] = R.aphi[2 * (st[1] + q)];
+      a.arc_phi[2 * (ao + q) + 1] = R.aphi[2 * (st[1] + q) + 1];
+    }
+    const int64_t rb = a.row_ptr[n], d = a.row_ptr[n + 1] - rb;
+    int64_t run = st[2];
+    for (int64_t li = 0; li < d; li++) {
+      const int32_t eid = a.adj[rb + li];
+      const int64_t eo = a.end_off[eid], ne = a.end_off[eid + 1] - eo;
+      for (int64_t q = lane; q < ne; q += 32) a.loop_ent[eo + q] = R.le[run + q];
+      run += ne;
+    }
+    const int64_t ho = a.hole_off_n[n], nh = a.hole_off_n[n + 1] - ho, heo = a.hent_off_n[n];
+    for (int64_t h = lane; h < nh; h += 32) a.hole_off[ho + h] = heo + R.ho[st[3] + h];
+    const int64_t nhe = a.hent_off_n[n + 1] - heo;
+    for (int64_t q = lane; q < nhe; q += 32) a.hole_ent[heo + q] = R.he[st[4] + q];
+  }
+}
+
+template <typename T>
+cudaError_t launch_mm_gather(const MMLaunch<T>& a, cudaStream_t st) {
+  if (a.n_nodes <= 0) return cudaSuccess;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  int64_t grid = (a.n_nodes + 7) / 8;
+  if (grid > (int64_t)sms * 16) grid = (int64_t)sms * 16;
+  count_launch();
+  k_mm_gather<T><<<(unsigned)grid, 256, 0, st>>>(a);
+  return cudaGetLastError();
 }
 
 }  // namespace lm

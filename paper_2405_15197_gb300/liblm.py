@@ -41,7 +41,7 @@ class lm_lattice(ctypes.Structure):
 class lm_options(ctypes.Structure):
     _fields_ = [("autotune", ctypes.c_int32), ("block_warps", ctypes.c_int32),
                 ("grid_ctas", ctypes.c_int32), ("nodes_per_task", ctypes.c_int32),
-                ("reserved", ctypes.c_int64 * 4)]
+                ("arena_bytes", ctypes.c_int64), ("reserved", ctypes.c_int64 * 3)]
 
 
 class lm_metamesh_view(ctypes.Structure):

@@ -233,3 +233,31 @@ def test_autotuned_build_is_identical():
         assert (bw, npt) == (0, 0) or (bw in (1, 2, 4) and npt in (1, 2, 4, 8))
     assert shape[0][0] > 0
     assert liblm.lm_fp64_counts(tuned.h)[:8] == liblm.lm_fp64_counts(ref.h)[:8]
+
+
+@pytest.mark.parametrize("dtype", [np.float32, np.float64])
+def test_arena_gather_is_identical(dtype):
+    """The count pass keeps each node's meta-mesh in an arena that a gather
+    copies into the CSR layout, and nodes that do not fit go through the emit
+    pass: with no arena, a small one (most nodes emitted) and the default one
+    (every node gathered) the meta-mesh and the triangles are the same."""
+    lat = P.lattice_as(LATTICES["irregular"](), dtype)
+    xyz, ends, radii = P.to_device(lat, dtype)
+    meshes = []
+    for nbytes in (-1, 1 << 17, 0):
+        opt = liblm.lm_options()
+        opt.arena_bytes = nbytes
+        meshes.append(liblm.MetaMesh(xyz, ends, radii, options=opt))
+    ref = meshes[0].download()
+    for mm in meshes[1:]:
+        got = mm.download()
+        for key in ref:
+            assert np.array_equal(ref[key], got[key]), key
+    recs = []
+    for mm in meshes:
+        mm.tri_count(8)
+        recs.append(mm.triangulate(8).cpu().numpy())
+    for r in recs[1:]:
+        assert np.array_equal(recs[0], r)
+    for mm in meshes:
+        mm.close()
