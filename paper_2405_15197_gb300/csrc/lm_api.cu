@@ -332,58 +332,30 @@ lm_status build_impl(lm_metamesh* mm, cudaStream_t st) {
   L.fb = mm->d_fb;
   int64_t cap = std::max<int64_t>(N, 1);
   // arena of the count pass (replaces the emit pass for the nodes it holds):
-  // room for about 4 vertices, 6 arcs and 12 loop entries per strut, scaled
-  // down to 30 % of the free memory (the CSR arrays are allocated beside it)
-  MMArena<T> arena{};
+  // up to 40 % of the free memory, at most about 300 B per strut (a node's
+  // block is about 100 B per strut end); the CSR arrays are allocated beside it
+  // (if they do not fit, the arena is released and every node is emitted)
+  MMArena arena{};
   void* arena_buf = nullptr;
-  {
-    int64_t cap[5] = {4 * E + 2 * N + 1024, 6 * E + 2 * N + 1024, 12 * E + 4 * N + 1024, N + 1024, 4 * N + 1024};
-    const size_t per[5] = {3 * sizeof(T) + 16, 8 + 4 + 2 * sizeof(T), 4, 4, 4};
-    size_t fixed = 40 * (size_t)std::max<int64_t>(N, 1) + 5 * 8 + 4096, var = 0;
-    for (int q = 0; q < 5; q++) var += per[q] * (size_t)cap[q];
+  if (mm->opt.arena_bytes >= 0) {
     size_t fr = 0, tot = 0;
     cudaMemGetInfo(&fr, &tot);
-    double budget = 0.3 * (double)fr;
+    double budget = 0.4 * (double)fr;
     if (mm->opt.arena_bytes > 0) budget = std::min(budget, (double)mm->opt.arena_bytes);
-    double f = (budget - (double)fixed) / (double)var;
-    if (f > 1.0) f = 1.0;
-    if (mm->opt.arena_bytes >= 0 && f > 0.0) {
-      for (int q = 0; q < 5; q++) cap[q] = (int64_t)((double)cap[q] * f) + 64;
-      size_t off[12], o = 0;
-      auto take = [&](size_t bytes) {
-        size_t at = o;
-        o += (bytes + 255) & ~(size_t)255;
-        return at;
-      };
-      off[0] = take(3 * sizeof(T) * (size_t)cap[0]);
-      off[1] = take(8 * (size_t)cap[0]);
-      off[2] = take(4 * (size_t)cap[0]);
-      off[3] = take(4 * (size_t)cap[0]);
-      off[4] = take(8 * (size_t)cap[1]);
-      off[5] = take(4 * (size_t)cap[1]);
-      off[6] = take(2 * sizeof(T) * (size_t)cap[1]);
-      off[7] = take(4 * (size_t)cap[2]);
-      off[8] = take(4 * (size_t)cap[3]);
-      off[9] = take(4 * (size_t)cap[4]);
-      off[10] = take(5 * 8 * (size_t)std::max<int64_t>(N, 1));
-      off[11] = take(64);
-      if (cudaMallocAsync(&arena_buf, o, st) == cudaSuccess) {
+    const double fixed = 8.0 * (double)std::max<int64_t>(N, 1) + 4096.0;
+    double want = (double)(sizeof(T) == 4 ? 300 : 400) * (double)E + 64.0 * (double)N + 65536.0;
+    double capb = std::min(budget - fixed, want);
+    if (capb > 4096.0) {
+      const size_t cap_bytes = ((size_t)capb) & ~(size_t)255;
+      const size_t start_off = cap_bytes, ctr_off = start_off + (((size_t)8 * std::max<int64_t>(N, 1) + 255) & ~(size_t)255);
+      if (cudaMallocAsync(&arena_buf, ctr_off + 256, st) == cudaSuccess) {
         unsigned char* b = (unsigned char*)arena_buf;
-        arena.vz = (T*)(b + off[0]);
-        arena.vkey = (uint64_t*)(b + off[1]);
-        arena.vfl = (uint32_t*)(b + off[2]);
-        arena.vgen = (uint32_t*)(b + off[3]);
-        arena.aends = (int32_t*)(b + off[4]);
-        arena.avtx = (uint32_t*)(b + off[5]);
-        arena.aphi = (T*)(b + off[6]);
-        arena.le = (uint32_t*)(b + off[7]);
-        arena.ho = (uint32_t*)(b + off[8]);
-        arena.he = (uint32_t*)(b + off[9]);
-        arena.start = (int64_t*)(b + off[10]);
-        arena.cnt = (unsigned long long*)(b + off[11]);
-        arena.miss = (int*)(b + off[11] + 40);
-        for (int q = 0; q < 5; q++) arena.cap[q] = cap[q];
-        LM_CK(cudaMemsetAsync(b + off[11], 0, 64, st));
+        arena.buf = b;
+        arena.cap = (int64_t)cap_bytes;
+        arena.start = (int64_t*)(b + start_off);
+        arena.used = (unsigned long long*)(b + ctr_off);
+        arena.miss = (int*)(b + ctr_off + 8);
+        LM_CK(cudaMemsetAsync(b + ctr_off, 0, 64, st));
       } else {
         (void)cudaGetLastError();
         arena_buf = nullptr;
@@ -429,18 +401,42 @@ lm_status build_impl(lm_metamesh* mm, cudaStream_t st) {
       mm->HE = tot[3];
       mm->LE = tot[4];
       T *vz = nullptr, *aphi = nullptr;
-      LM_CK(dalloc(&vz, 3 * mm->V, st));
+      auto alloc_out = [&]() -> cudaError_t {
+        cudaError_t e;
+        if ((e = dalloc(&vz, 3 * mm->V, st)) != cudaSuccess) return e;
+        if ((e = dalloc(&mm->vtx_key, mm->V, st)) != cudaSuccess) return e;
+        if ((e = dalloc(&mm->vtx_flags, mm->V, st)) != cudaSuccess) return e;
+        if ((e = dalloc(&mm->vtx_gen, mm->V, st)) != cudaSuccess) return e;
+        if ((e = dalloc(&mm->arc_ends, 2 * mm->A, st)) != cudaSuccess) return e;
+        if ((e = dalloc(&mm->arc_vtx, mm->A, st)) != cudaSuccess) return e;
+        if ((e = dalloc(&aphi, 2 * mm->A, st)) != cudaSuccess) return e;
+        if ((e = dalloc(&mm->loop_ent, mm->LE, st)) != cudaSuccess) return e;
+        if ((e = dalloc(&mm->hole_off, mm->H + 1, st)) != cudaSuccess) return e;
+        return dalloc(&mm->hole_ent, mm->HE, st);
+      };
+      cudaError_t ae = alloc_out();
+      if (ae != cudaSuccess && arena_buf) {
+        // no room beside the arena: release it and emit every node
+        (void)cudaGetLastError();
+        dfree(vz, st);
+        dfree(mm->vtx_key, st);
+        dfree(mm->vtx_flags, st);
+        dfree(mm->vtx_gen, st);
+        dfree(mm->arc_ends, st);
+        dfree(mm->arc_vtx, st);
+        dfree(aphi, st);
+        dfree(mm->loop_ent, st);
+        dfree(mm->hole_off, st);
+        dfree(mm->hole_ent, st);
+        cudaFreeAsync(arena_buf, st);
+        arena_buf = nullptr;
+        arena = MMArena{};
+        L.arena = MMArena{};
+        ae = alloc_out();
+      }
+      LM_CK(ae);
       mm->vtx_z = vz;
-      LM_CK(dalloc(&mm->vtx_key, mm->V, st));
-      LM_CK(dalloc(&mm->vtx_flags, mm->V, st));
-      LM_CK(dalloc(&mm->vtx_gen, mm->V, st));
-      LM_CK(dalloc(&mm->arc_ends, 2 * mm->A, st));
-      LM_CK(dalloc(&mm->arc_vtx, mm->A, st));
-      LM_CK(dalloc(&aphi, 2 * mm->A, st));
       mm->arc_phi = aphi;
-      LM_CK(dalloc(&mm->loop_ent, mm->LE, st));
-      LM_CK(dalloc(&mm->hole_off, mm->H + 1, st));
-      LM_CK(dalloc(&mm->hole_ent, mm->HE, st));
       LM_CK(cudaMemcpyAsync(mm->hole_off + mm->H, mm->hent_off_n + N, 8, cudaMemcpyDeviceToDevice, st));
       L.vtx_off = mm->vtx_off;
       L.arc_off = mm->arc_off;

@@ -16,26 +16,52 @@ struct Node64;
 enum { NB_BUCKETS = 3 };
 __host__ __device__ inline int bucket_of(int d) { return d <= 16 ? 0 : (d <= 32 ? 1 : 2); }
 
-// Arena of the meta-mesh count pass: each node's output, stashed at
-// atomically reserved positions, so that a gather into the CSR layout
-// replaces the emit pass (nodes that do not fit go through the emit pass).
-template <typename T>
+// Arena of the meta-mesh count pass: each node's output, stashed in one
+// atomically reserved block, so that a gather into the CSR layout replaces
+// the emit pass (nodes that do not fit go through the emit pass).
 struct MMArena {
-  T* vz;               // [cap[0]][3]
-  uint64_t* vkey;      // [cap[0]]
-  uint32_t* vfl;       // [cap[0]]
-  uint32_t* vgen;      // [cap[0]]
-  int32_t* aends;      // [cap[1]][2]
-  uint32_t* avtx;      // [cap[1]]
-  T* aphi;             // [cap[1]][2]
-  uint32_t* le;        // [cap[2]] loop entries of the node's ends, in adjacency order
-  uint32_t* ho;        // [cap[3]] hole starts, relative to the node's first hole entry
-  uint32_t* he;        // [cap[4]]
-  unsigned long long* cnt;  // [5] reserved so far
-  int64_t cap[5];
-  int64_t* start;      // [N][5] arena positions of each node's data; start[5n] < 0: not stored
-  int* miss;           // nodes not stored
+  unsigned char* buf;
+  unsigned long long* used;  // bytes reserved so far
+  int64_t cap;               // bytes
+  int64_t* start;            // [N] byte offset of each node's block; < 0: not stored
+  int* miss;                 // nodes not stored
 };
+
+// Layout of one node's block (byte offsets): vertex positions, keys, flags,
+// generators; arc ends, vertices, angles; hole starts (relative to the
+// node's first hole entry); hole entries; loop entries of its ends in
+// adjacency order.
+struct ArenaBlock {
+  int64_t vz, vkey, vfl, vgen, aends, avtx, aphi, ho, he, le, bytes;
+};
+__host__ __device__ inline int64_t arena_a8(int64_t x) { return (x + 7) & ~(int64_t)7; }
+__host__ __device__ inline ArenaBlock arena_block(int64_t nv, int64_t na, int64_t nh, int64_t nhe, int64_t nle,
+                                                  int64_t tsz) {
+  ArenaBlock b;
+  int64_t o = 0;
+  b.vz = o;
+  o = arena_a8(o + 3 * tsz * nv);
+  b.vkey = o;
+  o += 8 * nv;
+  b.vfl = o;
+  o += 4 * nv;
+  b.vgen = o;
+  o += 4 * nv;
+  b.aends = o;
+  o += 8 * na;
+  b.avtx = o;
+  o = arena_a8(o + 4 * na);
+  b.aphi = o;
+  o += 2 * tsz * na;
+  b.ho = o;
+  o += 4 * nh;
+  b.he = o;
+  o += 4 * nhe;
+  b.le = o;
+  o += 4 * nle;
+  b.bytes = (o + 15) & ~(int64_t)15;
+  return b;
+}
 
 template <typename T>
 struct MMLaunch {
@@ -66,7 +92,7 @@ struct MMLaunch {
   uint32_t* hole_ent;
   int* overflow;
   unsigned long long* fb;
-  MMArena<T> arena;  // arena.start NULL: none
+  MMArena arena;  // arena.start NULL: none
 };
 
 // persistent meta-mesh launch of one bucket; grid_ctas <= 0: resident CTAs

@@ -86,7 +86,7 @@ struct MMArgs {
   // One kernel instantiation serves both, so both write the same bits.
   int emit;
   // count pass: each node's output stashed in an arena (start NULL: none)
-  MMArena<T> ar;
+  MMArena ar;
 };
 
 // FP64 stability-step counters
@@ -191,7 +191,7 @@ __device__ void node_metamesh(WarpSmem<T, C>& S, const MMArgs<T>& A, int64_t n, 
   const bool EMIT = A.emit != 0;
   constexpr bool IS64 = sizeof(T) == 8;
   // stored in the arena by the count pass: gathered, not emitted
-  if (EMIT && A.ar.start && A.ar.start[5 * n] >= 0) return;
+  if (EMIT && A.ar.start && A.ar.start[n] >= 0) return;
   const int64_t base = L.row_ptr[n];
   const int d = (int)(L.row_ptr[n + 1] - base);
   const T R = L.node_R[n];
@@ -200,8 +200,7 @@ __device__ void node_metamesh(WarpSmem<T, C>& S, const MMArgs<T>& A, int64_t n, 
     if (!EMIT && lane == 0) {
       A.node_flags[n] = 0;
       for (int q = 0; q < 4; q++) A.node_cnt[4 * n + q] = 0;
-      if (A.ar.start)
-        for (int q = 0; q < 5; q++) A.ar.start[5 * n + q] = 0;
+      if (A.ar.start) A.ar.start[n] = 0;
     }
     return;
   }
@@ -828,7 +827,7 @@ __device__ void node_metamesh(WarpSmem<T, C>& S, const MMArgs<T>& A, int64_t n, 
         A.node_flags[n] = nflags | NF_OVERFLOW;
         for (int q = 0; q < 4; q++) A.node_cnt[4 * n + q] = 0;
         atomicAdd(A.overflow, 1);
-        if (A.ar.start) A.ar.start[5 * n] = -1;
+        if (A.ar.start) A.ar.start[n] = -1;
       }
       for (int li = lane; li < d; li += 32) A.end_cnt[L.adj[base + li]] = 0;
       return;
@@ -843,45 +842,53 @@ __device__ void node_metamesh(WarpSmem<T, C>& S, const MMArgs<T>& A, int64_t n, 
     for (int li = lane; li < d; li += 32)
       A.end_cnt[L.adj[base + li]] = S.loop_off[li + 1] - S.loop_off[li];
     if (A.ar.start) {
-      // stash the node's output in the arena (all five parts, or none)
+      // stash the node's output in the arena (one block, or not at all)
       const int nle = S.loop_off[d];
-      const long long want[5] = {S.nv, na, nle, nh, nhe};
-      long long at[5] = {0, 0, 0, 0, 0};
-      int ok = 1;
+      const ArenaBlock B = arena_block(S.nv, na, nh, nhe, nle, sizeof(T));
+      long long at = 0;
       if (lane == 0) {
-        for (int q = 0; q < 5; q++) {
-          at[q] = want[q] ? (long long)atomicAdd(A.ar.cnt + q, (unsigned long long)want[q]) : 0;
-          if (at[q] + want[q] > A.ar.cap[q]) ok = 0;
+        at = (long long)atomicAdd(A.ar.used, (unsigned long long)B.bytes);
+        if (at + B.bytes > A.ar.cap) {
+          at = -1;
+          atomicAdd(A.ar.miss, 1);
         }
-        for (int q = 0; q < 5; q++) A.ar.start[5 * n + q] = ok ? at[q] : -1;
-        if (!ok) atomicAdd(A.ar.miss, 1);
+        A.ar.start[n] = at;
       }
-      ok = __shfl_sync(0xffffffffu, ok, 0);
-      for (int q = 0; q < 5; q++) at[q] = __shfl_sync(0xffffffffu, at[q], 0);
-      if (ok) {
+      at = __shfl_sync(0xffffffffu, at, 0);
+      if (at >= 0) {
+        unsigned char* blk = A.ar.buf + at;
+        T* vz = reinterpret_cast<T*>(blk + B.vz);
+        uint64_t* vkey = reinterpret_cast<uint64_t*>(blk + B.vkey);
+        uint32_t* vfl = reinterpret_cast<uint32_t*>(blk + B.vfl);
+        uint32_t* vgen = reinterpret_cast<uint32_t*>(blk + B.vgen);
         for (int v = lane; v < S.nv; v += 32) {
-          A.ar.vz[3 * (at[0] + v)] = S.vz[v].x;
-          A.ar.vz[3 * (at[0] + v) + 1] = S.vz[v].y;
-          A.ar.vz[3 * (at[0] + v) + 2] = S.vz[v].z;
-          A.ar.vkey[at[0] + v] = S.vkey[v];
-          A.ar.vfl[at[0] + v] = S.vfl[v];
-          A.ar.vgen[at[0] + v] = S.vgen[v];
+          vz[3 * v] = S.vz[v].x;
+          vz[3 * v + 1] = S.vz[v].y;
+          vz[3 * v + 2] = S.vz[v].z;
+          vkey[v] = S.vkey[v];
+          vfl[v] = S.vfl[v];
+          vgen[v] = S.vgen[v];
         }
+        int32_t* aends = reinterpret_cast<int32_t*>(blk + B.aends);
+        uint32_t* avtx = reinterpret_cast<uint32_t*>(blk + B.avtx);
+        T* aphi = reinterpret_cast<T*>(blk + B.aphi);
         for (int a = lane; a < na; a += 32) {
-          A.ar.aends[2 * (at[1] + a)] = S.E[S.a_owner[a]].end_id;
-          A.ar.aends[2 * (at[1] + a) + 1] = S.a_other[a] < 0 ? -1 : S.E[S.a_other[a]].end_id;
-          A.ar.avtx[at[1] + a] = (uint32_t)S.a_v0[a] | ((uint32_t)S.a_v1[a] << 8) |
-                                 ((uint32_t)S.a_owner[a] << 16) | ((uint32_t)(S.a_other[a] + 1) << 24);
-          A.ar.aphi[2 * (at[1] + a)] = S.a_phi0[a];
-          A.ar.aphi[2 * (at[1] + a) + 1] = S.a_dphi[a];
+          aends[2 * a] = S.E[S.a_owner[a]].end_id;
+          aends[2 * a + 1] = S.a_other[a] < 0 ? -1 : S.E[S.a_other[a]].end_id;
+          avtx[a] = (uint32_t)S.a_v0[a] | ((uint32_t)S.a_v1[a] << 8) | ((uint32_t)S.a_owner[a] << 16) |
+                    ((uint32_t)(S.a_other[a] + 1) << 24);
+          aphi[2 * a] = S.a_phi0[a];
+          aphi[2 * a + 1] = S.a_dphi[a];
         }
-        for (int q = lane; q < nle; q += 32)
-          A.ar.le[at[2] + q] = (uint32_t)S.le_arc[q] | ((uint32_t)S.le_rev[q] << 31);
-        for (int h = lane; h < nh; h += 32) A.ar.ho[at[3] + h] = S.h_off[h];
+        uint32_t* ho = reinterpret_cast<uint32_t*>(blk + B.ho);
+        uint32_t* he = reinterpret_cast<uint32_t*>(blk + B.he);
+        uint32_t* le = reinterpret_cast<uint32_t*>(blk + B.le);
+        for (int h = lane; h < nh; h += 32) ho[h] = S.h_off[h];
         for (int q = lane; q < nhe; q += 32) {
           uint32_t e = S.h_ent[q];
-          A.ar.he[at[4] + q] = (e & 0x7fffu) | ((e & 0x8000u) ? 0x80000000u : 0u);
+          he[q] = (e & 0x7fffu) | ((e & 0x8000u) ? 0x80000000u : 0u);
         }
+        for (int q = lane; q < nle; q += 32) le[q] = (uint32_t)S.le_arc[q] | ((uint32_t)S.le_rev[q] << 31);
       }
     }
     return;

@@ -93,39 +93,46 @@ __global__ void __launch_bounds__(256) k_mm_gather(MMLaunch<T> a) {
   const int lane = threadIdx.x & 31;
   const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  const MMArena<T>& R = a.arena;
   for (int64_t n = w0; n < a.n_nodes; n += nw) {
-    const int64_t* st = R.start + 5 * n;
-    if (st[0] < 0) continue;
+    const int64_t at = a.arena.start[n];
+    if (at < 0) continue;
     const int64_t vo = a.vtx_off[n], nv = a.vtx_off[n + 1] - vo;
-    for (int64_t v = lane; v < nv; v += 32) {
-      a.vtx_z[3 * (vo + v)] = R.vz[3 * (st[0] + v)];
-      a.vtx_z[3 * (vo + v) + 1] = R.vz[3 * (st[0] + v) + 1];
-      a.vtx_z[3 * (vo + v) + 2] = R.vz[3 * (st[0] + v) + 2];
-      a.vtx_key[vo + v] = R.vkey[st[0] + v];
-      a.vtx_flags[vo + v] = R.vfl[st[0] + v];
-      a.vtx_gen[vo + v] = R.vgen[st[0] + v];
-    }
     const int64_t ao = a.arc_off[n], na = a.arc_off[n + 1] - ao;
-    for (int64_t q = lane; q < na; q += 32) {
-      a.arc_ends[2 * (ao + q)] = R.aends[2 * (st[1] + q)];
-      a.arc_ends[2 * (ao + q) + 1] = R.aends[2 * (st[1] + q) + 1];
-      a.arc_vtx[ao + q] = R.avtx[st[1] + q];
-      a.arc_phi[2 * (ao + q)] = R.aphi[2 * (st[1] + q)];
-      a.arc_phi[2 * (ao + q) + 1] = R.aphi[2 * (st[1] + q) + 1];
+    const int64_t ho = a.hole_off_n[n], nh = a.hole_off_n[n + 1] - ho;
+    const int64_t heo = a.hent_off_n[n], nhe = a.hent_off_n[n + 1] - heo;
+    const ArenaBlock B = arena_block(nv, na, nh, nhe, 0, sizeof(T));
+    const unsigned char* blk = a.arena.buf + at;
+    const T* vz = reinterpret_cast<const T*>(blk + B.vz);
+    const uint64_t* vkey = reinterpret_cast<const uint64_t*>(blk + B.vkey);
+    const uint32_t* vfl = reinterpret_cast<const uint32_t*>(blk + B.vfl);
+    const uint32_t* vgen = reinterpret_cast<const uint32_t*>(blk + B.vgen);
+    for (int64_t q = lane; q < 3 * nv; q += 32) a.vtx_z[3 * vo + q] = vz[q];
+    for (int64_t v = lane; v < nv; v += 32) {
+      a.vtx_key[vo + v] = vkey[v];
+      a.vtx_flags[vo + v] = vfl[v];
+      a.vtx_gen[vo + v] = vgen[v];
     }
+    const int32_t* aends = reinterpret_cast<const int32_t*>(blk + B.aends);
+    const uint32_t* avtx = reinterpret_cast<const uint32_t*>(blk + B.avtx);
+    const T* aphi = reinterpret_cast<const T*>(blk + B.aphi);
+    for (int64_t q = lane; q < 2 * na; q += 32) {
+      a.arc_ends[2 * ao + q] = aends[q];
+      a.arc_phi[2 * ao + q] = aphi[q];
+    }
+    for (int64_t q = lane; q < na; q += 32) a.arc_vtx[ao + q] = avtx[q];
+    const uint32_t* hos = reinterpret_cast<const uint32_t*>(blk + B.ho);
+    const uint32_t* hes = reinterpret_cast<const uint32_t*>(blk + B.he);
+    for (int64_t h = lane; h < nh; h += 32) a.hole_off[ho + h] = heo + hos[h];
+    for (int64_t q = lane; q < nhe; q += 32) a.hole_ent[heo + q] = hes[q];
+    const uint32_t* le = reinterpret_cast<const uint32_t*>(blk + B.le);
     const int64_t rb = a.row_ptr[n], d = a.row_ptr[n + 1] - rb;
-    int64_t run = st[2];
+    int64_t run = 0;
     for (int64_t li = 0; li < d; li++) {
       const int32_t eid = a.adj[rb + li];
       const int64_t eo = a.end_off[eid], ne = a.end_off[eid + 1] - eo;
-      for (int64_t q = lane; q < ne; q += 32) a.loop_ent[eo + q] = R.le[run + q];
+      for (int64_t q = lane; q < ne; q += 32) a.loop_ent[eo + q] = le[run + q];
       run += ne;
     }
-    const int64_t ho = a.hole_off_n[n], nh = a.hole_off_n[n + 1] - ho, heo = a.hent_off_n[n];
-    for (int64_t h = lane; h < nh; h += 32) a.hole_off[ho + h] = heo + R.ho[st[3] + h];
-    const int64_t nhe = a.hent_off_n[n + 1] - heo;
-    for (int64_t q = lane; q < nhe; q += 32) a.hole_ent[heo + q] = R.he[st[4] + q];
   }
 }
 
