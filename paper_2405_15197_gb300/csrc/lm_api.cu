@@ -332,19 +332,23 @@ lm_status build_impl(lm_metamesh* mm, cudaStream_t st) {
   L.fb = mm->d_fb;
   int64_t cap = std::max<int64_t>(N, 1);
   // arena of the count pass (replaces the emit pass for the nodes it holds):
-  // up to 40 % of the free memory, at most about 300 B per strut (a node's
-  // block is about 100 B per strut end); the CSR arrays are allocated beside it
-  // (if they do not fit, the arena is released and every node is emitted)
+  // up to 35 % of the free memory left beside the CSR offsets, at most about
+  // 300 B per strut (a node's block is about 100 B per strut end); the CSR
+  // arrays are allocated beside it (if they do not fit, the arena is released
+  // and every node is emitted)
   MMArena arena{};
   void* arena_buf = nullptr;
-  if (mm->opt.arena_bytes >= 0) {
+  const double arena_want = (double)(sizeof(T) == 4 ? 300 : 400) * (double)E + 64.0 * (double)N + 65536.0;
+  auto arena_room = [&]() {
     size_t fr = 0, tot = 0;
     cudaMemGetInfo(&fr, &tot);
-    double budget = 0.4 * (double)fr;
+    const double offs = 8.0 * (4.0 * (double)(N + 1) + 2.0 * (double)E + 1.0);
+    double budget = 0.35 * std::max(0.0, (double)fr - offs);
     if (mm->opt.arena_bytes > 0) budget = std::min(budget, (double)mm->opt.arena_bytes);
-    const double fixed = 8.0 * (double)std::max<int64_t>(N, 1) + 4096.0;
-    double want = (double)(sizeof(T) == 4 ? 300 : 400) * (double)E + 64.0 * (double)N + 65536.0;
-    double capb = std::min(budget - fixed, want);
+    return budget - 8.0 * (double)std::max<int64_t>(N, 1) - 4096.0;
+  };
+  if (mm->opt.arena_bytes >= 0) {
+    double capb = std::min(arena_room(), arena_want);
     if (capb > 4096.0) {
       const size_t cap_bytes = ((size_t)capb) & ~(size_t)255;
       const size_t start_off = cap_bytes, ctr_off = start_off + (((size_t)8 * std::max<int64_t>(N, 1) + 255) & ~(size_t)255);
