@@ -38,7 +38,15 @@ WORKLOADS = {
                 "desc": "octet-truss 24^3 cells (profiling case), k=8 and k=32"},
     "bcc500": {"kind": "bcc", "n": 500, "ks": (8, 32), "R": 0.05,
                "desc": "BCC 500^3 cells, 1.0e9 struts, R=0.05, k=8 and k=32"},
+    "bcc40": {"kind": "bcc", "n": 40, "ks": (8, 32), "R": 0.05,
+              "desc": "BCC 40^3 cells (profiling case of the 500^3 lattice), R=0.05, k=8 and k=32"},
 }
+
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum of the stitching,
+# FP64 and hole-fan launches) per triangle of the k = 32 emit, measured with
+# ncu on the profiling case of each lattice family (octet 24^3, BCC 40^3);
+# the benchmark scales it by the triangles of its own emit
+TRAFFIC_PER_TRI_K32 = {"octet": 52.0, "bcc": 51.1}
 
 
 def load_peaks():
@@ -248,7 +256,9 @@ def bench_gpu(args):
     tri_ms = phase[f"tri_k{k_big}_ms"]
     tri_bytes = 50.0 * totals[ks.index(k_big)]
     roof_tri = {"bound": "hbm", "achieved": tri_bytes / (tri_ms / 1e3) / 1e9, "peak": hbm, "unit": "GB/s",
-                "frac": tri_bytes / (tri_ms / 1e3) / 1e9 / hbm, "traffic": None,
+                "frac": tri_bytes / (tri_ms / 1e3) / 1e9 / hbm,
+                "traffic": (TRAFFIC_PER_TRI_K32[wl["kind"]] * totals[ks.index(k_big)]
+                            if k_big == 32 and wl["kind"] in TRAFFIC_PER_TRI_K32 else None),
                 "kernel": f"triangulation emit at k={k_big} (k_tri_tiles FP32 pass + FP64 pass + k_tri_holes)",
                 "algorithmic_bytes": "50 B written per triangle", "peak_kind": f"{peak_kind} hbm_gbs"}
     # end-to-end: pinned host inputs -> device -> meta-mesh -> triangles streamed to a pinned ring
