@@ -885,7 +885,7 @@ __device__ __noinline__ int segments64_cached(const TriArgs<T>& A, const EndG<do
 constexpr int SEG_UNC = 1 << 29;
 template <typename T, bool EXACT>
 __device__ __forceinline__ int tile_entry_setup_impl(const TriArgs<T>& A, int64_t node, int32_t eid, int64_t qi,
-                                                     TileEntry<T>* dst, const EndG<double>* E64 = nullptr,
+                                                     TileEntry<T>* dst, V3<T>& z0, const EndG<double>* E64 = nullptr,
                                                      int li = 0) {
   const LatDev<T>& L = A.lat;
   const int64_t ao = A.arc_off[node], rb = L.row_ptr[node], vo = A.vtx_off[node];
@@ -898,6 +898,9 @@ __device__ __forceinline__ int tile_entry_setup_impl(const TriArgs<T>& A, int64_
   en.pad0 = en.pad1 = 0;
   uint32_t av = A.arc_vtx[en.ga];
   int o = (av >> 16) & 255, ot = (int)((av >> 24) & 255) - 1;
+  // the entry's first vertex in loop order (its first point)
+  const int64_t vi = vo + (en.rev ? ((av >> 8) & 255) : (av & 255));
+  z0 = mk3(A.vtx_z[3 * vi], A.vtx_z[3 * vi + 1], A.vtx_z[3 * vi + 2]);
   en.phi0 = A.arc_phi[2 * en.ga];
   en.dphi = A.arc_phi[2 * en.ga + 1];
   bool unc;
@@ -915,10 +918,8 @@ __device__ __forceinline__ int tile_entry_setup_impl(const TriArgs<T>& A, int64_
   if (en.own && !en.rev) {
     en.psi = en.phi0;
   } else {
-    int64_t vi = vo + (en.rev ? ((av >> 8) & 255) : (av & 255));
-    V3<T> zs = mk3(A.vtx_z[3 * vi], A.vtx_z[3 * vi + 1], A.vtx_z[3 * vi + 2]);
     EndG<T> own = make_end<T, T>(L, node, eid);
-    T ang = raw_angle(own, zs);
+    T ang = raw_angle(own, z0);
     if (!IS64 && fabs(ang + T(PHI_CUT)) <= T(M_ANG)) {
       if (!EXACT) return -1;
       ang = (T)norm_angle(raw_angle(E64[li], gen_point<double>(E64, (double)R, A.vtx_gen[vi])));
@@ -933,8 +934,8 @@ __device__ __forceinline__ int tile_entry_setup_impl(const TriArgs<T>& A, int64_
 
 template <typename T>
 __device__ __noinline__ int tile_entry_setup_exact(const TriArgs<T>& A, int64_t node, int32_t eid, int64_t qi,
-                                                   TileEntry<T>* dst, const EndG<double>* E64, int li) {
-  return tile_entry_setup_impl<T, true>(A, node, eid, qi, dst, E64, li);
+                                                   TileEntry<T>* dst, V3<T>& z0, const EndG<double>* E64, int li) {
+  return tile_entry_setup_impl<T, true>(A, node, eid, qi, dst, z0, E64, li);
 }
 
 template <typename T, int TL>
@@ -1035,6 +1036,7 @@ __device__ __forceinline__ bool tile_strut(const TriArgs<T>& A, const TileSmem<T
     for (int c0 = 0; c0 < net && ok; c0 += TL) {
       int q = c0 + tl;
       int Nq = 0, X = 0, qq = q;
+      V3<T> z0 = mk3(T(0), T(0), T(0));
       if (q >= neA0) {
         X = 1;
         qq = q - neA0;
@@ -1044,8 +1046,8 @@ __device__ __forceinline__ bool tile_strut(const TriArgs<T>& A, const TileSmem<T
         int32_t eid = X == 0 ? eA : eB;
         int64_t qi = (X == 0 ? qa : qb) + qq;
         if (FP64_STEPS)
-          Nq = tile_entry_setup_exact<T>(A, node, eid, qi, ENT + X * A.emax + qq, S.E64 + X * A.dmax, H->li[X]);
-        else Nq = tile_entry_setup_impl<T, false>(A, node, eid, qi, ENT + X * A.emax + qq);
+          Nq = tile_entry_setup_exact<T>(A, node, eid, qi, ENT + X * A.emax + qq, z0, S.E64 + X * A.dmax, H->li[X]);
+        else Nq = tile_entry_setup_impl<T, false>(A, node, eid, qi, ENT + X * A.emax + qq, z0);
       }
       if (__any_sync(m, Nq < 0)) {
         tfb_add(A.fb, 12, tl == 0, m);
@@ -1066,7 +1068,15 @@ __device__ __forceinline__ bool tile_strut(const TriArgs<T>& A, const TileSmem<T
       // separately (loop B's entries follow loop A's in lane order)
       int nA_ = X == 0 ? Nq : 0, nB_ = X == 1 ? Nq : 0;
       int pa = tile_excl_scan<TL>(nA_, tl, m), pb = tile_excl_scan<TL>(nB_, tl, m);
-      if (q < net) ENT[X * A.emax + qq].pre = X == 0 ? cnt[0] + pa : cnt[1] + pb;
+      if (q < net) {
+        // the entry's first point is its first vertex (the points pass skips it)
+        const int pre = X == 0 ? cnt[0] + pa : cnt[1] + pb;
+        ENT[X * A.emax + qq].pre = pre;
+        if (pre < A.pmax) {
+          Z[X * A.pmax + pre] = z0;
+          TH[X * A.pmax + pre] = ENT[X * A.emax + qq].psi;
+        }
+      }
       cnt[0] += __shfl_sync(m, pa + nA_, TL - 1, TL);
       cnt[1] += __shfl_sync(m, pb + nB_, TL - 1, TL);
     }
@@ -1084,6 +1094,19 @@ __device__ __forceinline__ bool tile_strut(const TriArgs<T>& A, const TileSmem<T
         const int neX = uncX == 0 ? neA0 : neB0;
         for (int q = uncQ + 1 + tl; q < neX; q += TL) ENT[uncX * A.emax + q].pre += diff;
         if (tl == 0) eu->N += diff;
+        __syncwarp(m);
+        if (tl == 0) {
+          // the first points of the later entries move by diff (in the order
+          // that reads each before it is overwritten)
+          for (int r = 0; r < neX - uncQ - 1; r++) {
+            const int q = diff > 0 ? neX - 1 - r : uncQ + 1 + r;
+            const int pn = ENT[uncX * A.emax + q].pre, po = pn - diff;
+            if (pn >= 0 && pn < A.pmax && po >= 0 && po < A.pmax) {
+              Z[uncX * A.pmax + pn] = Z[uncX * A.pmax + po];
+              TH[uncX * A.pmax + pn] = TH[uncX * A.pmax + po];
+            }
+          }
+        }
         cnt[uncX] += diff;
       }
     }
@@ -1115,20 +1138,12 @@ __device__ __forceinline__ bool tile_strut(const TriArgs<T>& A, const TileSmem<T
       const TileEntry<T>& en = ents[tile_entry_of(ents, ne, p)];
       int sidx = p - en.pre;
       int mm = en.rev ? en.N - sidx : sidx;
-      V3<T> zz;
-      T th;
-      if (sidx == 0) {
-        uint32_t av = A.arc_vtx[en.ga];
-        int64_t vi = A.vtx_off[node] + (mm == 0 ? (av & 255) : ((av >> 8) & 255));
-        zz = mk3(A.vtx_z[3 * vi], A.vtx_z[3 * vi + 1], A.vtx_z[3 * vi + 2]);
-        th = en.psi;
-      } else {
+      if (sidx != 0) {
         T phi = en.phi0 + en.dphi * (T)mm / (T)en.N;
-        zz = geo_point(en.g, phi);
-        th = en.own ? phi : en.psi + wrap_from(raw_angle(own, zz) - en.psi, T(-ETA_PHI));
+        V3<T> zz = geo_point(en.g, phi);
+        Z[X * A.pmax + p] = zz;
+        TH[X * A.pmax + p] = en.own ? phi : en.psi + wrap_from(raw_angle(own, zz) - en.psi, T(-ETA_PHI));
       }
-      Z[X * A.pmax + p] = zz;
-      TH[X * A.pmax + p] = th;
       if (FP64_STEPS) FL[X * A.pmax + p] = 0;
       if constexpr (ADJ) {
         uint32_t av = A.arc_vtx[en.ga];
