@@ -687,6 +687,36 @@ __device__ __forceinline__ V3<T> geo_point(const ArcGeo<T>& g, T phi) {
   return g.u * (g.Rs + t * g.co) + r * (g.Rco - t * g.s);
 }
 
+// Exactly rounded operations: no contraction or reassociation is left to the
+// compiler, so an expression gives the same bits wherever it is inlined.
+__device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float div_rn(float a, float b) { return __fdiv_rn(a, b); }
+__device__ __forceinline__ double div_rn(double a, double b) { return __ddiv_rn(a, b); }
+
+// Subdivision point m of N of an arc (node-relative; Section 5: uniform in the
+// owner's angle, phi = phi0 + dphi m / N, also returned) with every operation
+// explicitly rounded: the kernels that emit a shared point (the two struts of
+// an elliptical arc, a strut and a hole fan of a circular arc) write the same
+// bits.
+template <typename T>
+__device__ __forceinline__ V3<T> arc_point_rn(const ArcGeo<T>& g, T phi0, T dphi, int m, int N, T& phi) {
+  phi = add_rn(phi0, div_rn(mul_rn(dphi, (T)m), (T)N));
+  T c, s;
+  lm_sincos(phi, &s, &c);
+  const T t = div_rn(fma_rn(g.n2, s, fma_rn(g.n1, c, g.n0)), fma_rn(g.d2, s, fma_rn(g.d1, c, g.d0)));
+  const T a = fma_rn(t, g.co, g.Rs), b = fma_rn(-t, g.s, g.Rco);
+  V3<T> z;
+  z.x = fma_rn(fma_rn(g.e2.x, s, mul_rn(g.e1.x, c)), b, mul_rn(g.u.x, a));
+  z.y = fma_rn(fma_rn(g.e2.y, s, mul_rn(g.e1.y, c)), b, mul_rn(g.u.y, a));
+  z.z = fma_rn(fma_rn(g.e2.z, s, mul_rn(g.e1.z, c)), b, mul_rn(g.u.z, a));
+  return z;
+}
+
 // Node-relative point of vertex generator `gcode` from the node's strut ends
 // (no screening: the vertex is known to be kept).  Circle point: unit n with
 // u_i.n = s_i and u_j.n = s_j, times R.  Triple point: line P_ij n P_ik cut

@@ -217,6 +217,76 @@ __global__ void __launch_bounds__(256) k_tri_count(TriArgs<T> A, Node64* scratch
   }
 }
 
+// Geometry of the arc owned by strut end `oid` (cut by the plane of `otid`, or
+// circular when otid < 0) at a node, with every operation explicitly rounded:
+// every kernel that subdivides the arc starts from the same bits (the same
+// arithmetic as make_end and arc_geo, in a fixed order).
+template <typename T>
+__device__ __forceinline__ T dot_rn(V3<T> a, V3<T> b) {
+  return fma_rn(a.z, b.z, fma_rn(a.y, b.y, mul_rn(a.x, b.x)));
+}
+template <typename T>
+__device__ __forceinline__ V3<T> cross_rn(V3<T> a, V3<T> b) {
+  return mk3(fma_rn(a.y, b.z, -mul_rn(a.z, b.y)), fma_rn(a.z, b.x, -mul_rn(a.x, b.z)),
+             fma_rn(a.x, b.y, -mul_rn(a.y, b.x)));
+}
+template <typename T>
+__device__ __forceinline__ V3<T> scale_rn(V3<T> a, T k) {
+  return mk3(mul_rn(a.x, k), mul_rn(a.y, k), mul_rn(a.z, k));
+}
+template <typename T>
+struct EndRn {
+  V3<T> u, e1, e2;
+  T s, co;
+};
+template <typename T>
+__device__ __forceinline__ EndRn<T> end_rn(const LatDev<T>& L, int64_t node, int32_t end_id) {
+  const int32_t strut = end_id >> 1;
+  const int32_t a = L.ends[2 * (int64_t)strut], b = L.ends[2 * (int64_t)strut + 1];
+  const int32_t far = (end_id & 1) ? a : b, lo = a < b ? a : b, hi = a < b ? b : a;
+  const V3<T> d = mk3(add_rn(L.xyz[3 * (int64_t)hi], -L.xyz[3 * (int64_t)lo]),
+                      add_rn(L.xyz[3 * (int64_t)hi + 1], -L.xyz[3 * (int64_t)lo + 1]),
+                      add_rn(L.xyz[3 * (int64_t)hi + 2], -L.xyz[3 * (int64_t)lo + 2]));
+  const T il = div_rn(T(1), lm_sqrt(dot_rn(d, d)));
+  const V3<T> ue = scale_rn(d, il);
+  EndRn<T> e;
+  e.u = node == lo ? ue : scale_rn(ue, T(-1));
+  e.s = mul_rn(add_rn(L.node_R[node], -L.node_R[far]), il);
+  e.co = lm_sqrt(fma_rn(-e.s, e.s, T(1)));
+  const int ax = frame_axis(L, lo, hi);
+  const V3<T> c1 = cross_rn(ue, mk3<T>(ax == 0, ax == 1, ax == 2));
+  e.e1 = scale_rn(c1, div_rn(T(1), lm_sqrt(dot_rn(c1, c1))));
+  e.e2 = cross_rn(ue, e.e1);
+  return e;
+}
+template <typename T>
+__device__ __forceinline__ ArcGeo<T> node_arc_geo(const LatDev<T>& L, int64_t node, int32_t oid, int32_t otid, T R) {
+  const EndRn<T> o = end_rn<T>(L, node, oid);
+  ArcGeo<T> g;
+  g.u = o.u;
+  g.e1 = o.e1;
+  g.e2 = o.e2;
+  g.Rs = mul_rn(R, o.s);
+  g.Rco = mul_rn(R, o.co);
+  g.co = o.co;
+  g.s = o.s;
+  if (otid >= 0) {
+    const EndRn<T> t = end_rn<T>(L, node, otid);
+    const T cij = dot_rn(o.u, t.u), a1 = dot_rn(t.u, o.e1), a2 = dot_rn(t.u, o.e2);
+    g.n0 = mul_rn(R, fma_rn(o.s, cij, -t.s));
+    g.n1 = mul_rn(g.Rco, a1);
+    g.n2 = mul_rn(g.Rco, a2);
+    g.d0 = fma_rn(-o.co, cij, t.co);
+    g.d1 = mul_rn(o.s, a1);
+    g.d2 = mul_rn(o.s, a2);
+  } else {
+    g.n0 = g.n1 = g.n2 = T(0);
+    g.d0 = T(1);
+    g.d1 = g.d2 = T(0);
+  }
+  return g;
+}
+
 // ------------------------------------------------------- strut stitching
 // Per-warp shared workspace for one strut (dynamic size from pmax, emax).
 template <typename T>
@@ -242,8 +312,8 @@ __device__ __forceinline__ void entry_point(const TriArgs<T>& A, int64_t node, c
     if (s != 0 && own) th = e.psi + wrap_from(raw_angle(*own, z) - e.psi, T(-ETA_PHI));
     return;
   }
-  T phi = e.phi0 + e.dphi * (T)m / (T)e.N;
-  z = geo_point(e.g, phi);
+  T phi;
+  z = arc_point_rn(e.g, e.phi0, e.dphi, m, e.N, phi);
   if (e.own) th = phi;
   else if (own) th = e.psi + wrap_from(raw_angle(*own, z) - e.psi, T(-ETA_PHI));
   else th = T(0);
@@ -398,13 +468,7 @@ __device__ __noinline__ void it_load(const TriArgs<T>& A, LoopIt<T>& it, int q) 
   it.N = it_segments(A, it, it.ga);
   int64_t b = L.row_ptr[it.node];
   int32_t oid = L.adj[b + o];
-  EndG<T> Eo = make_end<T, T>(L, it.node, oid);
-  if (ot >= 0) {
-    EndG<T> Et = make_end<T, T>(L, it.node, L.adj[b + ot]);
-    *it.g = arc_geo(Eo, &Et, it.R);
-  } else {
-    *it.g = arc_geo<T>(Eo, nullptr, it.R);
-  }
+  *it.g = node_arc_geo<T>(L, it.node, oid, ot >= 0 ? L.adj[b + ot] : -1, it.R);
   it.own = (oid == it.eid);
   if (it.own && !it.rev) {
     it.psi = it.phi0;
@@ -448,8 +512,8 @@ __device__ __forceinline__ void it_point(const TriArgs<T>& A, const LoopIt<T>& i
     th = it.psi;
     return;
   }
-  T phi = it.phi0 + it.dphi * (T)m / (T)it.N;
-  z = geo_point(*it.g, phi);
+  T phi;
+  z = arc_point_rn(*it.g, it.phi0, it.dphi, m, it.N, phi);
   if (it.own) th = phi;
   else th = it.psi + wrap_from(lm_atan2(dot(z, it.me2), dot(z, it.me1)) - it.psi, T(-ETA_PHI));
 }
@@ -907,13 +971,7 @@ __device__ __forceinline__ int tile_entry_setup_impl(const TriArgs<T>& A, int64_
   int Nq = seg_count<T>(en.dphi, A.k, unc);
   if (EXACT && unc) Nq = segments64_cached<T>(A, E64, node, en.ga);
   int32_t oid = L.adj[rb + o];
-  EndG<T> Eo = make_end<T, T>(L, node, oid);
-  if (ot >= 0) {
-    EndG<T> Et = make_end<T, T>(L, node, L.adj[rb + ot]);
-    en.g = arc_geo(Eo, &Et, R);
-  } else {
-    en.g = arc_geo<T>(Eo, nullptr, R);
-  }
+  en.g = node_arc_geo<T>(L, node, oid, ot >= 0 ? L.adj[rb + ot] : -1, R);
   en.own = (oid == eid);
   if (en.own && !en.rev) {
     en.psi = en.phi0;
@@ -1139,8 +1197,8 @@ __device__ __forceinline__ bool tile_strut(const TriArgs<T>& A, const TileSmem<T
       int sidx = p - en.pre;
       int mm = en.rev ? en.N - sidx : sidx;
       if (sidx != 0) {
-        T phi = en.phi0 + en.dphi * (T)mm / (T)en.N;
-        V3<T> zz = geo_point(en.g, phi);
+        T phi;
+        const V3<T> zz = arc_point_rn(en.g, en.phi0, en.dphi, mm, en.N, phi);
         Z[X * A.pmax + p] = zz;
         TH[X * A.pmax + p] = en.own ? phi : en.psi + wrap_from(raw_angle(own, zz) - en.psi, T(-ETA_PHI));
       }
@@ -1533,9 +1591,8 @@ __global__ void __launch_bounds__(256) k_tri_holes(TriArgs<T> A, Node64* scratch
           }
           Nq = arc_segments<T>(A, nd, ga, ctx, 0);
         }
-        EndG<T> Eo = make_end<T, T>(L, nd, L.adj[rb + ((A.arc_vtx[ga] >> 16) & 255)]);
         EntryS<T> en;
-        en.g = arc_geo<T>(Eo, nullptr, R);
+        en.g = node_arc_geo<T>(L, nd, L.adj[rb + ((A.arc_vtx[ga] >> 16) & 255)], -1, R);
         en.phi0 = A.arc_phi[2 * ga];
         en.dphi = A.arc_phi[2 * ga + 1];
         en.psi = T(0);

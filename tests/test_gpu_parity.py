@@ -121,6 +121,26 @@ def test_triangles_parity(name, dtype, k):
             assert not errs, (i, errs)
 
 
+@pytest.mark.parametrize("name,dtype,k", [("bcc3", np.float32, 8), ("bcc10", np.float32, 16),
+                                          ("octet3", np.float32, 8), ("octet3", np.float32, 32),
+                                          ("bccjit4", np.float32, 32), ("octet3", np.float64, 32),
+                                          ("star5", np.float32, 16)])
+def test_gpu_mesh_is_watertight(name, dtype, k):
+    """The GPU's triangles weld bitwise into a closed, consistently oriented
+    2-manifold (every edge used once in each direction) with chi = 2 (nodes -
+    struts): points shared by two struts, by a strut and a hole fan, or by a
+    strut of the FP32 pass and one of the FP64 pass carry the same bits."""
+    from tests import meshcheck as mc
+    lat, mm, g, o = build(name, dtype)
+    mm.tri_count(k)
+    _, gv = P.parse_stl(mm.triangulate(k).cpu().numpy())
+    ids, nv = mc.weld(gv)
+    chi, rep = mc.euler(ids, nv)
+    assert rep["mult"] == {2: rep["edges"]}, rep["mult"]
+    assert rep["dup_directed"] == 0 and rep["degenerate"] == 0
+    assert chi == 2 * (o.N - o.E)
+
+
 def test_stl_layout_and_header():
     """Binary STL records: 50 bytes, normal + 3 vertices f32, attribute 0;
     header count field little-endian, saturating at 2^32 - 1."""
