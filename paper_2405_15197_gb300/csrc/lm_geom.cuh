@@ -97,6 +97,8 @@ __device__ __forceinline__ V3<U> cvt3(V3<S> a) {
 __device__ __forceinline__ float lm_sqrt(float x) { return sqrtf(x); }
 __device__ __forceinline__ double lm_sqrt(double x) { return sqrt(x); }
 __device__ __forceinline__ df lm_sqrt(df x) { return df_sqrt(x); }
+__device__ __forceinline__ float lm_rsqrt(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double lm_rsqrt(double x) { return 1.0 / sqrt(x); }
 // FP32 atan2 from atan(r) ~ r P(r^2) on r = min/max in [0, 1] (degree-7 P,
 // weighted least-squares fit done for this library; largest error of the
 // FP32 evaluation 1.3e-7 rad) and the octant identities.  Every FP32 angle

@@ -1389,8 +1389,10 @@ __device__ __forceinline__ bool tile_strut(const TriArgs<T>& A, const TileSmem<T
         V3<T> ra = za, rb = isA ? q1 : dAB + q1, rc = dAB + zp;
         V3<T> pa = cA + za, pb = isA ? cA + q1 : cB + q1, pc = cB + zp;
         V3<T> cr = cross(rb - ra, rc - ra);
-        T len = norm3(cr);
-        V3<T> nn = len > T(0) ? cr * (T(1) / len) : mk3(T(0), T(0), T(0));
+        const T l2 = dot(cr, cr);
+        // unit normal (one reciprocal square root; the record's normal is
+        // informative, its error bound is far above 2 ulp)
+        V3<T> nn = l2 > T(0) ? cr * lm_rsqrt(l2) : mk3(T(0), T(0), T(0));
         if constexpr (ADJ) {
           int64_t ia_ = S.PID[i < nA ? i : 0];
           int64_t ib_ = isA ? S.PID[i + 1 < nA ? i + 1 : 0] : S.PID[A.pmax + wrap_idx(sB + jn, nB)];
@@ -1398,7 +1400,7 @@ __device__ __forceinline__ bool tile_strut(const TriArgs<T>& A, const TileSmem<T
           tri_point_adjoints<T>(A, ra, rb, rc, nn, cr, ia_, ib_, ic_);
         } else {
           if (OBJ) {
-            sa += 0.5 * (double)len;
+            sa += 0.5 * (double)lm_sqrt(l2);
             sv += ((double)dot(ra, cross(rb, rc)) +
                    dot(mk3((double)cA.x, (double)cA.y, (double)cA.z), mk3((double)cr.x, (double)cr.y, (double)cr.z))) *
                   (1.0 / 6.0);
