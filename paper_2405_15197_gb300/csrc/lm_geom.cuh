@@ -699,18 +699,22 @@ __device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, 
 __device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
 __device__ __forceinline__ float div_rn(float a, float b) { return __fdiv_rn(a, b); }
 __device__ __forceinline__ double div_rn(double a, double b) { return __ddiv_rn(a, b); }
+// a / b within 2 ulp (FP32: reciprocal approximation times a; the same two
+// instructions wherever it is inlined)
+__device__ __forceinline__ float div_fast(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double div_fast(double a, double b) { return __ddiv_rn(a, b); }
 
 // Subdivision point m of N of an arc (node-relative; Section 5: uniform in the
 // owner's angle, phi = phi0 + dphi m / N, also returned) with every operation
-// explicitly rounded: the kernels that emit a shared point (the two struts of
+// explicitly rounded (the two quotients within 2 ulp): the kernels that emit a shared point (the two struts of
 // an elliptical arc, a strut and a hole fan of a circular arc) write the same
 // bits.
 template <typename T>
 __device__ __forceinline__ V3<T> arc_point_rn(const ArcGeo<T>& g, T phi0, T dphi, int m, int N, T& phi) {
-  phi = add_rn(phi0, div_rn(mul_rn(dphi, (T)m), (T)N));
+  phi = add_rn(phi0, div_fast(mul_rn(dphi, (T)m), (T)N));
   T c, s;
   lm_sincos(phi, &s, &c);
-  const T t = div_rn(fma_rn(g.n2, s, fma_rn(g.n1, c, g.n0)), fma_rn(g.d2, s, fma_rn(g.d1, c, g.d0)));
+  const T t = div_fast(fma_rn(g.n2, s, fma_rn(g.n1, c, g.n0)), fma_rn(g.d2, s, fma_rn(g.d1, c, g.d0)));
   const T a = fma_rn(t, g.co, g.Rs), b = fma_rn(-t, g.s, g.Rco);
   V3<T> z;
   z.x = fma_rn(fma_rn(g.e2.x, s, mul_rn(g.e1.x, c)), b, mul_rn(g.u.x, a));
