@@ -567,7 +567,19 @@ TriLaunch<T> tri_launch(lm_metamesh* mm) {
   L.redo_base = 0;
   L.rlist = mm->redo_list;
   L.rcap = mm->redo_cap;
+  L.aux = mm->aux_st;
+  L.ev_fork = mm->ev_fork;
+  L.ev_join = mm->ev_join;
   return L;
+}
+
+// second stream and fork / join events of the hole fans (created once)
+cudaError_t ensure_aux(lm_metamesh* mm) {
+  if (mm->aux_st) return cudaSuccess;
+  cudaError_t e = cudaEventCreateWithFlags(&mm->ev_fork, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&mm->ev_join, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&mm->aux_st, cudaStreamNonBlocking);
+  return e;
 }
 
 template <typename T>
@@ -602,6 +614,7 @@ lm_status tri_count_impl(lm_metamesh* mm, int k, cudaStream_t st, int64_t* total
 template <typename T>
 lm_status tri_emit_impl(lm_metamesh* mm, int k, int64_t b, int64_t e, void* out, int64_t cap,
                         double* acc, cudaStream_t st) {
+  LM_CK(ensure_aux(mm));
   LM_CK(cudaMemsetAsync(mm->d_queue, 0, 2 * sizeof(int), st));
   TriLaunch<T> L = tri_launch<T>(mm);
   L.k = k;
@@ -624,6 +637,7 @@ lm_status tri_emit_impl(lm_metamesh* mm, int k, int64_t b, int64_t e, void* out,
 template <typename T>
 lm_status chunk_graphs(lm_metamesh* mm, int k, int64_t chunk, int64_t n_items, uint8_t* dbuf[2], int64_t cap,
                        int64_t* dev, cudaGraphExec_t ex[2], long long* kernels_per_launch) {
+  LM_CK(ensure_aux(mm));
   cudaStream_t cs;
   LM_CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
   lm_status s = LM_OK;
@@ -692,6 +706,12 @@ void lm_metamesh_free(lm_metamesh* mm) {
   for (void* p : ptrs)
     if (p) cudaFreeAsync(p, st);
   cudaStreamSynchronize(st);
+  if (mm->aux_st) {
+    cudaStreamSynchronize(mm->aux_st);
+    cudaStreamDestroy(mm->aux_st);
+  }
+  if (mm->ev_fork) cudaEventDestroy(mm->ev_fork);
+  if (mm->ev_join) cudaEventDestroy(mm->ev_join);
   delete mm;
 }
 

@@ -140,6 +140,10 @@ struct TriLaunch {
   unsigned long long* rlist;  // [1 + rcap]: count, then the deferred struts (NULL: bitmap only)
   int64_t rcap;
   const int64_t* range;  // device-side [begin, end) overriding item_begin/end, or NULL
+  // second stream for the hole fans, which then run beside the strut passes
+  // (fork and join through the two events); NULL: everything on one stream
+  cudaStream_t aux;
+  cudaEvent_t ev_fork, ev_join;
 };
 
 template <typename T>
@@ -169,6 +173,8 @@ struct lm_metamesh {
   const void* radii;
   lm_options opt;
   cudaStream_t st;
+  cudaStream_t aux_st;             // hole fans beside the strut passes (created on first use)
+  cudaEvent_t ev_fork, ev_join;
   // CSR and per-node data
   void* node_R;
   int64_t* row_ptr;

@@ -70,13 +70,49 @@ cudaError_t launch_tri_count(const TriLaunch<T>& a, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+// hole fans of the nodes in the item range (one warp per node with holes)
+template <typename T>
+cudaError_t launch_tri_holes(const TriLaunch<T>& a, cudaStream_t st) {
+  TriArgs<T> A = tri_args(a);
+  const int warps = 8, threads = warps * 32;
+  const int sms = sm_count();
+  size_t wsb = (size_t)a.pmax * sizeof(V3<T>) + 32 * 50 + 64;
+  wsb = (wsb + 15) & ~(size_t)15;
+  const size_t smem = warps * wsb;
+  cudaError_t e = cudaFuncSetAttribute(k_tri_holes<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tri_holes<T>, threads, smem);
+  if (per_sm < 1) per_sm = 1;
+  int64_t grid = (int64_t)per_sm * sms;
+  const int64_t gmax = a.scratch_warps / (2 * warps);
+  if (grid > gmax) grid = gmax;
+  const int64_t nb = a.item_begin > a.n_struts ? a.item_begin : a.n_struts;
+  const int64_t n = a.item_end - nb;
+  const int64_t gneed = ((n + 31) / 32 + warps - 1) / warps;  // groups of 32 nodes
+  if (grid > gneed) grid = gneed;
+  if (grid < 1) grid = 1;
+  A.queue = a.queue + 1;
+  count_launch();
+  k_tri_holes<T><<<(unsigned)grid, threads, smem, st>>>(A, a.scratch, a.first_ptr);
+  return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t launch_tri_emit(const TriLaunch<T>& a, cudaStream_t st) {
   TriArgs<T> A = tri_args(a);
-  const int warps = 8, threads = warps * 32;
   int sms = sm_count();
-  (void)threads;
   cudaError_t e;
+  const bool holes = a.item_end > a.n_struts;
+  const bool fork = holes && a.aux && a.item_begin < a.n_struts;
+  if (fork) {
+    // the hole fans are independent of the strut passes: they run on the
+    // second stream beside them and the stream joins before returning
+    if ((e = cudaEventRecord(a.ev_fork, st)) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(a.aux, a.ev_fork, 0)) != cudaSuccess) return e;
+    if ((e = launch_tri_holes(a, a.aux)) != cudaSuccess) return e;
+    if ((e = cudaEventRecord(a.ev_join, a.aux)) != cudaSuccess) return e;
+  }
   // struts: one 8-lane tile per strut (four per warp; measured faster than
   // 4, 16 or 32 lanes on octet and BCC lattices at k = 8 and 32) while the
   // per-tile shared memory fits; otherwise (very fine resolutions) one thread
@@ -167,30 +203,8 @@ cudaError_t launch_tri_emit(const TriLaunch<T>& a, cudaStream_t st) {
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
-  // hole fans
-  if (a.item_end > a.n_struts) {
-    size_t wsb = (size_t)a.pmax * sizeof(V3<T>) + 32 * 50 + 64;
-    wsb = (wsb + 15) & ~(size_t)15;
-    size_t smem = warps * wsb;
-    e = cudaFuncSetAttribute(k_tri_holes<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tri_holes<T>, threads, smem);
-    if (per_sm < 1) per_sm = 1;
-    int64_t grid = (int64_t)per_sm * sms;
-    int64_t gmax = a.scratch_warps / (2 * warps);
-    if (grid > gmax) grid = gmax;
-    int64_t nb = a.item_begin > a.n_struts ? a.item_begin : a.n_struts;
-    int64_t n = a.item_end - nb;
-    int64_t gneed = ((n + 31) / 32 + warps - 1) / warps;  // groups of 32 nodes
-    if (grid > gneed) grid = gneed;
-    if (grid < 1) grid = 1;
-    A.queue = a.queue + 1;
-    count_launch();
-    k_tri_holes<T><<<(unsigned)grid, threads, smem, st>>>(A, a.scratch, a.first_ptr);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-  }
+  if (fork) return cudaStreamWaitEvent(st, a.ev_join, 0);
+  if (holes) return launch_tri_holes(a, st);
   return cudaSuccess;
 }
 
