@@ -93,8 +93,9 @@ typedef struct {
  *   nodes_per_task: nodes a warp pops from the work queue at once (0 = 1)
  *   arena_bytes   : device memory for the count pass to keep each node's
  *                   meta-mesh, so that a gather into the CSR layout replaces
- *                   the emit pass for the nodes it holds (0 = up to 30 % of
- *                   the free memory; < 0 = none: every node is emitted);
+ *                   the emit pass for the nodes it holds (0 = up to 35 % of
+ *                   the memory free beside the CSR offsets; < 0 = none:
+ *                   every node is emitted);
  *                   the result is the same either way                       */
 typedef struct {
   int32_t autotune;
