@@ -187,6 +187,23 @@ def run_step(torch, liblm, xyz, ends, radii, ks, out, stream, want_times=False):
     return ends.shape[0], tris, times
 
 
+def max_over_ranks(torch, ms, dev):
+    """Largest per-step time over the ranks (one all-reduce; the time itself
+    when there is one process)."""
+    dist = torch.distributed
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return ms
+    t = torch.tensor([ms], device=dev, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(world, n_struts, ms):
+    """Whole-job struts/s: every replica meta-meshes and triangulates a lattice
+    of n_struts struts per step (weak scaling), the slowest sets the time."""
+    return world * n_struts / (ms / 1e3)
+
+
 def bench_gpu(args):
     import torch
 
@@ -241,15 +258,11 @@ def bench_gpu(args):
         stop.record(stream)
         torch.cuda.synchronize()
         l1 = liblm.lm_launch_count()
-    ms = start.elapsed_time(stop) / args.steps
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(torch, start.elapsed_time(stop) / args.steps, dev)
     # per-phase times of one extra step (not part of the timed region)
     _, _, phase = run_step(torch, liblm, xyz, ends, radii, ks, out, stream, want_times=True)
     E = ends.shape[0]
-    value = world * E / (ms / 1e3)
+    value = job_value(world, E, ms)
     peaks, peak_kind = load_peaks()
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     # dominant kernel: largest phase
