@@ -118,9 +118,10 @@ cudaError_t launch_tri_emit(const TriLaunch<T>& a, cudaStream_t st) {
   // per-tile shared memory fits; otherwise (very fine resolutions) one thread
   // per strut that streams its points
   if (a.item_begin < a.n_struts) {
-    // the FP64 pass (about 1 % of the struts, FP64 at 1/64 of the FP32 rate)
-    // gives each deferred strut a whole warp
-    constexpr int TL = 8, TLX = 32;
+    // the FP64 pass (about 1 % of the struts) is bound by the FP64 pipe (1/64
+    // of the FP32 rate) and its steps occupy few lanes: two deferred struts
+    // per warp (16-lane tiles) fill its instructions better than one
+    constexpr int TL = 8, TLX = 16;
     const int64_t n = (a.item_end < a.n_struts ? a.item_end : a.n_struts) - a.item_begin;
     TileLayout<T, TL> Lay{a.pmax, a.emax, false, false, a.dmax};
     TileLayout<T, TLX> LayX{a.pmax, a.emax, true, false, a.dmax};
