@@ -1,5 +1,5 @@
 // Adjoint of the triangulated area and volume (see lm_adjoint.cuh for the
-// method): kernels and the host driver behind lm_metamesh_backward.
+// method): kernels and the host code behind lm_metamesh_backward.
 #include <cuda_runtime.h>
 
 #include "lm_adjoint.cuh"
