@@ -38,3 +38,30 @@ def test_status_strings_and_header():
 
 def test_built_for_sm103a():
     assert "arch=compute_103a,code=sm_103a" in " ".join(build.ARCH)
+
+
+def test_struct_layouts_match_header(tmp_path):
+    """The ctypes mirrors of lm_lattice, lm_options and lm_metamesh_view have
+    the size and field offsets a C compiler gives the header's structs."""
+    import ctypes
+    structs = {"lm_lattice": liblm.lm_lattice, "lm_options": liblm.lm_options,
+               "lm_metamesh_view": liblm.lm_metamesh_view}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "liblm.h"', "int main(void) {"]
+    for name, cls in structs.items():
+        lines.append(f'  printf("{name} size %zu\\n", sizeof({name}));')
+        for f, _ in cls._fields_:
+            lines.append(f'  printf("{name} {f} %zu\\n", offsetof({name}, {f}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)],
+                   check=True, capture_output=True)
+    got = {}
+    for ln in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.splitlines():
+        name, field, val = ln.split()
+        got[(name, field)] = int(val)
+    for name, cls in structs.items():
+        assert got[(name, "size")] == ctypes.sizeof(cls), name
+        for f, _ in cls._fields_:
+            assert got[(name, f)] == getattr(cls, f).offset, (name, f)
