@@ -30,17 +30,29 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+# cpu_one / cpu_all: oracle samples timed on one core and on every core;
+# cpu_ref: the reference arm's per-step sample (all cores); cpu_extrapolate:
+# whole workload / cpu_all sample
 WORKLOADS = {
-    "octet100": {"kind": "octet", "n": 100, "ks": (8, 32),
-                 "desc": "octet-truss 100^3 cells, radii U[0.04,0.08] per node (cones), k=8 and k=32 from one meta-mesh"},
-    "octet40": {"kind": "octet", "n": 40, "ks": (8, 32),
-                "desc": "octet-truss 40^3 cells (smaller case), k=8 and k=32"},
-    "octet24": {"kind": "octet", "n": 24, "ks": (8, 32),
-                "desc": "octet-truss 24^3 cells (profiling case), k=8 and k=32"},
     "bcc500": {"kind": "bcc", "n": 500, "ks": (8, 32), "R": 0.05,
-               "desc": "BCC 500^3 cells, 1.0e9 struts, R=0.05, k=8 and k=32"},
+               "desc": "billion-scale BCC 500^3 cells (1.0e9 struts), R=0.05, meta-mesh once, "
+                       "triangulated at k=8 and k=32",
+               "cpu_one": ("bcc", 500, 50, 4, 0.05), "cpu_all": ("bcc", 500, 500, 4, 0.05),
+               "cpu_ref": ("bcc", 500, 100, 4, 0.05), "cpu_extrapolate": 125},
+    "octet100": {"kind": "octet", "n": 100, "ks": (8, 32),
+                 "desc": "octet-truss 100^3 cells, radii U[0.04,0.08] per node (cones), k=8 and k=32 from one meta-mesh",
+                 "cpu_one": ("octet", 24, 24, 24), "cpu_all": ("octet", 100, 100, 8),
+                 "cpu_ref": ("octet", 100, 100, 4), "cpu_extrapolate": 12.5},
+    "octet40": {"kind": "octet", "n": 40, "ks": (8, 32),
+                "desc": "octet-truss 40^3 cells (smaller case), k=8 and k=32",
+                "cpu_one": ("octet", 16, 16, 16), "cpu_all": ("octet", 40, 40, 40), "cpu_ref": ("octet", 40, 40, 8)},
+    "octet24": {"kind": "octet", "n": 24, "ks": (8, 32),
+                "desc": "octet-truss 24^3 cells (profiling case), k=8 and k=32",
+                "cpu_one": ("octet", 16, 16, 16), "cpu_all": ("octet", 24, 24, 24), "cpu_ref": ("octet", 24, 24, 8)},
     "bcc40": {"kind": "bcc", "n": 40, "ks": (8, 32), "R": 0.05,
-              "desc": "BCC 40^3 cells (profiling case of the 500^3 lattice), R=0.05, k=8 and k=32"},
+              "desc": "BCC 40^3 cells (profiling case of the 500^3 lattice), R=0.05, k=8 and k=32",
+              "cpu_one": ("bcc", 40, 40, 8, 0.05), "cpu_all": ("bcc", 40, 40, 40, 0.05),
+              "cpu_ref": ("bcc", 40, 40, 8, 0.05)},
 }
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum of the stitching,
@@ -49,6 +61,9 @@ WORKLOADS = {
 # current kernels; the benchmark scales it by the triangles of its own emit
 # (no entry: not measured with the current kernels, reported as null)
 TRAFFIC_PER_TRI_K32 = {"octet": 52.4}
+
+
+METRIC = "meta-mesh struts/s; triangles/s & write GB/s vs HBM peak; adjoint struts/s"
 
 
 def load_peaks():
@@ -282,7 +297,7 @@ def bench_gpu(args):
     e2e = bench_e2e(torch, liblm, xyz, ends, radii, ks, stream, dev, args) if not args.no_e2e else None
     adjoint = bench_adjoint(torch, liblm, dev, stream) if not args.no_adjoint else None
     res = {
-        "metric": "meta-mesh struts/s; triangles/s & write GB/s vs HBM peak; adjoint struts/s",
+        "metric": METRIC,
         "value": value, "unit": "struts/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32 (f64 stability steps)", "data": "synthetic",
@@ -386,53 +401,243 @@ def bench_adjoint(torch, liblm, dev, stream):
             "includes": "objective evaluation + point adjoints + per-node forward-mode pass"}
 
 
-def cpu_baseline(args, quick=False):
-    """The FP64 oracle, as it stands, single-threaded, on a bounded sample of
-    the workload: an octet 32^3 sub-block (same generator and radii law) for
-    the octet workloads, a BCC 40x40x8 slab for BCC; meta-mesh + both k."""
-    import oracle
+# ------------------------------------------------------------ CPU oracle timing
+# The FP64 oracle runs unchanged; only the work is split across processes.
+# Worker w of P takes struts [E w / P, E (w+1) / P), meta-meshes every node
+# those struts touch (nodes on a range boundary are meta-meshed twice), and
+# triangulates its struts and the hole fans of the nodes it owns (a node is
+# owned by the worker holding its lowest-id strut).  Processes are spawned
+# (never forked after CUDA initialisation) and start their timed region
+# together at a barrier; the rate is all struts / the slowest worker's time.
+
+
+def sample_lattice(spec):
+    """Lattice of a CPU-timing spec: ('bcc', nx, ny, nz, R), ('octet', nx, ny,
+    nz), ('bccjit', n) or ('npz', path).  FP32-rounded coordinates and radii
+    (the GPU workloads are FP32)."""
     from paper_2405_15197_gb300 import lattices as L
-    wl = WORKLOADS[args.workload]
-    if wl["kind"] == "octet":
-        n = 32 if not quick else 16
-        lat = L.octet(n)
-        sample = f"octet {n}^3 cells ({lat['ends'].shape[0]} struts), meta-mesh + k=8 + k=32"
+    kind = spec[0]
+    if kind == "bcc":
+        lat = L.bcc(spec[1], spec[2], spec[3], radius=spec[4])
+    elif kind == "bcc64":
+        lat = L.bcc(spec[1], spec[1], spec[1], radius=spec[2])
+    elif kind == "octet":
+        lat = L.octet(0, ncells=(spec[1], spec[2], spec[3]))
+    elif kind == "bccjit":
+        lat = L.bcc(spec[1], jitter=0.05, radius_range=(0.05, 0.09))
+    elif kind == "npz":
+        d = np.load(spec[1])
+        lat = {"xyz": d["xyz"], "ends": d["ends"], "radii": d["radii"]}
     else:
-        lat = L.bcc(40, 40, 8 if not quick else 4, radius=wl["R"])
-        sample = f"BCC slab ({lat['ends'].shape[0]} struts), meta-mesh + k=8 + k=32"
-    lat = {k: (v.astype(np.float32).astype(np.float64) if k in ("xyz", "radii") else v) for k, v in lat.items()}
-    oracle.build()
-    t0 = time.perf_counter()
-    o = oracle.Oracle(lat)
-    for k in wl["ks"]:
-        o.triangulate(k, want_tris=False)
-    dt = time.perf_counter() - t0
-    E = lat["ends"].shape[0]
-    return {"value": E / dt, "unit": "struts/s", "cores": 1, "kind": "oracle", "sample": sample,
-            "seconds": dt}
+        raise ValueError(spec)
+    if kind != "bcc64":
+        lat = {k: (v.astype(np.float32).astype(np.float64) if k in ("xyz", "radii") else v)
+               for k, v in lat.items() if k in ("xyz", "ends", "radii")}
+    return lat
+
+
+def _worker_items(lat, w, procs, nodes=None):
+    """Struts (ranges), node-item runs and the nodes to meta-mesh of worker w.
+    nodes: restrict the work to these nodes (struts whose lower-id end is in
+    the set, hole fans of the set), else the whole lattice."""
+    ends = lat["ends"]
+    E, N = ends.shape[0], lat["xyz"].shape[0]
+    if nodes is None:
+        e0, e1 = E * w // procs, E * (w + 1) // procs
+        first = np.full(N, E, dtype=np.int64)
+        sid = np.arange(E, dtype=np.int64)
+        np.minimum.at(first, ends[:, 0], sid)
+        np.minimum.at(first, ends[:, 1], sid)
+        owned = np.nonzero((first >= e0) & (first < e1))[0]
+        strut_runs = [(e0, e1)] if e1 > e0 else []
+        need = np.unique(ends[e0:e1].ravel())
+    else:
+        mine = np.sort(np.asarray(nodes))[w::procs]
+        lo = np.minimum(ends[:, 0], ends[:, 1])
+        sel = np.nonzero(np.isin(lo, mine))[0]
+        cut = np.nonzero(np.diff(sel) != 1)[0] + 1
+        strut_runs = [(int(r[0]), int(r[-1]) + 1) for r in np.split(sel, cut) if r.size]
+        owned = mine
+        need = np.unique(np.concatenate([ends[sel].ravel(), mine]))
+    cut = np.nonzero(np.diff(owned) != 1)[0] + 1
+    node_runs = [(E + int(r[0]), E + int(r[-1]) + 1) for r in np.split(owned, cut) if r.size]
+    n_struts = sum(b - a for a, b in strut_runs)
+    return strut_runs, node_runs, need, n_struts
+
+
+def _oracle_worker(w, procs, inq, outq, barrier):
+    import oracle
+    cache = {}
+    while True:
+        job = inq.get()
+        if job is None:
+            return
+        spec, ks, nodes_path = job
+        key = (spec, nodes_path)
+        if key not in cache:
+            cache.clear()
+            lat = sample_lattice(spec)
+            nodes = np.load(nodes_path) if nodes_path else None
+            cache[key] = (lat, _worker_items(lat, w, procs, nodes))
+        lat, (sruns, nruns, need, n_struts) = cache[key]
+        barrier.wait()
+        t0 = time.perf_counter()
+        o = oracle.Oracle(lat, nodes=[])
+        o.metamesh_nodes(need)
+        for k in ks:
+            for a, b in sruns + nruns:
+                o.triangulate(k, a, b, want_tris=False)
+        dt = time.perf_counter() - t0
+        del o
+        outq.put((w, dt, n_struts))
+
+
+class OraclePool:
+    """`procs` spawned processes that time the oracle together."""
+
+    def __init__(self, procs):
+        import multiprocessing as mp
+        import oracle
+        oracle.build()
+        ctx = mp.get_context("spawn")
+        self.procs = procs
+        self.barrier = ctx.Barrier(procs)
+        self.outq = ctx.Queue()
+        self.inqs = [ctx.Queue() for _ in range(procs)]
+        self.ps = [ctx.Process(target=_oracle_worker, args=(w, procs, self.inqs[w], self.outq, self.barrier),
+                               daemon=True) for w in range(procs)]
+        for p in self.ps:
+            p.start()
+
+    def run(self, spec, ks, nodes_path=None):
+        """(struts meta-meshed and triangulated, seconds of the slowest worker)."""
+        for q in self.inqs:
+            q.put((spec, tuple(ks), nodes_path))
+        res = [self.outq.get(timeout=3600) for _ in range(self.procs)]
+        return sum(r[2] for r in res), max(r[1] for r in res)
+
+    def close(self):
+        for q in self.inqs:
+            q.put(None)
+        for p in self.ps:
+            p.join(timeout=30)
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def cpu_baseline(args, quick=False):
+    """The FP64 oracle as it stands, on the machine's host cores: one core on a
+    block of the workload and every core (one process each) on a larger
+    block; for the billion-strut lattice the all-core time of its
+    500x500x4-cell slab is also scaled by 125 (extrapolated)."""
+    wl = WORKLOADS[args.workload]
+    cores = host_cores()
+    one_spec, all_spec = wl["cpu_one"], wl["cpu_all"]
+    pool = OraclePool(1)
+    e1, t1 = pool.run(one_spec, wl["ks"])
+    pool.close()
+    pool = OraclePool(cores)
+    ea, ta = pool.run(all_spec, wl["ks"])
+    pool.close()
+    out = {"value": ea / ta, "unit": "struts/s", "cores": cores, "kind": "oracle",
+           "sample": f"{_spec_desc(all_spec)} ({ea} struts) on {cores} processes, meta-mesh + "
+                     + " + ".join(f"k={k}" for k in wl["ks"]),
+           "seconds": ta,
+           "one_core": {"value": e1 / t1, "unit": "struts/s", "cores": 1, "seconds": t1,
+                        "sample": f"{_spec_desc(one_spec)} ({e1} struts)"},
+           "nproc": cores}
+    if wl.get("cpu_extrapolate"):
+        f = wl["cpu_extrapolate"]
+        out["extrapolated"] = {"factor": f, "seconds_all_cores": ta * f, "seconds_one_core": t1 * f * ea / e1,
+                               "note": f"whole workload = the slab x {f} (extrapolated, not run)"}
+    return out
+
+
+def _spec_desc(spec):
+    if spec[0] == "bcc":
+        return f"BCC {spec[1]}x{spec[2]}x{spec[3]} cells, R={spec[4]}"
+    if spec[0] == "octet":
+        return f"octet-truss {spec[1]}x{spec[2]}x{spec[3]} cells"
+    if spec[0] == "bccjit":
+        return f"jittered BCC {spec[1]}^3 cells"
+    if spec[0] == "bcc64":
+        return f"BCC {spec[1]}^3 cells, R={spec[2]} (FP64)"
+    return str(spec[0])
 
 
 def bench_reference(args):
+    """Reference arm: the FP64 oracle as it stands, on every host core (one
+    spawned process each), each step a bounded sample of the workload."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    t_steps = []
-    cb = None
-    for _ in range(args.warmup):
-        cpu_baseline(args, quick=True)
-    for _ in range(args.steps):
-        cb = cpu_baseline(args, quick=True)
-        t_steps.append(cb["seconds"])
     wl = WORKLOADS[args.workload]
-    res = {"impl": "reference", "metric": "meta-mesh struts/s; triangles/s & write GB/s vs HBM peak; adjoint struts/s",
-           "value": cb["value"], "unit": "struts/s", "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
-           "ms_per_step": 1e3 * statistics.mean(t_steps), "higher_is_better": True, "scaling": "weak",
+    cores = host_cores()
+    spec = wl["cpu_ref"]
+    pool = OraclePool(cores)
+    try:
+        for _ in range(args.warmup):
+            pool.run(spec, wl["ks"])
+        t_steps, n = [], 0
+        for _ in range(args.steps):
+            n, dt = pool.run(spec, wl["ks"])
+            t_steps.append(dt)
+    finally:
+        pool.close()
+    ms = 1e3 * statistics.mean(t_steps)
+    value = n / (ms / 1e3)
+    sample = f"{_spec_desc(spec)} ({n} struts) per step on {cores} processes, meta-mesh + " + \
+        " + ".join(f"k={k}" for k in wl["ks"])
+    res = {"impl": "reference", "metric": METRIC,
+           "value": value, "unit": "struts/s", "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": {"workload": wl["desc"], "name": args.workload},
-           "cpu_baseline": {"value": cb["value"], "unit": "struts/s", "cores": 1, "kind": "oracle",
-                            "sample": cb["sample"]},
-           "e2e": {"value": cb["value"], "unit": "struts/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+           "cpu_baseline": {"value": value, "unit": "struts/s", "cores": cores, "kind": "oracle",
+                            "sample": sample},
+           "e2e": {"value": value, "unit": "struts/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(res))
+
+
+def cpu_configs(args):
+    """The oracle on every host core over each configuration of the
+    benchmark suite: BCC 10^3 (FP64, k=16), octet 100^3 (k=8, 32) and jittered
+    BCC 64^3 (k=32) whole; the 2e6-node irregular lattice (k=16) on a
+    1e5-node sub-cube and BCC 500^3 (k=8, 32) on its 500x500x4-cell slab,
+    both scaled to the whole lattice (extrapolated).  Prints one JSON line."""
+    from paper_2405_15197_gb300 import lattices as L
+    cores = host_cores()
+    pool = OraclePool(cores)
+    out = {"cores": cores, "configs": {}}
+    try:
+        for name, spec, ks, factor in [("bcc10_fp64", ("bcc64", 10, 0.08), (16,), 1.0),
+                                       ("octet100", ("octet", 100, 100, 100), (8, 32), 1.0),
+                                       ("bccjit64", ("bccjit", 64), (32,), 1.0),
+                                       ("bcc500_slab", ("bcc", 500, 500, 4, 0.05), (8, 32), 125.0)]:
+            n, dt = pool.run(spec, ks)
+            out["configs"][name] = {"struts": n, "seconds": dt, "struts_per_s": n / dt, "ks": list(ks),
+                                    "whole_seconds": dt * factor, "extrapolated": factor != 1.0}
+        lat = L.irregular(2_000_000, r_scale=0.3)
+        lat = {k: (v.astype(np.float32).astype(np.float64) if k in ("xyz", "radii") else v)
+               for k, v in lat.items() if k in ("xyz", "ends", "radii")}
+        sub = np.nonzero(np.all(lat["xyz"] < 0.368, axis=1))[0]
+        with tempfile.TemporaryDirectory() as td:
+            lp, npth = os.path.join(td, "irr.npz"), os.path.join(td, "sub.npy")
+            np.savez(lp, **lat)
+            np.save(npth, sub)
+            n, dt = pool.run(("npz", lp), (16,), npth)
+        f = lat["xyz"].shape[0] / sub.size
+        out["configs"]["irregular2m_subcube"] = {"struts": n, "nodes": int(sub.size), "seconds": dt,
+                                                 "struts_per_s": n / dt, "ks": [16], "whole_seconds": dt * f,
+                                                 "extrapolated": True}
+    finally:
+        pool.close()
+    print(json.dumps(out))
 
 
 def main():
@@ -441,12 +646,16 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="octet100", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="bcc500", choices=sorted(WORKLOADS))
+    ap.add_argument("--cpu-configs", action="store_true",
+                    help="time the oracle on every configuration (all host cores) and exit")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.cpu_configs:
+        cpu_configs(args)
+    elif args.impl == "reference":
         bench_reference(args)
     else:
         bench_gpu(args)

@@ -42,7 +42,8 @@ typedef enum {
   LM_ERR_CAPACITY = 4,        /* an output or per-node work buffer too small */
   LM_ERR_OOM = 5,             /* device allocation failed */
   LM_ERR_CUDA = 6,            /* a CUDA runtime call failed */
-  LM_ERR_TIMEOUT = 7,         /* a bounded device-side wait gave up */
+  LM_ERR_TIMEOUT = 7,         /* reserved: no kernel of this library waits on
+                                 another, so no call returns it */
   LM_ERR_VALENCE = 8,         /* a node with more than LM_MAX_VALENCE struts */
   LM_ERR_STATE = 9            /* call order violated (e.g. triangulate before
                                  lm_tri_count for that k) */
@@ -118,13 +119,23 @@ typedef struct lm_metamesh lm_metamesh;
 lm_status lm_build_metamesh(const lm_lattice* lat, const lm_options* opt, void* stream,
                             lm_metamesh** out);
 
-/* Totals (host, after the build's synchronisation):
- *   out[0] vertices, [1] elliptical arcs, [2] circular arcs, [3] holes,
- *   [4] faces (struts + holes), [5] nodes flagged LM_NODE_DEGENERATE,
- *   [6] max valence, [7] OR of all node flags                            */
+/* Totals of the meta-mesh (Section 4.1, "Meta-mesh definition": the
+ * vertices, circular / elliptical arcs and trimmed strut surfaces that bound
+ * the lattice; Section 5's hole contours are the circular-arc loops left on
+ * the nodal spheres).  Host values, read after the build's synchronisation;
+ * no device work.
+ *   out   : host, 8 int64: [0] vertices, [1] elliptical arcs, [2] circular
+ *           arcs, [3] holes, [4] faces (struts + holes), [5] nodes flagged
+ *           LM_NODE_DEGENERATE, [6] max valence, [7] OR of all node flags
+ * Returns LM_ERR_INVALID_ARG for a NULL handle or array.                 */
 lm_status lm_metamesh_counts(const lm_metamesh* mm, int64_t out[8]);
 
-/* Device views of the meta-mesh arrays (library-owned, valid until free).
+/* Device views of the meta-mesh arrays (Section 4.1's vertices, arcs and arc
+ * loops in the layout of Section 4.3.2, "Coalesced-access memory layout": an
+ * index region of prefix sums (the *_off arrays, one CSR range per node or
+ * strut end) over structure-of-arrays data).  Library-owned device memory,
+ * valid until lm_metamesh_free; the call fills `view` on the host and does no
+ * device work.  Returns LM_ERR_INVALID_ARG for a NULL handle or view.
  * Node-local vertex and arc ids index from node_vtx_off[n] / node_arc_off[n].
  *   vtx_z     : [V][3] dtype, vertex position relative to its node centre
  *   arc_ends  : [A][2] int32 global strut-end ids (2*strut+side): owner, other
@@ -174,7 +185,10 @@ lm_status lm_tri_count(lm_metamesh* mm, int32_t k, void* stream, int64_t* h_tota
 lm_status lm_tri_range(const lm_metamesh* mm, int64_t item_begin, int64_t item_end,
                        int64_t* h_first, int64_t* h_count);
 
-/* Emit the triangles of items [item_begin, item_end) at resolution k as
+/* Triangulation at resolution k (Section 5: arc subdivision by Eq. sampling
+ * and Eq. parameter-range, strut stitching, hole filling; Algorithm 1,
+ * subdivide / triangulate / fillHoles, with write(T) here a device buffer in
+ * STL layout).  Emits the triangles of items [item_begin, item_end) as
  * binary-STL records (50 bytes: normal f32x3, v0, v1, v2 f32x3, uint16
  * attribute 0; outward counter-clockwise) into d_out, the record of global
  * triangle t at byte 50*(t - first(item_begin)).  Asynchronous; requires
@@ -201,8 +215,13 @@ lm_status lm_triangulate_stream(lm_metamesh* mm, int32_t k, int64_t chunk_items,
                                 int64_t slot_bytes, int32_t n_slots, lm_chunk_cb cb, void* user,
                                 void* stream, int64_t* h_total);
 
-/* 80-byte header (text, zero padded) + little-endian uint32 triangle count;
- * counts above 2^32-1 write 0xFFFFFFFF (the true count is the int64).    */
+/* Binary-STL file header for the records of lm_triangulate (Section 5 and
+ * Algorithm 1 write the triangles as STL; Table 1 reports the STL file
+ * sizes, 84 + 50 bytes per triangle): 80-byte text header (zero padded) +
+ * little-endian uint32 triangle count; counts above 2^32-1 write 0xFFFFFFFF
+ * (the true count is the int64 the caller holds).  Host only.
+ *   hdr    : host, 84 bytes written
+ *   n_tris : triangle count (negative counts write 0)                     */
 void lm_stl_header(uint8_t hdr[84], int64_t n_tris);
 
 /* Objective of the triangulated mesh at k: area = sum |(v1-v0)x(v2-v0)|/2,
@@ -228,7 +247,7 @@ lm_status lm_metamesh_backward(lm_metamesh* mm, int32_t k, double w_area, double
 lm_status lm_metamesh_launch_shape(const lm_metamesh* mm, int32_t out[6]);
 
 /* First asynchronous error recorded on the handle by a device-side check
- * (capacity, timeout); synchronises `stream`, then clears it.            */
+ * (LM_ERR_CAPACITY); synchronises `stream`, then clears it.              */
 lm_status lm_last_error(lm_metamesh* mm, void* stream);
 
 void lm_metamesh_free(lm_metamesh* mm);
@@ -275,9 +294,13 @@ lm_status lm_copy_to_host(void* h_dst, const void* d_src, int64_t bytes);
  *   angles, [11] fan centre (triangulation); struts deferred from the FP32
  *   stitching pass because of [12] an entry's segment count or start
  *   angle, [13] a key at the edge of the angular window, [14] a pair of
- *   keys within the zipper margin; [15] pairs of zipper keys decided in
- *   FP64.                                                                  */
-lm_status lm_fp64_counts(const lm_metamesh* mm, int64_t out[16]);
+ *   keys within the zipper margin, [16] keys out of angular order (a loop
+ *   that turns back on a degenerate node; stitched by the sequential zipper
+ *   in FP64), [17] an ill-conditioned elliptical arc (a steep section on a
+ *   degenerate node; its points are subdivided in FP64); [15] pairs of
+ *   zipper keys decided in FP64.                                           */
+enum { LM_N_FP64_COUNTS = 18 };
+lm_status lm_fp64_counts(const lm_metamesh* mm, int64_t out[LM_N_FP64_COUNTS]);
 
 /* Utility (no counterpart in the paper): number of CUDA kernels this library
  * has launched in the process so far (host-side counter).                */

@@ -103,8 +103,17 @@ class Oracle:
         if nodes is None:
             lib.lmo_metamesh(self.h, 0, self.N)
         else:
-            for n in np.asarray(nodes).ravel():
-                lib.lmo_metamesh(self.h, int(n), int(n) + 1)
+            self.metamesh_nodes(nodes)
+
+    def metamesh_nodes(self, nodes):
+        """Meta-mesh the listed nodes (one call per run of consecutive ids)."""
+        lib = _load()
+        ids = np.unique(np.asarray(nodes, dtype=np.int64).ravel())
+        if ids.size == 0:
+            return
+        cut = np.nonzero(np.diff(ids) != 1)[0] + 1
+        for run in np.split(ids, cut):
+            lib.lmo_metamesh(self.h, int(run[0]), int(run[-1]) + 1)
 
     def __del__(self):
         if getattr(self, "h", None):

@@ -260,8 +260,8 @@ lm_status build_impl(lm_metamesh* mm, cudaStream_t st) {
   LM_CK(dalloc(&mm->d_queue, 8, st));
   LM_CK(dalloc(&mm->d_misc, 8, st));
   LM_CK(dalloc(&mm->d_acc, 4, st));
-  LM_CK(dalloc(&mm->d_fb, 16, st));
-  LM_CK(cudaMemsetAsync(mm->d_fb, 0, 16 * sizeof(unsigned long long), st));
+  LM_CK(dalloc(&mm->d_fb, LM_N_FP64_COUNTS, st));
+  LM_CK(cudaMemsetAsync(mm->d_fb, 0, LM_N_FP64_COUNTS * sizeof(unsigned long long), st));
   LM_CK(cudaMemsetAsync(mm->d_err, 0, 4 * sizeof(int), st));
   LM_CK(cudaMemsetAsync(mm->d_misc, 0, 8 * sizeof(int), st));
   T* node_R = nullptr;
@@ -475,7 +475,7 @@ lm_status build_impl(lm_metamesh* mm, cudaStream_t st) {
         mm->tuned[b][1] = npt;
       }
       // the sample runs counted their FP64 steps too
-      LM_CK(cudaMemsetAsync(mm->d_fb, 0, 16 * sizeof(unsigned long long), st));
+      LM_CK(cudaMemsetAsync(mm->d_fb, 0, LM_N_FP64_COUNTS * sizeof(unsigned long long), st));
     }
     if (arena_buf) L.arena = arena;
     if (pass == 1 && arena_buf && arena_miss == 0) break;
@@ -966,11 +966,11 @@ lm_status lm_triangulate_stream(lm_metamesh* mm, int32_t k, int64_t chunk_items,
 
 long long lm_launch_count(void) { return g_launches.load(); }
 
-lm_status lm_fp64_counts(const lm_metamesh* mm, int64_t out[16]) {
+lm_status lm_fp64_counts(const lm_metamesh* mm, int64_t out[LM_N_FP64_COUNTS]) {
   if (!mm || !out) return LM_ERR_INVALID_ARG;
-  unsigned long long h[16];
+  unsigned long long h[LM_N_FP64_COUNTS];
   if (cudaMemcpy(h, mm->d_fb, sizeof(h), cudaMemcpyDeviceToHost) != cudaSuccess) return LM_ERR_CUDA;
-  for (int i = 0; i < 16; i++) out[i] = (int64_t)h[i];
+  for (int i = 0; i < LM_N_FP64_COUNTS; i++) out[i] = (int64_t)h[i];
   return LM_OK;
 }
 

@@ -55,6 +55,13 @@ constexpr float M_POS = 1e-1f;   // conditioning floor for keeping an FP32 circl
 // line P_ij n P_ik moves with the plane normals and meets the cone at an
 // angle) stays below M_SENS R per unit roundoff, i.e. about 3e-6 R.
 constexpr float M_SENS = 50.0f;
+// An elliptical arc whose points t(phi) = (n0 + n1 c + n2 s) / (d0 + d1 c +
+// d2 s) have a first-order FP32 error bound above M_ILL R per unit angle or
+// coefficient error (the bound (sum|n| + |t| sum|d|) / |D| + |t| over the
+// arc, in units of R) is subdivided in FP64 from the inputs: a steep section
+// (degenerate node) can send D through zero, where FP32 points drift by far
+// more than the vertex tolerance.
+constexpr float M_ILL = 8.0f;
 
 // node flags (same bits as LM_NODE_* in liblm.h)
 constexpr uint32_t NF_NEAR_TANGENT = 1u, NF_DEGENERATE = 2u, NF_INCONSISTENT = 4u,
@@ -687,6 +694,41 @@ __device__ __forceinline__ V3<T> geo_point(const ArcGeo<T>& g, T phi) {
   T t = (g.n0 + g.n1 * c + g.n2 * s) / (g.d0 + g.d1 * c + g.d2 * s);
   V3<T> r = g.e1 * c + g.e2 * s;
   return g.u * (g.Rs + t * g.co) + r * (g.Rco - t * g.s);
+}
+
+// Whether an elliptical arc [phi0, phi0 + dphi] of geometry g at a node of
+// radius R is ill-conditioned in the sense of M_ILL: D(phi) = d0 + rho
+// cos(phi - phi_d) is bounded away from zero over the arc by its values at
+// the ends and at its interior minimum / maximum; a sign change is ill.
+template <typename T>
+__device__ __forceinline__ bool arc_ill(const ArcGeo<T>& g, T phi0, T dphi, T R) {
+  const T nsum = fabs(g.n0) + fabs(g.n1) + fabs(g.n2), dsum = fabs(g.d0) + fabs(g.d1) + fabs(g.d2);
+  const T rho = lm_sqrt(g.d1 * g.d1 + g.d2 * g.d2), nr = fabs(g.n0) + lm_sqrt(g.n1 * g.n1 + g.n2 * g.n2);
+  auto bound = [&](T dmin) {
+    const T tmax = nr / dmin;
+    return (nsum + tmax * dsum) / dmin + tmax <= T(M_ILL) * R;
+  };
+  // D keeps its sign on the whole circle
+  if (fabs(g.d0) > rho && bound(fabs(g.d0) - rho)) return false;
+  // extremes of D over the arc: the ends, and phi_d (max) / phi_d + pi (min)
+  // when inside
+  T c, s;
+  lm_sincos(phi0, &s, &c);
+  const T D0 = g.d0 + g.d1 * c + g.d2 * s;
+  lm_sincos(phi0 + dphi, &s, &c);
+  const T D1 = g.d0 + g.d1 * c + g.d2 * s;
+  T lo = fmin(D0, D1), hi = fmax(D0, D1);
+  if (rho > T(0)) {
+    const T pd = lm_atan2(g.d2, g.d1);
+    T r = pd - phi0;
+    r -= T(PI2) * floor(r * T(1.0 / PI2));
+    if (r <= dphi) hi = fmax(hi, g.d0 + rho);
+    r = pd + T(0.5 * PI2) - phi0;
+    r -= T(PI2) * floor(r * T(1.0 / PI2));
+    if (r <= dphi) lo = fmin(lo, g.d0 - rho);
+  }
+  if (lo <= T(0) && hi >= T(0)) return true;
+  return !bound(lo > T(0) ? lo : -hi);
 }
 
 // Exactly rounded operations: no contraction or reassociation is left to the

@@ -422,9 +422,11 @@ __device__ void node_metamesh(WarpSmem<T, C>& S, const MMArgs<T>& A, int64_t n, 
   }
   nflags = __reduce_or_sync(0xffffffffu, nflags);
 
-  // ---- seam vertices for strut ends no vertex touches
+  // ---- seam vertices for strut ends no vertex touches, in end order: a seam
+  // cut by plane P_ij also touches end j, which then needs no seam of its own
   if (!overflow) {
     uint32_t seam_need = 0;
+    uint64_t covered = 0;  // ends touched by the seams added so far
     for (int i0 = 0; i0 < d; i0 += 32) {
       int i = i0 + lane;
       bool need = false, unc = false;
@@ -471,10 +473,22 @@ __device__ void node_metamesh(WarpSmem<T, C>& S, const MMArgs<T>& A, int64_t n, 
         int li = i0 + src;
         int lb = __shfl_sync(0xffffffffu, lab, src);
         T bs = __shfl_sync(0xffffffffu, best, src);
+        if ((covered >> li) & 1ull) continue;
+        covered |= (1ull << li) | (lb >= 0 ? (1ull << lb) : 0ull);
         int nvc = S.nv;
         if (nvc >= C::V) { overflow = true; break; }
+        // a seam cut by a plane lies on a steep section (the node is
+        // degenerate): its position is ill-conditioned in FP32 and is taken
+        // in FP64 from the inputs
+        if (!IS64 && lb >= 0) ensure64(S, L, n, d, lane);
         if (lane == 0) {
-          S.vz[nvc] = surf_point(S.E[li], T(1), T(0), bs, R);
+          if (!IS64 && lb >= 0) {
+            const EndG<double>* E = ends64(S);
+            V3<double> z64 = surf_point(E[li], 1.0, 0.0, hval(E[li], E[lb], 1.0, 0.0, R64), R64);
+            S.vz[nvc] = mk3((T)z64.x, (T)z64.y, (T)z64.z);
+          } else {
+            S.vz[nvc] = surf_point(S.E[li], T(1), T(0), bs, R);
+          }
           S.vkey[nvc] = (1ull << li) | (lb >= 0 ? (1ull << lb) : 0ull);
           S.vfl[nvc] = VF_SEAM | (lb < 0 ? VF_SPHERE : 0u);
           S.vgen[nvc] = gen_code(2, 0, li, lb < 0 ? 0 : lb, 0) | (lb >= 0 ? (1u << 21) : 0u);

@@ -646,12 +646,12 @@ __global__ void __launch_bounds__(128, 3) k_tri_thread(TriArgs<T> A, const int64
       }
       return x;
     };
-    // rotation of B: first point after the single drop of its keys
+    // rotation of B: its first smallest key (one pass for the keys, one to
+    // bring the iterator there and keep the point before it)
     V3<T> bprev = mk3(T(0), T(0), T(0));
     int sB = 0;
     {
-      T kprev = T(0);
-      bool found = false;
+      T kmin = T(0);
       for (int j = 0; j < nB; j++) {
         V3<T> z;
         T th;
@@ -659,20 +659,23 @@ __global__ void __launch_bounds__(128, 3) k_tri_thread(TriArgs<T> A, const int64
         bool ex;
         double k64;
         T kj = keyB(IB, th, ex, k64);
-        if (j > 0 && kj < kprev) {
+        if (j == 0 || kj < kmin) {
+          kmin = kj;
           sB = j;
-          found = true;
-          break;
         }
-        bprev = z;
-        kprev = kj;
         it_next(A, IB);
       }
-      if (!found) {
-        // no drop: rotation 0; B's last point is the one before it
-        sB = 0;
-        it_load(A, IB, 0);
+      it_load(A, IB, 0);
+      const int jprev = sB > 0 ? sB - 1 : nB - 1;
+      for (int j = 0; j <= jprev; j++) {
+        if (j == jprev) {
+          T th;
+          it_point(A, IB, bprev, th);
+        }
+        if (j == jprev && sB == 0) break;
+        it_next(A, IB);
       }
+      if (sB == 0) it_load(A, IB, 0);
     }
     // zipper (ties advance A)
     const int64_t t0 = A.tri_off[e] - out_first;
@@ -803,7 +806,7 @@ struct TileEntry {
   T phi0, dphi, psi;
   int N, pre;
   int64_t ga;
-  uint8_t rev, own, pad0, pad1;
+  uint8_t rev, own, ill, pad1;  // ill: points subdivided in FP64 (arc_ill)
 };
 
 struct TileHdr {
@@ -840,7 +843,11 @@ struct TileLayout {
   __host__ __device__ size_t z() const { return th() + r16c(2 * (size_t)pmax * sizeof(T)); }
   __host__ __device__ size_t fl() const { return z() + r16c(2 * (size_t)pmax * sizeof(V3<T>)); }
   __host__ __device__ size_t stage() const { return ent(); }
-  __host__ __device__ size_t ea64() const { return fl() + (exact ? r16c(2 * (size_t)pmax) : 0); }
+  // flags per point (FP64 pass) or zipper decisions per triangle (sequential
+  // zipper of the FP64 pass and of FP64 lattices)
+  __host__ __device__ size_t ea64() const {
+    return fl() + ((exact || sizeof(T) == 8) ? r16c(2 * (size_t)pmax) : 0);
+  }
   __host__ __device__ size_t th64() const { return ea64() + (exact ? r16c(2 * (size_t)emax * 32) : 0); }
   __host__ __device__ size_t e64() const { return th64() + (exact ? r16c(2 * (size_t)pmax * 8) : 0); }
   __host__ __device__ size_t pid() const {
@@ -922,6 +929,27 @@ __device__ __noinline__ double point64_theta(const TriArgs<T>& A, const EndG<dou
   return d.psi + wrap_from(raw_angle(E[li], z) - d.psi, -ETA_PHI);
 }
 
+// FP64 position of subdivision point m of N of arc ga (node-relative), from
+// the FP64 strut ends E of its node (rare path: ill-conditioned arcs)
+template <typename T>
+__device__ __noinline__ V3<double> point64_pos(const TriArgs<T>& A, const EndG<double>* E, int64_t node,
+                                               int64_t ga, int N, int m) {
+  uint32_t av = A.arc_vtx[ga];
+  int v0 = av & 255, v1 = (av >> 8) & 255, o = (av >> 16) & 255, ot = (int)((av >> 24) & 255) - 1;
+  int64_t vo = A.vtx_off[node];
+  double R = (double)A.lat.node_R[node];
+  V3<double> z0 = gen_point<double>(E, R, A.vtx_gen[vo + v0]);
+  V3<double> z1 = v1 == v0 ? z0 : gen_point<double>(E, R, A.vtx_gen[vo + v1]);
+  double a0 = norm_angle(raw_angle(E[o], z0)), a1 = norm_angle(raw_angle(E[o], z1));
+  double dd = a1 - a0;
+  if (v0 == v1) dd = PI2;
+  else if (dd <= 0.0) dd += PI2;
+  double phi = a0 + dd * (double)m / (double)N, c, sn;
+  sincos(phi, &sn, &c);
+  double t = ot >= 0 ? hval(E[o], E[ot], c, sn, R) : 0.0;
+  return surf_point(E[o], c, sn, t, R);
+}
+
 // exact segment count of arc ga (rare path; E as above)
 template <typename T>
 __device__ __noinline__ int segments64_cached(const TriArgs<T>& A, const EndG<double>* E, int64_t node,
@@ -959,7 +987,7 @@ __device__ __forceinline__ int tile_entry_setup_impl(const TriArgs<T>& A, int64_
   uint32_t ent = A.loop_ent[qi];
   en.ga = ao + (ent & 0x7fffffffu);
   en.rev = (uint8_t)(ent >> 31);
-  en.pad0 = en.pad1 = 0;
+  en.ill = en.pad1 = 0;
   uint32_t av = A.arc_vtx[en.ga];
   int o = (av >> 16) & 255, ot = (int)((av >> 24) & 255) - 1;
   // the entry's first vertex in loop order (its first point)
@@ -973,6 +1001,12 @@ __device__ __forceinline__ int tile_entry_setup_impl(const TriArgs<T>& A, int64_
   int32_t oid = L.adj[rb + o];
   en.g = node_arc_geo<T>(L, node, oid, ot >= 0 ? L.adj[rb + ot] : -1, R);
   en.own = (oid == eid);
+  // an ill-conditioned elliptical arc is subdivided in FP64 (FP64 pass; both
+  // struts of the arc take this decision from the same bits)
+  if (!IS64 && ot >= 0 && arc_ill<T>(en.g, en.phi0, en.dphi, R)) {
+    if (!EXACT) return -2;
+    en.ill = 1;
+  }
   if (en.own && !en.rev) {
     en.psi = en.phi0;
   } else {
@@ -1108,7 +1142,7 @@ __device__ __forceinline__ bool tile_strut(const TriArgs<T>& A, const TileSmem<T
         else Nq = tile_entry_setup_impl<T, false>(A, node, eid, qi, ENT + X * A.emax + qq, z0);
       }
       if (__any_sync(m, Nq < 0)) {
-        tfb_add(A.fb, 12, tl == 0, m);
+        tfb_add(A.fb, __any_sync(m, Nq == -2) ? 17 : 12, tl == 0, m);
         defer = true;
         break;
       }
@@ -1198,7 +1232,13 @@ __device__ __forceinline__ bool tile_strut(const TriArgs<T>& A, const TileSmem<T
       int mm = en.rev ? en.N - sidx : sidx;
       if (sidx != 0) {
         T phi;
-        const V3<T> zz = arc_point_rn(en.g, en.phi0, en.dphi, mm, en.N, phi);
+        V3<T> zz = arc_point_rn(en.g, en.phi0, en.dphi, mm, en.N, phi);
+        if constexpr (FP64_STEPS) {
+          if (en.ill) {
+            const V3<double> z64 = point64_pos<T>(A, S.E64 + X * A.dmax, node, en.ga, en.N, mm);
+            zz = mk3((T)z64.x, (T)z64.y, (T)z64.z);
+          }
+        }
         Z[X * A.pmax + p] = zz;
         TH[X * A.pmax + p] = en.own ? phi : en.psi + wrap_from(raw_angle(own, zz) - en.psi, T(-ETA_PHI));
       }
@@ -1240,7 +1280,25 @@ __device__ __forceinline__ bool tile_strut(const TriArgs<T>& A, const TileSmem<T
     return first == 0x7fffffff ? 0 : first;
   };
   int sB = rotation();
-  if (!IS64) {
+  // The merge-path placement below equals the oracle's sequential zipper only
+  // when A's angles and B's rotated keys are both non-decreasing.  On
+  // degenerate nodes (sections past a strut's length, steep sections) a loop
+  // can turn back in angle: the FP32 pass defers such a strut, and the FP64
+  // pass and FP64 lattices run the sequential zipper instead.
+  bool unsorted = false;
+  {
+    bool u = false;
+    for (int i = tl; i < nA; i += TL)
+      if ((i + 1 < nA ? TH[i + 1] : thA0 + T(PI2)) < TH[i]) u = true;
+    for (int j = tl; j + 1 < nB; j += TL)
+      if (KB[wrap_idx(sB + j + 1, nB)] < KB[wrap_idx(sB + j, nB)]) u = true;
+    unsorted = __any_sync(m, u);
+  }
+  if (!IS64 && !EXACT && unsorted) {
+    tfb_add(A.fb, 16, tl == 0, m);
+    return true;
+  }
+  if (!IS64 && !unsorted) {
     // A points whose angle lies within M_ZIP of some B key + ETA_ZIP: every
     // such pair is decided in FP64 (B keys are sorted after the rotation up
     // to FP32 rounding, so each scan stops at the first key clearly out of
@@ -1284,8 +1342,14 @@ __device__ __forceinline__ bool tile_strut(const TriArgs<T>& A, const TileSmem<T
     tfb_add(A.fb, 14, tl == 0, m);
     return true;
   }
-  if (FP64_STEPS) tfb_add(A.fb, 10, anyt && tl == 0, m);
-  if (FP64_STEPS && anyt) {
+  if (FP64_STEPS) tfb_add(A.fb, 10, (anyt || unsorted) && tl == 0, m);
+  if (FP64_STEPS && (anyt || unsorted)) {
+    // out of order: every key is taken in FP64 for the sequential zipper
+    if (unsorted) {
+      for (int p = tl; p < nA; p += TL) FL[p] = 1;
+      for (int j = tl; j < nB; j += TL) FL[A.pmax + j] = 1;
+      __syncwarp(m);
+    }
     // A's first point fixes the window: always taken in FP64 here
     if (tl == 0) FL[0] |= 4;
     __syncwarp(m);
@@ -1329,7 +1393,7 @@ __device__ __forceinline__ bool tile_strut(const TriArgs<T>& A, const TileSmem<T
       if (f & 2) KB[j] = (T)x64;
     }
     __syncwarp(m);
-    if (A.fb) {
+    if (A.fb && !unsorted) {
       // pairs of keys decided in FP64 (within M_ZIP of the tie band's edge)
       int pairs = 0;
       for (int i = tl + 1; i <= nA; i += TL) {
@@ -1341,9 +1405,51 @@ __device__ __forceinline__ bool tile_strut(const TriArgs<T>& A, const TileSmem<T
       if (pairs) atomicAdd(A.fb + 15, (unsigned long long)pairs);
     }
     __syncwarp(m);
-    sB = rotation();
+    if (unsorted) {
+      // B rotated to its first smallest FP64 key
+      double mn = 1e300;
+      for (int j = tl; j < nB; j += TL) mn = fmin(mn, S.TH64[A.pmax + j]);
+#pragma unroll
+      for (int o = TL / 2; o > 0; o >>= 1) mn = fmin(mn, __shfl_xor_sync(m, mn, o, TL));
+      int first = 0x7fffffff;
+      for (int j = tl; j < nB; j += TL)
+        if (S.TH64[A.pmax + j] == mn) first = min(first, j);
+#pragma unroll
+      for (int o = TL / 2; o > 0; o >>= 1) first = min(first, __shfl_xor_sync(m, first, o, TL));
+      sB = first == 0x7fffffff ? 0 : first;
+    } else {
+      sB = rotation();
+    }
   }
-  const double a0_64 = FP64_STEPS && anyt ? S.TH64[0] : 0.0;
+  const double a0_64 = FP64_STEPS && (anyt || unsorted) ? S.TH64[0] : 0.0;
+  const int ntri = nA + nB;
+  if (unsorted) {
+    // sequential zipper (the oracle's process; ties advance A): the decision
+    // of each triangle goes to FL, and lanes place their triangles by prefix
+    // counts of the decisions
+    if (tl == 0) {
+      auto keyA = [&](int i) -> double {
+        if constexpr (FP64_STEPS) return i < nA ? S.TH64[i] : a0_64 + PI2;
+        else return i < nA ? (double)TH[i] : (double)thA0 + PI2;
+      };
+      auto keyB = [&](int j) -> double {
+        const int jb = wrap_idx(sB + j, nB);
+        if constexpr (FP64_STEPS) return S.TH64[A.pmax + jb];
+        else return (double)KB[jb];
+      };
+      int ia = 0, ib = -1;
+      for (int p = 0; p < ntri; p++) {
+        bool takeA;
+        if (ib == nB - 1) takeA = true;
+        else if (ia >= nA) takeA = false;
+        else takeA = keyA(ia + 1) <= keyB(ib + 1) + ETA_ZIP;
+        FL[p] = takeA ? 1 : 0;
+        if (takeA) ia++;
+        else ib++;
+      }
+    }
+    __syncwarp(m);
+  }
   auto a_before_b = [&](int i, int j) -> bool {
     int jb = wrap_idx(sB + j, nB);
     if (FP64_STEPS && anyt && FL[i < nA ? i : 0] && FL[A.pmax + jb]) {
@@ -1355,7 +1461,6 @@ __device__ __forceinline__ bool tile_strut(const TriArgs<T>& A, const TileSmem<T
   };
   // ---- triangles by merge-path; TL * RPL records per round
   constexpr int RPL = TILE_RPL;
-  const int ntri = nA + nB;
   const int64_t t0 = A.tri_off[e] - out_first;
   V3<T> cA = node_xyz<T, T>(L, lo), cB = node_xyz<T, T>(L, hi);
   V3<T> dAB = cB - cA;
@@ -1366,22 +1471,32 @@ __device__ __forceinline__ bool tile_strut(const TriArgs<T>& A, const TileSmem<T
     // 16-byte aligned: 50 t = 2 t mod 16)
     const int sh = vec_ok ? (int)((2 * (t0 + c0)) & 15) : 0;
     int i = ibase;
+    if (unsorted) {
+      // A events before this lane's first position, from the decisions
+      int na_ = 0;
+#pragma unroll
+      for (int r = 0; r < RPL; r++)
+        if (p + r < ntri) na_ += FL[p + r];
+      i = ibase + tile_excl_scan<TL>(na_, tl, m);
+    }
     if (p < ntri) {
-      // i = A events among the first p (ties -> A first); i(p) - i(c0) is
-      // between 0 and p - c0, so the search spans at most RPL TL + 1 values
-      int li_ = p - nB > ibase ? p - nB : ibase, hi_ = ibase + RPL * tl;
-      if (hi_ > nA) hi_ = nA;
-      while (li_ < hi_) {
-        int mid = (li_ + hi_) >> 1;
-        if (a_before_b(mid + 1, p - mid - 1)) li_ = mid + 1;
-        else hi_ = mid;
+      if (!unsorted) {
+        // i = A events among the first p (ties -> A first); i(p) - i(c0) is
+        // between 0 and p - c0, so the search spans at most RPL TL + 1 values
+        int li_ = p - nB > ibase ? p - nB : ibase, hi_ = ibase + RPL * tl;
+        if (hi_ > nA) hi_ = nA;
+        while (li_ < hi_) {
+          int mid = (li_ + hi_) >> 1;
+          if (a_before_b(mid + 1, p - mid - 1)) li_ = mid + 1;
+          else hi_ = mid;
+        }
+        i = li_;
       }
-      i = li_;
 #pragma unroll
       for (int r = 0; r < RPL; r++) {
         if (p + r >= ntri) break;
         const int jn = p + r - i;
-        const bool isA = (i < nA) && (jn == nB || a_before_b(i + 1, jn));
+        const bool isA = unsorted ? FL[p + r] != 0 : (i < nA) && (jn == nB || a_before_b(i + 1, jn));
         int jp = wrap_idx(sB + jn - 1, nB);
         V3<T> za = Z[i < nA ? i : 0];
         V3<T> zp = Z[A.pmax + jp];

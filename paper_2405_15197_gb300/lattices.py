@@ -119,7 +119,7 @@ def irregular(n_nodes: int, kmin=4, kmax=16, sigma=0.25, seed: int = SEED, r_sca
     pts = rng.random((n_nodes, 3))
     kv = rng.integers(kmin, kmax + 1, size=n_nodes)
     tree = cKDTree(pts)
-    _, nb = tree.query(pts, k=kmax + 1)
+    _, nb = tree.query(pts, k=kmax + 1, workers=-1)
     nb = nb[:, 1:]
     cols = np.arange(kmax)[None, :] < kv[:, None]
     src = np.repeat(np.arange(n_nodes), kv)

@@ -211,8 +211,11 @@ def lm_status_string(s):
     return load().lm_status_string(int(s)).decode()
 
 
+N_FP64_COUNTS = 18
+
+
 def lm_fp64_counts(h):
-    out = (ctypes.c_int64 * 16)()
+    out = (ctypes.c_int64 * N_FP64_COUNTS)()
     _ck(load().lm_fp64_counts(h, out), "lm_fp64_counts")
     return list(out)
 

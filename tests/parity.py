@@ -1,11 +1,12 @@
 """GPU-vs-oracle comparison helpers for the parity tests.
 
-Index data (vertex keys and generators, arc records, loops, holes, triangle
-counts per item) must match bit-exactly on every node that is not flagged
-near-tangent (a strut pair within 1e-6 of tangency) or degenerate (the node
-violates the lattice model: a plane section that is not an ellipse, a vertex
-past a strut's far end; there the per-node algorithm still runs but its
-ill-conditioned decisions are not compared); coordinates within 2e-5 relative for
+Node flags must agree on every node.  Index data (vertex keys and
+generators, arc records, loops, holes, triangle counts per item) must match
+bit-exactly on every node that is not flagged near-tangent (a strut pair
+within 1e-6 of tangency, the one exemption the parity contract allows);
+nodes flagged degenerate (the lattice model is violated there, e.g. a
+vertex past a strut's far end) run the same per-node algorithm on both sides
+and are compared like any other.  Coordinates agree within 2e-5 relative for
 FP32 (vertex offsets relative to the nodal radius, angles relative to 2 pi,
 absolute STL coordinates relative to their magnitude plus the radius), and
 1e-12 for the FP64 instantiation's meta-mesh data.
@@ -18,7 +19,7 @@ import oracle
 
 NEAR_TANGENT = 1
 DEGENERATE = 2
-EXEMPT = NEAR_TANGENT | DEGENERATE
+EXEMPT = NEAR_TANGENT
 
 
 def lattice_as(lat, dtype):
@@ -42,8 +43,11 @@ class Report:
         self.exempt_nodes = 0
         self.max_dz = 0.0
         self.max_dphi = 0.0
+        self.bad_nodes = []
 
-    def fail(self, msg):
+    def fail(self, msg, node=None):
+        if node is not None:
+            self.bad_nodes.append(node)
         if len(self.errors) < 50:
             self.errors.append(msg)
 
@@ -51,9 +55,12 @@ class Report:
         return not self.errors
 
 
-def compare_metamesh(g, o: oracle.Oracle, nodes=None, z_tol=2e-5, phi_tol=2e-5, node_map=None):
+def compare_metamesh(g, o: oracle.Oracle, nodes=None, z_tol=2e-5, phi_tol=2e-5, node_map=None,
+                     exempt=EXEMPT):
     """Compare the GPU download `g` with oracle `o` node by node.
-    node_map: oracle node id -> GPU node id (sub-lattice comparisons)."""
+    node_map: oracle node id -> GPU node id (sub-lattice comparisons).
+    exempt: node-flag bits that exempt a node from the data comparison (its
+    flags are still compared)."""
     rep = Report()
     row_o, adj_o, R_o = o.csr()
     nodes = range(o.N) if nodes is None else nodes
@@ -63,31 +70,31 @@ def compare_metamesh(g, o: oracle.Oracle, nodes=None, z_tol=2e-5, phi_tol=2e-5, 
         nd = o.node(n)
         fo = nd["flags"]
         fg = int(g["node_flags"][gn])
-        if (fo | fg) & EXEMPT:
+        if fo != fg:
+            rep.fail(f"node {n}: flags oracle {fo} gpu {fg}", n)
+            continue
+        if fo & exempt:
             rep.exempt_nodes += 1
-            rep.exempt_flags = getattr(rep, "exempt_flags", 0) | fo | fg
+            rep.exempt_flags = getattr(rep, "exempt_flags", 0) | fo
             continue
         rep.checked_nodes += 1
-        if fo != fg:
-            rep.fail(f"node {n}: flags oracle {fo} gpu {fg}")
-            continue
         R = R_o[n]
         v0, v1 = g["vtx_off"][gn], g["vtx_off"][gn + 1]
         if v1 - v0 != len(nd["vz"]):
-            rep.fail(f"node {n}: V oracle {len(nd['vz'])} gpu {v1 - v0}")
+            rep.fail(f"node {n}: V oracle {len(nd['vz'])} gpu {v1 - v0}", n)
             continue
         if not np.array_equal(g["vtx_key"][v0:v1], nd["vkey"]) or \
            not np.array_equal(g["vtx_flags"][v0:v1], nd["vflags"]) or \
            not np.array_equal(g["vtx_gen"][v0:v1], nd["vgen"]):
-            rep.fail(f"node {n}: vertex keys/flags/generators differ\n  o {nd['vkey']} {nd['vgen']}\n  g {g['vtx_key'][v0:v1]} {g['vtx_gen'][v0:v1]}")
+            rep.fail(f"node {n}: vertex keys/flags/generators differ\n  o {nd['vkey']} {nd['vgen']}\n  g {g['vtx_key'][v0:v1]} {g['vtx_gen'][v0:v1]}", n)
             continue
         dz = np.abs(g["vtx_z"][v0:v1].astype(np.float64) - nd["vz"]).max(initial=0.0) / R
         rep.max_dz = max(rep.max_dz, dz)
         if dz > z_tol:
-            rep.fail(f"node {n}: vertex positions differ by {dz:.3g} R")
+            rep.fail(f"node {n}: vertex positions differ by {dz:.3g} R", n)
         a0, a1 = g["arc_off"][gn], g["arc_off"][gn + 1]
         if a1 - a0 != len(nd["arc_i"]):
-            rep.fail(f"node {n}: arcs oracle {len(nd['arc_i'])} gpu {a1 - a0}")
+            rep.fail(f"node {n}: arcs oracle {len(nd['arc_i'])} gpu {a1 - a0}", n)
             continue
         ga = g["arc_ends"][a0:a1]
         av = g["arc_vtx"][a0:a1]
@@ -99,12 +106,12 @@ def compare_metamesh(g, o: oracle.Oracle, nodes=None, z_tol=2e-5, phi_tol=2e-5, 
             oe = np.where(oe >= 0, gmap[np.maximum(oe, 0)], -1)
         if not np.array_equal(ga, oe) or not np.array_equal(av & 255, nd["arc_i"][:, 2]) or \
            not np.array_equal((av >> 8) & 255, nd["arc_i"][:, 3]):
-            rep.fail(f"node {n}: arc records differ\n  o {nd['arc_i'].tolist()}\n  g {np.c_[ga, av & 255, (av >> 8) & 255].tolist()}")
+            rep.fail(f"node {n}: arc records differ\n  o {nd['arc_i'].tolist()}\n  g {np.c_[ga, av & 255, (av >> 8) & 255].tolist()}", n)
             continue
         dp = np.abs(g["arc_phi"][a0:a1].astype(np.float64) - nd["arc_f"]).max(initial=0.0) / (2 * np.pi)
         rep.max_dphi = max(rep.max_dphi, dp)
         if dp > phi_tol:
-            rep.fail(f"node {n}: arc angles differ by {dp:.3g} x 2pi")
+            rep.fail(f"node {n}: arc angles differ by {dp:.3g} x 2pi", n)
         # loops, per local strut end
         p = 0
         b = row_o[n]
@@ -113,17 +120,17 @@ def compare_metamesh(g, o: oracle.Oracle, nodes=None, z_tol=2e-5, phi_tol=2e-5, 
             geid = eid if gmap is None else gmap[eid]
             e0, e1 = g["end_off"][geid], g["end_off"][geid + 1]
             if not np.array_equal(g["loop_ent"][e0:e1], nd["loop_ent"][p:p + ln]):
-                rep.fail(f"node {n} end {eid}: loop entries differ\n  o {nd['loop_ent'][p:p + ln]}\n  g {g['loop_ent'][e0:e1]}")
+                rep.fail(f"node {n} end {eid}: loop entries differ\n  o {nd['loop_ent'][p:p + ln]}\n  g {g['loop_ent'][e0:e1]}", n)
             p += ln
         h0, h1 = g["hole_off_n"][gn], g["hole_off_n"][gn + 1]
         if h1 - h0 != len(nd["hole_len"]):
-            rep.fail(f"node {n}: holes oracle {len(nd['hole_len'])} gpu {h1 - h0}")
+            rep.fail(f"node {n}: holes oracle {len(nd['hole_len'])} gpu {h1 - h0}", n)
             continue
         p = 0
         for hh, ln in enumerate(nd["hole_len"]):
             q0, q1 = g["hole_off"][h0 + hh], g["hole_off"][h0 + hh + 1]
             if not np.array_equal(g["hole_ent"][q0:q1], nd["hole_ent"][p:p + ln]):
-                rep.fail(f"node {n} hole {hh}: entries differ")
+                rep.fail(f"node {n} hole {hh}: entries differ", n)
             p += ln
     return rep
 

@@ -272,6 +272,37 @@ def test_segment_count_reading():
     assert set(cnt[:o.E].tolist()) <= {34, 35, 36}
 
 
+@pytest.mark.parametrize("excess,want", [(2.0 ** -11, 10), (2.0 ** -9, 11), (1e-9, 10)])
+def test_segment_count_offset_band(excess, want):
+    """The segment-count offset 2^-10 in N = ceil(dphi k / 2pi - 2^-10): an
+    arc whose ratio dphi k / 2pi exceeds the integer 10 by 2^-11 gets 10
+    segments (a 1e-6 offset would give 11), by 2^-9 gets 11, by 1e-9 gets
+    10 under either reading.
+
+    The arc is built from a closed form.  A node with a cylinder (strut 0,
+    s_0 = 0) and a cone (strut 1, s_1 = (R - R_far)/L) whose axes meet at a
+    right angle has two circle points n = a u_0 + b u_1 +- g w with
+    u_0.n = 0 and u_1.n = s_1, i.e. at angles +-acos(s_1) from u_1 around
+    u_0, so the elliptical arc of strut 0 spans dphi = 2 acos(s_1 / sin 90deg).
+    Choosing s_1 = cos(dphi / 2) puts the ratio where the test wants it."""
+    R, k = 0.1, 16
+    x = 10.0 + excess
+    dphi = x * 2.0 * math.pi / k
+    s1 = math.cos(dphi / 2.0)
+    lat = L.star([(1, 0, 0), (0, 1, 0)], radius=R, far_radii=[R, R - s1])
+    o = oracle.Oracle(lat)
+    nd = o.node(0)
+    ell = [a for a in range(len(nd["arc_i"])) if nd["arc_i"][a, 1] >= 0]
+    assert len(ell) == 1 and nd["arc_i"][ell[0], 0] == 0       # owned by strut 0's end
+    a = ell[0]
+    assert nd["arc_f"][a, 1] == pytest.approx(2.0 * math.acos(s1), abs=1e-12)
+    assert len(o.arc_points(0, a, k)) - 1 == want
+    # strut 0's band: its loop at the centre (elliptical + circular arc of
+    # 2pi - dphi, ratio 16 - x) and the far end's full circle (16)
+    n_circ = math.ceil(k - x - 2.0 ** -10)
+    assert o.tri_counts(k)[0] == want + n_circ + k
+
+
 # ------------------------------------------------------- P6: brute force
 @pytest.mark.parametrize("name", ["bccjit2", "octet1", "irregular"])
 def test_envelope_dense_sampling(name):
