@@ -703,16 +703,21 @@ void strut_tris(const Mesh& M, int64_t e, int k, std::vector<Tri>& T, Frozen* fz
   // B's angles moved into the window [thA0 - ETA_ZIP, thA0 + 2pi - ETA_ZIP)
   // that starts at A's first point; B is rotated to start at its smallest
   // key, and the band starts from the B point just before A's first point.
+  // Keys within ETA_PHI of the smallest are ties (the angle tie rule): the
+  // first of them in loop order is taken (a loop that runs along an arc and
+  // back, on a degenerate node, meets each of its points twice).
   double thA0 = PA.th[0];
   std::vector<double> kB(nB);
-  int sB = 0;
+  double kmin = INFINITY;
   for (int j = 0; j < nB; j++) {
     double x = PB.th[j];
     while (x < thA0 - ETA_ZIP) x += PI2;
     while (x >= thA0 + PI2 - ETA_ZIP) x -= PI2;
     kB[j] = x;
-    if (x < kB[sB]) sB = j;
+    kmin = std::min(kmin, x);
   }
+  int sB = 0;
+  while (kB[sB] > kmin + ETA_PHI) sB++;
   auto thA = [&](int i) { return i < nA ? PA.th[i] : thA0 + PI2; };
   auto thB = [&](int j) { return kB[(sB + j) % nB]; };  // j = 0..nB-1
   auto pA = [&](int i) { return PA.z[i % nA]; };

@@ -536,6 +536,10 @@ __device__ void node_metamesh(WarpSmem<T, C>& S, const MMArgs<T>& A, int64_t n, 
           if (!((S.vkey[v] >> i) & 1ull)) continue;
           T a = raw_angle(S.E[i], S.vz[v]);
           if (!IS64 && fabs(a + T(PHI_CUT)) <= T(M_ANG)) unc = true;
+          // a vertex far from the node (past a strut's length: degenerate
+          // node) has an FP32 position error of ulp(|z|), too coarse for its
+          // angle: the loop is ordered with FP64 angles
+          if (!IS64 && dot(S.vz[v], S.vz[v]) > T(256) * R * R) unc = true;
           a = norm_angle(a);
           // stable insertion by angle
           int p = q;

@@ -646,8 +646,9 @@ __global__ void __launch_bounds__(128, 3) k_tri_thread(TriArgs<T> A, const int64
       }
       return x;
     };
-    // rotation of B: its first smallest key (one pass for the keys, one to
-    // bring the iterator there and keep the point before it)
+    // rotation of B: its first key within ETA_PHI of the smallest (one pass
+    // for the smallest key, one to find the start, keeping the point before
+    // it; the whole loop when the start is point 0)
     V3<T> bprev = mk3(T(0), T(0), T(0));
     int sB = 0;
     {
@@ -659,23 +660,27 @@ __global__ void __launch_bounds__(128, 3) k_tri_thread(TriArgs<T> A, const int64
         bool ex;
         double k64;
         T kj = keyB(IB, th, ex, k64);
-        if (j == 0 || kj < kmin) {
-          kmin = kj;
-          sB = j;
-        }
+        if (j == 0 || kj < kmin) kmin = kj;
         it_next(A, IB);
       }
       it_load(A, IB, 0);
-      const int jprev = sB > 0 ? sB - 1 : nB - 1;
-      for (int j = 0; j <= jprev; j++) {
-        if (j == jprev) {
-          T th;
-          it_point(A, IB, bprev, th);
+      bool found = false;
+      for (int j = 0; j < nB; j++) {
+        V3<T> z;
+        T th;
+        it_point(A, IB, z, th);
+        bool ex;
+        double k64;
+        T kj = keyB(IB, th, ex, k64);
+        if (!found && kj <= kmin + T(ETA_PHI)) {
+          found = true;
+          sB = j;
+          if (j > 0) break;  // the iterator stays at the start point
         }
-        if (j == jprev && sB == 0) break;
+        bprev = z;
         it_next(A, IB);
       }
-      if (sB == 0) it_load(A, IB, 0);
+      if (sB == 0) it_load(A, IB, 0);  // bprev is the loop's last point
     }
     // zipper (ties advance A)
     const int64_t t0 = A.tri_off[e] - out_first;
@@ -1267,14 +1272,18 @@ __device__ __forceinline__ bool tile_strut(const TriArgs<T>& A, const TileSmem<T
     return true;
   }
   __syncwarp(m);
+  // B starts at its first key within ETA_PHI of the smallest (ties: loop
+  // order); kmin receives the smallest key
+  T kmin = T(0);
   auto rotation = [&]() {
     T mn = T(1e30);
     for (int j = tl; j < nB; j += TL) mn = fmin(mn, KB[j]);
 #pragma unroll
     for (int o = TL / 2; o > 0; o >>= 1) mn = fmin(mn, __shfl_xor_sync(m, mn, o, TL));
+    kmin = mn;
     int first = 0x7fffffff;
     for (int j = tl; j < nB; j += TL)
-      if (KB[j] == mn) first = min(first, j);
+      if (KB[j] <= mn + T(ETA_PHI)) first = min(first, j);
 #pragma unroll
     for (int o = TL / 2; o > 0; o >>= 1) first = min(first, __shfl_xor_sync(m, first, o, TL));
     return first == 0x7fffffff ? 0 : first;
@@ -1285,14 +1294,21 @@ __device__ __forceinline__ bool tile_strut(const TriArgs<T>& A, const TileSmem<T
   // degenerate nodes (sections past a strut's length, steep sections) a loop
   // can turn back in angle: the FP32 pass defers such a strut, and the FP64
   // pass and FP64 lattices run the sequential zipper instead.
+  // In FP32 a second key within M_ZIP of the smallest makes the rotation
+  // uncertain: it is taken like out-of-order keys, from FP64 keys.
   bool unsorted = false;
   {
     bool u = false;
+    int near_min = 0;
     for (int i = tl; i < nA; i += TL)
       if ((i + 1 < nA ? TH[i + 1] : thA0 + T(PI2)) < TH[i]) u = true;
     for (int j = tl; j + 1 < nB; j += TL)
       if (KB[wrap_idx(sB + j + 1, nB)] < KB[wrap_idx(sB + j, nB)]) u = true;
-    unsorted = __any_sync(m, u);
+    if (!IS64)
+      for (int j = tl; j < nB; j += TL) near_min += KB[j] <= kmin + T(M_ZIP);
+#pragma unroll
+    for (int o = TL / 2; o > 0; o >>= 1) near_min += __shfl_xor_sync(m, near_min, o, TL);
+    unsorted = __any_sync(m, u) || near_min > 1;
   }
   if (!IS64 && !EXACT && unsorted) {
     tfb_add(A.fb, 16, tl == 0, m);
@@ -1413,7 +1429,7 @@ __device__ __forceinline__ bool tile_strut(const TriArgs<T>& A, const TileSmem<T
       for (int o = TL / 2; o > 0; o >>= 1) mn = fmin(mn, __shfl_xor_sync(m, mn, o, TL));
       int first = 0x7fffffff;
       for (int j = tl; j < nB; j += TL)
-        if (S.TH64[A.pmax + j] == mn) first = min(first, j);
+        if (S.TH64[A.pmax + j] <= mn + ETA_PHI) first = min(first, j);
 #pragma unroll
       for (int o = TL / 2; o > 0; o >>= 1) first = min(first, __shfl_xor_sync(m, first, o, TL));
       sB = first == 0x7fffffff ? 0 : first;

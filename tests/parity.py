@@ -7,7 +7,8 @@ within 1e-6 of tangency, the one exemption the parity contract allows);
 nodes flagged degenerate (the lattice model is violated there, e.g. a
 vertex past a strut's far end) run the same per-node algorithm on both sides
 and are compared like any other.  Coordinates agree within 2e-5 relative for
-FP32 (vertex offsets relative to the nodal radius, angles relative to 2 pi,
+FP32 (vertex offsets relative to their length plus the nodal radius, angles
+relative to 2 pi,
 absolute STL coordinates relative to their magnitude plus the radius), and
 1e-12 for the FP64 instantiation's meta-mesh data.
 """
@@ -56,11 +57,13 @@ class Report:
 
 
 def compare_metamesh(g, o: oracle.Oracle, nodes=None, z_tol=2e-5, phi_tol=2e-5, node_map=None,
-                     exempt=EXEMPT):
+                     exempt=EXEMPT, degenerate_tol=None):
     """Compare the GPU download `g` with oracle `o` node by node.
     node_map: oracle node id -> GPU node id (sub-lattice comparisons).
     exempt: node-flag bits that exempt a node from the data comparison (its
-    flags are still compared)."""
+    flags are still compared; on an exempt node only the exempting bits).
+    degenerate_tol: coordinate tolerance on nodes flagged degenerate (their
+    steep sections are ill-conditioned), default z_tol / phi_tol."""
     rep = Report()
     row_o, adj_o, R_o = o.csr()
     nodes = range(o.N) if nodes is None else nodes
@@ -70,7 +73,7 @@ def compare_metamesh(g, o: oracle.Oracle, nodes=None, z_tol=2e-5, phi_tol=2e-5, 
         nd = o.node(n)
         fo = nd["flags"]
         fg = int(g["node_flags"][gn])
-        if fo != fg:
+        if (fo & exempt) != (fg & exempt) or (not fo & exempt and fo != fg):
             rep.fail(f"node {n}: flags oracle {fo} gpu {fg}", n)
             continue
         if fo & exempt:
@@ -78,6 +81,9 @@ def compare_metamesh(g, o: oracle.Oracle, nodes=None, z_tol=2e-5, phi_tol=2e-5, 
             rep.exempt_flags = getattr(rep, "exempt_flags", 0) | fo
             continue
         rep.checked_nodes += 1
+        ztol, ptol = z_tol, phi_tol
+        if degenerate_tol is not None and fo & DEGENERATE:
+            ztol = ptol = degenerate_tol
         R = R_o[n]
         v0, v1 = g["vtx_off"][gn], g["vtx_off"][gn + 1]
         if v1 - v0 != len(nd["vz"]):
@@ -88,10 +94,13 @@ def compare_metamesh(g, o: oracle.Oracle, nodes=None, z_tol=2e-5, phi_tol=2e-5, 
            not np.array_equal(g["vtx_gen"][v0:v1], nd["vgen"]):
             rep.fail(f"node {n}: vertex keys/flags/generators differ\n  o {nd['vkey']} {nd['vgen']}\n  g {g['vtx_key'][v0:v1]} {g['vtx_gen'][v0:v1]}", n)
             continue
-        dz = np.abs(g["vtx_z"][v0:v1].astype(np.float64) - nd["vz"]).max(initial=0.0) / R
+        # relative to |z| + R: a vertex far from its node (degenerate nodes)
+        # is stored to FP32 precision of its magnitude
+        scale = np.linalg.norm(nd["vz"], axis=1) + R
+        dz = (np.abs(g["vtx_z"][v0:v1].astype(np.float64) - nd["vz"]).max(axis=1, initial=0.0) / scale).max(initial=0.0)
         rep.max_dz = max(rep.max_dz, dz)
-        if dz > z_tol:
-            rep.fail(f"node {n}: vertex positions differ by {dz:.3g} R", n)
+        if dz > ztol:
+            rep.fail(f"node {n}: vertex positions differ by {dz:.3g} (|z| + R)", n)
         a0, a1 = g["arc_off"][gn], g["arc_off"][gn + 1]
         if a1 - a0 != len(nd["arc_i"]):
             rep.fail(f"node {n}: arcs oracle {len(nd['arc_i'])} gpu {a1 - a0}", n)
@@ -110,7 +119,7 @@ def compare_metamesh(g, o: oracle.Oracle, nodes=None, z_tol=2e-5, phi_tol=2e-5, 
             continue
         dp = np.abs(g["arc_phi"][a0:a1].astype(np.float64) - nd["arc_f"]).max(initial=0.0) / (2 * np.pi)
         rep.max_dphi = max(rep.max_dphi, dp)
-        if dp > phi_tol:
+        if dp > ptol:
             rep.fail(f"node {n}: arc angles differ by {dp:.3g} x 2pi", n)
         # loops, per local strut end
         p = 0
@@ -156,11 +165,13 @@ def compare_triangles(gn, gv, otris, R_max, tol=2e-5):
     e = [ov[:, 1] - ov[:, 0], ov[:, 2] - ov[:, 1], ov[:, 0] - ov[:, 2]]
     emax = np.max([np.linalg.norm(x, axis=1) for x in e], axis=0)
     area2 = np.linalg.norm(np.cross(e[0], -e[2]), axis=1)
-    cond = np.where(area2 > 0, R_max * emax / np.maximum(area2, 1e-300), np.inf)
-    # a vertex error of d R moves the normal by about d R / height, and the
-    # height of a triangle is area2 / emax = R_max / cond: the FP32 vertex
-    # tolerance of 2e-5 R therefore allows normal errors up to 2e-5 cond
-    ntol = 1e-4 + 2e-5 * cond
+    smax = np.abs(ov).max(axis=(1, 2)) + R_max
+    cond = np.where(area2 > 0, smax * emax / np.maximum(area2, 1e-300), np.inf)
+    # a vertex error d moves the normal by about d / height, and the height
+    # of a triangle is area2 / emax: the vertex tolerance tol (|x| + R) allows
+    # normal errors up to about 2 tol (|x| + R) emax / area2 = 2 tol cond
+    # (two vertices moving)
+    ntol = 1e-4 + 2.0 * tol * cond
     dn = np.linalg.norm(gn.astype(np.float64) - on, axis=1)
     good = np.isfinite(cond)
     errs = []
