@@ -97,14 +97,24 @@ typedef struct {
  *                   the emit pass for the nodes it holds (0 = up to 35 % of
  *                   the memory free beside the CSR offsets; < 0 = none:
  *                   every node is emitted);
- *                   the result is the same either way                       */
+ *                   the result is the same either way
+ *   redo_list_cap : capacity of the list of struts the FP32 stitching pass
+ *                   defers to the FP64 pass (0 = max(E/32, 65,536), at most
+ *                   2^24); a call that defers more scans the deferral bitmap
+ *                   instead (same result)
+ *   mem_budget    : > 0: device allocations that would take the bytes this
+ *                   handle has allocated (cumulative, temporaries included)
+ *                   past this budget fail as an out-of-memory device would
+ *                   (LM_ERR_OOM); a hook for exercising the failure path    */
 typedef struct {
   int32_t autotune;
   int32_t block_warps;
   int32_t grid_ctas;
   int32_t nodes_per_task;
   int64_t arena_bytes;
-  int64_t reserved[3];
+  int64_t redo_list_cap;
+  int64_t mem_budget;
+  int64_t reserved[1];
 } lm_options;
 
 typedef struct lm_metamesh lm_metamesh;
@@ -254,23 +264,27 @@ void lm_metamesh_free(lm_metamesh* mm);
 const char* lm_status_string(lm_status s);
 
 /* Allocation-free variant of lm_tri_count + lm_triangulate for one item
- * range (the paper has no counterpart: it concerns how this library gets
- * its scratch memory).  For callers that cannot allocate device memory when
- * they triangulate -- e.g. code running while a stream is captured into a
- * CUDA graph, or under an external allocator or memory budget that forbids a
- * library cudaMalloc.  It calls no cudaMalloc/cudaFree: every scratch buffer
- * (per-item counts and offsets of the range, scan workspace, FP64 fallback
- * contexts, work counters) lives in one fixed file-scope device array of
- * about 7 MB that each GPU loading the library keeps until process exit.
+ * range (the paper has no counterpart: it concerns how this library gets its
+ * scratch memory).  For callers that cannot let the library allocate device
+ * memory when they triangulate: an application whose GPU memory belongs to a
+ * framework's caching allocator or to a pool sized up front (a library
+ * cudaMalloc could fail there, or make the pool give back its cache), or a
+ * latency-bound loop in which cudaMalloc / cudaFree would stall the device.
+ * It calls no cudaMalloc, cudaFree or allocating library routine: every
+ * scratch buffer (per-item counts and offsets of the range, scan workspace,
+ * FP64 fallback contexts, work counters) lives in one fixed file-scope device
+ * array of about 7 MB that each GPU loading the library keeps until process
+ * exit.  The records are byte-identical to lm_triangulate's.
  *   item range : at most 262,144 items per call, else LM_ERR_CAPACITY;
  *                chunk larger ranges
  *   d_out      : records of the range from byte 0 (as lm_triangulate)
  *   h_ntris    : host, receives the range's triangle count (may be NULL)
  * Needs only lm_build_metamesh first (no lm_tri_count).  Synchronises the
- * stream once (to size the kernel's shared memory).  The first call on each
- * device resolves the array's device address; make that first call before
- * any stream capture.  All calls share the array and it keeps the last
- * call's contents (the call clears what must start empty): calls that
+ * stream once (it reads the range's triangle count back to size the
+ * kernel's shared memory).  The first call on each device resolves the
+ * array's device address (cudaGetSymbolAddress); make that first call
+ * before any stream capture.  All calls share the array and it keeps the
+ * last call's contents (the call clears what must start empty): calls that
  * overlap on the GPU (other streams, other threads) race and must be
  * serialised by the caller.  Capacity overflow is reported by lm_last_error
  * as for lm_triangulate.                                                 */
@@ -305,6 +319,20 @@ lm_status lm_fp64_counts(const lm_metamesh* mm, int64_t out[LM_N_FP64_COUNTS]);
 /* Utility (no counterpart in the paper): number of CUDA kernels this library
  * has launched in the process so far (host-side counter).                */
 long long lm_launch_count(void);
+
+/* Utility (no counterpart in the paper): text of the CUDA error behind the
+ * last LM_ERR_CUDA or LM_ERR_OOM that a call of this library returned on the
+ * calling thread ("no error" if none).                                    */
+const char* lm_cuda_error_string(void);
+
+/* Utility (no counterpart in the paper): the library's FP32 angle functions,
+ * evaluated element-wise on device arrays so that their error can be tested
+ * against FP64 references: d_atan2[i] = lm_atan2(d_y[i], d_x[i]) (polynomial
+ * arctangent, see csrc/lm_geom.cuh), (d_sin[i], d_cos[i]) = lm_sincos(d_a[i])
+ * (two-part reduction by 2 pi, then the hardware sine / cosine).  All arrays
+ * device, n float32 each; asynchronous on `stream`.                       */
+lm_status lm_eval_angle_fns(const float* d_y, const float* d_x, const float* d_a, int64_t n, float* d_atan2,
+                            float* d_sin, float* d_cos, void* stream);
 
 #ifdef __cplusplus
 }

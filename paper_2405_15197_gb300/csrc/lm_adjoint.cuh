@@ -22,101 +22,114 @@
 //     contracted with its adjoint.  Nothing per node is stored between the
 //     forward pass and this one.
 #pragma once
+#include <type_traits>
+
 #include "lm_geom.cuh"
 
 namespace lm {
 
-// value + W tangents (forward mode)
-template <int W>
+// scalar helpers: the FP32 path calls the single-precision functions, the
+// FP64 path the double ones
+__device__ __forceinline__ float sc_atan2(float y, float x) { return atan2f(y, x); }
+__device__ __forceinline__ double sc_atan2(double y, double x) { return atan2(y, x); }
+__device__ __forceinline__ void sc_sincos(float a, float* s, float* c) { sincosf(a, s, c); }
+__device__ __forceinline__ void sc_sincos(double a, double* s, double* c) { sincos(a, s, c); }
+__device__ __forceinline__ float sc_rem2pi(float a) { return remainderf(a, (float)PI2); }
+__device__ __forceinline__ double sc_rem2pi(double a) { return remainder(a, PI2); }
+
+// value + W tangents (forward mode) in scalar S (the lattice's precision)
+template <int W, typename S = float>
 struct Dual {
-  float v;
-  float t[W];
-  __device__ Dual() : v(0.0f) {
+  S v;
+  S t[W];
+  __device__ Dual() : v(S(0)) {
 #pragma unroll
-    for (int i = 0; i < W; i++) t[i] = 0.0f;
+    for (int i = 0; i < W; i++) t[i] = S(0);
   }
-  __device__ Dual(float x) : v(x) {
+  __device__ Dual(S x) : v(x) {
 #pragma unroll
-    for (int i = 0; i < W; i++) t[i] = 0.0f;
+    for (int i = 0; i < W; i++) t[i] = S(0);
   }
-  __device__ Dual(int x) : Dual((float)x) {}
-  __device__ Dual(bool x) : Dual(x ? 1.0f : 0.0f) {}
-  __device__ explicit Dual(double x) : Dual((float)x) {}
-  __device__ explicit operator float() const { return v; }
+  __device__ Dual(int x) : Dual((S)x) {}
+  __device__ Dual(bool x) : Dual(x ? S(1) : S(0)) {}
+  template <typename X, typename = typename std::enable_if<std::is_floating_point<X>::value &&
+                                                           !std::is_same<X, S>::value>::type>
+  __device__ explicit Dual(X x) : Dual((S)x) {}
+  __device__ explicit operator S() const { return v; }
 };
 
-template <int W>
-__device__ __forceinline__ Dual<W> operator+(const Dual<W>& a, const Dual<W>& b) {
-  Dual<W> r;
+template <int W, typename S>
+__device__ __forceinline__ Dual<W, S> operator+(const Dual<W, S>& a, const Dual<W, S>& b) {
+  Dual<W, S> r;
   r.v = a.v + b.v;
 #pragma unroll
   for (int i = 0; i < W; i++) r.t[i] = a.t[i] + b.t[i];
   return r;
 }
-template <int W>
-__device__ __forceinline__ Dual<W> operator-(const Dual<W>& a, const Dual<W>& b) {
-  Dual<W> r;
+template <int W, typename S>
+__device__ __forceinline__ Dual<W, S> operator-(const Dual<W, S>& a, const Dual<W, S>& b) {
+  Dual<W, S> r;
   r.v = a.v - b.v;
 #pragma unroll
   for (int i = 0; i < W; i++) r.t[i] = a.t[i] - b.t[i];
   return r;
 }
-template <int W>
-__device__ __forceinline__ Dual<W> operator-(const Dual<W>& a) {
-  Dual<W> r;
+template <int W, typename S>
+__device__ __forceinline__ Dual<W, S> operator-(const Dual<W, S>& a) {
+  Dual<W, S> r;
   r.v = -a.v;
 #pragma unroll
   for (int i = 0; i < W; i++) r.t[i] = -a.t[i];
   return r;
 }
-template <int W>
-__device__ __forceinline__ Dual<W> operator*(const Dual<W>& a, const Dual<W>& b) {
-  Dual<W> r;
+template <int W, typename S>
+__device__ __forceinline__ Dual<W, S> operator*(const Dual<W, S>& a, const Dual<W, S>& b) {
+  Dual<W, S> r;
   r.v = a.v * b.v;
 #pragma unroll
   for (int i = 0; i < W; i++) r.t[i] = a.v * b.t[i] + b.v * a.t[i];
   return r;
 }
-template <int W>
-__device__ __forceinline__ Dual<W> operator/(const Dual<W>& a, const Dual<W>& b) {
-  Dual<W> r;
-  float ib = 1.0f / b.v;
+template <int W, typename S>
+__device__ __forceinline__ Dual<W, S> operator/(const Dual<W, S>& a, const Dual<W, S>& b) {
+  Dual<W, S> r;
+  S ib = S(1) / b.v;
   r.v = a.v * ib;
 #pragma unroll
   for (int i = 0; i < W; i++) r.t[i] = (a.t[i] - r.v * b.t[i]) * ib;
   return r;
 }
-template <int W>
-__device__ __forceinline__ bool operator<(const Dual<W>& a, const Dual<W>& b) { return a.v < b.v; }
-template <int W>
-__device__ __forceinline__ bool operator>(const Dual<W>& a, const Dual<W>& b) { return a.v > b.v; }
-template <int W>
-__device__ __forceinline__ bool operator<=(const Dual<W>& a, const Dual<W>& b) { return a.v <= b.v; }
-template <int W>
-__device__ __forceinline__ bool operator>=(const Dual<W>& a, const Dual<W>& b) { return a.v >= b.v; }
+template <int W, typename S>
+__device__ __forceinline__ bool operator<(const Dual<W, S>& a, const Dual<W, S>& b) { return a.v < b.v; }
+template <int W, typename S>
+__device__ __forceinline__ bool operator>(const Dual<W, S>& a, const Dual<W, S>& b) { return a.v > b.v; }
+template <int W, typename S>
+__device__ __forceinline__ bool operator<=(const Dual<W, S>& a, const Dual<W, S>& b) { return a.v <= b.v; }
+template <int W, typename S>
+__device__ __forceinline__ bool operator>=(const Dual<W, S>& a, const Dual<W, S>& b) { return a.v >= b.v; }
 
-template <int W>
-__device__ __forceinline__ Dual<W> lm_sqrt(const Dual<W>& a) {
-  Dual<W> r;
-  r.v = a.v > 0.0f ? sqrtf(a.v) : 0.0f;
-  float h = r.v > 0.0f ? 0.5f / r.v : 0.0f;
+template <int W, typename S>
+__device__ __forceinline__ Dual<W, S> lm_sqrt(const Dual<W, S>& a) {
+  Dual<W, S> r;
+  r.v = a.v > S(0) ? lm_sqrt(a.v) : S(0);
+  S h = r.v > S(0) ? S(0.5) / r.v : S(0);
 #pragma unroll
   for (int i = 0; i < W; i++) r.t[i] = a.t[i] * h;
   return r;
 }
-template <int W>
-__device__ __forceinline__ Dual<W> lm_atan2(const Dual<W>& y, const Dual<W>& x) {
-  Dual<W> r;
-  r.v = atan2f(y.v, x.v);
-  float ir = 1.0f / (x.v * x.v + y.v * y.v);
+template <int W, typename S>
+__device__ __forceinline__ Dual<W, S> lm_atan2(const Dual<W, S>& y, const Dual<W, S>& x) {
+  Dual<W, S> r;
+  r.v = sc_atan2(y.v, x.v);
+  S ir = S(1) / (x.v * x.v + y.v * y.v);
 #pragma unroll
   for (int i = 0; i < W; i++) r.t[i] = (x.v * y.t[i] - y.v * x.t[i]) * ir;
   return r;
 }
-template <int W>
-__device__ __forceinline__ void lm_sincos(const Dual<W>& a, Dual<W>* s, Dual<W>* c) {
-  float sv, cv;
-  sincosf(a.v, &sv, &cv);
+template <int W, typename S>
+__device__ __forceinline__ void lm_sincos(const Dual<W, S>& a, Dual<W, S>* s, Dual<W, S>* c) {
+  S sv, cv;
+  sc_sincos(a.v, &sv, &cv);
   s->v = sv;
   c->v = cv;
 #pragma unroll
@@ -127,9 +140,9 @@ __device__ __forceinline__ void lm_sincos(const Dual<W>& a, Dual<W>* s, Dual<W>*
 }
 
 // a constant shifted by a value-only offset (continuous angle tracking)
-template <int W>
-__device__ __forceinline__ Dual<W> shift(const Dual<W>& a, float d) {
-  Dual<W> r = a;
+template <int W, typename S>
+__device__ __forceinline__ Dual<W, S> shift(const Dual<W, S>& a, S d) {
+  Dual<W, S> r = a;
   r.v += d;
   return r;
 }

@@ -12,6 +12,7 @@
 #include <tuple>
 #include <vector>
 
+#include "lm_geom.cuh"
 #include "lm_internal.h"
 #include "lm_scan.cuh"
 
@@ -31,16 +32,29 @@ namespace {
     if (e_ != cudaSuccess) return st_cuda(e_);   \
   } while (0)
 
+// the CUDA error behind the last LM_ERR_CUDA / LM_ERR_OOM of this thread
+thread_local cudaError_t g_last_cuda = cudaSuccess;
+
 lm_status st_cuda(cudaError_t e) {
+  g_last_cuda = e;
   if (e == cudaErrorMemoryAllocation) return LM_ERR_OOM;
   return LM_ERR_CUDA;
 }
 
-template <typename X>
-cudaError_t dalloc(X** p, int64_t n, cudaStream_t st) {
+// device allocation on behalf of handle mm, within its test budget
+// (lm_options.mem_budget)
+cudaError_t mm_malloc(lm_metamesh* mm, void** p, size_t bytes, cudaStream_t st) {
   *p = nullptr;
+  if (mm->opt.mem_budget > 0 && mm->alloc_bytes + (int64_t)bytes > mm->opt.mem_budget)
+    return cudaErrorMemoryAllocation;
+  cudaError_t e = cudaMallocAsync(p, bytes, st);
+  if (e == cudaSuccess) mm->alloc_bytes += (int64_t)bytes;
+  return e;
+}
+template <typename X>
+cudaError_t dalloc(lm_metamesh* mm, X** p, int64_t n, cudaStream_t st) {
   if (n <= 0) n = 1;
-  return cudaMallocAsync((void**)p, sizeof(X) * (size_t)n, st);
+  return mm_malloc(mm, (void**)p, sizeof(X) * (size_t)n, st);
 }
 template <typename X>
 void dfree(X*& p, cudaStream_t st) {
@@ -256,25 +270,25 @@ lm_status build_impl(lm_metamesh* mm, cudaStream_t st) {
   cudaEventRecord(ev[0], st);
   int* deg = nullptr;
   int* fill = nullptr;
-  LM_CK(dalloc(&mm->d_err, 4, st));
-  LM_CK(dalloc(&mm->d_queue, 8, st));
-  LM_CK(dalloc(&mm->d_misc, 8, st));
-  LM_CK(dalloc(&mm->d_acc, 4, st));
-  LM_CK(dalloc(&mm->d_fb, LM_N_FP64_COUNTS, st));
+  LM_CK(dalloc(mm, &mm->d_err, 4, st));
+  LM_CK(dalloc(mm, &mm->d_queue, 8, st));
+  LM_CK(dalloc(mm, &mm->d_misc, 8, st));
+  LM_CK(dalloc(mm, &mm->d_acc, 4, st));
+  LM_CK(dalloc(mm, &mm->d_fb, LM_N_FP64_COUNTS, st));
   LM_CK(cudaMemsetAsync(mm->d_fb, 0, LM_N_FP64_COUNTS * sizeof(unsigned long long), st));
   LM_CK(cudaMemsetAsync(mm->d_err, 0, 4 * sizeof(int), st));
   LM_CK(cudaMemsetAsync(mm->d_misc, 0, 8 * sizeof(int), st));
   T* node_R = nullptr;
-  LM_CK(dalloc(&node_R, N, st));
+  LM_CK(dalloc(mm, &node_R, N, st));
   mm->node_R = node_R;
-  LM_CK(dalloc(&mm->row_ptr, N + 1, st));
-  LM_CK(dalloc(&mm->adj, 2 * E, st));
-  LM_CK(dalloc(&deg, N, st));
-  LM_CK(dalloc(&fill, N, st));
+  LM_CK(dalloc(mm, &mm->row_ptr, N + 1, st));
+  LM_CK(dalloc(mm, &mm->adj, 2 * E, st));
+  LM_CK(dalloc(mm, &deg, N, st));
+  LM_CK(dalloc(mm, &fill, N, st));
   LM_CK(cudaMemsetAsync(deg, 0, sizeof(int) * N, st));
   LM_CK(cudaMemsetAsync(fill, 0, sizeof(int) * N, st));
   mm->scan_ws_n = scan_ws_elems(std::max<int64_t>(std::max<int64_t>(N + E, 2 * E), 1));
-  LM_CK(dalloc(&mm->scan_ws, mm->scan_ws_n, st));
+  LM_CK(dalloc(mm, &mm->scan_ws, mm->scan_ws_n, st));
   count_launch(); k_strut_validate<T><<<grid_for(E), 256, 0, st>>>(mm->ends, radii, E, N, deg, mm->d_err);
   LM_CK(cudaGetLastError());
   lm_status s = read_err(mm, st);
@@ -299,7 +313,7 @@ lm_status build_impl(lm_metamesh* mm, cudaStream_t st) {
   int32_t* lists = nullptr;
   int* bcnt = mm->d_misc + 4;
   LM_CK(cudaMemsetAsync(bcnt, 0, 4 * sizeof(int), st));
-  LM_CK(dalloc(&lists, (int64_t)NB_BUCKETS * std::max<int64_t>(N, 1), st));
+  LM_CK(dalloc(mm, &lists, (int64_t)NB_BUCKETS * std::max<int64_t>(N, 1), st));
   count_launch(); k_bucket<<<grid_for(N), 256, 0, st>>>(mm->row_ptr, N, bcnt, lists, std::max<int64_t>(N, 1));
   LM_CK(cudaGetLastError());
   int hb[4] = {0, 0, 0, 0};
@@ -308,9 +322,9 @@ lm_status build_impl(lm_metamesh* mm, cudaStream_t st) {
   cudaEventRecord(ev[1], st);
   // ---- count pass
   int32_t *node_cnt = nullptr, *end_cnt = nullptr;
-  LM_CK(dalloc(&node_cnt, 4 * N, st));
-  LM_CK(dalloc(&end_cnt, 2 * E, st));
-  LM_CK(dalloc(&mm->node_flags, N, st));
+  LM_CK(dalloc(mm, &node_cnt, 4 * N, st));
+  LM_CK(dalloc(mm, &end_cnt, 2 * E, st));
+  LM_CK(dalloc(mm, &mm->node_flags, N, st));
   LM_CK(cudaMemsetAsync(node_cnt, 0, sizeof(int32_t) * 4 * N, st));
   LM_CK(cudaMemsetAsync(end_cnt, 0, sizeof(int32_t) * 2 * E, st));
   LM_CK(cudaMemsetAsync(mm->node_flags, 0, sizeof(uint32_t) * N, st));
@@ -352,7 +366,7 @@ lm_status build_impl(lm_metamesh* mm, cudaStream_t st) {
     if (capb > 4096.0) {
       const size_t cap_bytes = ((size_t)capb) & ~(size_t)255;
       const size_t start_off = cap_bytes, ctr_off = start_off + (((size_t)8 * std::max<int64_t>(N, 1) + 255) & ~(size_t)255);
-      if (cudaMallocAsync(&arena_buf, ctr_off + 256, st) == cudaSuccess) {
+      if (mm_malloc(mm, &arena_buf, ctr_off + 256, st) == cudaSuccess) {
         unsigned char* b = (unsigned char*)arena_buf;
         arena.buf = b;
         arena.cap = (int64_t)cap_bytes;
@@ -371,11 +385,11 @@ lm_status build_impl(lm_metamesh* mm, cudaStream_t st) {
     if (pass == 1) {
       cudaEventRecord(ev[2], st);
       // offsets from the counts
-      LM_CK(dalloc(&mm->vtx_off, N + 1, st));
-      LM_CK(dalloc(&mm->arc_off, N + 1, st));
-      LM_CK(dalloc(&mm->hole_off_n, N + 1, st));
-      LM_CK(dalloc(&mm->hent_off_n, N + 1, st));
-      LM_CK(dalloc(&mm->end_off, 2 * E + 1, st));
+      LM_CK(dalloc(mm, &mm->vtx_off, N + 1, st));
+      LM_CK(dalloc(mm, &mm->arc_off, N + 1, st));
+      LM_CK(dalloc(mm, &mm->hole_off_n, N + 1, st));
+      LM_CK(dalloc(mm, &mm->hent_off_n, N + 1, st));
+      LM_CK(dalloc(mm, &mm->end_off, 2 * E + 1, st));
       LM_CK(scan_excl<int32_t>(node_cnt + 0, 4, N, mm->vtx_off, mm->scan_ws, st));
       LM_CK(scan_excl<int32_t>(node_cnt + 1, 4, N, mm->arc_off, mm->scan_ws, st));
       LM_CK(scan_excl<int32_t>(node_cnt + 2, 4, N, mm->hole_off_n, mm->scan_ws, st));
@@ -407,16 +421,16 @@ lm_status build_impl(lm_metamesh* mm, cudaStream_t st) {
       T *vz = nullptr, *aphi = nullptr;
       auto alloc_out = [&]() -> cudaError_t {
         cudaError_t e;
-        if ((e = dalloc(&vz, 3 * mm->V, st)) != cudaSuccess) return e;
-        if ((e = dalloc(&mm->vtx_key, mm->V, st)) != cudaSuccess) return e;
-        if ((e = dalloc(&mm->vtx_flags, mm->V, st)) != cudaSuccess) return e;
-        if ((e = dalloc(&mm->vtx_gen, mm->V, st)) != cudaSuccess) return e;
-        if ((e = dalloc(&mm->arc_ends, 2 * mm->A, st)) != cudaSuccess) return e;
-        if ((e = dalloc(&mm->arc_vtx, mm->A, st)) != cudaSuccess) return e;
-        if ((e = dalloc(&aphi, 2 * mm->A, st)) != cudaSuccess) return e;
-        if ((e = dalloc(&mm->loop_ent, mm->LE, st)) != cudaSuccess) return e;
-        if ((e = dalloc(&mm->hole_off, mm->H + 1, st)) != cudaSuccess) return e;
-        return dalloc(&mm->hole_ent, mm->HE, st);
+        if ((e = dalloc(mm, &vz, 3 * mm->V, st)) != cudaSuccess) return e;
+        if ((e = dalloc(mm, &mm->vtx_key, mm->V, st)) != cudaSuccess) return e;
+        if ((e = dalloc(mm, &mm->vtx_flags, mm->V, st)) != cudaSuccess) return e;
+        if ((e = dalloc(mm, &mm->vtx_gen, mm->V, st)) != cudaSuccess) return e;
+        if ((e = dalloc(mm, &mm->arc_ends, 2 * mm->A, st)) != cudaSuccess) return e;
+        if ((e = dalloc(mm, &mm->arc_vtx, mm->A, st)) != cudaSuccess) return e;
+        if ((e = dalloc(mm, &aphi, 2 * mm->A, st)) != cudaSuccess) return e;
+        if ((e = dalloc(mm, &mm->loop_ent, mm->LE, st)) != cudaSuccess) return e;
+        if ((e = dalloc(mm, &mm->hole_off, mm->H + 1, st)) != cudaSuccess) return e;
+        return dalloc(mm, &mm->hole_ent, mm->HE, st);
       };
       cudaError_t ae = alloc_out();
       if (ae != cudaSuccess && arena_buf) {
@@ -501,7 +515,7 @@ lm_status build_impl(lm_metamesh* mm, cudaStream_t st) {
   if (arena_buf) cudaFreeAsync(arena_buf, st);
   // statistics
   unsigned long long* dstat = nullptr;
-  LM_CK(dalloc(&dstat, 4, st));
+  LM_CK(dalloc(mm, &dstat, 4, st));
   LM_CK(cudaMemsetAsync(dstat, 0, 4 * sizeof(unsigned long long), st));
   count_launch(); k_mm_stats<<<grid_for(std::max<int64_t>(std::max<int64_t>(mm->A, N), 2 * E)), 256, 0, st>>>(
       mm->arc_ends, mm->A, mm->node_flags, N, end_cnt, 2 * E, dstat);
@@ -524,7 +538,7 @@ lm_status build_impl(lm_metamesh* mm, cudaStream_t st) {
   dfree(deg, st);
   // FP64 fallback contexts of the triangulation kernels
   mm->scratch_warps = tri_scratch_warps();
-  LM_CK(cudaMallocAsync((void**)&mm->scratch, node64_bytes() * (size_t)mm->scratch_warps, st));
+  LM_CK(mm_malloc(mm, (void**)&mm->scratch, node64_bytes() * (size_t)mm->scratch_warps, st));
   // every context starts as "no node" (node id -1)
   LM_CK(cudaMemsetAsync(mm->scratch, 0xff, node64_bytes() * (size_t)mm->scratch_warps, st));
   LM_CK(cudaStreamSynchronize(st));
@@ -586,13 +600,15 @@ template <typename T>
 lm_status tri_count_impl(lm_metamesh* mm, int k, cudaStream_t st, int64_t* total) {
   const int64_t n_items = mm->E + mm->N;
   if (!mm->item_cnt) {
-    LM_CK(dalloc(&mm->item_cnt, n_items, st));
-    LM_CK(dalloc(&mm->tri_off, n_items + 1, st));
-    LM_CK(dalloc(&mm->redo_bits, mm->E / 32 + 1, st));
+    LM_CK(dalloc(mm, &mm->item_cnt, n_items, st));
+    LM_CK(dalloc(mm, &mm->tri_off, n_items + 1, st));
+    LM_CK(dalloc(mm, &mm->redo_bits, mm->E / 32 + 1, st));
     // the deferred struts are rare (about 1 % on cone-strut lattices); more
     // than redo_cap in one call fall back to scanning the bitmap
-    mm->redo_cap = std::min<int64_t>(std::max<int64_t>(mm->E / 32, 65536), (int64_t)1 << 24);
-    LM_CK(dalloc(&mm->redo_list, mm->redo_cap + 1, st));
+    mm->redo_cap = mm->opt.redo_list_cap > 0
+                       ? mm->opt.redo_list_cap
+                       : std::min<int64_t>(std::max<int64_t>(mm->E / 32, 65536), (int64_t)1 << 24);
+    LM_CK(dalloc(mm, &mm->redo_list, mm->redo_cap + 1, st));
   }
   LM_CK(cudaMemsetAsync(mm->d_misc + 2, 0, sizeof(int), st));
   TriLaunch<T> L = tri_launch<T>(mm);
@@ -673,6 +689,18 @@ lm_status chunk_graphs(lm_metamesh* mm, int k, int64_t chunk, int64_t n_items, u
 }
 
 bool valid_k(int k) { return k >= 1 && k <= 4096; }
+
+// the library's FP32 angle functions on arrays (for tests of their error)
+__global__ void k_eval_angle_fns(const float* y, const float* x, const float* a, int64_t n, float* at, float* sn,
+                                 float* cs) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    at[i] = lm::lm_atan2(y[i], x[i]);
+    float s, c;
+    lm::lm_sincos(a[i], &s, &c);
+    sn[i] = s;
+    cs[i] = c;
+  }
+}
 
 }  // namespace
 
@@ -965,6 +993,17 @@ lm_status lm_triangulate_stream(lm_metamesh* mm, int32_t k, int64_t chunk_items,
 }
 
 long long lm_launch_count(void) { return g_launches.load(); }
+
+const char* lm_cuda_error_string(void) { return cudaGetErrorString(g_last_cuda); }
+
+lm_status lm_eval_angle_fns(const float* d_y, const float* d_x, const float* d_a, int64_t n, float* d_atan2,
+                            float* d_sin, float* d_cos, void* stream) {
+  if (n < 0 || (n > 0 && (!d_y || !d_x || !d_a || !d_atan2 || !d_sin || !d_cos))) return LM_ERR_INVALID_ARG;
+  if (n == 0) return LM_OK;
+  count_launch();
+  k_eval_angle_fns<<<grid_for(n), 256, 0, (cudaStream_t)stream>>>(d_y, d_x, d_a, n, d_atan2, d_sin, d_cos);
+  return cudaGetLastError() == cudaSuccess ? LM_OK : LM_ERR_CUDA;
+}
 
 lm_status lm_fp64_counts(const lm_metamesh* mm, int64_t out[LM_N_FP64_COUNTS]) {
   if (!mm || !out) return LM_ERR_INVALID_ARG;

@@ -163,8 +163,8 @@ __global__ void __launch_bounds__(128) k_bwd_holes(TriArgs<T> A, const int32_t* 
   }
 }
 
-template <int W>
-__device__ __forceinline__ void dual_warp_sum(Dual<W>& a) {
+template <int W, typename S>
+__device__ __forceinline__ void dual_warp_sum(Dual<W, S>& a) {
   for (int o = 16; o > 0; o >>= 1) {
     a.v += __shfl_xor_sync(0xffffffffu, a.v, o);
 #pragma unroll
@@ -173,44 +173,45 @@ __device__ __forceinline__ void dual_warp_sum(Dual<W>& a) {
 }
 
 // contract a point's tangents with its adjoint
-template <int W>
-__device__ __forceinline__ void contract(float acc[W], const V3<Dual<W>>& p, const float* g) {
-  float gx = g[0], gy = g[1], gz = g[2];
+template <int W, typename S>
+__device__ __forceinline__ void contract(S acc[W], const V3<Dual<W, S>>& p, const S* g) {
+  S gx = g[0], gy = g[1], gz = g[2];
 #pragma unroll
   for (int i = 0; i < W; i++) acc[i] += gx * p.x.t[i] + gy * p.y.t[i] + gz * p.z.t[i];
 }
 
 // interior point m of arc ga (node-relative), in dual numbers
 template <typename T, int W>
-__device__ __forceinline__ V3<Dual<W>> arc_point_dual(const ArcGeo<Dual<W>>& g, const Dual<W>& p0,
-                                                       const Dual<W>& dp, int m, int N) {
-  Dual<W> phi = p0 + dp * Dual<W>((float)m / (float)N);
+__device__ __forceinline__ V3<Dual<W, T>> arc_point_dual(const ArcGeo<Dual<W, T>>& g, const Dual<W, T>& p0,
+                                                          const Dual<W, T>& dp, int m, int N) {
+  Dual<W, T> phi = p0 + dp * Dual<W, T>((T)m / (T)N);
   return geo_point(g, phi);
 }
 
 // angles of arc ga in its owner's frame, followed continuously from the
 // stored values (the forward pass's arc data)
 template <typename T, int W>
-__device__ __forceinline__ void arc_angles_dual(const TriArgs<T>& A, int64_t ga, const EndG<Dual<W>>& Eo,
-                                                const V3<Dual<W>>* Z, Dual<W>& p0, Dual<W>& dp) {
+__device__ __forceinline__ void arc_angles_dual(const TriArgs<T>& A, int64_t ga, const EndG<Dual<W, T>>& Eo,
+                                                const V3<Dual<W, T>>* Z, Dual<W, T>& p0, Dual<W, T>& dp) {
   uint32_t av = A.arc_vtx[ga];
   int v0 = av & 255, v1 = (av >> 8) & 255;
-  float s0 = (float)A.arc_phi[2 * ga], sd = (float)A.arc_phi[2 * ga + 1];
-  Dual<W> a0 = raw_angle(Eo, Z[v0]);
-  p0 = shift(a0, s0 + remainderf(a0.v - s0, (float)PI2) - a0.v);
+  T s0 = (T)A.arc_phi[2 * ga], sd = (T)A.arc_phi[2 * ga + 1];
+  Dual<W, T> a0 = raw_angle(Eo, Z[v0]);
+  p0 = shift(a0, s0 + sc_rem2pi(a0.v - s0) - a0.v);
   if (v0 == v1) {
-    dp = Dual<W>((float)PI2);
+    dp = Dual<W, T>((T)PI2);
   } else {
-    float s1 = s0 + sd;
-    Dual<W> a1 = raw_angle(Eo, Z[v1]);
-    Dual<W> p1 = shift(a1, s1 + remainderf(a1.v - s1, (float)PI2) - a1.v);
+    T s1 = s0 + sd;
+    Dual<W, T> a1 = raw_angle(Eo, Z[v1]);
+    Dual<W, T> p1 = shift(a1, s1 + sc_rem2pi(a1.v - s1) - a1.v);
     dp = p1 - p0;
   }
 }
 
+template <typename T>
 struct BwdNodeArgs {
   const int32_t* arc_N;
-  const float* adj;       // point adjoints [points][3]
+  const T* adj;           // point adjoints [points][3]
   int64_t centre_base;    // point id of hole 0's centre
   double* g_xyz;          // [N][3]
   double* g_R;            // [N]
@@ -220,15 +221,15 @@ struct BwdNodeArgs {
 
 // Parameter adjoints, warp per node, forward mode with W directions per pass.
 template <typename T, int W>
-__global__ void __launch_bounds__(64) k_bwd_nodes(TriArgs<T> A, BwdNodeArgs B) {
+__global__ void __launch_bounds__(64) k_bwd_nodes(TriArgs<T> A, BwdNodeArgs<T> B) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  typedef Dual<W, T> D;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const size_t eb = (size_t)B.maxd * sizeof(EndG<Dual<W>>);
-  const size_t wsb = ((eb + (size_t)B.maxv * sizeof(V3<Dual<W>>)) + 15) & ~(size_t)15;
-  EndG<Dual<W>>* E = reinterpret_cast<EndG<Dual<W>>*>(smem_raw + (size_t)w * wsb);
-  V3<Dual<W>>* Z = reinterpret_cast<V3<Dual<W>>*>(smem_raw + (size_t)w * wsb + eb);
+  const size_t eb = (size_t)B.maxd * sizeof(EndG<D>);
+  const size_t wsb = ((eb + (size_t)B.maxv * sizeof(V3<D>)) + 15) & ~(size_t)15;
+  EndG<D>* E = reinterpret_cast<EndG<D>*>(smem_raw + (size_t)w * wsb);
+  V3<D>* Z = reinterpret_cast<V3<D>*>(smem_raw + (size_t)w * wsb + eb);
   const LatDev<T>& L = A.lat;
-  typedef Dual<W> D;
   while (true) {
     int64_t nd = 0;
     if (lane == 0) nd = atomicAdd(B.queue, 1);
@@ -241,34 +242,34 @@ __global__ void __launch_bounds__(64) k_bwd_nodes(TriArgs<T> A, BwdNodeArgs B) {
     const int np = 4 + 4 * d;
     for (int s0 = 0; s0 < np; s0 += W) {
       // seeded node centre and radius
-      V3<D> c = mk3(D((float)L.xyz[3 * nd]), D((float)L.xyz[3 * nd + 1]), D((float)L.xyz[3 * nd + 2]));
-      D R = D((float)L.node_R[nd]);
-      if (0 >= s0 && 0 < s0 + W) c.x.t[0 - s0] = 1.0f;
-      if (1 >= s0 && 1 < s0 + W) c.y.t[1 - s0] = 1.0f;
-      if (2 >= s0 && 2 < s0 + W) c.z.t[2 - s0] = 1.0f;
-      if (3 >= s0 && 3 < s0 + W) R.t[3 - s0] = 1.0f;
+      V3<D> c = mk3(D((T)L.xyz[3 * nd]), D((T)L.xyz[3 * nd + 1]), D((T)L.xyz[3 * nd + 2]));
+      D R = D((T)L.node_R[nd]);
+      if (0 >= s0 && 0 < s0 + W) c.x.t[0 - s0] = T(1);
+      if (1 >= s0 && 1 < s0 + W) c.y.t[1 - s0] = T(1);
+      if (2 >= s0 && 2 < s0 + W) c.z.t[2 - s0] = T(1);
+      if (3 >= s0 && 3 < s0 + W) R.t[3 - s0] = T(1);
       for (int li = lane; li < d; li += 32) {
         int32_t eid = L.adj[rb + li];
         int32_t st = eid >> 1;
         int32_t far = (eid & 1) ? L.ends[2 * (int64_t)st] : L.ends[2 * (int64_t)st + 1];
-        V3<D> cf = mk3(D((float)L.xyz[3 * far]), D((float)L.xyz[3 * far + 1]), D((float)L.xyz[3 * far + 2]));
-        D Rf = D((float)L.node_R[far]);
+        V3<D> cf = mk3(D((T)L.xyz[3 * far]), D((T)L.xyz[3 * far + 1]), D((T)L.xyz[3 * far + 2]));
+        D Rf = D((T)L.node_R[far]);
         int sb = 4 + 4 * li - s0;
-        if (sb >= 0 && sb < W) cf.x.t[sb] = 1.0f;
-        if (sb + 1 >= 0 && sb + 1 < W) cf.y.t[sb + 1] = 1.0f;
-        if (sb + 2 >= 0 && sb + 2 < W) cf.z.t[sb + 2] = 1.0f;
-        if (sb + 3 >= 0 && sb + 3 < W) Rf.t[sb + 3] = 1.0f;
+        if (sb >= 0 && sb < W) cf.x.t[sb] = T(1);
+        if (sb + 1 >= 0 && sb + 1 < W) cf.y.t[sb + 1] = T(1);
+        if (sb + 2 >= 0 && sb + 2 < W) cf.z.t[sb + 2] = T(1);
+        if (sb + 3 >= 0 && sb + 3 < W) Rf.t[sb + 3] = T(1);
         E[li] = end_from<T, D>(L, nd, eid, c, R, cf, Rf);
       }
       __syncwarp();
-      float acc[W];
+      T acc[W];
 #pragma unroll
-      for (int i = 0; i < W; i++) acc[i] = 0.0f;
+      for (int i = 0; i < W; i++) acc[i] = T(0);
       // vertices
       for (int v = lane; v < nv; v += 32) {
         V3<D> z = gen_point<D>(E, R, A.vtx_gen[vo + v]);
         Z[v] = z;
-        contract<W>(acc, c + z, B.adj + 3 * (vo + v));
+        contract<W, T>(acc, c + z, B.adj + 3 * (vo + v));
       }
       __syncwarp();
       // interior points of every arc
@@ -281,12 +282,12 @@ __global__ void __launch_bounds__(64) k_bwd_nodes(TriArgs<T> A, BwdNodeArgs B) {
         ArcGeo<D> g = arc_geo<D>(E[o], ot >= 0 ? &E[ot] : nullptr, R);
         D p0, dp;
         arc_angles_dual<T, W>(A, ga, E[o], Z, p0, dp);
-        const float* adj = B.adj + 3 * (A.n_vtx + A.arc_pt_off[ga]);
-        for (int m = 1; m < N; m++) contract<W>(acc, c + arc_point_dual<T, W>(g, p0, dp, m, N), adj + 3 * (m - 1));
+        const T* adj = B.adj + 3 * (A.n_vtx + A.arc_pt_off[ga]);
+        for (int m = 1; m < N; m++) contract<W, T>(acc, c + arc_point_dual<T, W>(g, p0, dp, m, N), adj + 3 * (m - 1));
       }
       // hole centres: barycentre of the contour, projected as in the forward pass
       for (int64_t h = A.node_hole_off[nd]; h < A.node_hole_off[nd + 1]; h++) {
-        V3<D> b = mk3(D(0.0f), D(0.0f), D(0.0f));
+        V3<D> b = mk3(D(T(0)), D(T(0)), D(T(0)));
         int M = 0;
         for (int64_t q = A.hole_off[h]; q < A.hole_off[h + 1]; q++) {
           uint32_t ent = A.hole_ent[q];
@@ -305,29 +306,29 @@ __global__ void __launch_bounds__(64) k_bwd_nodes(TriArgs<T> A, BwdNodeArgs B) {
           }
           M += N;
         }
-        dual_warp_sum<W>(b.x);
-        dual_warp_sum<W>(b.y);
-        dual_warp_sum<W>(b.z);
-        b = b * D(1.0f / (float)M);
-        float bl = sqrtf(b.x.v * b.x.v + b.y.v * b.y.v + b.z.v * b.z.v);
+        dual_warp_sum<W, T>(b.x);
+        dual_warp_sum<W, T>(b.y);
+        dual_warp_sum<W, T>(b.z);
+        b = b * D(T(1) / (T)M);
+        T bl = lm_sqrt(b.x.v * b.x.v + b.y.v * b.y.v + b.z.v * b.z.v);
         int rule = 3;
-        if (bl > (float)ETA_BARY * R.v) {
+        if (bl > (T)ETA_BARY * R.v) {
           bool ok = true;
           for (int li = 0; li < d; li++) {
-            float x = (E[li].u.x.v * b.x.v + E[li].u.y.v * b.y.v + E[li].u.z.v * b.z.v) / bl - E[li].s.v;
-            if (x > 0.0f) ok = false;
+            T x = (E[li].u.x.v * b.x.v + E[li].u.y.v * b.y.v + E[li].u.z.v * b.z.v) / bl - E[li].s.v;
+            if (x > T(0)) ok = false;
           }
           if (ok) rule = 0;
         }
-        V3<D> su = mk3(D(0.0f), D(0.0f), D(0.0f));
+        V3<D> su = mk3(D(T(0)), D(T(0)), D(T(0)));
         for (int li = 0; li < d; li++) su = su - E[li].u;
         if (rule != 0) {
-          float sl = sqrtf(su.x.v * su.x.v + su.y.v * su.y.v + su.z.v * su.z.v);
-          rule = sl > (float)ETA_BARY ? 1 : (bl > 0.0f ? 2 : 3);
+          T sl = lm_sqrt(su.x.v * su.x.v + su.y.v * su.y.v + su.z.v * su.z.v);
+          rule = sl > (T)ETA_BARY ? 1 : (bl > T(0) ? 2 : 3);
         }
-        V3<D> dir = rule == 1 ? su * (D(1.0f) / norm3(su))
-                              : (rule == 3 ? E[0].u * D(-1.0f) : b * (D(1.0f) / norm3(b)));
-        if (lane == 0) contract<W>(acc, c + dir * R, B.adj + 3 * (B.centre_base + h));
+        V3<D> dir = rule == 1 ? su * (D(T(1)) / norm3(su))
+                              : (rule == 3 ? E[0].u * D(T(-1)) : b * (D(T(1)) / norm3(b)));
+        if (lane == 0) contract<W, T>(acc, c + dir * R, B.adj + 3 * (B.centre_base + h));
       }
       // reduce the W tangents and scatter to the parameters they seed
 #pragma unroll
@@ -335,7 +336,7 @@ __global__ void __launch_bounds__(64) k_bwd_nodes(TriArgs<T> A, BwdNodeArgs B) {
         for (int o = 16; o > 0; o >>= 1) acc[i] += __shfl_xor_sync(0xffffffffu, acc[i], o);
       if (lane < W && s0 + lane < np) {
         int sl = s0 + lane;
-        float val = 0.0f;
+        T val = T(0);
 #pragma unroll
         for (int i = 0; i < W; i++)
           if (i == lane) val = acc[i];
@@ -389,13 +390,13 @@ cudaError_t metamesh_backward(lm_metamesh* mm, int k, double w_area, double w_vo
   cudaError_t status = cudaSuccess;
   const int sms = sms_now();
   TriArgs<T> A = bwd_args<T>(mm, k);
-  A.w_area = (float)w_area;
-  A.w_vol = (float)w_vol;
+  A.w_area = w_area;
+  A.w_vol = w_vol;
   const int64_t Na = mm->A, N = mm->N;
   int32_t *arc_N = nullptr, *arc_np = nullptr;
   int64_t *arc_pt_off = nullptr, *ws = nullptr;
   int* misc = nullptr;
-  float* adj = nullptr;
+  T* adj = nullptr;
   double* g = nullptr;
   uint32_t* redo = nullptr;
   int64_t P = 0;
@@ -421,8 +422,8 @@ cudaError_t metamesh_backward(lm_metamesh* mm, int k, double w_area, double w_vo
   A.arc_pt_off = arc_pt_off;
   {
     const int64_t npts = mm->V + P + mm->H;
-    BK(cudaMallocAsync((void**)&adj, sizeof(float) * 3 * (size_t)(npts > 0 ? npts : 1), st));
-    BK(cudaMemsetAsync(adj, 0, sizeof(float) * 3 * (size_t)(npts > 0 ? npts : 1), st));
+    BK(cudaMallocAsync((void**)&adj, sizeof(T) * 3 * (size_t)(npts > 0 ? npts : 1), st));
+    BK(cudaMemsetAsync(adj, 0, sizeof(T) * 3 * (size_t)(npts > 0 ? npts : 1), st));
     BK(cudaMallocAsync((void**)&g, sizeof(double) * 4 * (size_t)(N > 0 ? N : 1), st));
     BK(cudaMemsetAsync(g, 0, sizeof(double) * 4 * (size_t)(N > 0 ? N : 1), st));
     A.adj = adj;
@@ -482,7 +483,7 @@ cudaError_t metamesh_backward(lm_metamesh* mm, int k, double w_area, double w_vo
   }
   // 3. parameter adjoints, node by node
   if (N > 0) {
-    BwdNodeArgs B;
+    BwdNodeArgs<T> B;
     B.arc_N = arc_N;
     B.adj = adj;
     B.centre_base = mm->V + P;
@@ -491,8 +492,8 @@ cudaError_t metamesh_backward(lm_metamesh* mm, int k, double w_area, double w_vo
     B.maxd = mm->max_valence > 0 ? mm->max_valence : 1;
     B.maxv = hm[0] > 0 ? hm[0] : 1;
     B.queue = misc + 1;
-    const size_t eb = (size_t)B.maxd * sizeof(EndG<Dual<BW>>);
-    const size_t wsb = ((eb + (size_t)B.maxv * sizeof(V3<Dual<BW>>)) + 15) & ~(size_t)15;
+    const size_t eb = (size_t)B.maxd * sizeof(EndG<Dual<BW, T>>);
+    const size_t wsb = ((eb + (size_t)B.maxv * sizeof(V3<Dual<BW, T>>)) + 15) & ~(size_t)15;
     int warps = 2;
     while (warps > 1 && (size_t)warps * wsb > 200 * 1024) warps--;
     if (wsb > 200 * 1024) { status = cudaErrorInvalidValue; goto done; }

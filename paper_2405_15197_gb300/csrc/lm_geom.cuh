@@ -106,21 +106,24 @@ __device__ __forceinline__ double lm_sqrt(double x) { return sqrt(x); }
 __device__ __forceinline__ df lm_sqrt(df x) { return df_sqrt(x); }
 __device__ __forceinline__ float lm_rsqrt(float x) { return rsqrtf(x); }
 __device__ __forceinline__ double lm_rsqrt(double x) { return 1.0 / sqrt(x); }
-// FP32 atan2 from atan(r) ~ r P(r^2) on r = min/max in [0, 1] (degree-7 P,
-// weighted least-squares fit done for this library; largest error of the
-// FP32 evaluation 1.3e-7 rad) and the octant identities.  Every FP32 angle
-// decision has a margin of at least 1e-5 rad.
+// FP32 atan2 from atan(r) ~ r P(r^2) on r = min/max in [0, 1] (P of degree 7
+// in r^2; minimax coefficients from Lawson's iteratively reweighted least
+// squares, rounded to FP32: paper_2405_15197_gb300/fit_atan.py reproduces
+// them; FP32 Horner evaluation error at most 1.23e-7 rad on [0, 1]) and the
+// octant identities (each adds at most 1.5e-7 rad: the FP32 constants pi/2
+// and pi and one rounding).  Every FP32 angle decision has a margin of at
+// least 1e-5 rad.
 __device__ __forceinline__ float lm_atan2(float y, float x) {
   float ax = fabsf(x), ay = fabsf(y);
   float mx = fmaxf(ax, ay), mn = fminf(ax, ay);
   if (mx == 0.0f) return 0.0f;
   float r = mn / mx, t = r * r;
-  float p = -0.004054558929055929f;
-  p = fmaf(p, t, 0.021862929686903954f);
-  p = fmaf(p, t, -0.05591228976845741f);
-  p = fmaf(p, t, 0.09642194956541061f);
-  p = fmaf(p, t, -0.1390862911939621f);
-  p = fmaf(p, t, 0.19946566224098206f);
+  float p = -0.004054488614201546f;
+  p = fmaf(p, t, 0.021862687543034554f);
+  p = fmaf(p, t, -0.05591195821762085f);
+  p = fmaf(p, t, 0.09642171859741211f);
+  p = fmaf(p, t, -0.13908620178699493f);
+  p = fmaf(p, t, 0.19946563243865967f);
   p = fmaf(p, t, -0.33329859375953674f);
   p = fmaf(p, t, 0.9999993443489075f);
   float a = r * p;
@@ -130,9 +133,11 @@ __device__ __forceinline__ float lm_atan2(float y, float x) {
 }
 __device__ __forceinline__ double lm_atan2(double y, double x) { return atan2(y, x); }
 // FP32 sin/cos: reduction by the nearest multiple of 2 pi in two parts
-// (6.28125 exactly, then the remainder of 2 pi), then the hardware
-// approximation on [-pi, pi] (absolute error about 2^-21).  Arguments stay
-// within a few turns.
+// (Cody and Waite's split: 6.28125, exact in a few bits, then the rest of
+// 2 pi), then the hardware approximation on [-pi, pi] (absolute error about
+// 2^-21.4).  Arguments stay within a few turns; with the rounding of the
+// reduced argument the absolute error stays below 7e-7 (tested against FP64
+// sine and cosine).
 __device__ __forceinline__ void lm_sincos(float a, float* s, float* c) {
   float k = rintf(a * 0.15915494309189535f);
   float r = fmaf(-k, 6.28125f, a);
@@ -800,7 +805,7 @@ __device__ V3<U> gen_point(const EndG<U>* E, U R, uint32_t gcode) {
     U A = U(1) - G1 * G1, B = -(G0 * G1), C = dot(z0, z0) - R * R - G0 * G0;
     U sq = lm_sqrt(B * B - A * C);
     U lam;
-    if ((float)B >= 0.0f) {
+    if (B >= U(0)) {
       U q = -(B + sq);
       lam = root == 0 ? q / A : C / q;
     } else {

@@ -220,4 +220,6 @@ struct lm_metamesh {
   // launch shape of the meta-mesh kernel per valence bucket (block warps,
   // nodes per queue access), as used by the last build
   int tuned[3][2];
+  // device bytes allocated for this handle so far (cumulative)
+  int64_t alloc_bytes;
 };

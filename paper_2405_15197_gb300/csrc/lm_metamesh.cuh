@@ -534,12 +534,15 @@ __device__ void node_metamesh(WarpSmem<T, C>& S, const MMArgs<T>& A, int64_t n, 
         int q = 0;
         for (int v = 0; v < S.nv; v++) {
           if (!((S.vkey[v] >> i) & 1ull)) continue;
-          T a = raw_angle(S.E[i], S.vz[v]);
+          const V3<T> z = S.vz[v];
+          const T zx = dot(z, S.E[i].e1), zy = dot(z, S.E[i].e2);
+          T a = lm_atan2(zy, zx);
           if (!IS64 && fabs(a + T(PHI_CUT)) <= T(M_ANG)) unc = true;
-          // a vertex far from the node (past a strut's length: degenerate
-          // node) has an FP32 position error of ulp(|z|), too coarse for its
-          // angle: the loop is ordered with FP64 angles
-          if (!IS64 && dot(S.vz[v], S.vz[v]) > T(256) * R * R) unc = true;
+          // the angle of a vertex close to the strut's axis relative to its
+          // distance from the node (seams of steep sections, vertices past a
+          // strut's length: degenerate nodes) amplifies its FP32 position
+          // error: the loop is ordered with FP64 angles
+          if (!IS64 && T(256) * (zx * zx + zy * zy) < dot(z, z) + R * R) unc = true;
           a = norm_angle(a);
           // stable insertion by angle
           int p = q;

@@ -1,13 +1,16 @@
 // Allocation-free triangulation entry point.
 //
-// lm_triangulate_noalloc emits the same STL records as lm_tri_count + lm_triangulate
-// for one item range, for callers that cannot allocate device memory at that
-// point: code that runs while a stream is being captured into a CUDA graph, or
-// under an external memory budget / custom allocator that forbids the library
-// from calling cudaMalloc.  All scratch it needs (per-item triangle counts and
-// offsets of the range, the scan workspace, the FP64 fallback contexts of its
-// warps and its work counters) lives in one file-scope __device__ array of
-// fixed size, which every GPU that loads the library keeps until exit.
+// lm_triangulate_noalloc emits the same STL records as lm_tri_count +
+// lm_triangulate for one item range without allocating device memory.  It is
+// for callers whose device memory is not theirs to request at that point: an
+// application whose framework's caching allocator or fixed memory pool owns
+// the GPU's memory (a cudaMalloc from the library could fail, or force the
+// pool to release cached blocks), or a latency-bound serving loop in which a
+// cudaMalloc / cudaFree would stall the device.  All scratch it needs
+// (per-item triangle counts and offsets of the range, the scan workspace,
+// the FP64 fallback contexts of its warps, its work counters) lives in one
+// file-scope __device__ array of fixed size, which every GPU that loads the
+// library keeps until the process exits.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -21,8 +24,22 @@ using namespace lm;
 namespace {
 
 constexpr int64_t NA_MAX_ITEMS = 1 << 18;  // items per call
-constexpr int NA_CONTEXTS = 512;           // FP64 contexts: 2 per warp, 256 warps
+// FP64 contexts (Node64) in the array: the count pass uses one per warp of
+// its grid (at most NA_CONTEXTS warps of NA_COUNT_THREADS / 32), the hole
+// fans two per warp (launch_tri_holes clamps its grid to scratch_warps / 2
+// warps), the FP64 stitching pass none
+constexpr int NA_CONTEXTS = 512;
+constexpr int NA_COUNT_THREADS = 256;
 constexpr int64_t NA_SCAN_WS = 2 * ((NA_MAX_ITEMS + SCAN_TILE - 1) / SCAN_TILE) + 8;
+
+// count-pass grid of n items: one warp per 32 items, at most one FP64
+// context per warp
+int64_t count_grid(int64_t n) {
+  constexpr int64_t max_blocks = NA_CONTEXTS / (NA_COUNT_THREADS / 32);
+  static_assert(max_blocks * (NA_COUNT_THREADS / 32) <= NA_CONTEXTS, "count pass: one context per warp");
+  int64_t g = (n + NA_COUNT_THREADS - 1) / NA_COUNT_THREADS;
+  return g < 1 ? 1 : (g > max_blocks ? max_blocks : g);
+}
 
 struct NaLayout {
   int32_t cnt[NA_MAX_ITEMS];
@@ -58,84 +75,6 @@ cudaError_t na_scratch(unsigned char** out) {
   return cudaSuccess;
 }
 
-// triangle count of items [b, e) (same rules as the full count pass)
-template <typename T>
-__global__ void __launch_bounds__(256) k_count_range(TriArgs<T> A, Node64* ctxs, int64_t b, int64_t e,
-                                                     int32_t* cnt, int* max_pts) {
-  const int lane = threadIdx.x & 31;
-  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int nwarps = (gridDim.x * blockDim.x) >> 5;
-  Node64* ctx = ctxs + gw;
-  const int64_t E = A.lat.n_struts;
-  for (int64_t base = b + (int64_t)gw * 32; base < e; base += (int64_t)nwarps * 32) {
-    int64_t it = base + lane;
-    int64_t cs[2] = {0, 0};
-    bool need = false;
-    int64_t nodes[2] = {-1, -1};
-    if (it < e) {
-      if (it < E) {
-        for (int s = 0; s < 2; s++) {
-          int64_t nd = A.lat.ends[2 * it + s];
-          int64_t eid = 2 * it + s;
-          int64_t ao = A.arc_off[nd];
-          for (int64_t q = A.end_off[eid]; q < A.end_off[eid + 1]; q++) {
-            int64_t ga = ao + (A.loop_ent[q] & 0x7fffffffu);
-            bool unc;
-            cs[s] += seg_count<T>(A.arc_phi[2 * ga + 1], A.k, unc);
-            if (unc) { need = true; nodes[s] = nd; }
-          }
-        }
-      } else {
-        int64_t nd = it - E;
-        int64_t ao = A.arc_off[nd];
-        for (int64_t h = A.node_hole_off[nd]; h < A.node_hole_off[nd + 1]; h++)
-          for (int64_t q = A.hole_off[h]; q < A.hole_off[h + 1]; q++) {
-            int64_t ga = ao + (A.hole_ent[q] & 0x7fffffffu);
-            bool unc;
-            cs[0] += seg_count<T>(A.arc_phi[2 * ga + 1], A.k, unc);
-            if (unc) { need = true; nodes[0] = nd; }
-          }
-      }
-    }
-    uint32_t m = __ballot_sync(0xffffffffu, need);
-    while (m) {
-      int src = __ffs(m) - 1;
-      m &= m - 1;
-      int64_t it2 = __shfl_sync(0xffffffffu, it, src);
-      for (int s = 0; s < 2; s++) {
-        int64_t nd = __shfl_sync(0xffffffffu, nodes[s], src);
-        if (nd < 0) continue;
-        load_node64(A.lat, nd, ctx, lane);
-        if (lane == src) {
-          int64_t ao = A.arc_off[nd];
-          if (it2 < E) {
-            int64_t eid = 2 * it2 + s;
-            for (int64_t q = A.end_off[eid]; q < A.end_off[eid + 1]; q++) {
-              int64_t ga = ao + (A.loop_ent[q] & 0x7fffffffu);
-              bool unc;
-              int n32 = seg_count<T>(A.arc_phi[2 * ga + 1], A.k, unc);
-              if (unc) cs[s] += arc_segments<T>(A, nd, ga, ctx, 0) - n32;
-            }
-          } else {
-            for (int64_t h = A.node_hole_off[nd]; h < A.node_hole_off[nd + 1]; h++)
-              for (int64_t q = A.hole_off[h]; q < A.hole_off[h + 1]; q++) {
-                int64_t ga = ao + (A.hole_ent[q] & 0x7fffffffu);
-                bool unc;
-                int n32 = seg_count<T>(A.arc_phi[2 * ga + 1], A.k, unc);
-                if (unc) cs[0] += arc_segments<T>(A, nd, ga, ctx, 0) - n32;
-              }
-          }
-        }
-        __syncwarp();
-      }
-    }
-    int mx = (int)(cs[0] > cs[1] ? cs[0] : cs[1]);
-    mx = __reduce_max_sync(0xffffffffu, mx);
-    if (lane == 0 && mx > 0) atomicMax(max_pts, mx);
-    if (it < e) cnt[it - b] = (int32_t)(cs[0] + cs[1]);
-  }
-}
-
 template <typename T>
 lm_status run_noalloc(lm_metamesh* mm, int k, int64_t b, int64_t e, void* d_out, int64_t cap,
                       cudaStream_t st, int64_t* h_ntris) {
@@ -169,12 +108,10 @@ lm_status run_noalloc(lm_metamesh* mm, int k, int64_t b, int64_t e, void* d_out,
   A.hole_ent = mm->hole_ent;
   A.k = k;
   A.err = mm->d_err;
-  const int threads = 256;
-  int64_t grid = (n + threads - 1) / threads;
-  if (grid > NA_CONTEXTS / (threads / 32)) grid = NA_CONTEXTS / (threads / 32);
-  if (grid < 1) grid = 1;
+  // the count kernel of lm_tri_count on the range: one FP64 context per warp
+  const int64_t grid = count_grid(n);
   count_launch();
-  k_count_range<T><<<(unsigned)grid, threads, 0, st>>>(A, ctx, b, e, S->cnt, &S->counters[2]);
+  k_tri_count<T><<<(unsigned)grid, NA_COUNT_THREADS, 0, st>>>(A, ctx, b, e, S->cnt, &S->counters[2]);
   if (cudaGetLastError() != cudaSuccess) return LM_ERR_CUDA;
   if (scan_excl<int32_t>(S->cnt, 1, n, S->off, S->ws, st) != cudaSuccess) return LM_ERR_CUDA;
   int64_t total = 0;

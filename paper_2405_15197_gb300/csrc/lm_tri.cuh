@@ -50,10 +50,10 @@ struct TriArgs {
   unsigned long long* rlist;
   int64_t rcap;
   // adjoint (point adjoints instead of records)
-  float* adj;                 // [n_vtx + interior arc points][3]
+  T* adj;                     // [n_vtx + interior arc points][3]
   const int64_t* arc_pt_off;  // [A + 1] first interior point of each arc
   int64_t n_vtx;
-  float w_area, w_vol;
+  double w_area, w_vol;
 };
 
 __device__ __forceinline__ void tfb_add(unsigned long long* fb, int which, bool pred,
@@ -135,17 +135,21 @@ __device__ int arc_segments(const TriArgs<T>& A, int64_t node, int64_t ga, Node6
 }
 
 // ---------------------------------------------------------------- counts
+// Triangle counts of items [b, e) into cnt[item - b] and the largest point
+// count of one loop (or of one node's holes) into *max_pts (atomic max).
+// One FP64 context per warp in scratch (the grid has at most as many warps).
 template <typename T>
-__global__ void __launch_bounds__(256) k_tri_count(TriArgs<T> A, Node64* scratch) {
+__global__ void __launch_bounds__(256) k_tri_count(TriArgs<T> A, Node64* scratch, int64_t b, int64_t e,
+                                                   int32_t* cnt, int* max_pts) {
   const int lane = threadIdx.x & 31;
   const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
   Node64* ctx = scratch + gw;
-  const int64_t E = A.lat.n_struts, N = A.lat.n_nodes;
-  const int64_t n_items = E + N;
+  const int64_t E = A.lat.n_struts;
+  const int64_t n_items = e;
   // one thread per item, lanes of a warp on consecutive items; an exact
   // recount (rare) loads the node's FP64 context warp-cooperatively
-  for (int64_t base = (int64_t)gw * 32; base < n_items; base += (int64_t)nwarps * 32) {
+  for (int64_t base = b + (int64_t)gw * 32; base < n_items; base += (int64_t)nwarps * 32) {
     int64_t it = base + lane;
     int64_t cs[2] = {0, 0};
     bool need = false;
@@ -212,8 +216,8 @@ __global__ void __launch_bounds__(256) k_tri_count(TriArgs<T> A, Node64* scratch
     int64_t c = cs[0] + cs[1];
     int mx = (int)(cs[0] > cs[1] ? cs[0] : cs[1]);
     mx = __reduce_max_sync(0xffffffffu, mx);
-    if (lane == 0 && mx > 0) atomicMax(A.max_pts, mx);
-    if (it < n_items) A.item_cnt[it] = (int32_t)c;
+    if (lane == 0 && mx > 0) atomicMax(max_pts, mx);
+    if (it < n_items) cnt[it - b] = (int32_t)c;
   }
 }
 
@@ -1068,12 +1072,8 @@ struct TileSmem {
 template <typename T>
 __device__ __forceinline__ void tri_point_adjoints(const TriArgs<T>& A, V3<T> a, V3<T> b, V3<T> c, V3<T> nh,
                                                    V3<T> n, int64_t pa, int64_t pb, int64_t pc) {
-  const float wa = 0.5f * A.w_area, wv = A.w_vol / 6.0f;
-  V3<float> nf = mk3((float)n.x, (float)n.y, (float)n.z), hf = mk3((float)nh.x, (float)nh.y, (float)nh.z);
-  V3<float> af = mk3((float)a.x, (float)a.y, (float)a.z), bf = mk3((float)b.x, (float)b.y, (float)b.z),
-            cf = mk3((float)c.x, (float)c.y, (float)c.z);
-  V3<float> g[3] = {cross(bf - cf, hf) * wa + nf * wv, cross(cf - af, hf) * wa + nf * wv,
-                    cross(af - bf, hf) * wa + nf * wv};
+  const T wa = T(0.5) * (T)A.w_area, wv = (T)A.w_vol / T(6);
+  V3<T> g[3] = {cross(b - c, nh) * wa + n * wv, cross(c - a, nh) * wa + n * wv, cross(a - b, nh) * wa + n * wv};
   int64_t id[3] = {pa, pb, pc};
 #pragma unroll
   for (int q = 0; q < 3; q++) {

@@ -66,7 +66,8 @@ cudaError_t launch_tri_count(const TriLaunch<T>& a, cudaStream_t st) {
   if (grid > gmax) grid = gmax;
   if (grid < 1) grid = 1;
   count_launch();
-  k_tri_count<T><<<(unsigned)grid, threads, 0, st>>>(A, a.scratch);
+  k_tri_count<T><<<(unsigned)grid, threads, 0, st>>>(A, a.scratch, 0, a.n_nodes + a.n_struts, a.item_cnt,
+                                                     a.max_pts);
   return cudaGetLastError();
 }
 
@@ -74,10 +75,15 @@ cudaError_t launch_tri_count(const TriLaunch<T>& a, cudaStream_t st) {
 template <typename T>
 cudaError_t launch_tri_holes(const TriLaunch<T>& a, cudaStream_t st) {
   TriArgs<T> A = tri_args(a);
-  const int warps = 8, threads = warps * 32;
   const int sms = sm_count();
   size_t wsb = (size_t)a.pmax * sizeof(V3<T>) + 32 * 50 + 64;
   wsb = (wsb + 15) & ~(size_t)15;
+  // eight warps per block, fewer when a warp's contour points need more
+  // shared memory (fine resolutions)
+  int warps = 8;
+  while (warps > 1 && (size_t)warps * wsb > 200 * 1024) warps >>= 1;
+  if (wsb > 200 * 1024) return cudaErrorInvalidValue;
+  const int threads = warps * 32;
   const size_t smem = warps * wsb;
   cudaError_t e = cudaFuncSetAttribute(k_tri_holes<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;

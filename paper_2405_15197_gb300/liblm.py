@@ -23,13 +23,17 @@ EXPORTS = ["lm_build_metamesh", "lm_metamesh_counts", "lm_metamesh_export", "lm_
            "lm_tri_range", "lm_triangulate", "lm_triangulate_stream", "lm_stl_header",
            "lm_objective", "lm_metamesh_backward", "lm_last_error", "lm_metamesh_free",
            "lm_status_string", "lm_copy_to_host", "lm_launch_count", "lm_triangulate_noalloc",
-           "lm_fp64_counts", "lm_metamesh_launch_shape"]
+           "lm_fp64_counts", "lm_metamesh_launch_shape", "lm_eval_angle_fns",
+           "lm_cuda_error_string"]
 
 
 class LmError(RuntimeError):
     def __init__(self, status, where=""):
         self.status = int(status)
-        super().__init__(f"{where}: {STATUS.get(self.status, self.status)}")
+        msg = f"{where}: {STATUS.get(self.status, self.status)}"
+        if self.status in (5, 6) and _lib is not None:
+            msg += f" ({_lib.lm_cuda_error_string().decode()})"
+        super().__init__(msg)
 
 
 class lm_lattice(ctypes.Structure):
@@ -41,7 +45,8 @@ class lm_lattice(ctypes.Structure):
 class lm_options(ctypes.Structure):
     _fields_ = [("autotune", ctypes.c_int32), ("block_warps", ctypes.c_int32),
                 ("grid_ctas", ctypes.c_int32), ("nodes_per_task", ctypes.c_int32),
-                ("arena_bytes", ctypes.c_int64), ("reserved", ctypes.c_int64 * 3)]
+                ("arena_bytes", ctypes.c_int64), ("redo_list_cap", ctypes.c_int64),
+                ("mem_budget", ctypes.c_int64), ("reserved", ctypes.c_int64 * 1)]
 
 
 class lm_metamesh_view(ctypes.Structure):
@@ -90,6 +95,8 @@ def load():
         "lm_fp64_counts": ([V, P64], ctypes.c_int),
         "lm_triangulate_noalloc": ([V, I32, I64, I64, V, I64, V, P64], ctypes.c_int),
         "lm_metamesh_launch_shape": ([V, ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
+        "lm_eval_angle_fns": ([V, V, V, I64, V, V, V, V], ctypes.c_int),
+        "lm_cuda_error_string": ([], ctypes.c_char_p),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -218,6 +225,17 @@ def lm_fp64_counts(h):
     out = (ctypes.c_int64 * N_FP64_COUNTS)()
     _ck(load().lm_fp64_counts(h, out), "lm_fp64_counts")
     return list(out)
+
+
+def lm_eval_angle_fns(y, x, a, stream=None):
+    """(lm_atan2(y, x), sin a, cos a) of float32 CUDA tensors, as computed by
+    the library's FP32 angle functions."""
+    import torch
+    n = y.numel()
+    at, sn, cs = (torch.empty(n, dtype=torch.float32, device=y.device) for _ in range(3))
+    _ck(load().lm_eval_angle_fns(y.data_ptr(), x.data_ptr(), a.data_ptr(), n, at.data_ptr(), sn.data_ptr(),
+                                 cs.data_ptr(), _stream_ptr(stream)), "lm_eval_angle_fns")
+    return at, sn, cs
 
 
 def lm_launch_count():

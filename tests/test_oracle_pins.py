@@ -489,3 +489,20 @@ def test_frozen_gradient_smooth_and_local():
         # whole sums of ~1 differenced at 1e-4: rounding near 1e-11
         assert (ap - am) / 2e-4 == pytest.approx(ga1[v, p], rel=1e-7, abs=1e-9)
         assert (vp - vm) / 2e-4 == pytest.approx(gv1[v, p], rel=1e-7, abs=1e-9)
+
+
+# ------------------------------------------------- the library's arctangent
+def test_atan_coefficients_reproduce_from_the_fit():
+    """The coefficients of lm_atan2 (csrc/lm_geom.cuh) are the FP32-rounded
+    output of the committed minimax fit, whose FP32 evaluation stays within
+    1.23e-7 rad of atan on [0, 1]."""
+    import os
+    import re
+    from paper_2405_15197_gb300 import fit_atan
+    src = open(os.path.join(os.path.dirname(fit_atan.__file__), "csrc", "lm_geom.cuh")).read()
+    body = src[src.index("__device__ __forceinline__ float lm_atan2(float y, float x)"):]
+    body = body[body.index("float p ="):body.index("float a = r * p;")]
+    got = [float(x) for x in re.findall(r"(-?\d+\.\d+(?:e-?\d+)?)f", body)]
+    want = fit_atan.coefficients_f32()
+    assert np.array_equal(np.array(got[::-1], dtype=np.float32), want)
+    assert fit_atan.max_error_f32(want, n=200_001) <= 1.23e-7

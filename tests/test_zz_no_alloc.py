@@ -1,12 +1,16 @@
 """The allocation-free triangulation entry point (lm_triangulate_noalloc).
 
-It serves callers that cannot allocate device memory when they triangulate
-(stream capture into a CUDA graph, an external allocator or memory budget):
-its scratch is a fixed device array inside the library.  Its records must
-match the allocating entry point's (lm_tri_count + lm_triangulate) for the
-same items, on two calls in a row (the shared array keeps the previous
-call's contents), and ranges beyond its capacity must be refused.  This file
-is collected last so a failure here leaves every other test already run.
+It serves callers that cannot let the library allocate device memory when
+they triangulate: an application whose GPU memory belongs to a framework's
+caching allocator or to a pool sized up front, where a library cudaMalloc
+could fail or force the pool to give memory back, or a latency-bound loop
+in which cudaMalloc / cudaFree would stall the device.  Its scratch is a
+fixed device array inside the library.  Its records must be byte-identical
+to the allocating entry point's (lm_tri_count + lm_triangulate) for the same
+items, on two calls in a row (the shared array keeps the previous call's
+contents), in FP32 and FP64, and ranges beyond its capacity must be
+refused.  This file is collected last so a failure here leaves every other
+test already run.
 """
 import numpy as np
 import pytest
@@ -19,9 +23,10 @@ from paper_2405_15197_gb300 import liblm  # noqa: E402
 from tests import parity as P  # noqa: E402
 
 
-def test_noalloc_matches_allocating_path():
-    lat = P.lattice_as(L.octet(3), np.float32)
-    xyz, ends, radii = P.to_device(lat, np.float32)
+@pytest.mark.parametrize("dtype", [np.float32, np.float64])
+def test_noalloc_matches_allocating_path(dtype):
+    lat = P.lattice_as(L.octet(3), dtype)
+    xyz, ends, radii = P.to_device(lat, dtype)
     mm = liblm.MetaMesh(xyz, ends, radii)
     n_items = mm.n_struts + mm.n_nodes
     for k, (b, e) in [(8, (0, n_items)), (32, (17, n_items - 5)), (16, (mm.n_struts - 3, n_items))]:
@@ -31,7 +36,6 @@ def test_noalloc_matches_allocating_path():
         liblm.lm_triangulate(mm.h, k, b, e, ref.data_ptr(), cnt)
         assert liblm.lm_last_error(mm.h) == 0
         ref = ref[:cnt].cpu().numpy()
-        gn_r, gv_r = P.parse_stl(ref)
         for call in range(2):
             out = torch.full((cnt + 1, 50), 0xAB, dtype=torch.uint8, device="cuda")
             n = liblm.lm_triangulate_noalloc(mm.h, k, b, e, out.data_ptr(), cnt)
@@ -39,10 +43,8 @@ def test_noalloc_matches_allocating_path():
             assert n == cnt
             got = out.cpu().numpy()
             assert np.all(got[cnt] == 0xAB)  # nothing written past the range
-            gn, gv = P.parse_stl(got[:cnt])
-            assert np.allclose(gv, gv_r, rtol=2e-5, atol=2e-5 * float(lat["radii"].max()))
-            assert np.allclose(gn, gn_r, atol=1e-4)
-            assert np.all(got[:cnt, 48:] == 0)
+            # the same kernels on the same meta-mesh: the same bytes
+            assert np.array_equal(got[:cnt], ref)
     mm.close()
 
 
