@@ -87,9 +87,14 @@ typedef struct {
 
 /* Tuning knobs; zero-initialised = library defaults.
  *   autotune      : 1 = time the candidate launch shapes of the persistent
- *                   meta-mesh kernel once per device and valence mix, cache
- *                   the winner (host memory) and use it
- *   block_warps   : warps per block of the meta-mesh kernel (0 = default)
+ *                   meta-mesh launch (nodes a warp takes per queue access,
+ *                   CTAs per SM) on a sample of the lattice's nodes, once
+ *                   per device, dtype and valence mix (the shares of the
+ *                   valence buckets), cache the winner (host memory) and use
+ *                   it; costs one extra synchronisation per build
+ *   block_warps   : unused (the meta-mesh blocks have four warps: four
+ *                   workspaces for nodes of valence <= 16, two for <= 32,
+ *                   one for <= 64)
  *   grid_ctas     : persistent grid size (0 = resident CTAs x SM count)
  *   nodes_per_task: nodes a warp pops from the work queue at once (0 = 1)
  *   arena_bytes   : device memory for the count pass to keep each node's
@@ -121,8 +126,11 @@ typedef struct lm_metamesh lm_metamesh;
 
 /* Build the meta-mesh (Section 4.3: auxiliary planes P_ij, strut-plane
  * ellipses, ellipse-plane trimming, arc loops; Section 5: hole flags).
- * Runs the node-sorted CSR build and the persistent meta-mesh kernel on
- * `stream`; synchronises the stream once to size the outputs.
+ * Runs the node-sorted CSR build, the valence bucketing and one persistent,
+ * work-stealing meta-mesh launch over nodes of every valence (Section
+ * 4.3.3's warp scheduling) on `stream` with no host synchronisation between
+ * them; synchronises the stream once to size the outputs (input errors are
+ * reported then) and once at the end for the totals.
  *   lat  : input lattice (device arrays, see lm_lattice)
  *   opt  : NULL = defaults
  *   out  : receives the handle (NULL on error)                           */
@@ -250,8 +258,9 @@ lm_status lm_metamesh_backward(lm_metamesh* mm, int32_t k, double w_area, double
                                double* h_volume);
 
 /* Launch shape the build used for the persistent meta-mesh kernel, per
- * valence bucket (d <= 16, d <= 32, d <= 64): out[2b] = warps per block,
- * out[2b+1] = nodes a warp takes per work-queue access.  With
+ * valence bucket (d <= 16, d <= 32, d <= 64): out[2b] = warps of a block
+ * working on the bucket, out[2b+1] = nodes a warp takes per work-queue
+ * access.  With
  * lm_options.autotune these are the autotuner's choices (Section 4.3.3's
  * workload balancing, done by measurement); 0 for buckets without nodes. */
 lm_status lm_metamesh_launch_shape(const lm_metamesh* mm, int32_t out[6]);

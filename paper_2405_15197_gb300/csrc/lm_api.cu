@@ -83,11 +83,15 @@ __global__ void k_strut_validate(const int32_t* ends, const T* radii, int64_t E,
   }
 }
 
-__global__ void k_scatter(const int32_t* ends, int64_t E2, const int64_t* row_ptr, int* fill,
+__global__ void k_scatter(const int32_t* ends, int64_t E2, int64_t N, const int64_t* row_ptr, int* fill,
                           int32_t* adj) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < E2;
        i += (int64_t)gridDim.x * blockDim.x) {
     int32_t nd = ends[i];
+    // a strut with an invalid end was reported by k_strut_validate and was
+    // not counted: none of its ends is placed
+    const int32_t a = ends[i & ~(int64_t)1], b = ends[i | 1];
+    if (a < 0 || a >= N || b < 0 || b >= N || a == b) continue;
     int pos = atomicAdd(&fill[nd], 1);
     adj[row_ptr[nd] + pos] = (int32_t)i;
   }
@@ -133,10 +137,11 @@ __global__ void k_node_finalize(const T* xyz, const T* radii, int64_t N, const i
 }
 
 template <typename T>
-__global__ void k_strut_taper(const T* xyz, const int32_t* ends, const T* node_R, int64_t E, int* err) {
+__global__ void k_strut_taper(const T* xyz, const int32_t* ends, const T* node_R, int64_t E, int64_t N, int* err) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < E;
        e += (int64_t)gridDim.x * blockDim.x) {
     int32_t a = ends[2 * e], b = ends[2 * e + 1];
+    if (a < 0 || a >= N || b < 0 || b >= N || a == b) continue;  // reported by k_strut_validate
     double dx = (double)xyz[3 * b] - (double)xyz[3 * a], dy = (double)xyz[3 * b + 1] - (double)xyz[3 * a + 1],
            dz = (double)xyz[3 * b + 2] - (double)xyz[3 * a + 2];
     double L = sqrt(dx * dx + dy * dy + dz * dz);
@@ -198,65 +203,73 @@ int grid_for(int64_t n, int threads = 256) {
   return (int)(g < 1 ? 1 : g);
 }
 
-lm_status read_err(lm_metamesh* mm, cudaStream_t st) {
-  int e = 0;
-  LM_CK(cudaMemcpyAsync(&e, mm->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
-  LM_CK(cudaStreamSynchronize(st));
-  return (lm_status)e;
-}
-
-// ---- autotuner of the persistent meta-mesh launch (block shape and nodes
-// popped per queue access), per device, lattice dtype and valence bucket:
-// each candidate runs the count pass on a sample of the bucket's nodes and
-// the fastest is cached for the process.
+// ---- autotuner of the persistent meta-mesh launch: nodes a warp takes per
+// queue access in each bucket and CTAs per SM, per device, lattice dtype and
+// valence mix (the bucket shares in eighths); each candidate runs the count
+// pass on a sample of every bucket and the fastest is cached for the process.
+struct TuneKey {
+  int dev, dtype, mix1, mix2, big;
+  bool operator<(const TuneKey& o) const {
+    return std::tie(dev, dtype, mix1, mix2, big) < std::tie(o.dev, o.dtype, o.mix1, o.mix2, o.big);
+  }
+};
+struct TuneVal {
+  int npt0, ctas_per_sm;
+};
 std::mutex g_tune_mu;
-std::map<std::tuple<int, int, int>, std::pair<int, int>> g_tune;
+std::map<TuneKey, TuneVal> g_tune;
 
 template <typename T>
-lm_status tune_bucket(lm_metamesh* mm, MMLaunch<T> L, int b, int n_list, cudaStream_t st, int* bw, int* npt) {
+lm_status tune_launch(lm_metamesh* mm, const MMLaunch<T>& L, MMBuckets bk, const int hb[3], cudaStream_t st,
+                      TuneVal* out) {
   int dev = 0;
   cudaGetDevice(&dev);
-  auto key = std::make_tuple(dev, (int)mm->dtype, b);
+  const int64_t tot = std::max<int64_t>(1, (int64_t)hb[0] + hb[1] + hb[2]);
+  TuneKey key{dev, mm->dtype, (int)(8 * (int64_t)hb[1] / tot), (int)(8 * (int64_t)hb[2] / tot), hb[2] > 0};
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tune.find(key);
     if (it != g_tune.end()) {
-      *bw = it->second.first;
-      *npt = it->second.second;
+      *out = it->second;
       return LM_OK;
     }
   }
-  const int cand_bw[3] = {1, 2, 4}, cand_npt[4] = {1, 2, 4, 8};
-  L.n_list = std::min(n_list, 8192);
-  L.queue = mm->d_queue + 3;
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int per_sm = metamesh_ctas_per_sm<T>();
+  if (per_sm < 1) return LM_ERR_CUDA;
+  // a sample of each bucket in proportion to the mix (the first nodes of
+  // each list)
+  const int cap = 16384;
+  for (int b = 0; b < NB_BUCKETS; b++)
+    bk.limit[b] = hb[b] == 0 ? 0 : (int)std::max<int64_t>(64, (int64_t)cap * hb[b] / tot);
+  const int cand_npt[4] = {1, 2, 4, 8};
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   float best = 1e30f;
-  int bbw = 4, bnpt = 1;
-  for (int rep = 0; rep < 2; rep++)  // first round warms up
-    for (int i = 0; i < 3; i++)
+  TuneVal bv{1, per_sm};
+  for (int rep = 0; rep < 2; rep++)  // the first round warms up
+    for (int c = per_sm; c >= std::max(1, per_sm - 2); c--)
       for (int j = 0; j < 4; j++) {
-        L.nodes_per_task = cand_npt[j];
-        LM_CK(cudaMemsetAsync(L.queue, 0, sizeof(int), st));
+        bk.npt[0] = cand_npt[j];
+        LM_CK(cudaMemsetAsync(bk.queues, 0, NB_BUCKETS * sizeof(int), st));
         cudaEventRecord(e0, st);
-        LM_CK(launch_metamesh<T>(b, false, L, cand_bw[i], 0, st, nullptr));
+        LM_CK(launch_metamesh<T>(false, L, bk, c * sms, st, nullptr));
         cudaEventRecord(e1, st);
         LM_CK(cudaEventSynchronize(e1));
         float ms = 0.0f;
         cudaEventElapsedTime(&ms, e0, e1);
         if (rep == 1 && ms < best) {
           best = ms;
-          bbw = cand_bw[i];
-          bnpt = cand_npt[j];
+          bv = TuneVal{cand_npt[j], c};
         }
       }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  *bw = bbw;
-  *npt = bnpt;
+  *out = bv;
   std::lock_guard<std::mutex> lk(g_tune_mu);
-  g_tune[key] = std::make_pair(bbw, bnpt);
+  g_tune[key] = bv;
   return LM_OK;
 }
 
@@ -278,6 +291,7 @@ lm_status build_impl(lm_metamesh* mm, cudaStream_t st) {
   LM_CK(cudaMemsetAsync(mm->d_fb, 0, LM_N_FP64_COUNTS * sizeof(unsigned long long), st));
   LM_CK(cudaMemsetAsync(mm->d_err, 0, 4 * sizeof(int), st));
   LM_CK(cudaMemsetAsync(mm->d_misc, 0, 8 * sizeof(int), st));
+  LM_CK(cudaMemsetAsync(mm->d_queue, 0, 8 * sizeof(int), st));
   T* node_R = nullptr;
   LM_CK(dalloc(mm, &node_R, N, st));
   mm->node_R = node_R;
@@ -289,36 +303,25 @@ lm_status build_impl(lm_metamesh* mm, cudaStream_t st) {
   LM_CK(cudaMemsetAsync(fill, 0, sizeof(int) * N, st));
   mm->scan_ws_n = scan_ws_elems(std::max<int64_t>(std::max<int64_t>(N + E, 2 * E), 1));
   LM_CK(dalloc(mm, &mm->scan_ws, mm->scan_ws_n, st));
+  // CSR build and bucketing, with no host synchronisation: input errors are
+  // recorded on the device (every kernel skips invalid ids) and read at the
+  // sizing synchronisation below, before anything is allocated from counts
   count_launch(); k_strut_validate<T><<<grid_for(E), 256, 0, st>>>(mm->ends, radii, E, N, deg, mm->d_err);
   LM_CK(cudaGetLastError());
-  lm_status s = read_err(mm, st);
-  if (s != LM_OK) return s;
   LM_CK(scan_excl<int>(deg, 1, N, mm->row_ptr, mm->scan_ws, st));
-  count_launch(); k_scatter<<<grid_for(2 * E), 256, 0, st>>>(mm->ends, 2 * E, mm->row_ptr, fill, mm->adj);
+  count_launch(); k_scatter<<<grid_for(2 * E), 256, 0, st>>>(mm->ends, 2 * E, N, mm->row_ptr, fill, mm->adj);
   count_launch(); k_node_finalize<T><<<grid_for(N), 256, 0, st>>>(xyz, radii, N, mm->row_ptr, mm->adj, node_R, mm->d_err,
                                                  mm->d_misc);
-  count_launch(); k_strut_taper<T><<<grid_for(E), 256, 0, st>>>(xyz, mm->ends, node_R, E, mm->d_err);
+  count_launch(); k_strut_taper<T><<<grid_for(E), 256, 0, st>>>(xyz, mm->ends, node_R, E, N, mm->d_err);
   LM_CK(cudaGetLastError());
   dfree(fill, st);
-  s = read_err(mm, st);
-  int maxdeg = 0;
-  LM_CK(cudaMemcpyAsync(&maxdeg, mm->d_misc, sizeof(int), cudaMemcpyDeviceToHost, st));
-  LM_CK(cudaStreamSynchronize(st));
-  mm->max_valence = maxdeg;
-  if (s != LM_OK) {
-    dfree(deg, st);
-    return s;
-  }
-  // valence buckets
+  // valence buckets (device-side counts)
   int32_t* lists = nullptr;
   int* bcnt = mm->d_misc + 4;
-  LM_CK(cudaMemsetAsync(bcnt, 0, 4 * sizeof(int), st));
-  LM_CK(dalloc(mm, &lists, (int64_t)NB_BUCKETS * std::max<int64_t>(N, 1), st));
-  count_launch(); k_bucket<<<grid_for(N), 256, 0, st>>>(mm->row_ptr, N, bcnt, lists, std::max<int64_t>(N, 1));
+  const int64_t cap = std::max<int64_t>(N, 1);
+  LM_CK(dalloc(mm, &lists, (int64_t)NB_BUCKETS * cap, st));
+  count_launch(); k_bucket<<<grid_for(N), 256, 0, st>>>(mm->row_ptr, N, bcnt, lists, cap);
   LM_CK(cudaGetLastError());
-  int hb[4] = {0, 0, 0, 0};
-  LM_CK(cudaMemcpyAsync(hb, bcnt, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
-  LM_CK(cudaStreamSynchronize(st));
   cudaEventRecord(ev[1], st);
   // ---- count pass
   int32_t *node_cnt = nullptr, *end_cnt = nullptr;
@@ -329,7 +332,6 @@ lm_status build_impl(lm_metamesh* mm, cudaStream_t st) {
   LM_CK(cudaMemsetAsync(end_cnt, 0, sizeof(int32_t) * 2 * E, st));
   LM_CK(cudaMemsetAsync(mm->node_flags, 0, sizeof(uint32_t) * N, st));
   int* overflow = mm->d_misc + 1;
-  LM_CK(cudaMemsetAsync(overflow, 0, sizeof(int), st));
   MMLaunch<T> L{};
   L.xyz = xyz;
   L.ends = mm->ends;
@@ -338,13 +340,19 @@ lm_status build_impl(lm_metamesh* mm, cudaStream_t st) {
   L.adj = mm->adj;
   L.n_nodes = N;
   L.n_struts = E;
-  L.nodes_per_task = mm->opt.nodes_per_task > 0 ? mm->opt.nodes_per_task : 1;
+  L.err = mm->d_err;
   L.node_flags = mm->node_flags;
   L.node_cnt = node_cnt;
   L.end_cnt = end_cnt;
   L.overflow = overflow;
   L.fb = mm->d_fb;
-  int64_t cap = std::max<int64_t>(N, 1);
+  MMBuckets bk{};
+  bk.lists = lists;
+  bk.cap = cap;
+  bk.counts = bcnt;
+  bk.queues = mm->d_queue + 4;
+  for (int b = 0; b < NB_BUCKETS; b++) bk.npt[b] = mm->opt.nodes_per_task > 0 ? mm->opt.nodes_per_task : 1;
+  int ctas = mm->opt.grid_ctas;
   // arena of the count pass (replaces the emit pass for the nodes it holds):
   // up to 35 % of the free memory left beside the CSR offsets, at most about
   // 300 B per strut (a node's block is about 100 B per strut end); the CSR
@@ -380,136 +388,139 @@ lm_status build_impl(lm_metamesh* mm, cudaStream_t st) {
       }
     }
   }
-  int arena_miss = 0;
-  for (int pass = 0; pass < 2; pass++) {
-    if (pass == 1) {
-      cudaEventRecord(ev[2], st);
-      // offsets from the counts
-      LM_CK(dalloc(mm, &mm->vtx_off, N + 1, st));
-      LM_CK(dalloc(mm, &mm->arc_off, N + 1, st));
-      LM_CK(dalloc(mm, &mm->hole_off_n, N + 1, st));
-      LM_CK(dalloc(mm, &mm->hent_off_n, N + 1, st));
-      LM_CK(dalloc(mm, &mm->end_off, 2 * E + 1, st));
-      LM_CK(scan_excl<int32_t>(node_cnt + 0, 4, N, mm->vtx_off, mm->scan_ws, st));
-      LM_CK(scan_excl<int32_t>(node_cnt + 1, 4, N, mm->arc_off, mm->scan_ws, st));
-      LM_CK(scan_excl<int32_t>(node_cnt + 2, 4, N, mm->hole_off_n, mm->scan_ws, st));
-      LM_CK(scan_excl<int32_t>(node_cnt + 3, 4, N, mm->hent_off_n, mm->scan_ws, st));
-      LM_CK(scan_excl<int32_t>(end_cnt, 1, 2 * E, mm->end_off, mm->scan_ws, st));
-      int64_t tot[5];
-      LM_CK(cudaMemcpyAsync(&tot[0], mm->vtx_off + N, 8, cudaMemcpyDeviceToHost, st));
-      LM_CK(cudaMemcpyAsync(&tot[1], mm->arc_off + N, 8, cudaMemcpyDeviceToHost, st));
-      LM_CK(cudaMemcpyAsync(&tot[2], mm->hole_off_n + N, 8, cudaMemcpyDeviceToHost, st));
-      LM_CK(cudaMemcpyAsync(&tot[3], mm->hent_off_n + N, 8, cudaMemcpyDeviceToHost, st));
-      LM_CK(cudaMemcpyAsync(&tot[4], mm->end_off + 2 * E, 8, cudaMemcpyDeviceToHost, st));
-      int ovf = 0;
-      LM_CK(cudaMemcpyAsync(&ovf, overflow, sizeof(int), cudaMemcpyDeviceToHost, st));
-      if (arena_buf) LM_CK(cudaMemcpyAsync(&arena_miss, arena.miss, sizeof(int), cudaMemcpyDeviceToHost, st));
-      LM_CK(cudaStreamSynchronize(st));
-      if (ovf) {
-        if (arena_buf) cudaFreeAsync(arena_buf, st);
-        dfree(node_cnt, st);
-        dfree(end_cnt, st);
-        dfree(lists, st);
-        dfree(deg, st);
-        return LM_ERR_CAPACITY;
-      }
-      mm->V = tot[0];
-      mm->A = tot[1];
-      mm->H = tot[2];
-      mm->HE = tot[3];
-      mm->LE = tot[4];
-      T *vz = nullptr, *aphi = nullptr;
-      auto alloc_out = [&]() -> cudaError_t {
-        cudaError_t e;
-        if ((e = dalloc(mm, &vz, 3 * mm->V, st)) != cudaSuccess) return e;
-        if ((e = dalloc(mm, &mm->vtx_key, mm->V, st)) != cudaSuccess) return e;
-        if ((e = dalloc(mm, &mm->vtx_flags, mm->V, st)) != cudaSuccess) return e;
-        if ((e = dalloc(mm, &mm->vtx_gen, mm->V, st)) != cudaSuccess) return e;
-        if ((e = dalloc(mm, &mm->arc_ends, 2 * mm->A, st)) != cudaSuccess) return e;
-        if ((e = dalloc(mm, &mm->arc_vtx, mm->A, st)) != cudaSuccess) return e;
-        if ((e = dalloc(mm, &aphi, 2 * mm->A, st)) != cudaSuccess) return e;
-        if ((e = dalloc(mm, &mm->loop_ent, mm->LE, st)) != cudaSuccess) return e;
-        if ((e = dalloc(mm, &mm->hole_off, mm->H + 1, st)) != cudaSuccess) return e;
-        return dalloc(mm, &mm->hole_ent, mm->HE, st);
-      };
-      cudaError_t ae = alloc_out();
-      if (ae != cudaSuccess && arena_buf) {
-        // no room beside the arena: release it and emit every node
-        (void)cudaGetLastError();
-        dfree(vz, st);
-        dfree(mm->vtx_key, st);
-        dfree(mm->vtx_flags, st);
-        dfree(mm->vtx_gen, st);
-        dfree(mm->arc_ends, st);
-        dfree(mm->arc_vtx, st);
-        dfree(aphi, st);
-        dfree(mm->loop_ent, st);
-        dfree(mm->hole_off, st);
-        dfree(mm->hole_ent, st);
-        cudaFreeAsync(arena_buf, st);
-        arena_buf = nullptr;
-        arena = MMArena{};
-        L.arena = MMArena{};
-        ae = alloc_out();
-      }
-      LM_CK(ae);
-      mm->vtx_z = vz;
-      mm->arc_phi = aphi;
-      LM_CK(cudaMemcpyAsync(mm->hole_off + mm->H, mm->hent_off_n + N, 8, cudaMemcpyDeviceToDevice, st));
-      L.vtx_off = mm->vtx_off;
-      L.arc_off = mm->arc_off;
-      L.hole_off_n = mm->hole_off_n;
-      L.hent_off_n = mm->hent_off_n;
-      L.end_off = mm->end_off;
-      L.vtx_z = vz;
-      L.vtx_key = mm->vtx_key;
-      L.vtx_flags = mm->vtx_flags;
-      L.vtx_gen = mm->vtx_gen;
-      L.arc_ends = mm->arc_ends;
-      L.arc_vtx = mm->arc_vtx;
-      L.arc_phi = aphi;
-      L.loop_ent = mm->loop_ent;
-      L.hole_off = mm->hole_off;
-      L.hole_ent = mm->hole_ent;
-      if (arena_buf) {
-        // nodes held by the arena go to their CSR ranges; the emit pass below
-        // computes only the others
-        L.arena = arena;
-        LM_CK(launch_mm_gather<T>(L, st));
-      }
-    }
-    if (pass == 0 && mm->opt.autotune) {
-      for (int b = 0; b < NB_BUCKETS; b++) {
-        if (hb[b] == 0) continue;
-        L.nodes = lists + b * cap;
-        int bw = 0, npt = 0;
-        lm_status ts = tune_bucket<T>(mm, L, b, hb[b], st, &bw, &npt);
-        if (ts != LM_OK) return ts;
-        mm->tuned[b][0] = bw;
-        mm->tuned[b][1] = npt;
+  if (mm->opt.autotune) {
+    // the tuner needs the valence mix and times its samples: the one extra
+    // synchronisation of an autotuned build
+    int hb[4] = {0, 0, 0, 0};
+    int herr = 0;
+    LM_CK(cudaMemcpyAsync(hb, bcnt, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    LM_CK(cudaMemcpyAsync(&herr, mm->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    LM_CK(cudaStreamSynchronize(st));
+    if (herr == 0) {
+      TuneVal tv{1, 0};
+      lm_status ts = tune_launch<T>(mm, L, bk, hb, st, &tv);
+      if (ts != LM_OK) return ts;
+      if (mm->opt.nodes_per_task <= 0) bk.npt[0] = tv.npt0;
+      if (ctas <= 0) {
+        int sms = 0, dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        ctas = tv.ctas_per_sm * sms;
       }
       // the sample runs counted their FP64 steps too
       LM_CK(cudaMemsetAsync(mm->d_fb, 0, LM_N_FP64_COUNTS * sizeof(unsigned long long), st));
+      LM_CK(cudaMemsetAsync(overflow, 0, sizeof(int), st));
+      if (arena_buf) LM_CK(cudaMemsetAsync(arena.used, 0, 64, st));
     }
-    if (arena_buf) L.arena = arena;
-    if (pass == 1 && arena_buf && arena_miss == 0) break;
-    for (int b = NB_BUCKETS - 1; b >= 0; b--) {
-      if (hb[b] == 0) continue;
-      L.nodes = lists + b * cap;
-      L.n_list = hb[b];
-      L.queue = mm->d_queue + b;
-      int bw = mm->opt.block_warps, npt = mm->opt.nodes_per_task;
-      if (mm->opt.autotune) {
-        if (bw <= 0) bw = mm->tuned[b][0];
-        if (npt <= 0) npt = mm->tuned[b][1];
-      }
-      L.nodes_per_task = npt > 0 ? npt : 1;
-      mm->tuned[b][0] = bw > 0 ? bw : 4;
-      mm->tuned[b][1] = L.nodes_per_task;
-      LM_CK(cudaMemsetAsync(mm->d_queue + b, 0, sizeof(int), st));
-      int used = 0;
-      LM_CK(launch_metamesh<T>(b, pass == 1, L, bw, mm->opt.grid_ctas, st, &used));
-    }
+  }
+  for (int b = 0; b < NB_BUCKETS; b++) {
+    mm->tuned[b][0] = MM_SLOTS[b];
+    mm->tuned[b][1] = bk.npt[b];
+  }
+  if (arena_buf) L.arena = arena;
+  LM_CK(cudaMemsetAsync(bk.queues, 0, NB_BUCKETS * sizeof(int), st));
+  int used = 0;
+  LM_CK(launch_metamesh<T>(false, L, bk, ctas, st, &used));
+  cudaEventRecord(ev[2], st);
+  // ---- sizing: offsets from the counts, and the one synchronisation
+  LM_CK(dalloc(mm, &mm->vtx_off, N + 1, st));
+  LM_CK(dalloc(mm, &mm->arc_off, N + 1, st));
+  LM_CK(dalloc(mm, &mm->hole_off_n, N + 1, st));
+  LM_CK(dalloc(mm, &mm->hent_off_n, N + 1, st));
+  LM_CK(dalloc(mm, &mm->end_off, 2 * E + 1, st));
+  LM_CK(scan_excl<int32_t>(node_cnt + 0, 4, N, mm->vtx_off, mm->scan_ws, st));
+  LM_CK(scan_excl<int32_t>(node_cnt + 1, 4, N, mm->arc_off, mm->scan_ws, st));
+  LM_CK(scan_excl<int32_t>(node_cnt + 2, 4, N, mm->hole_off_n, mm->scan_ws, st));
+  LM_CK(scan_excl<int32_t>(node_cnt + 3, 4, N, mm->hent_off_n, mm->scan_ws, st));
+  LM_CK(scan_excl<int32_t>(end_cnt, 1, 2 * E, mm->end_off, mm->scan_ws, st));
+  int64_t tot[5];
+  LM_CK(cudaMemcpyAsync(&tot[0], mm->vtx_off + N, 8, cudaMemcpyDeviceToHost, st));
+  LM_CK(cudaMemcpyAsync(&tot[1], mm->arc_off + N, 8, cudaMemcpyDeviceToHost, st));
+  LM_CK(cudaMemcpyAsync(&tot[2], mm->hole_off_n + N, 8, cudaMemcpyDeviceToHost, st));
+  LM_CK(cudaMemcpyAsync(&tot[3], mm->hent_off_n + N, 8, cudaMemcpyDeviceToHost, st));
+  LM_CK(cudaMemcpyAsync(&tot[4], mm->end_off + 2 * E, 8, cudaMemcpyDeviceToHost, st));
+  int hmisc[4] = {0, 0, 0, 0};  // [0] max valence, [1] overflow
+  int herr = 0, arena_miss = 0;
+  LM_CK(cudaMemcpyAsync(hmisc, mm->d_misc, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+  LM_CK(cudaMemcpyAsync(&herr, mm->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  if (arena_buf) LM_CK(cudaMemcpyAsync(&arena_miss, arena.miss, sizeof(int), cudaMemcpyDeviceToHost, st));
+  LM_CK(cudaStreamSynchronize(st));
+  mm->max_valence = hmisc[0];
+  if (herr != 0 || hmisc[1] != 0) {
+    if (arena_buf) cudaFreeAsync(arena_buf, st);
+    dfree(node_cnt, st);
+    dfree(end_cnt, st);
+    dfree(lists, st);
+    dfree(deg, st);
+    return herr != 0 ? (lm_status)herr : LM_ERR_CAPACITY;
+  }
+  mm->V = tot[0];
+  mm->A = tot[1];
+  mm->H = tot[2];
+  mm->HE = tot[3];
+  mm->LE = tot[4];
+  T *vz = nullptr, *aphi = nullptr;
+  auto alloc_out = [&]() -> cudaError_t {
+    cudaError_t e;
+    if ((e = dalloc(mm, &vz, 3 * mm->V, st)) != cudaSuccess) return e;
+    if ((e = dalloc(mm, &mm->vtx_key, mm->V, st)) != cudaSuccess) return e;
+    if ((e = dalloc(mm, &mm->vtx_flags, mm->V, st)) != cudaSuccess) return e;
+    if ((e = dalloc(mm, &mm->vtx_gen, mm->V, st)) != cudaSuccess) return e;
+    if ((e = dalloc(mm, &mm->arc_ends, 2 * mm->A, st)) != cudaSuccess) return e;
+    if ((e = dalloc(mm, &mm->arc_vtx, mm->A, st)) != cudaSuccess) return e;
+    if ((e = dalloc(mm, &aphi, 2 * mm->A, st)) != cudaSuccess) return e;
+    if ((e = dalloc(mm, &mm->loop_ent, mm->LE, st)) != cudaSuccess) return e;
+    if ((e = dalloc(mm, &mm->hole_off, mm->H + 1, st)) != cudaSuccess) return e;
+    return dalloc(mm, &mm->hole_ent, mm->HE, st);
+  };
+  cudaError_t ae = alloc_out();
+  if (ae != cudaSuccess && arena_buf) {
+    // no room beside the arena: release it and emit every node
+    (void)cudaGetLastError();
+    dfree(vz, st);
+    dfree(mm->vtx_key, st);
+    dfree(mm->vtx_flags, st);
+    dfree(mm->vtx_gen, st);
+    dfree(mm->arc_ends, st);
+    dfree(mm->arc_vtx, st);
+    dfree(aphi, st);
+    dfree(mm->loop_ent, st);
+    dfree(mm->hole_off, st);
+    dfree(mm->hole_ent, st);
+    cudaFreeAsync(arena_buf, st);
+    arena_buf = nullptr;
+    arena = MMArena{};
+    L.arena = MMArena{};
+    ae = alloc_out();
+  }
+  LM_CK(ae);
+  mm->vtx_z = vz;
+  mm->arc_phi = aphi;
+  LM_CK(cudaMemcpyAsync(mm->hole_off + mm->H, mm->hent_off_n + N, 8, cudaMemcpyDeviceToDevice, st));
+  L.vtx_off = mm->vtx_off;
+  L.arc_off = mm->arc_off;
+  L.hole_off_n = mm->hole_off_n;
+  L.hent_off_n = mm->hent_off_n;
+  L.end_off = mm->end_off;
+  L.vtx_z = vz;
+  L.vtx_key = mm->vtx_key;
+  L.vtx_flags = mm->vtx_flags;
+  L.vtx_gen = mm->vtx_gen;
+  L.arc_ends = mm->arc_ends;
+  L.arc_vtx = mm->arc_vtx;
+  L.arc_phi = aphi;
+  L.loop_ent = mm->loop_ent;
+  L.hole_off = mm->hole_off;
+  L.hole_ent = mm->hole_ent;
+  // ---- outputs: nodes held by the arena go to their CSR ranges; the emit
+  // pass computes only the others (none when the arena held every node)
+  if (arena_buf) {
+    L.arena = arena;
+    LM_CK(launch_mm_gather<T>(L, st));
+  }
+  if (!arena_buf || arena_miss > 0) {
+    LM_CK(cudaMemsetAsync(bk.queues, 0, NB_BUCKETS * sizeof(int), st));
+    LM_CK(launch_metamesh<T>(true, L, bk, ctas, st, &used));
   }
   cudaEventRecord(ev[3], st);
   if (arena_buf) cudaFreeAsync(arena_buf, st);
@@ -519,6 +530,11 @@ lm_status build_impl(lm_metamesh* mm, cudaStream_t st) {
   LM_CK(cudaMemsetAsync(dstat, 0, 4 * sizeof(unsigned long long), st));
   count_launch(); k_mm_stats<<<grid_for(std::max<int64_t>(std::max<int64_t>(mm->A, N), 2 * E)), 256, 0, st>>>(
       mm->arc_ends, mm->A, mm->node_flags, N, end_cnt, 2 * E, dstat);
+  // FP64 fallback contexts of the triangulation kernels, every context
+  // starting as "no node" (node id -1)
+  mm->scratch_warps = tri_scratch_warps();
+  LM_CK(mm_malloc(mm, (void**)&mm->scratch, node64_bytes() * (size_t)mm->scratch_warps, st));
+  LM_CK(cudaMemsetAsync(mm->scratch, 0xff, node64_bytes() * (size_t)mm->scratch_warps, st));
   unsigned long long hs[4];
   LM_CK(cudaMemcpyAsync(hs, dstat, sizeof(hs), cudaMemcpyDeviceToHost, st));
   LM_CK(cudaStreamSynchronize(st));
@@ -536,12 +552,6 @@ lm_status build_impl(lm_metamesh* mm, cudaStream_t st) {
   dfree(end_cnt, st);
   dfree(lists, st);
   dfree(deg, st);
-  // FP64 fallback contexts of the triangulation kernels
-  mm->scratch_warps = tri_scratch_warps();
-  LM_CK(mm_malloc(mm, (void**)&mm->scratch, node64_bytes() * (size_t)mm->scratch_warps, st));
-  // every context starts as "no node" (node id -1)
-  LM_CK(cudaMemsetAsync(mm->scratch, 0xff, node64_bytes() * (size_t)mm->scratch_warps, st));
-  LM_CK(cudaStreamSynchronize(st));
   return LM_OK;
 }
 

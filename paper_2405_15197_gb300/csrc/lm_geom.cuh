@@ -56,9 +56,10 @@ constexpr float M_POS = 1e-1f;   // conditioning floor for keeping an FP32 circl
 // angle) stays below M_SENS R per unit roundoff, i.e. about 3e-6 R.
 constexpr float M_SENS = 50.0f;
 // An elliptical arc whose points t(phi) = (n0 + n1 c + n2 s) / (d0 + d1 c +
-// d2 s) have a first-order FP32 error bound above M_ILL R per unit angle or
-// coefficient error (the bound (sum|n| + |t| sum|d|) / |D| + |t| over the
-// arc, in units of R) is subdivided in FP64 from the inputs: a steep section
+// d2 s) have a first-order FP32 error bound, relative to the point's
+// distance from the node (about R + |t|), above M_ILL per unit angle or
+// coefficient error (the bound (sum|n| + |t| sum|d|) / (|D| (R + |t|)) over
+// the arc) is subdivided in FP64 from the inputs: a steep section
 // (degenerate node) can send D through zero, where FP32 points drift by far
 // more than the vertex tolerance.
 constexpr float M_ILL = 8.0f;
@@ -704,14 +705,15 @@ __device__ __forceinline__ V3<T> geo_point(const ArcGeo<T>& g, T phi) {
 // Whether an elliptical arc [phi0, phi0 + dphi] of geometry g at a node of
 // radius R is ill-conditioned in the sense of M_ILL: D(phi) = d0 + rho
 // cos(phi - phi_d) is bounded away from zero over the arc by its values at
-// the ends and at its interior minimum / maximum; a sign change is ill.
+// the ends and at its interior minimum / maximum (a sign change is ill), and
+// |t| <= (|n0| + |(n1, n2)|) / min |D|.
 template <typename T>
 __device__ __forceinline__ bool arc_ill(const ArcGeo<T>& g, T phi0, T dphi, T R) {
   const T nsum = fabs(g.n0) + fabs(g.n1) + fabs(g.n2), dsum = fabs(g.d0) + fabs(g.d1) + fabs(g.d2);
   const T rho = lm_sqrt(g.d1 * g.d1 + g.d2 * g.d2), nr = fabs(g.n0) + lm_sqrt(g.n1 * g.n1 + g.n2 * g.n2);
   auto bound = [&](T dmin) {
     const T tmax = nr / dmin;
-    return (nsum + tmax * dsum) / dmin + tmax <= T(M_ILL) * R;
+    return nsum + tmax * dsum <= T(M_ILL) * dmin * (R + tmax);
   };
   // D keeps its sign on the whole circle
   if (fabs(g.d0) > rho && bound(fabs(g.d0) - rho)) return false;

@@ -14,6 +14,11 @@ struct Node64;
 
 // valence buckets of the meta-mesh kernel
 enum { NB_BUCKETS = 3 };
+// warps of a meta-mesh block working on each bucket: the block's shared
+// memory holds four workspaces of the first bucket (d <= 16), two of the
+// second (d <= 32) or one of the third (d <= 64)
+constexpr int MM_BLOCK_WARPS = 4;
+constexpr int MM_SLOTS[3] = {4, 2, 1};
 __host__ __device__ inline int bucket_of(int d) { return d <= 16 ? 0 : (d <= 32 ? 1 : 2); }
 
 // Arena of the meta-mesh count pass: each node's output, stashed in one
@@ -63,6 +68,17 @@ __host__ __device__ inline ArenaBlock arena_block(int64_t nv, int64_t na, int64_
   return b;
 }
 
+// Valence buckets of the persistent meta-mesh launch (device-side counts:
+// no host synchronisation between the bucketing and the launch).
+struct MMBuckets {
+  const int32_t* lists;  // [3][cap] node lists
+  int64_t cap;           // stride between the lists
+  const int* counts;     // device [3]: nodes in each list
+  int limit[3];          // > 0: at most this many nodes of a list (autotuner samples)
+  int* queues;           // device [3]: work counters, zero at launch
+  int npt[3];            // nodes a warp takes per queue access
+};
+
 template <typename T>
 struct MMLaunch {
   // inputs
@@ -72,10 +88,7 @@ struct MMLaunch {
   const int64_t* row_ptr;
   const int32_t* adj;
   int64_t n_nodes, n_struts;
-  const int32_t* nodes;
-  int64_t n_list;
-  int* queue;
-  int nodes_per_task;
+  const int* err;  // input errors of the CSR build (the launch does nothing then)
   uint32_t* node_flags;
   int32_t* node_cnt;
   int32_t* end_cnt;
@@ -95,11 +108,14 @@ struct MMLaunch {
   MMArena arena;  // arena.start NULL: none
 };
 
-// persistent meta-mesh launch of one bucket; grid_ctas <= 0: resident CTAs
-// x SM count.  Returns the CTAs launched in *used_ctas.
+// the persistent meta-mesh launch over every valence bucket; grid_ctas <= 0:
+// resident CTAs x SM count.  Returns the CTAs launched in *used_ctas.
 template <typename T>
-cudaError_t launch_metamesh(int bucket, bool emit, const MMLaunch<T>& a, int block_warps,
-                            int grid_ctas, cudaStream_t st, int* used_ctas);
+cudaError_t launch_metamesh(bool emit, const MMLaunch<T>& a, const MMBuckets& bk, int grid_ctas,
+                            cudaStream_t st, int* used_ctas);
+// resident CTAs per SM of the meta-mesh launch
+template <typename T>
+int metamesh_ctas_per_sm();
 // copy the arena-stored nodes into the CSR layout (the launch's output arrays
 // and offsets)
 template <typename T>

@@ -18,6 +18,7 @@
 // in FP64 from the inputs (near-parallel pairs, tangencies, angular ties).
 #pragma once
 #include "lm_geom.cuh"
+#include "lm_internal.h"
 
 namespace lm {
 
@@ -25,6 +26,21 @@ template <int MD, int MV, int MLE, int MA>
 struct Cap {
   static constexpr int D = MD, V = MV, LE = MLE, A = MA;
 };
+
+// A root kept or uncertain after the evaluation of its generator, waiting in
+// canonical order for its re-decision and its append.
+template <typename T>
+struct CandRec {
+  V3<T> z;
+  uint64_t key, umask;  // key; strut ends whose FP32 screening was uncertain
+  uint32_t code;        // generator code | root << 2
+  uint32_t kflags;      // node flags raised if kept as a new vertex
+  uint8_t state;        // 1 kept, 2 uncertain (0 after a rejection)
+  uint8_t sphere, whole, pad;  // whole: the generator was uncertain as a whole
+};
+// records per warp (a round of 32 generators adds up to 64: the list is
+// flushed as often as it fills)
+constexpr int CAND_CAP = 32;
 
 template <typename T, typename C>
 struct WarpSmem {
@@ -54,15 +70,13 @@ struct WarpSmem {
   uint16_t h_off[C::A + 1];
   uint16_t h_ent[C::A];
   int nh, nhe;
+  CandRec<T> cand[CAND_CAP];
 };
 
 template <typename T>
 struct MMArgs {
   LatDev<T> lat;
-  const int32_t* nodes;  // node list of this valence bucket
-  int64_t n_list;
-  int* queue;            // work counter (persistent scheduling)
-  int nodes_per_task;
+  const int* err;        // input errors found by the CSR build: skip all work
   uint32_t* node_flags;  // [N]
   // count pass
   int32_t* node_cnt;     // [N][4]: V, A, H, HE
@@ -278,14 +292,113 @@ __device__ void node_metamesh(WarpSmem<T, C>& S, const MMArgs<T>& A, int64_t n, 
   }
   __syncwarp();
 
-  // ---- candidate vertices in canonical order, screened, deduplicated
+  // ---- candidate vertices in canonical order, screened, deduplicated.
+  // (1) The generators are evaluated in the kernel's precision, 32 at a
+  // time; the roots they keep and the roots whose decisions FP32 cannot take
+  // safely go to a per-warp list in canonical order.  (2) When the list is
+  // full, or the generators are done, its uncertain roots are re-decided in
+  // double-float together, a root per lane.  (3) The list is appended in
+  // canonical order with the deduplication of the oracle.
   const int np = d * (d - 1) / 2;
   const int nt = d * (d - 1) * (d - 2) / 6;
   const int ng = np + nt;
   bool overflow = false;
   uint32_t nflags = 0;
+  int nrec = 0;  // records in S.cand (warp-uniform)
+  auto flush = [&]() {
+    if constexpr (!IS64) {
+      // (2) dense double-float re-decisions of the uncertain roots
+      bool need = false;
+      for (int q = lane; q < nrec; q += 32) need |= S.cand[q].state == 2;
+      if (__any_sync(0xffffffffu, need)) {
+        ensure_df(S, L, n, d, lane);
+        for (int q0 = 0; q0 < nrec; q0 += 32) {
+          const int q = q0 + lane;
+          const bool mine = q < nrec && S.cand[q].state == 2;
+          fb_add(A.fb, FB_GEN, mine);
+          if (mine) {
+            CandRec<T>& c = S.cand[q];
+            const int r = (c.code >> 2) & 1;
+            // a generator uncertain as a whole is redone in full; otherwise
+            // only the uncertain screening decisions of this root are retaken
+            GenHint hint;
+            hint.st[r] = 2;
+            hint.st[1 - r] = 0;
+            hint.umask[r] = c.umask;
+            hint.umask[1 - r] = 0;
+            GenOut<df> o64;
+            eval_gen<df, true>(S.EDF, d, df(R), c.code & ~4u, o64, c.whole ? nullptr : &hint);
+            nflags |= o64.nflags;
+            if (o64.nroot == 2) {
+              c.z = mk3((T)(float)o64.z[r].x, (T)(float)o64.z[r].y, (T)(float)o64.z[r].z);
+              c.key = o64.key[r];
+              c.sphere = o64.sphere[r];
+              c.state = o64.state[r];
+              c.kflags = o64.kflags[r];
+            } else {
+              c.state = 0;
+            }
+          }
+        }
+        __syncwarp();
+      }
+    }
+    // (3) append in canonical order
+    for (int q = 0; q < nrec && !overflow; q++) {
+      const CandRec<T>& c = S.cand[q];
+      if (c.state != 1) continue;
+      const V3<T> z = c.z;
+      const uint64_t key = c.key;
+      const int sph = c.sphere;
+      const uint32_t kf = c.kflags;
+      const uint32_t gc = c.code;
+      int nvc = S.nv;
+      bool dup = false, dunc = false;
+      for (int v = lane; v < nvc; v += 32) {
+        if (S.vkey[v] != key || ((S.vfl[v] & VF_SPHERE) != 0) != (sph != 0)) continue;
+        V3<T> dz = z - S.vz[v];
+        T dd = lm_sqrt(dot(dz, dz));
+        if (IS64) {
+          dup |= dd <= T(ETA_DEDUP) * R;
+        } else {
+          if (dd <= T(0.5 * ETA_DEDUP) * R) dup = true;
+          else if (dd <= T(2.0 * ETA_DEDUP) * R) dunc = true;
+        }
+      }
+      dup = __any_sync(0xffffffffu, dup);
+      fb_add(A.fb, FB_DEDUP, !IS64 && !dup && dunc && lane == 0);
+      if (!IS64 && !dup && __any_sync(0xffffffffu, dunc)) {
+        ensure64(S, L, n, d, lane);
+        V3<double> z64 = vertex_from_gen<double>(ends64(S), d, R64, gc);
+        for (int v = lane; v < nvc; v += 32) {
+          if (S.vkey[v] != key || ((S.vfl[v] & VF_SPHERE) != 0) != (sph != 0)) continue;
+          V3<double> w = vertex_from_gen<double>(ends64(S), d, R64, S.vgen[v]);
+          V3<double> dz = z64 - w;
+          dup |= sqrt(dot(dz, dz)) <= ETA_DEDUP * R64;
+        }
+        dup = __any_sync(0xffffffffu, dup);
+      }
+      if (dup) continue;
+      if (nvc >= C::V) {
+        overflow = true;
+        break;
+      }
+      if (lane == 0) {
+        S.vz[nvc] = z;
+        S.vkey[nvc] = key;
+        S.vfl[nvc] = sph ? VF_SPHERE : 0;
+        S.vgen[nvc] = gc;
+        S.nv = nvc + 1;
+      }
+      nflags |= kf;
+      __syncwarp();
+    }
+    nrec = 0;
+    __syncwarp();
+  };
   for (int c0 = 0; c0 < ng && !overflow; c0 += 32) {
-    int g = c0 + lane;
+    // (1) evaluation
+    const int g = c0 + lane;
     GenOut<T> o;
     uint32_t code = 0;
     o.nroot = 0;
@@ -295,131 +408,42 @@ __device__ void node_metamesh(WarpSmem<T, C>& S, const MMArgs<T>& A, int64_t n, 
       code = decode_gen(g, d, np);
       eval_gen<T, IS64>(S.E, d, R, code, o);
     }
-    uint64_t gmask = 0;
-    if (g < ng) {
-      int t = code & 3;
-      gmask = (1ull << ((code >> 3) & 63)) | (1ull << ((code >> 9) & 63));
-      if (t == 1) gmask |= 1ull << ((code >> 15) & 63);
-    }
-    // duplicates of vertices found by earlier chunks: same point, generators
-    // all incident to that vertex
-    const int nv0 = S.nv;
-    if (o.nroot == 2) {
-      for (int r = 0; r < 2; r++) {
-        if (o.state[r] == 0) continue;
-        for (int v = 0; v < nv0; v++) {
-          if ((S.vkey[v] & gmask) != gmask) continue;
-          V3<T> dz = o.z[r] - S.vz[v];
-          if (dot(dz, dz) < T(1e-8) * R * R) {
-            o.state[r] = 3;
-            break;
-          }
-        }
-      }
-    }
-    bool need64 = !IS64 && (o.unc || (o.nroot == 2 && (o.state[0] == 2 || o.state[1] == 2)));
-    bool needref = !IS64 && !need64 && o.refine && o.nroot == 2 && (o.state[0] == 1 || o.state[1] == 1);
-    fb_add(A.fb, FB_GEN, need64);
-    fb_add(A.fb, FB_REFINE, needref);
-    if (needref) {
-      V3<double> z64[2];
-      double t64[2];
-      gen_points64<T>(S.E, R, code, z64, t64);
-      for (int r = 0; r < 2; r++) {
-        o.z[r] = mk3((T)z64[r].x, (T)z64[r].y, (T)z64[r].z);
-        o.t0[r] = (T)t64[r];
-      }
-    }
-    if constexpr (!IS64) {
-      if (__any_sync(0xffffffffu, need64)) {
-        // re-decision in double-float (about 48 bits; see lm_df.cuh)
-        ensure_df(S, L, n, d, lane);
-        if (need64) {
-          // a generator uncertain as a whole is redone in full; otherwise only
-          // the uncertain screening decisions of its roots are retaken
-          GenHint hint;
-          for (int r = 0; r < 2; r++) {
-            hint.st[r] = o.state[r];
-            hint.umask[r] = o.umask[r];
-          }
-          GenOut<df> o64;
-          eval_gen<df, true>(S.EDF, d, df(R), code, o64, o.unc ? nullptr : &hint);
-          o.nroot = o64.nroot;
-          o.unc = 0;
-          o.nflags = o64.nflags;
-          for (int r = 0; r < 2; r++) {
-            o.z[r] = mk3((T)(float)o64.z[r].x, (T)(float)o64.z[r].y, (T)(float)o64.z[r].z);
-            o.t0[r] = (T)(float)o64.t0[r];
-            o.key[r] = o64.key[r];
-            o.sphere[r] = o64.sphere[r];
-            o.state[r] = o64.state[r];
-            o.tangent[r] = o64.tangent[r];
-            o.kflags[r] = o64.kflags[r];
-          }
-        }
-      }
-    }
     nflags |= o.nflags;
-    // sequential append of survivors in canonical order
-    uint32_t k0 = __ballot_sync(0xffffffffu, o.nroot == 2 && o.state[0] == 1);
-    uint32_t k1 = __ballot_sync(0xffffffffu, o.nroot == 2 && o.state[1] == 1);
-    uint32_t any = k0 | k1;
-    while (any) {
-      int src = __ffs(any) - 1;
-      any &= any - 1;
-      for (int r = 0; r < 2; r++) {
-        if (!(((r == 0 ? k0 : k1) >> src) & 1u)) continue;
-        V3<T> z = mk3(__shfl_sync(0xffffffffu, o.z[r].x, src), __shfl_sync(0xffffffffu, o.z[r].y, src),
-                      __shfl_sync(0xffffffffu, o.z[r].z, src));
-        uint64_t key = __shfl_sync(0xffffffffu, (unsigned long long)o.key[r], src);
-        int sph = __shfl_sync(0xffffffffu, (int)o.sphere[r], src);
-        uint32_t kf = __shfl_sync(0xffffffffu, o.kflags[r], src);
-        uint32_t gc = __shfl_sync(0xffffffffu, code, src) | ((uint32_t)r << 2);
-        int nvc = S.nv;
-        bool dup = false, dunc = false;
-        for (int v = lane; v < nvc; v += 32) {
-          if (S.vkey[v] != key || ((S.vfl[v] & VF_SPHERE) != 0) != (sph != 0)) continue;
-          V3<T> dz = z - S.vz[v];
-          T dd = lm_sqrt(dot(dz, dz));
-          if (IS64) {
-            dup |= dd <= T(ETA_DEDUP) * R;
-          } else {
-            if (dd <= T(0.5 * ETA_DEDUP) * R) dup = true;
-            else if (dd <= T(2.0 * ETA_DEDUP) * R) dunc = true;
+    // records of this lane: both roots of a generator uncertain as a whole,
+    // else the roots kept or uncertain
+    const int nr = o.unc ? 2 : (o.nroot == 2 ? (o.state[0] != 0) + (o.state[1] != 0) : 0);
+    const int pre = warp_excl_scan(nr, lane);
+    const int tot = __shfl_sync(0xffffffffu, pre + nr, 31);
+    // the lanes' records go to the list in lane order, as many lanes at a
+    // time as the list has room for (the list is flushed when full)
+    int done = 0;  // records of this round already in the list
+    while (done < tot && !overflow) {
+      const bool fits = nr > 0 && pre >= done && pre + nr - done <= CAND_CAP - nrec;
+      if (fits) {
+        int pos = nrec + pre - done;
+        for (int r = 0; r < 2; r++) {
+          if (!o.unc && (o.nroot != 2 || o.state[r] == 0)) continue;
+          CandRec<T>& c = S.cand[pos++];
+          c.code = code | ((uint32_t)r << 2);
+          c.whole = o.unc;
+          c.state = o.unc ? 2 : o.state[r];
+          if (!o.unc) {
+            c.z = o.z[r];
+            c.key = o.key[r];
+            c.umask = o.umask[r];
+            c.sphere = o.sphere[r];
+            c.kflags = o.kflags[r];
           }
         }
-        dup = __any_sync(0xffffffffu, dup);
-        fb_add(A.fb, FB_DEDUP, !IS64 && !dup && dunc && lane == 0);
-        if (!IS64 && !dup && __any_sync(0xffffffffu, dunc)) {
-          ensure64(S, L, n, d, lane);
-          V3<double> z64 = vertex_from_gen<double>(ends64(S), d, R64, gc);
-          for (int v = lane; v < nvc; v += 32) {
-            if (S.vkey[v] != key || ((S.vfl[v] & VF_SPHERE) != 0) != (sph != 0)) continue;
-            V3<double> w = vertex_from_gen<double>(ends64(S), d, R64, S.vgen[v]);
-            V3<double> dz = z64 - w;
-            dup |= sqrt(dot(dz, dz)) <= ETA_DEDUP * R64;
-          }
-          dup = __any_sync(0xffffffffu, dup);
-        }
-        if (dup) continue;
-        if (nvc >= C::V) {
-          overflow = true;
-          break;
-        }
-        if (lane == 0) {
-          S.vz[nvc] = z;
-          S.vkey[nvc] = key;
-          S.vfl[nvc] = sph ? VF_SPHERE : 0;
-          S.vgen[nvc] = gc;
-          S.nv = nvc + 1;
-        }
-        nflags |= kf;
-        __syncwarp();
       }
-      if (overflow) break;
+      const int w = __reduce_add_sync(0xffffffffu, fits ? nr : 0);
+      nrec += w;
+      done += w;
+      __syncwarp();
+      if (done < tot) flush();
     }
-    __syncwarp();
   }
+  if (!overflow) flush();
   nflags = __reduce_or_sync(0xffffffffu, nflags);
 
   // ---- seam vertices for strut ends no vertex touches, in end order: a seam
@@ -947,26 +971,60 @@ __device__ void node_metamesh(WarpSmem<T, C>& S, const MMArgs<T>& A, int64_t n, 
   }
 }
 
-// Persistent work-stealing launch: each warp pops tasks of nodes_per_task
+// capacities of the three valence buckets (d <= 16, <= 32, <= 64): strut
+// ends, vertices, loop entries, arcs per node
+using Cap16 = Cap<16, 64, 192, 160>;
+using Cap32 = Cap<32, 128, 384, 320>;
+using Cap64 = Cap<64, 224, 640, 480>;
+
+template <typename T>
+__host__ __device__ constexpr size_t mm_smem_bytes() {
+  return 4 * sizeof(WarpSmem<T, Cap16>) > 2 * sizeof(WarpSmem<T, Cap32>)
+             ? (4 * sizeof(WarpSmem<T, Cap16>) > sizeof(WarpSmem<T, Cap64>) ? 4 * sizeof(WarpSmem<T, Cap16>)
+                                                                             : sizeof(WarpSmem<T, Cap64>))
+             : (2 * sizeof(WarpSmem<T, Cap32>) > sizeof(WarpSmem<T, Cap64>) ? 2 * sizeof(WarpSmem<T, Cap32>)
+                                                                             : sizeof(WarpSmem<T, Cap64>));
+}
+
+// Work of one bucket: each warp with a workspace pops tasks of npt
 // consecutive entries of the bucket's node list from an atomic counter.
-template <typename T, typename C>
-__global__ void __launch_bounds__(128) k_metamesh(MMArgs<T> A) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  WarpSmem<T, C>& S = reinterpret_cast<WarpSmem<T, C>*>(smem_raw)[w];
-  const int npt = A.nodes_per_task > 0 ? A.nodes_per_task : 1;
+template <typename T, typename C, int SLOTS>
+__device__ __forceinline__ void mm_bucket(const MMArgs<T>& A, const MMBuckets& Bk, int b, unsigned char* smem,
+                                          int w, int lane) {
+  if (w >= SLOTS) return;
+  if (A.err && *(volatile const int*)A.err != 0) return;  // invalid input: nothing to compute
+  WarpSmem<T, C>& S = reinterpret_cast<WarpSmem<T, C>*>(smem)[w];
+  int64_t n = Bk.counts[b];
+  if (Bk.limit[b] > 0 && n > Bk.limit[b]) n = Bk.limit[b];
+  const int npt = Bk.npt[b] > 0 ? Bk.npt[b] : 1;
+  const int32_t* list = Bk.lists + (int64_t)b * Bk.cap;
   while (true) {
     int task = 0;
-    if (lane == 0) task = atomicAdd(A.queue, 1);
+    if (lane == 0) task = atomicAdd(Bk.queues + b, 1);
     task = __shfl_sync(0xffffffffu, task, 0);
-    int64_t first = (int64_t)task * npt;
-    if (first >= A.n_list) break;
-    int64_t last = first + npt < A.n_list ? first + npt : A.n_list;
+    const int64_t first = (int64_t)task * npt;
+    if (first >= n) break;
+    const int64_t last = first + npt < n ? first + npt : n;
     for (int64_t t = first; t < last; t++) {
-      node_metamesh<T, C>(S, A, A.nodes[t], lane);
+      node_metamesh<T, C>(S, A, list[t], lane);
       __syncwarp();
     }
   }
+}
+
+// One persistent, work-stealing launch over nodes of every valence: the
+// blocks work through the buckets in turn (a block passes to the next
+// bucket once its warps have found the current one's queue empty), each
+// warp with the workspace its bucket needs in the block's shared memory.
+template <typename T>
+__global__ void __launch_bounds__(128) k_metamesh(MMArgs<T> A, MMBuckets Bk) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  mm_bucket<T, Cap16, MM_SLOTS[0]>(A, Bk, 0, smem_raw, w, lane);
+  __syncthreads();
+  mm_bucket<T, Cap32, MM_SLOTS[1]>(A, Bk, 1, smem_raw, w, lane);
+  __syncthreads();
+  mm_bucket<T, Cap64, MM_SLOTS[2]>(A, Bk, 2, smem_raw, w, lane);
 }
 
 }  // namespace lm

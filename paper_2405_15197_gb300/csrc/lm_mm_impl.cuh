@@ -6,40 +6,21 @@
 
 namespace lm {
 
-using Cap16 = Cap<16, 64, 192, 160>;
-using Cap32 = Cap<32, 128, 384, 320>;
-using Cap64 = Cap<64, 224, 640, 480>;
-
-template <typename T, typename C>
-cudaError_t go_metamesh(bool emit, const MMArgs<T>& A, int block_warps, int grid_ctas,
-                        cudaStream_t st, int* used) {
-  size_t per = sizeof(WarpSmem<T, C>);
-  if (block_warps <= 0) block_warps = 4;
-  while (block_warps > 1 && per * block_warps > 200 * 1024) block_warps >>= 1;
-  size_t smem = per * block_warps;
-  auto kern = k_metamesh<T, C>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  int dev = 0, sms = 0, per_sm = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, block_warps * 32, smem);
-  if (e != cudaSuccess) return e;
-  if (per_sm < 1) per_sm = 1;
-  int grid = grid_ctas > 0 ? grid_ctas : per_sm * sms;
-  int64_t need = (A.n_list + (A.nodes_per_task > 0 ? A.nodes_per_task : 1) - 1) /
-                 (A.nodes_per_task > 0 ? A.nodes_per_task : 1);
-  int64_t maxg = (need + block_warps - 1) / block_warps;
-  if (grid > maxg) grid = (int)(maxg > 0 ? maxg : 1);
-  if (used) *used = grid;
-  count_launch();
-  kern<<<grid, block_warps * 32, smem, st>>>(A);
-  return cudaGetLastError();
+template <typename T>
+int metamesh_ctas_per_sm() {
+  const size_t smem = mm_smem_bytes<T>();
+  if (cudaFuncSetAttribute(k_metamesh<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    return 0;
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_metamesh<T>, MM_BLOCK_WARPS * 32, smem) !=
+      cudaSuccess)
+    return 0;
+  return per_sm;
 }
 
 template <typename T>
-cudaError_t launch_metamesh(int bucket, bool emit, const MMLaunch<T>& a, int block_warps,
-                            int grid_ctas, cudaStream_t st, int* used) {
+cudaError_t launch_metamesh(bool emit, const MMLaunch<T>& a, const MMBuckets& bk, int grid_ctas, cudaStream_t st,
+                            int* used) {
   MMArgs<T> A{};
   A.lat.xyz = a.xyz;
   A.lat.ends = a.ends;
@@ -48,10 +29,7 @@ cudaError_t launch_metamesh(int bucket, bool emit, const MMLaunch<T>& a, int blo
   A.lat.adj = a.adj;
   A.lat.n_nodes = a.n_nodes;
   A.lat.n_struts = a.n_struts;
-  A.nodes = a.nodes;
-  A.n_list = a.n_list;
-  A.queue = a.queue;
-  A.nodes_per_task = a.nodes_per_task;
+  A.err = a.err;
   A.node_flags = a.node_flags;
   A.node_cnt = a.node_cnt;
   A.end_cnt = a.end_cnt;
@@ -74,15 +52,17 @@ cudaError_t launch_metamesh(int bucket, bool emit, const MMLaunch<T>& a, int blo
   A.fb = a.fb;
   A.emit = emit ? 1 : 0;
   A.ar = a.arena;
-  if (A.n_list <= 0) {
-    if (used) *used = 0;
-    return cudaSuccess;
-  }
-  switch (bucket) {
-    case 0: return go_metamesh<T, Cap16>(emit, A, block_warps, grid_ctas, st, used);
-    case 1: return go_metamesh<T, Cap32>(emit, A, block_warps, grid_ctas, st, used);
-    default: return go_metamesh<T, Cap64>(emit, A, block_warps, grid_ctas, st, used);
-  }
+  const size_t smem = mm_smem_bytes<T>();
+  int per_sm = metamesh_ctas_per_sm<T>();
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  int grid = grid_ctas > 0 ? grid_ctas : per_sm * sms;
+  if (used) *used = grid;
+  count_launch();
+  k_metamesh<T><<<grid, MM_BLOCK_WARPS * 32, smem, st>>>(A, bk);
+  return cudaGetLastError();
 }
 
 // One warp per node stored in the arena: its vertices, arcs, holes and hole
