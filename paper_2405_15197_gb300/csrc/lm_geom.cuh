@@ -56,13 +56,14 @@ constexpr float M_POS = 1e-1f;   // conditioning floor for keeping an FP32 circl
 // angle) stays below M_SENS R per unit roundoff, i.e. about 3e-6 R.
 constexpr float M_SENS = 50.0f;
 // An elliptical arc whose points t(phi) = (n0 + n1 c + n2 s) / (d0 + d1 c +
-// d2 s) have a first-order FP32 error bound, relative to the point's
-// distance from the node (about R + |t|), above M_ILL per unit angle or
-// coefficient error (the bound (sum|n| + |t| sum|d|) / (|D| (R + |t|)) over
-// the arc) is subdivided in FP64 from the inputs: a steep section
-// (degenerate node) can send D through zero, where FP32 points drift by far
-// more than the vertex tolerance.
-constexpr float M_ILL = 8.0f;
+// d2 s) come close to the pole of that ratio is subdivided in FP64 from the
+// inputs.  The coefficients d_i are differences of terms of order one (d0 =
+// co_j - co_i u_i.u_j), so the FP32 denominator carries an absolute error of
+// about 1e-6 whatever its size, and a point's error relative to its distance
+// from the node is about that over |D|: arcs on which |D| drops below D_ILL
+// (steep sections of degenerate nodes, near-parallel strut pairs) are taken
+// in FP64.  Regular lattices stay far above it (BCC 2/3, octet 1/2).
+constexpr float D_ILL = 0.125f;
 
 // node flags (same bits as LM_NODE_* in liblm.h)
 constexpr uint32_t NF_NEAR_TANGENT = 1u, NF_DEGENERATE = 2u, NF_INCONSISTENT = 4u,
@@ -327,7 +328,10 @@ __device__ void eval_gen(const EndG<U>* E, int d, U R, uint32_t gcode, GenOut<U>
   bool sph0;
   U tanq;
   bool well = true;                  // FP32 circle points accurate to ~1e-6 R
-  bool wellr[2] = {true, true};      // FP32 triple points accurate to ~3e-6 R
+  // triple points: the data of their FP32 conditioning estimate, evaluated
+  // only for the roots that survive screening
+  V3<U> cmj = mk3(U(0), U(0), U(0)), cmk = cmj, cv = cmj;
+  U csvv = U(0), cicom = U(0);
   if (type == 0) {
     // circle points: unit n with u_i.n = s_i, u_j.n = s_j (two tangency
     // circles on the nodal sphere)
@@ -424,19 +428,11 @@ __device__ void eval_gen(const EndG<U>* E, int d, U R, uint32_t gcode, GenOut<U>
     o.t0[0] = G0 + lam0 * G1;
     o.t0[1] = G0 + lam1 * G1;
     if constexpr (!F64) {
-      // z solves (G_i - G_j, G_i - G_k, |z|^2 - R^2 - G_i^2) = 0 with Jacobian
-      // rows mj, mk, nc = z - G_i ico_i u_i; a perturbation of the axes by one
-      // roundoff moves the residuals by about |z| ico (|t| ico for the cone
-      // row), and the Jacobian inverse is adj / (v . nc)
-      U icom = fmax(E[i].ico, fmax(E[j].ico, E[k].ico));
-      U svv = lm_sqrt(vv);
-#pragma unroll
-      for (int r = 0; r < 2; r++) {
-        V3<U> nc = o.z[r] - E[i].u * (o.t0[r] * E[i].ico);
-        U num = norm3(o.z[r]) * (norm3(cross(mk, nc)) + norm3(cross(nc, mj))) +
-                svv * norm3(nc) * fabs(o.t0[r]) * icom;
-        wellr[r] = icom * num <= U(M_SENS) * R * fabs(dot(v, nc));
-      }
+      cmj = mj;
+      cmk = mk;
+      cv = v;
+      cicom = fmax(E[i].ico, fmax(E[j].ico, E[k].ico));
+      csvv = lm_sqrt(vv);
     }
     gmask = (1ull << i) | (1ull << j) | (1ull << k);
     sph0 = false;
@@ -501,7 +497,20 @@ __device__ void eval_gen(const EndG<U>* E, int d, U R, uint32_t gcode, GenOut<U>
       if (!F64 && fabs(t0 - lim) <= M) unc = true;
       if (t0 > lim) kf |= NF_DEGENERATE | NF_BEYOND;
     }
-    if (unc || !well || !wellr[r]) {
+    if constexpr (!F64) {
+      if (type == 1 && !unc && well) {
+        // z solves (G_i - G_j, G_i - G_k, |z|^2 - R^2 - G_i^2) = 0 with
+        // Jacobian rows mj, mk, nc = z - G_i ico_i u_i; a perturbation of the
+        // axes by one roundoff moves the residuals by about |z| ico (|t| ico
+        // for the cone row), and the Jacobian inverse is adj / (v . nc): a
+        // root too sensitive for its FP32 position is decided again
+        const V3<U> nc = z - E[i].u * (t0 * E[i].ico);
+        const U num = norm3(z) * (norm3(cross(cmk, nc)) + norm3(cross(nc, cmj))) +
+                      csvv * norm3(nc) * fabs(t0) * cicom;
+        if (!(cicom * num <= U(M_SENS) * R * fabs(dot(cv, nc)))) unc = true;
+      }
+    }
+    if (unc || !well) {
       o.state[r] = 2;
       continue;
     }
@@ -510,6 +519,74 @@ __device__ void eval_gen(const EndG<U>* E, int d, U R, uint32_t gcode, GenOut<U>
     o.state[r] = 1;
     o.kflags[r] = kf | (o.tangent[r] ? NF_NEAR_TANGENT : 0u);
   }
+}
+
+// Re-decision of a triple-point root whose FP32 screening was uncertain
+// (partially: the generator itself was well conditioned), without
+// recomputing the point from scratch.  Newton steps from its FP32 position
+// zf on F(z) = (G_i - G_j, G_i - G_k, |z|^2 - R^2 - G_i^2) = 0, the residual
+// in double-float and the correction from the FP32 Jacobian J (rows m_j,
+// m_k, 2 (z - G_i ico_i u_i)) taken at zf.  A point is accepted once the
+// first-order error bound |J^-1| |F| (row by row) times (1 + max ico) is
+// below 1e-12 R, three orders inside the tie tolerance ETA_SIGMA R: after at
+// most two steps (the FP32 error ~1e-6 R shrinks by the Jacobian's relative
+// error ~1e-7 per step, plus a quadratic term ~|e|^2 / R).  If J is ill
+// conditioned or the bound is not met, false is returned and the caller
+// recomputes the generator in double-float.  Otherwise the screening
+// decisions of the ends in umask and the root-level decisions are taken as
+// eval_gen does in exact mode.  Outputs: state (0 rejected, 1 kept), key,
+// sphere flag, node flags if kept, the refined position.
+inline __device__ __noinline__ bool rescreen_triple_df(const EndG<df>* E, const EndG<float>* EF, int d, float Rf,
+                                                       uint32_t gcode, V3<float> zf, uint64_t umask,
+                                                       uint8_t& state, uint64_t& key, uint8_t& sphere,
+                                                       uint32_t& kflags, V3<float>& zout) {
+  const int i = (gcode >> 3) & 63, j = (gcode >> 9) & 63, k = (gcode >> 15) & 63;
+  const df R(Rf);
+  auto G = [&](int l, const V3<df>& p) { return (dot(E[l].u, p) - R * E[l].s) * E[l].ico; };
+  const float tf = (dot(EF[i].u, zf) - Rf * EF[i].s) * EF[i].ico;
+  const V3<float> a = EF[i].u * EF[i].ico - EF[j].u * EF[j].ico;
+  const V3<float> b = EF[i].u * EF[i].ico - EF[k].u * EF[k].ico;
+  const V3<float> c = (zf - EF[i].u * (tf * EF[i].ico)) * 2.0f;
+  const V3<float> bc = cross(b, c), ca = cross(c, a), ab = cross(a, b);
+  const float det = dot(a, bc);
+  if (!(fabsf(det) > 1e-3f * norm3(a) * norm3(b) * norm3(c))) return false;
+  const float idet = 1.0f / det;
+  const float nbc = norm3(bc), nca = norm3(ca), nab = norm3(ab);
+  const float tol = 1e-12f * Rf * fabsf(det) / (1.0f + fmaxf(EF[i].ico, fmaxf(EF[j].ico, EF[k].ico)));
+  V3<df> z = mk3(df(zf.x), df(zf.y), df(zf.z));
+  df t0;
+  for (int it = 0;; it++) {
+    t0 = G(i, z);
+    const float F0 = (float)(t0 - G(j, z)), F1 = (float)(t0 - G(k, z));
+    const float F2 = (float)(dot(z, z) - R * R - t0 * t0);
+    if (nbc * fabsf(F0) + nca * fabsf(F1) + nab * fabsf(F2) <= tol) break;
+    if (it == 2) return false;
+    const V3<float> dz = (bc * F0 + ca * F1 + ab * F2) * (-idet);
+    z = z + mk3(df(dz.x), df(dz.y), df(dz.z));
+  }
+  const uint64_t gmask = (1ull << i) | (1ull << j) | (1ull << k);
+  const df eta = df(ETA_SIGMA) * R;
+  zout = mk3((float)z.x, (float)z.y, (float)z.z);
+  state = 0;
+  if (t0 < -eta) return true;
+  key = gmask;
+  for (int l = 0; l < d; l++) {
+    if (!((umask >> l) & 1ull)) continue;
+    if ((gmask >> l) & 1ull) {
+      if (R - E[l].s * dot(E[l].u, z) <= df(0.0f)) return true;  // wrong nappe
+      continue;
+    }
+    const df sg = G(l, z) - t0;
+    if (sg > eta) return true;
+    if (sg >= -eta) key |= 1ull << l;
+  }
+  sphere = fabs(t0) <= eta;
+  uint32_t kf = 0;
+  for (int l = 0; l < d; l++)
+    if (((key >> l) & 1ull) && t0 > E[l].L * E[l].co) kf |= NF_DEGENERATE | NF_BEYOND;
+  kflags = kf;
+  state = 1;
+  return true;
 }
 
 // Recompute vertex `gcode` (a kept candidate root, or a seam) in precision U.
@@ -702,23 +779,15 @@ __device__ __forceinline__ V3<T> geo_point(const ArcGeo<T>& g, T phi) {
   return g.u * (g.Rs + t * g.co) + r * (g.Rco - t * g.s);
 }
 
-// Whether an elliptical arc [phi0, phi0 + dphi] of geometry g at a node of
-// radius R is ill-conditioned in the sense of M_ILL: D(phi) = d0 + rho
-// cos(phi - phi_d) is bounded away from zero over the arc by its values at
-// the ends and at its interior minimum / maximum (a sign change is ill), and
-// |t| <= (|n0| + |(n1, n2)|) / min |D|.
+// Whether an elliptical arc [phi0, phi0 + dphi] of geometry g is
+// ill-conditioned in the sense of D_ILL: D(phi) = d0 + rho cos(phi - phi_d)
+// is bounded on the arc by its values at the ends and at its interior
+// extremes.
 template <typename T>
-__device__ __forceinline__ bool arc_ill(const ArcGeo<T>& g, T phi0, T dphi, T R) {
-  const T nsum = fabs(g.n0) + fabs(g.n1) + fabs(g.n2), dsum = fabs(g.d0) + fabs(g.d1) + fabs(g.d2);
-  const T rho = lm_sqrt(g.d1 * g.d1 + g.d2 * g.d2), nr = fabs(g.n0) + lm_sqrt(g.n1 * g.n1 + g.n2 * g.n2);
-  auto bound = [&](T dmin) {
-    const T tmax = nr / dmin;
-    return nsum + tmax * dsum <= T(M_ILL) * dmin * (R + tmax);
-  };
-  // D keeps its sign on the whole circle
-  if (fabs(g.d0) > rho && bound(fabs(g.d0) - rho)) return false;
-  // extremes of D over the arc: the ends, and phi_d (max) / phi_d + pi (min)
-  // when inside
+__device__ __forceinline__ bool arc_ill(const ArcGeo<T>& g, T phi0, T dphi) {
+  const T rho = lm_sqrt(g.d1 * g.d1 + g.d2 * g.d2);
+  // D keeps |D| >= D_ILL on the whole circle
+  if (fabs(g.d0) - rho >= T(D_ILL)) return false;
   T c, s;
   lm_sincos(phi0, &s, &c);
   const T D0 = g.d0 + g.d1 * c + g.d2 * s;
@@ -734,8 +803,7 @@ __device__ __forceinline__ bool arc_ill(const ArcGeo<T>& g, T phi0, T dphi, T R)
     r -= T(PI2) * floor(r * T(1.0 / PI2));
     if (r <= dphi) lo = fmin(lo, g.d0 - rho);
   }
-  if (lo <= T(0) && hi >= T(0)) return true;
-  return !bound(lo > T(0) ? lo : -hi);
+  return lo < T(D_ILL) && hi > -T(D_ILL);
 }
 
 // Exactly rounded operations: no contraction or reassociation is left to the

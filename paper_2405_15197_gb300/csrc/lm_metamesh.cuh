@@ -316,7 +316,17 @@ __device__ void node_metamesh(WarpSmem<T, C>& S, const MMArgs<T>& A, int64_t n, 
           const int q = q0 + lane;
           const bool mine = q < nrec && S.cand[q].state == 2;
           fb_add(A.fb, FB_GEN, mine);
-          if (mine) {
+          // a partially uncertain triple point: one Newton step in
+          // double-float (most roots of symmetric lattices: exact 4-strut ties)
+          bool done = false;
+          if constexpr (sizeof(T) == 4) {
+            if (mine && !S.cand[q].whole && (S.cand[q].code & 3) == 1) {
+              CandRec<T>& c = S.cand[q];
+              done = rescreen_triple_df(S.EDF, S.E, d, (float)R, c.code,
+                                        c.z, c.umask, c.state, c.key, c.sphere, c.kflags, c.z);
+            }
+          }
+          if (mine && !done) {
             CandRec<T>& c = S.cand[q];
             const int r = (c.code >> 2) & 1;
             // a generator uncertain as a whole is redone in full; otherwise
@@ -1017,7 +1027,7 @@ __device__ __forceinline__ void mm_bucket(const MMArgs<T>& A, const MMBuckets& B
 // bucket once its warps have found the current one's queue empty), each
 // warp with the workspace its bucket needs in the block's shared memory.
 template <typename T>
-__global__ void __launch_bounds__(128) k_metamesh(MMArgs<T> A, MMBuckets Bk) {
+__global__ void __launch_bounds__(128, 4) k_metamesh(MMArgs<T> A, MMBuckets Bk) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   mm_bucket<T, Cap16, MM_SLOTS[0]>(A, Bk, 0, smem_raw, w, lane);

@@ -1012,7 +1012,7 @@ __device__ __forceinline__ int tile_entry_setup_impl(const TriArgs<T>& A, int64_
   en.own = (oid == eid);
   // an ill-conditioned elliptical arc is subdivided in FP64 (FP64 pass; both
   // struts of the arc take this decision from the same bits)
-  if (!IS64 && ot >= 0 && arc_ill<T>(en.g, en.phi0, en.dphi, R)) {
+  if (!IS64 && ot >= 0 && arc_ill<T>(en.g, en.phi0, en.dphi)) {
     if (!EXACT) return -2;
     en.ill = 1;
   }
