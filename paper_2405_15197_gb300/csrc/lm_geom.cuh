@@ -328,10 +328,7 @@ __device__ void eval_gen(const EndG<U>* E, int d, U R, uint32_t gcode, GenOut<U>
   bool sph0;
   U tanq;
   bool well = true;                  // FP32 circle points accurate to ~1e-6 R
-  // triple points: the data of their FP32 conditioning estimate, evaluated
-  // only for the roots that survive screening
-  V3<U> cmj = mk3(U(0), U(0), U(0)), cmk = cmj, cv = cmj;
-  U csvv = U(0), cicom = U(0);
+  bool wellr[2] = {true, true};      // FP32 triple points accurate to ~3e-6 R
   if (type == 0) {
     // circle points: unit n with u_i.n = s_i, u_j.n = s_j (two tangency
     // circles on the nodal sphere)
@@ -428,11 +425,19 @@ __device__ void eval_gen(const EndG<U>* E, int d, U R, uint32_t gcode, GenOut<U>
     o.t0[0] = G0 + lam0 * G1;
     o.t0[1] = G0 + lam1 * G1;
     if constexpr (!F64) {
-      cmj = mj;
-      cmk = mk;
-      cv = v;
-      cicom = fmax(E[i].ico, fmax(E[j].ico, E[k].ico));
-      csvv = lm_sqrt(vv);
+      // z solves (G_i - G_j, G_i - G_k, |z|^2 - R^2 - G_i^2) = 0 with Jacobian
+      // rows mj, mk, nc = z - G_i ico_i u_i; a perturbation of the axes by one
+      // roundoff moves the residuals by about |z| ico (|t| ico for the cone
+      // row), and the Jacobian inverse is adj / (v . nc)
+      U icom = fmax(E[i].ico, fmax(E[j].ico, E[k].ico));
+      U svv = lm_sqrt(vv);
+#pragma unroll
+      for (int r = 0; r < 2; r++) {
+        V3<U> nc = o.z[r] - E[i].u * (o.t0[r] * E[i].ico);
+        U num = norm3(o.z[r]) * (norm3(cross(mk, nc)) + norm3(cross(nc, mj))) +
+                svv * norm3(nc) * fabs(o.t0[r]) * icom;
+        wellr[r] = icom * num <= U(M_SENS) * R * fabs(dot(v, nc));
+      }
     }
     gmask = (1ull << i) | (1ull << j) | (1ull << k);
     sph0 = false;
@@ -497,20 +502,7 @@ __device__ void eval_gen(const EndG<U>* E, int d, U R, uint32_t gcode, GenOut<U>
       if (!F64 && fabs(t0 - lim) <= M) unc = true;
       if (t0 > lim) kf |= NF_DEGENERATE | NF_BEYOND;
     }
-    if constexpr (!F64) {
-      if (type == 1 && !unc && well) {
-        // z solves (G_i - G_j, G_i - G_k, |z|^2 - R^2 - G_i^2) = 0 with
-        // Jacobian rows mj, mk, nc = z - G_i ico_i u_i; a perturbation of the
-        // axes by one roundoff moves the residuals by about |z| ico (|t| ico
-        // for the cone row), and the Jacobian inverse is adj / (v . nc): a
-        // root too sensitive for its FP32 position is decided again
-        const V3<U> nc = z - E[i].u * (t0 * E[i].ico);
-        const U num = norm3(z) * (norm3(cross(cmk, nc)) + norm3(cross(nc, cmj))) +
-                      csvv * norm3(nc) * fabs(t0) * cicom;
-        if (!(cicom * num <= U(M_SENS) * R * fabs(dot(cv, nc)))) unc = true;
-      }
-    }
-    if (unc || !well) {
+    if (unc || !well || !wellr[r]) {
       o.state[r] = 2;
       continue;
     }
@@ -536,7 +528,7 @@ __device__ void eval_gen(const EndG<U>* E, int d, U R, uint32_t gcode, GenOut<U>
 // decisions of the ends in umask and the root-level decisions are taken as
 // eval_gen does in exact mode.  Outputs: state (0 rejected, 1 kept), key,
 // sphere flag, node flags if kept, the refined position.
-inline __device__ __noinline__ bool rescreen_triple_df(const EndG<df>* E, const EndG<float>* EF, int d, float Rf,
+__device__ __forceinline__ bool rescreen_triple_df(const EndG<df>* E, const EndG<float>* EF, int d, float Rf,
                                                        uint32_t gcode, V3<float> zf, uint64_t umask,
                                                        uint8_t& state, uint64_t& key, uint8_t& sphere,
                                                        uint32_t& kflags, V3<float>& zout) {

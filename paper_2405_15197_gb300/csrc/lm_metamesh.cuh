@@ -353,55 +353,102 @@ __device__ void node_metamesh(WarpSmem<T, C>& S, const MMArgs<T>& A, int64_t n, 
         __syncwarp();
       }
     }
-    // (3) append in canonical order
-    for (int q = 0; q < nrec && !overflow; q++) {
-      const CandRec<T>& c = S.cand[q];
-      if (c.state != 1) continue;
-      const V3<T> z = c.z;
-      const uint64_t key = c.key;
-      const int sph = c.sphere;
-      const uint32_t kf = c.kflags;
-      const uint32_t gc = c.code;
-      int nvc = S.nv;
-      bool dup = false, dunc = false;
-      for (int v = lane; v < nvc; v += 32) {
-        if (S.vkey[v] != key || ((S.vfl[v] & VF_SPHERE) != 0) != (sph != 0)) continue;
-        V3<T> dz = z - S.vz[v];
-        T dd = lm_sqrt(dot(dz, dz));
-        if (IS64) {
-          dup |= dd <= T(ETA_DEDUP) * R;
-        } else {
-          if (dd <= T(0.5 * ETA_DEDUP) * R) dup = true;
-          else if (dd <= T(2.0 * ETA_DEDUP) * R) dunc = true;
-        }
-      }
-      dup = __any_sync(0xffffffffu, dup);
-      fb_add(A.fb, FB_DEDUP, !IS64 && !dup && dunc && lane == 0);
-      if (!IS64 && !dup && __any_sync(0xffffffffu, dunc)) {
-        ensure64(S, L, n, d, lane);
-        V3<double> z64 = vertex_from_gen<double>(ends64(S), d, R64, gc);
-        for (int v = lane; v < nvc; v += 32) {
+    // (3) append in canonical order.  A record is dropped as a duplicate of
+    // an earlier vertex (same key and sphere flag, within ETA_DEDUP R) or of
+    // an earlier record of the list that is kept.  Lane q holds record q and
+    // compares it with the vertices already stored and with every earlier
+    // kept-or-uncertain record (masks of certain and uncertain matches); the
+    // keep decisions are then resolved in canonical order over those masks,
+    // which gives the decisions of a one-record-at-a-time append.  A distance
+    // the FP32 margins cannot decide is taken in FP64 from the generators.
+    static_assert(CAND_CAP <= 32, "one candidate record per lane");
+    {
+      const int nv0 = S.nv;
+      const int q = lane;
+      const bool live = q < nrec && S.cand[q].state == 1;
+      V3<T> z = mk3(T(0), T(0), T(0));
+      uint64_t key = 0;
+      int sph = 0;
+      bool dpre = false, upre = false;
+      uint32_t mm = 0, um = 0;
+      if (live) {
+        const CandRec<T>& c = S.cand[q];
+        z = c.z;
+        key = c.key;
+        sph = c.sphere;
+        for (int v = 0; v < nv0; v++) {
           if (S.vkey[v] != key || ((S.vfl[v] & VF_SPHERE) != 0) != (sph != 0)) continue;
-          V3<double> w = vertex_from_gen<double>(ends64(S), d, R64, S.vgen[v]);
-          V3<double> dz = z64 - w;
-          dup |= sqrt(dot(dz, dz)) <= ETA_DEDUP * R64;
+          V3<T> dz = z - S.vz[v];
+          T dd = lm_sqrt(dot(dz, dz));
+          if (IS64) {
+            dpre |= dd <= T(ETA_DEDUP) * R;
+          } else {
+            if (dd <= T(0.5 * ETA_DEDUP) * R) dpre = true;
+            else if (dd <= T(2.0 * ETA_DEDUP) * R) upre = true;
+          }
         }
-        dup = __any_sync(0xffffffffu, dup);
+        for (int p = 0; p < q; p++) {
+          const CandRec<T>& o = S.cand[p];
+          if (o.state != 1 || o.key != key || (o.sphere != 0) != (sph != 0)) continue;
+          V3<T> dz = z - o.z;
+          T dd = lm_sqrt(dot(dz, dz));
+          if (IS64) {
+            if (dd <= T(ETA_DEDUP) * R) mm |= 1u << p;
+          } else {
+            if (dd <= T(0.5 * ETA_DEDUP) * R) mm |= 1u << p;
+            else if (dd <= T(2.0 * ETA_DEDUP) * R) um |= 1u << p;
+          }
+        }
       }
-      if (dup) continue;
-      if (nvc >= C::V) {
-        overflow = true;
-        break;
+      const uint32_t liveM = __ballot_sync(0xffffffffu, live);
+      const uint32_t dpreM = __ballot_sync(0xffffffffu, dpre);
+      const uint32_t upreM = __ballot_sync(0xffffffffu, upre);
+      uint32_t K = 0;  // kept records
+      for (int r = 0; r < nrec; r++) {
+        const uint32_t mr = __shfl_sync(0xffffffffu, mm, r);
+        const uint32_t ur = __shfl_sync(0xffffffffu, um, r);
+        if (!((liveM >> r) & 1u)) continue;
+        bool dup = ((dpreM >> r) & 1u) || (mr & K);
+        if (!IS64 && !dup && (((upreM >> r) & 1u) || (ur & K))) {
+          fb_add(A.fb, FB_DEDUP, lane == 0);
+          ensure64(S, L, n, d, lane);
+          const CandRec<T>& c = S.cand[r];
+          const V3<double> z64 = vertex_from_gen<double>(ends64(S), d, R64, c.code);
+          bool d64 = false;
+          for (int v = lane; v < nv0 + r; v += 32) {
+            uint32_t g;
+            if (v < nv0) {
+              if (S.vkey[v] != c.key || ((S.vfl[v] & VF_SPHERE) != 0) != (c.sphere != 0)) continue;
+              g = S.vgen[v];
+            } else {
+              const int p = v - nv0;
+              if (!((K >> p) & 1u) || S.cand[p].key != c.key || (S.cand[p].sphere != 0) != (c.sphere != 0)) continue;
+              g = S.cand[p].code;
+            }
+            const V3<double> w = vertex_from_gen<double>(ends64(S), d, R64, g);
+            const V3<double> dz = z64 - w;
+            d64 |= sqrt(dot(dz, dz)) <= ETA_DEDUP * R64;
+          }
+          dup = __any_sync(0xffffffffu, d64);
+        }
+        if (!dup) K |= 1u << r;
       }
-      if (lane == 0) {
-        S.vz[nvc] = z;
-        S.vkey[nvc] = key;
-        S.vfl[nvc] = sph ? VF_SPHERE : 0;
-        S.vgen[nvc] = gc;
-        S.nv = nvc + 1;
+      const int room = C::V - nv0;
+      const int nk = __popc(K);
+      if (live && ((K >> q) & 1u)) {
+        const int rank = __popc(K & ((1u << q) - 1u));
+        if (rank < room) {
+          const CandRec<T>& c = S.cand[q];
+          S.vz[nv0 + rank] = z;
+          S.vkey[nv0 + rank] = key;
+          S.vfl[nv0 + rank] = sph ? VF_SPHERE : 0;
+          S.vgen[nv0 + rank] = c.code;
+          nflags |= c.kflags;
+        }
       }
-      nflags |= kf;
       __syncwarp();
+      if (lane == 0) S.nv = nv0 + (nk < room ? nk : room);
+      if (nk > room) overflow = true;
     }
     nrec = 0;
     __syncwarp();
