@@ -316,11 +316,15 @@ __device__ void node_metamesh(WarpSmem<T, C>& S, const MMArgs<T>& A, int64_t n, 
           const int q = q0 + lane;
           const bool mine = q < nrec && S.cand[q].state == 2;
           fb_add(A.fb, FB_GEN, mine);
-          // a partially uncertain triple point: one Newton step in
-          // double-float (most roots of symmetric lattices: exact 4-strut ties)
+          // a partially uncertain triple point at a node of valence <= 8:
+          // Newton steps in double-float (there most such roots are exact
+          // ties of four struts, as on BCC lattices).  At higher valence the
+          // uncertain roots are mostly near-threshold non-ties whose steps
+          // fail the error bound about a quarter of the time (irregular
+          // lattice at r_scale 0.3), and the full re-evaluation is faster.
           bool done = false;
           if constexpr (sizeof(T) == 4) {
-            if (mine && !S.cand[q].whole && (S.cand[q].code & 3) == 1) {
+            if (mine && d <= 8 && !S.cand[q].whole && (S.cand[q].code & 3) == 1) {
               CandRec<T>& c = S.cand[q];
               done = rescreen_triple_df(S.EDF, S.E, d, (float)R, c.code,
                                         c.z, c.umask, c.state, c.key, c.sphere, c.kflags, c.z);

@@ -1314,7 +1314,10 @@ __device__ __forceinline__ bool tile_strut(const TriArgs<T>& A, const TileSmem<T
     tfb_add(A.fb, 16, tl == 0, m);
     return true;
   }
-  if (!IS64 && !unsorted) {
+  // FP32 strut pass (no adjoint): the comparisons that decide the zipper are
+  // checked against the margin where the emission makes them (see below)
+  constexpr bool FOLD = !IS64 && !EXACT && !ADJ;
+  if (!IS64 && !unsorted && !FOLD) {
     // A points whose angle lies within M_ZIP of some B key + ETA_ZIP: every
     // such pair is decided in FP64 (B keys are sorted after the rotation up
     // to FP32 rounding, so each scan stops at the first key clearly out of
@@ -1466,6 +1469,14 @@ __device__ __forceinline__ bool tile_strut(const TriArgs<T>& A, const TileSmem<T
     }
     __syncwarp(m);
   }
+  // In the FOLD pass every comparison the placement searches and the walks
+  // make is checked against the margin M_ZIP, and a strut with one inside it
+  // is deferred to the FP64 pass after its records are written (that pass
+  // writes the same range again).  When every comparison made is outside the
+  // margin, each has the outcome the FP64 keys give, so the searches and
+  // walks follow the FP64 path exactly: this replaces a check of every A-B
+  // pair by a check of the pairs that decide the output.
+  bool near = false;
   auto a_before_b = [&](int i, int j) -> bool {
     int jb = wrap_idx(sB + j, nB);
     if (FP64_STEPS && anyt && FL[i < nA ? i : 0] && FL[A.pmax + jb]) {
@@ -1473,13 +1484,16 @@ __device__ __forceinline__ bool tile_strut(const TriArgs<T>& A, const TileSmem<T
       return x <= S.TH64[A.pmax + jb] + ETA_ZIP;
     }
     T x = i < nA ? TH[i] : thA0 + T(PI2);
-    return x <= KB[jb] + T(ETA_ZIP);
+    const T y = KB[jb] + T(ETA_ZIP);
+    if (FOLD) near |= fabs(x - y) <= T(M_ZIP);
+    return x <= y;
   };
   // ---- triangles by merge-path; TL * RPL records per round
   constexpr int RPL = TILE_RPL;
   const int64_t t0 = A.tri_off[e] - out_first;
   V3<T> cA = node_xyz<T, T>(L, lo), cB = node_xyz<T, T>(L, hi);
   V3<T> dAB = cB - cA;
+  double sa_s = 0.0, sv_s = 0.0;  // this strut's area and volume terms
   int ibase = 0;  // A events before position c0 (carried from round to round)
   for (int c0 = 0; c0 < ntri; c0 += TL * RPL) {
     const int p = c0 + RPL * tl;  // this lane's first position
@@ -1531,8 +1545,8 @@ __device__ __forceinline__ bool tile_strut(const TriArgs<T>& A, const TileSmem<T
           tri_point_adjoints<T>(A, ra, rb, rc, nn, cr, ia_, ib_, ic_);
         } else {
           if (OBJ) {
-            sa += 0.5 * (double)lm_sqrt(l2);
-            sv += ((double)dot(ra, cross(rb, rc)) +
+            sa_s += 0.5 * (double)lm_sqrt(l2);
+            sv_s += ((double)dot(ra, cross(rb, rc)) +
                    dot(mk3((double)cA.x, (double)cA.y, (double)cA.z), mk3((double)cr.x, (double)cr.y, (double)cr.z))) *
                   (1.0 / 6.0);
           }
@@ -1564,6 +1578,16 @@ __device__ __forceinline__ bool tile_strut(const TriArgs<T>& A, const TileSmem<T
       }
     }
     __syncwarp(m);
+  }
+  if constexpr (FOLD) {
+    if (__any_sync(m, near)) {
+      tfb_add(A.fb, 14, tl == 0, m);
+      return true;
+    }
+  }
+  if (OBJ) {
+    sa += sa_s;
+    sv += sv_s;
   }
   return false;
 }
