@@ -276,11 +276,19 @@ __device__ __forceinline__ ArcGeo<T> node_arc_geo(const LatDev<T>& L, int64_t no
   g.s = o.s;
   if (otid >= 0) {
     const EndRn<T> t = end_rn<T>(L, node, otid);
-    const T cij = dot_rn(o.u, t.u), a1 = dot_rn(t.u, o.e1), a2 = dot_rn(t.u, o.e2);
-    g.n0 = mul_rn(R, fma_rn(o.s, cij, -t.s));
+    const T a1 = dot_rn(t.u, o.e1), a2 = dot_rn(t.u, o.e2);
+    // n0 = R (s_o c - s_t) and d0 = co_t - co_o c (c = u_o.u_t) without the
+    // cancellation of nearly parallel struts: 1 - c = |u_o - u_t|^2 / 2 and
+    // co_t - co_o = (s_o - s_t)(s_o + s_t) / (co_o + co_t), each accurate
+    // relative to its own size
+    const V3<T> w = mk3(add_rn(o.u.x, -t.u.x), add_rn(o.u.y, -t.u.y), add_rn(o.u.z, -t.u.z));
+    const T h = mul_rn(T(0.5), dot_rn(w, w));
+    const T ds = add_rn(o.s, -t.s);
+    const T dco = div_rn(mul_rn(ds, add_rn(o.s, t.s)), add_rn(o.co, t.co));
+    g.n0 = mul_rn(R, fma_rn(-o.s, h, ds));
     g.n1 = mul_rn(g.Rco, a1);
     g.n2 = mul_rn(g.Rco, a2);
-    g.d0 = fma_rn(-o.co, cij, t.co);
+    g.d0 = fma_rn(o.co, h, dco);
     g.d1 = mul_rn(o.s, a1);
     g.d2 = mul_rn(o.s, a2);
   } else {
