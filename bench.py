@@ -340,6 +340,7 @@ def bench_gpu(args):
     totals = [mm.tri_count(k, stream) for k in ks]
     counts = mm.counts()
     launch_shape = liblm.lm_metamesh_launch_shape(mm.h)
+    twice = liblm.lm_metamesh_emit_nodes(mm.h)
     fb = liblm.lm_fp64_counts(mm.h)
     fp64 = dict(zip(["pair", "candidate", "position_refine", "dedup", "seam", "loop_angle", "label",
                      "arc_extent", "tri_segments", "tri_start_angle", "tri_stitch_order", "tri_fan_centre"],
@@ -400,7 +401,8 @@ def bench_gpu(args):
         "valence_histogram": {str(d): c for d, c in sorted(vhist.items())},
         "fp64_stability_steps": fp64,
         "metamesh_launch_shape": {"buckets": ["d<=16", "d<=32", "d<=64"],
-                                  "warps_per_block_nodes_per_pop": launch_shape, "autotuned": True},
+                                  "warps_per_block_nodes_per_pop": launch_shape, "autotuned": True,
+                                  "nodes_computed_twice": twice},
         "roofline": roof,
         "rooflines": roofs,
         "gpu_launches": int((l1 - l0) // max(1, args.steps)) * args.steps,
@@ -517,18 +519,28 @@ def bench_e2e(torch, liblm, xyz, ends, radii, ks, stream, dev, args):
         mm_tris[k] = probe.tri_count(k, stream)
     probe.close()
 
+    phases = {}
+
     def one():
+        t_a = time.perf_counter()
         dx = hx.to(dev, non_blocking=True)
         de = he.to(dev, non_blocking=True)
         dr = hr.to(dev, non_blocking=True)
         mm = liblm.MetaMesh(dx, de, dr, options=tuned_options(liblm), stream=stream)
+        torch.cuda.synchronize()
+        phases["h2d_and_build_s"] = time.perf_counter() - t_a
         tot = 0
         for k in ks:
+            t_k = time.perf_counter()
             mm.tri_count(k, stream)
             # ~(slot / 50 / 80) items per chunk keeps a chunk inside one slot
             per_item = max(1.0, mm_tris[k] / (mm.n_struts + mm.n_nodes))
             chunk = int(0.8 * slot / 50 / (4 * per_item))
-            tot += liblm.lm_triangulate_stream(mm.h, k, chunk, ring.data_ptr(), slot, n_slots, None, stream)
+            n = liblm.lm_triangulate_stream(mm.h, k, chunk, ring.data_ptr(), slot, n_slots, None, stream)
+            torch.cuda.synchronize()
+            phases[f"count_and_stream_k{k}_s"] = time.perf_counter() - t_k
+            phases[f"d2h_gbs_k{k}"] = 50.0 * n / phases[f"count_and_stream_k{k}_s"] / 1e9
+            tot += n
         mm.close()
         return tot
 
@@ -542,10 +554,23 @@ def bench_e2e(torch, liblm, xyz, ends, radii, ks, stream, dev, args):
     torch.cuda.synchronize()
     dt = (time.perf_counter() - t0) / steps
     E = ends.shape[0]
+    # the device-to-host bandwidth this link gives one large copy into pinned
+    # memory (the bound of the streaming phases)
+    probe_d = torch.empty(1 << 32, dtype=torch.uint8, device=dev)
+    probe_h = ring[: 1 << 32] if ring.numel() >= 1 << 32 else torch.empty(1 << 32, dtype=torch.uint8, pin_memory=True)
+    probe_h.copy_(probe_d, non_blocking=True)
+    torch.cuda.synchronize()
+    t_c = time.perf_counter()
+    probe_h.copy_(probe_d, non_blocking=True)
+    torch.cuda.synchronize()
+    c2c = probe_d.numel() / (time.perf_counter() - t_c) / 1e9
+    del probe_d
     return {"value": E / dt, "unit": "struts/s", "ms_per_step": dt * 1e3,
             "h2d_bytes_per_step": int(hx.numel() * hx.element_size() + he.numel() * he.element_size()
                                       + hr.numel() * hr.element_size()),
-            "d2h_bytes_per_step": int(50 * tot), "steps": steps,
+            "d2h_bytes_per_step": int(50 * tot), "steps": steps, "phases": phases,
+            "d2h_copy_gbs_measured": c2c,
+            "d2h_bound_s": 50.0 * tot / (c2c * 1e9),
             "path": "pinned host lattice -> lm_build_metamesh -> lm_triangulate_stream (pinned ring)"}
 
 

@@ -152,8 +152,12 @@ lm_status lm_metamesh_counts(const lm_metamesh* mm, int64_t out[8]);
  * loops in the layout of Section 4.3.2, "Coalesced-access memory layout": an
  * index region of prefix sums (the *_off arrays, one CSR range per node or
  * strut end) over structure-of-arrays data).  Library-owned device memory,
- * valid until lm_metamesh_free; the call fills `view` on the host and does no
- * device work.  Returns LM_ERR_INVALID_ARG for a NULL handle or view.
+ * valid until lm_metamesh_free; the call fills `view` on the host.  arc_ends
+ * is not kept by the build (no kernel reads it; it follows from arc_vtx and
+ * the CSR): the first call derives it on the handle's stream (one allocation
+ * of 8 B per arc and one kernel, synchronised), later calls reuse it.
+ * Returns LM_ERR_INVALID_ARG for a NULL handle or view, LM_ERR_OOM or
+ * LM_ERR_CUDA if that first derivation fails.
  * Node-local vertex and arc ids index from node_vtx_off[n] / node_arc_off[n].
  *   vtx_z     : [V][3] dtype, vertex position relative to its node centre
  *   arc_ends  : [A][2] int32 global strut-end ids (2*strut+side): owner, other
@@ -188,7 +192,7 @@ typedef struct {
   const uint32_t* hole_ent;
 } lm_metamesh_view;
 
-lm_status lm_metamesh_export(const lm_metamesh* mm, lm_metamesh_view* view);
+lm_status lm_metamesh_export(lm_metamesh* mm, lm_metamesh_view* view);
 
 /* Triangle counts at resolution k (Section 5, Eq. sampling with chord error
  * CE = 1 - cos(pi/k); Algorithm 1).  Items 0..E-1 are struts (lateral band
@@ -262,8 +266,11 @@ lm_status lm_metamesh_backward(lm_metamesh* mm, int32_t k, double w_area, double
  * working on the bucket, out[2b+1] = nodes a warp takes per work-queue
  * access.  With
  * lm_options.autotune these are the autotuner's choices (Section 4.3.3's
- * workload balancing, done by measurement); 0 for buckets without nodes. */
-lm_status lm_metamesh_launch_shape(const lm_metamesh* mm, int32_t out[6]);
+ * workload balancing, done by measurement); 0 for buckets without nodes.
+ * out[6] = nodes the emit pass computed a second time (those the count
+ * pass's arena could not hold; every node when the build ran without an
+ * arena), out[7] = 0 (reserved).  Host values; no device work.          */
+lm_status lm_metamesh_launch_shape(const lm_metamesh* mm, int32_t out[8]);
 
 /* First asynchronous error recorded on the handle by a device-side check
  * (LM_ERR_CAPACITY); synchronises `stream`, then clears it.              */

@@ -149,6 +149,23 @@ __global__ void k_strut_taper(const T* xyz, const int32_t* ends, const T* node_R
   }
 }
 
+// global strut-end ids of every arc (owner, other or -1) from its node-local
+// end indices in arc_vtx, one warp per node
+__global__ void k_arc_ends(const int64_t* row_ptr, const int32_t* adj, const int64_t* arc_off,
+                           const uint32_t* arc_vtx, int64_t N, int32_t* arc_ends) {
+  const int lane = threadIdx.x & 31;
+  for (int64_t n = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; n < N;
+       n += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+    const int64_t rb = row_ptr[n], d = row_ptr[n + 1] - rb;
+    for (int64_t a = arc_off[n] + lane; a < arc_off[n + 1]; a += 32) {
+      const uint32_t av = arc_vtx[a];
+      const int64_t o = (av >> 16) & 255, ot = (int64_t)(av >> 24) - 1;
+      arc_ends[2 * a] = o < d ? adj[rb + o] : -1;
+      arc_ends[2 * a + 1] = ot >= 0 && ot < d ? adj[rb + ot] : -1;
+    }
+  }
+}
+
 // warp-aggregated bucketing of nodes by valence (keeps runs of nodes)
 __global__ void k_bucket(const int64_t* row_ptr, int64_t N, int* cnt, int32_t* lists, int64_t cap) {
   const int lane = threadIdx.x & 31;
@@ -171,12 +188,12 @@ __global__ void k_bucket(const int64_t* row_ptr, int64_t N, int* cnt, int32_t* l
   }
 }
 
-__global__ void k_mm_stats(const int32_t* arc_ends, int64_t A, const uint32_t* node_flags, int64_t N,
+__global__ void k_mm_stats(const uint32_t* arc_vtx, int64_t A, const uint32_t* node_flags, int64_t N,
                            const int32_t* end_cnt, int64_t E2, unsigned long long* out) {
   // out: [0] circular arcs, [1] degenerate nodes, [2] flags OR, [3] max loop entries
   unsigned long long circ = 0, deg = 0, fl = 0, mx = 0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < A; i += (int64_t)gridDim.x * blockDim.x)
-    circ += arc_ends[2 * i + 1] < 0;
+    circ += (arc_vtx[i] >> 24) == 0u;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
     deg += (node_flags[i] & 2u) != 0;
     fl |= node_flags[i];
@@ -354,10 +371,10 @@ lm_status build_impl(lm_metamesh* mm, cudaStream_t st) {
   for (int b = 0; b < NB_BUCKETS; b++) bk.npt[b] = mm->opt.nodes_per_task > 0 ? mm->opt.nodes_per_task : 1;
   int ctas = mm->opt.grid_ctas;
   // arena of the count pass (replaces the emit pass for the nodes it holds):
-  // up to 35 % of the free memory left beside the CSR offsets, at most about
-  // 300 B per strut (a node's block is about 100 B per strut end); the CSR
-  // arrays are allocated beside it (if they do not fit, the arena is released
-  // and every node is emitted)
+  // up to 45 % of the free memory left beside the CSR offsets, at most about
+  // 300 B per strut (a node's block is about 50 B per strut end); the CSR
+  // arrays, about 1.05 times the arena's content, are allocated beside it
+  // (if they do not fit, the arena is released and every node is emitted)
   MMArena arena{};
   void* arena_buf = nullptr;
   const double arena_want = (double)(sizeof(T) == 4 ? 300 : 400) * (double)E + 64.0 * (double)N + 65536.0;
@@ -365,7 +382,7 @@ lm_status build_impl(lm_metamesh* mm, cudaStream_t st) {
     size_t fr = 0, tot = 0;
     cudaMemGetInfo(&fr, &tot);
     const double offs = 8.0 * (4.0 * (double)(N + 1) + 2.0 * (double)E + 1.0);
-    double budget = 0.35 * std::max(0.0, (double)fr - offs);
+    double budget = 0.45 * std::max(0.0, (double)fr - offs);
     if (mm->opt.arena_bytes > 0) budget = std::min(budget, (double)mm->opt.arena_bytes);
     return budget - 8.0 * (double)std::max<int64_t>(N, 1) - 4096.0;
   };
@@ -466,7 +483,6 @@ lm_status build_impl(lm_metamesh* mm, cudaStream_t st) {
     if ((e = dalloc(mm, &mm->vtx_key, mm->V, st)) != cudaSuccess) return e;
     if ((e = dalloc(mm, &mm->vtx_flags, mm->V, st)) != cudaSuccess) return e;
     if ((e = dalloc(mm, &mm->vtx_gen, mm->V, st)) != cudaSuccess) return e;
-    if ((e = dalloc(mm, &mm->arc_ends, 2 * mm->A, st)) != cudaSuccess) return e;
     if ((e = dalloc(mm, &mm->arc_vtx, mm->A, st)) != cudaSuccess) return e;
     if ((e = dalloc(mm, &aphi, 2 * mm->A, st)) != cudaSuccess) return e;
     if ((e = dalloc(mm, &mm->loop_ent, mm->LE, st)) != cudaSuccess) return e;
@@ -481,7 +497,6 @@ lm_status build_impl(lm_metamesh* mm, cudaStream_t st) {
     dfree(mm->vtx_key, st);
     dfree(mm->vtx_flags, st);
     dfree(mm->vtx_gen, st);
-    dfree(mm->arc_ends, st);
     dfree(mm->arc_vtx, st);
     dfree(aphi, st);
     dfree(mm->loop_ent, st);
@@ -506,7 +521,6 @@ lm_status build_impl(lm_metamesh* mm, cudaStream_t st) {
   L.vtx_key = mm->vtx_key;
   L.vtx_flags = mm->vtx_flags;
   L.vtx_gen = mm->vtx_gen;
-  L.arc_ends = mm->arc_ends;
   L.arc_vtx = mm->arc_vtx;
   L.arc_phi = aphi;
   L.loop_ent = mm->loop_ent;
@@ -518,6 +532,7 @@ lm_status build_impl(lm_metamesh* mm, cudaStream_t st) {
     L.arena = arena;
     LM_CK(launch_mm_gather<T>(L, st));
   }
+  mm->emit_nodes = arena_buf ? arena_miss : N;
   if (!arena_buf || arena_miss > 0) {
     LM_CK(cudaMemsetAsync(bk.queues, 0, NB_BUCKETS * sizeof(int), st));
     LM_CK(launch_metamesh<T>(true, L, bk, ctas, st, &used));
@@ -529,7 +544,7 @@ lm_status build_impl(lm_metamesh* mm, cudaStream_t st) {
   LM_CK(dalloc(mm, &dstat, 4, st));
   LM_CK(cudaMemsetAsync(dstat, 0, 4 * sizeof(unsigned long long), st));
   count_launch(); k_mm_stats<<<grid_for(std::max<int64_t>(std::max<int64_t>(mm->A, N), 2 * E)), 256, 0, st>>>(
-      mm->arc_ends, mm->A, mm->node_flags, N, end_cnt, 2 * E, dstat);
+      mm->arc_vtx, mm->A, mm->node_flags, N, end_cnt, 2 * E, dstat);
   // FP64 fallback contexts of the triangulation kernels, every context
   // starting as "no node" (node id -1)
   mm->scratch_warps = tri_scratch_warps();
@@ -796,8 +811,22 @@ lm_status lm_metamesh_counts(const lm_metamesh* mm, int64_t out[8]) {
   return LM_OK;
 }
 
-lm_status lm_metamesh_export(const lm_metamesh* mm, lm_metamesh_view* v) {
+lm_status lm_metamesh_export(lm_metamesh* mm, lm_metamesh_view* v) {
   if (!mm || !v) return LM_ERR_INVALID_ARG;
+  if (!mm->arc_ends && mm->A > 0) {
+    cudaStream_t st = mm->st;
+    if (dalloc(mm, &mm->arc_ends, 2 * mm->A, st) != cudaSuccess) {
+      (void)cudaGetLastError();
+      mm->arc_ends = nullptr;
+      return LM_ERR_OOM;
+    }
+    count_launch();
+    k_arc_ends<<<grid_for(32 * mm->N), 256, 0, st>>>(mm->row_ptr, mm->adj, mm->arc_off, mm->arc_vtx, mm->N,
+                                                     mm->arc_ends);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return st_cuda(e);
+  }
   v->n_nodes = mm->N;
   v->n_struts = mm->E;
   v->n_vtx = mm->V;
@@ -874,12 +903,14 @@ lm_status lm_objective(lm_metamesh* mm, int32_t k, void* stream, double* h_area,
   return LM_OK;
 }
 
-lm_status lm_metamesh_launch_shape(const lm_metamesh* mm, int32_t out[6]) {
+lm_status lm_metamesh_launch_shape(const lm_metamesh* mm, int32_t out[8]) {
   if (!mm || !out) return LM_ERR_INVALID_ARG;
   for (int b = 0; b < 3; b++) {
     out[2 * b] = mm->tuned[b][0];
     out[2 * b + 1] = mm->tuned[b][1];
   }
+  out[6] = (int32_t)mm->emit_nodes;
+  out[7] = 0;
   return LM_OK;
 }
 

@@ -32,12 +32,14 @@ struct MMArena {
   int* miss;                 // nodes not stored
 };
 
-// Layout of one node's block (byte offsets): vertex positions, keys, flags,
-// generators; arc ends, vertices, angles; hole starts (relative to the
-// node's first hole entry); hole entries; loop entries of its ends in
-// adjacency order.
+// Layout of one node's block (byte offsets): vertex positions, keys,
+// generators; arc vertices (owner and other local end included: the gather
+// derives the arcs' global end ids from them), angles; hole starts (relative
+// to the node's first hole entry); hole entries; vertex flags (one byte
+// each); loop entries of its ends in adjacency order (last: the other
+// offsets do not depend on their number).  Blocks are 8-byte aligned.
 struct ArenaBlock {
-  int64_t vz, vkey, vfl, vgen, aends, avtx, aphi, ho, he, le, bytes;
+  int64_t vz, vkey, vgen, avtx, aphi, ho, he, vfl, le, bytes;
 };
 __host__ __device__ inline int64_t arena_a8(int64_t x) { return (x + 7) & ~(int64_t)7; }
 __host__ __device__ inline ArenaBlock arena_block(int64_t nv, int64_t na, int64_t nh, int64_t nhe, int64_t nle,
@@ -48,12 +50,8 @@ __host__ __device__ inline ArenaBlock arena_block(int64_t nv, int64_t na, int64_
   o = arena_a8(o + 3 * tsz * nv);
   b.vkey = o;
   o += 8 * nv;
-  b.vfl = o;
-  o += 4 * nv;
   b.vgen = o;
   o += 4 * nv;
-  b.aends = o;
-  o += 8 * na;
   b.avtx = o;
   o = arena_a8(o + 4 * na);
   b.aphi = o;
@@ -62,9 +60,11 @@ __host__ __device__ inline ArenaBlock arena_block(int64_t nv, int64_t na, int64_
   o += 4 * nh;
   b.he = o;
   o += 4 * nhe;
+  b.vfl = o;
+  o = (o + nv + 3) & ~(int64_t)3;
   b.le = o;
   o += 4 * nle;
-  b.bytes = (o + 15) & ~(int64_t)15;
+  b.bytes = arena_a8(o);
   return b;
 }
 
@@ -97,7 +97,6 @@ struct MMLaunch {
   uint64_t* vtx_key;
   uint32_t* vtx_flags;
   uint32_t* vtx_gen;
-  int32_t* arc_ends;
   uint32_t* arc_vtx;
   T* arc_phi;
   uint32_t* loop_ent;
@@ -203,13 +202,14 @@ struct lm_metamesh {
   void* vtx_z;
   uint64_t* vtx_key;
   uint32_t *vtx_flags, *vtx_gen;
-  int32_t* arc_ends;
+  int32_t* arc_ends;  // derived on the first export (not used by the kernels)
   uint32_t* arc_vtx;
   void* arc_phi;
   uint32_t* loop_ent;
   int64_t* hole_off;
   uint32_t* hole_ent;
   int64_t V, A, LE, H, HE;
+  int64_t emit_nodes;  // nodes the build's emit pass computed again
   int64_t n_ell, n_circ, n_degenerate;
   uint32_t flags_or;
   // triangulation state (one k at a time)

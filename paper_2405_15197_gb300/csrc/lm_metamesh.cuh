@@ -87,7 +87,6 @@ struct MMArgs {
   uint64_t* vtx_key;
   uint32_t* vtx_flags;
   uint32_t* vtx_gen;
-  int32_t* arc_ends;
   uint32_t* arc_vtx;
   T* arc_phi;
   uint32_t* loop_ent;
@@ -965,7 +964,7 @@ __device__ void node_metamesh(WarpSmem<T, C>& S, const MMArgs<T>& A, int64_t n, 
         unsigned char* blk = A.ar.buf + at;
         T* vz = reinterpret_cast<T*>(blk + B.vz);
         uint64_t* vkey = reinterpret_cast<uint64_t*>(blk + B.vkey);
-        uint32_t* vfl = reinterpret_cast<uint32_t*>(blk + B.vfl);
+        uint8_t* vfl = blk + B.vfl;
         uint32_t* vgen = reinterpret_cast<uint32_t*>(blk + B.vgen);
         for (int v = lane; v < S.nv; v += 32) {
           vz[3 * v] = S.vz[v].x;
@@ -975,12 +974,9 @@ __device__ void node_metamesh(WarpSmem<T, C>& S, const MMArgs<T>& A, int64_t n, 
           vfl[v] = S.vfl[v];
           vgen[v] = S.vgen[v];
         }
-        int32_t* aends = reinterpret_cast<int32_t*>(blk + B.aends);
         uint32_t* avtx = reinterpret_cast<uint32_t*>(blk + B.avtx);
         T* aphi = reinterpret_cast<T*>(blk + B.aphi);
         for (int a = lane; a < na; a += 32) {
-          aends[2 * a] = S.E[S.a_owner[a]].end_id;
-          aends[2 * a + 1] = S.a_other[a] < 0 ? -1 : S.E[S.a_other[a]].end_id;
           avtx[a] = (uint32_t)S.a_v0[a] | ((uint32_t)S.a_v1[a] << 8) | ((uint32_t)S.a_owner[a] << 16) |
                     ((uint32_t)(S.a_other[a] + 1) << 24);
           aphi[2 * a] = S.a_phi0[a];
@@ -1010,8 +1006,6 @@ __device__ void node_metamesh(WarpSmem<T, C>& S, const MMArgs<T>& A, int64_t n, 
     A.vtx_gen[vo + v] = S.vgen[v];
   }
   for (int a = lane; a < na; a += 32) {
-    A.arc_ends[2 * (ao + a)] = S.E[S.a_owner[a]].end_id;
-    A.arc_ends[2 * (ao + a) + 1] = S.a_other[a] < 0 ? -1 : S.E[S.a_other[a]].end_id;
     A.arc_vtx[ao + a] = (uint32_t)S.a_v0[a] | ((uint32_t)S.a_v1[a] << 8) |
                         ((uint32_t)S.a_owner[a] << 16) | ((uint32_t)(S.a_other[a] + 1) << 24);
     A.arc_phi[2 * (ao + a)] = S.a_phi0[a];

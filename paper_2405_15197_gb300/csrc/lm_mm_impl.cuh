@@ -42,7 +42,6 @@ cudaError_t launch_metamesh(bool emit, const MMLaunch<T>& a, const MMBuckets& bk
   A.vtx_key = a.vtx_key;
   A.vtx_flags = a.vtx_flags;
   A.vtx_gen = a.vtx_gen;
-  A.arc_ends = a.arc_ends;
   A.arc_vtx = a.arc_vtx;
   A.arc_phi = a.arc_phi;
   A.loop_ent = a.loop_ent;
@@ -84,7 +83,7 @@ __global__ void __launch_bounds__(256) k_mm_gather(MMLaunch<T> a) {
     const unsigned char* blk = a.arena.buf + at;
     const T* vz = reinterpret_cast<const T*>(blk + B.vz);
     const uint64_t* vkey = reinterpret_cast<const uint64_t*>(blk + B.vkey);
-    const uint32_t* vfl = reinterpret_cast<const uint32_t*>(blk + B.vfl);
+    const uint8_t* vfl = blk + B.vfl;
     const uint32_t* vgen = reinterpret_cast<const uint32_t*>(blk + B.vgen);
     for (int64_t q = lane; q < 3 * nv; q += 32) a.vtx_z[3 * vo + q] = vz[q];
     for (int64_t v = lane; v < nv; v += 32) {
@@ -92,13 +91,9 @@ __global__ void __launch_bounds__(256) k_mm_gather(MMLaunch<T> a) {
       a.vtx_flags[vo + v] = vfl[v];
       a.vtx_gen[vo + v] = vgen[v];
     }
-    const int32_t* aends = reinterpret_cast<const int32_t*>(blk + B.aends);
     const uint32_t* avtx = reinterpret_cast<const uint32_t*>(blk + B.avtx);
     const T* aphi = reinterpret_cast<const T*>(blk + B.aphi);
-    for (int64_t q = lane; q < 2 * na; q += 32) {
-      a.arc_ends[2 * ao + q] = aends[q];
-      a.arc_phi[2 * ao + q] = aphi[q];
-    }
+    for (int64_t q = lane; q < 2 * na; q += 32) a.arc_phi[2 * ao + q] = aphi[q];
     for (int64_t q = lane; q < na; q += 32) a.arc_vtx[ao + q] = avtx[q];
     const uint32_t* hos = reinterpret_cast<const uint32_t*>(blk + B.ho);
     const uint32_t* hes = reinterpret_cast<const uint32_t*>(blk + B.he);

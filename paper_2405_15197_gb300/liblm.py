@@ -328,6 +328,13 @@ class MetaMesh:
 
 def lm_metamesh_launch_shape(h):
     """[(warps per block, nodes per queue access)] per valence bucket."""
-    out = (ctypes.c_int32 * 6)()
+    out = (ctypes.c_int32 * 8)()
     _ck(load().lm_metamesh_launch_shape(h, out), "lm_metamesh_launch_shape")
     return [(out[2 * b], out[2 * b + 1]) for b in range(3)]
+
+
+def lm_metamesh_emit_nodes(h):
+    """Nodes the build computed a second time (not held by its arena)."""
+    out = (ctypes.c_int32 * 8)()
+    _ck(load().lm_metamesh_launch_shape(h, out), "lm_metamesh_launch_shape")
+    return int(out[6])
