@@ -406,8 +406,16 @@ __device__ void node_metamesh(WarpSmem<T, C>& S, const MMArgs<T>& A, int64_t n, 
       const uint32_t liveM = __ballot_sync(0xffffffffu, live);
       const uint32_t dpreM = __ballot_sync(0xffffffffu, dpre);
       const uint32_t upreM = __ballot_sync(0xffffffffu, upre);
-      uint32_t K = 0;  // kept records
-      for (int r = 0; r < nrec; r++) {
+      // With no FP32-uncertain distance the keep set is the unique solution
+      // of K_q = live_q and not dpre_q and (mm_q & K) = 0 over the earlier
+      // records; the guess "no earlier live match" is that solution when it
+      // satisfies every equation (checked lane-parallel), else the equations
+      // are solved in canonical order below.
+      uint32_t K = liveM & ~dpreM & ~__ballot_sync(0xffffffffu, (mm & liveM) != 0u);
+      const bool fast = !__any_sync(0xffffffffu, upre || um != 0u) &&
+                        __all_sync(0xffffffffu, ((K >> q) & 1u) == (uint32_t)(live && !dpre && (mm & K) == 0u));
+      if (!fast) K = 0;
+      for (int r = 0; r < nrec && !fast; r++) {
         const uint32_t mr = __shfl_sync(0xffffffffu, mm, r);
         const uint32_t ur = __shfl_sync(0xffffffffu, um, r);
         if (!((liveM >> r) & 1u)) continue;
