@@ -61,12 +61,14 @@ WORKLOADS = {
               "cpu_ref": ("bcc", 40, 40, 8, 0.05)},
 }
 
-# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum of the stitching,
-# FP64 and hole-fan launches) per triangle of the k = 32 emit, measured with
-# ncu on the profiling case of the lattice family (octet 24^3) with the
-# current kernels; the benchmark scales it by the triangles of its own emit
-# (no entry: not measured with the current kernels, reported as null)
-TRAFFIC_PER_TRI_K32 = {"octet": 52.4}
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per triangle of
+# the FP32 stitching launch k_tri_tiles at k = 32 (its FP64 and hole-fan
+# launches take 1.4 % of the emit's time on BCC), measured with ncu on the
+# profiling case of the lattice family (BCC 40^3: 1,727.8 MB over 32.7 M
+# triangles of one launch) with the current kernels; the benchmark scales it
+# by the triangles of its own emit (no entry: not measured with the current
+# kernels, reported as null)
+TRAFFIC_PER_TRI_K32 = {"bcc": 52.8}
 
 
 METRIC = "meta-mesh struts/s; triangles/s & write GB/s vs HBM peak; adjoint struts/s"
@@ -202,6 +204,8 @@ def run_step(torch, liblm, xyz, ends, radii, ks, out, stream, want_times=False):
     if want_times:
         stream.synchronize()
         times = {"metamesh_ms": ev[0].elapsed_time(ev[1])}
+        bt = liblm.lm_metamesh_build_times(mm.h)
+        times["metamesh_csr_tune_ms"], times["metamesh_count_kernel_ms"], times["metamesh_emit_ms"] = bt
         for q, k in enumerate(ks):
             times[f"tri_k{k}_ms"] = ev[2 + 2 * q].elapsed_time(ev[3 + 2 * q])
             times[f"count_k{k}_ms"] = (ev[1] if q == 0 else ev[1 + 2 * q]).elapsed_time(ev[2 + 2 * q])
@@ -276,10 +280,14 @@ def valence_hist(torch, ends, n_nodes):
 
 
 # ncu-measured figures of the meta-mesh count pass on the profiling case of
-# each lattice family (see profiles/): FP32-pipe issue fraction, FP64 share
-# of executed thread instructions.  Absent: not measured with the current
+# each lattice family (BCC 40^3, 132,921 nodes, one launch): DRAM bytes per
+# node (read + write, scaled by the benchmark's node count), FMA / ALU / FP64
+# pipe fractions, issue-active fraction, active lanes per warp instruction,
+# instruction-cache (GCC) hit rate.  Absent: not measured with the current
 # kernel (reported as null).
-METAMESH_NCU = {}
+METAMESH_NCU = {"bcc": {"dram_bytes_per_node": 507.6, "fp32_issue_frac_ncu": 0.133, "alu_pipe_frac_ncu": 0.259,
+                        "fp64_pipe_frac_ncu": 0.013, "issue_active_ncu": 0.371, "lanes_per_inst_ncu": 11.5,
+                        "icache_gcc_hit_ncu": 0.865}}
 
 
 def rooflines(wl, ks, totals, phase, counts, vhist, N, E, peaks, peak_kind):
@@ -295,19 +303,26 @@ def rooflines(wl, ks, totals, phase, counts, vhist, N, E, peaks, peak_kind):
            "algorithmic_bytes": f"50 B written per triangle x {totals[ks.index(k_big)]} triangles",
            "peak_kind": f"{peak_kind} hbm_gbs (copy burst)"}
     mm_ms = phase["metamesh_ms"]
+    kern_ms = phase["metamesh_count_kernel_ms"]
     fl = metamesh_flops(vhist)
     pk = fp32_peak_tflops(peaks)
-    ach = fl / (mm_ms / 1e3) / 1e12
+    ach = fl / (kern_ms / 1e3) / 1e12
     by = metamesh_bytes(counts, N, E)
-    mm = {"bound": "alu", "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": ach / pk, "traffic": None,
-          "kernel": "meta-mesh build (CSR + persistent k_metamesh count pass, arena gather, emit pass)",
+    ncu = METAMESH_NCU.get(wl["kind"], {})
+    mm = {"bound": "alu", "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": ach / pk,
+          "traffic": ncu["dram_bytes_per_node"] * N if "dram_bytes_per_node" in ncu else None,
+          "kernel": "k_metamesh count pass (persistent launch, every node computed once; CUDA events "
+                    "around the launch inside the library)",
+          "launch_ms": kern_ms,
+          "build_achieved": fl / (mm_ms / 1e3) / 1e12, "build_ms": mm_ms,
           "algorithmic_flops": fl, "flops_per_strut": fl / max(E, 1),
           "flop_model": "per node of valence d: 15 d(d-1) + C(d,2)(40 + 16 d) + C(d,3)(170 + 16 d)",
           "peak_kind": f"derived: {N_SMS} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x "
                        f"{float(peaks.get('sm_max_mhz', 2070.0)):.0f} MHz",
           "dram_gbs_algorithmic": by / (mm_ms / 1e3) / 1e9, "algorithmic_bytes": by,
-          "dram_frac_algorithmic": by / (mm_ms / 1e3) / 1e9 / hbm}
-    mm.update(METAMESH_NCU.get(wl["kind"], {"fp32_issue_frac_ncu": None, "fp64_inst_share_ncu": None}))
+          "dram_frac_algorithmic": by / (mm_ms / 1e3) / 1e9 / hbm,
+          "traffic_note": "ncu dram bytes per node of the BCC 40^3 count-pass launch x nodes"}
+    mm.update({k: v for k, v in ncu.items() if k != "dram_bytes_per_node"})
     dominant = mm if mm_ms >= tri_ms else tri
     return dominant, {"metamesh": mm, f"triangulation_k{k_big}": tri}
 

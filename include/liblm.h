@@ -272,6 +272,15 @@ lm_status lm_metamesh_backward(lm_metamesh* mm, int32_t k, double w_area, double
  * arena), out[7] = 0 (reserved).  Host values; no device work.          */
 lm_status lm_metamesh_launch_shape(const lm_metamesh* mm, int32_t out[8]);
 
+/* Device time of the build's phases, milliseconds from CUDA events on the
+ * build's stream: out[0] = input checks, CSR, bucketing and (with
+ * lm_options.autotune) the tuner's sample launches; out[1] = the persistent
+ * count-pass launch of the meta-mesh kernel alone (every node computed once);
+ * out[2] = sizing, the arena gather and the emit pass of the nodes the arena
+ * could not hold.  Host values; no device work.  Returns
+ * LM_ERR_INVALID_ARG for a NULL handle or array.                          */
+lm_status lm_metamesh_build_times(const lm_metamesh* mm, float out[3]);
+
 /* First asynchronous error recorded on the handle by a device-side check
  * (LM_ERR_CAPACITY); synchronises `stream`, then clears it.              */
 lm_status lm_last_error(lm_metamesh* mm, void* stream);

@@ -339,7 +339,6 @@ lm_status build_impl(lm_metamesh* mm, cudaStream_t st) {
   LM_CK(dalloc(mm, &lists, (int64_t)NB_BUCKETS * cap, st));
   count_launch(); k_bucket<<<grid_for(N), 256, 0, st>>>(mm->row_ptr, N, bcnt, lists, cap);
   LM_CK(cudaGetLastError());
-  cudaEventRecord(ev[1], st);
   // ---- count pass
   int32_t *node_cnt = nullptr, *end_cnt = nullptr;
   LM_CK(dalloc(mm, &node_cnt, 4 * N, st));
@@ -437,6 +436,7 @@ lm_status build_impl(lm_metamesh* mm, cudaStream_t st) {
   if (arena_buf) L.arena = arena;
   LM_CK(cudaMemsetAsync(bk.queues, 0, NB_BUCKETS * sizeof(int), st));
   int used = 0;
+  cudaEventRecord(ev[1], st);
   LM_CK(launch_metamesh<T>(false, L, bk, ctas, st, &used));
   cudaEventRecord(ev[2], st);
   // ---- sizing: offsets from the counts, and the one synchronisation
@@ -900,6 +900,14 @@ lm_status lm_objective(lm_metamesh* mm, int32_t k, void* stream, double* h_area,
   LM_CK(cudaStreamSynchronize(st));
   if (h_area) *h_area = h[0];
   if (h_volume) *h_volume = h[1];
+  return LM_OK;
+}
+
+lm_status lm_metamesh_build_times(const lm_metamesh* mm, float out[3]) {
+  if (!mm || !out) return LM_ERR_INVALID_ARG;
+  out[0] = mm->t_csr;
+  out[1] = mm->t_count;
+  out[2] = mm->t_emit;
   return LM_OK;
 }
 

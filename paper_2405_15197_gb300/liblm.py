@@ -23,7 +23,7 @@ EXPORTS = ["lm_build_metamesh", "lm_metamesh_counts", "lm_metamesh_export", "lm_
            "lm_tri_range", "lm_triangulate", "lm_triangulate_stream", "lm_stl_header",
            "lm_objective", "lm_metamesh_backward", "lm_last_error", "lm_metamesh_free",
            "lm_status_string", "lm_copy_to_host", "lm_launch_count", "lm_triangulate_noalloc",
-           "lm_fp64_counts", "lm_metamesh_launch_shape", "lm_eval_angle_fns",
+           "lm_fp64_counts", "lm_metamesh_launch_shape", "lm_metamesh_build_times", "lm_eval_angle_fns",
            "lm_cuda_error_string"]
 
 
@@ -95,6 +95,7 @@ def load():
         "lm_fp64_counts": ([V, P64], ctypes.c_int),
         "lm_triangulate_noalloc": ([V, I32, I64, I64, V, I64, V, P64], ctypes.c_int),
         "lm_metamesh_launch_shape": ([V, ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
+        "lm_metamesh_build_times": ([V, ctypes.POINTER(ctypes.c_float)], ctypes.c_int),
         "lm_eval_angle_fns": ([V, V, V, I64, V, V, V, V], ctypes.c_int),
         "lm_cuda_error_string": ([], ctypes.c_char_p),
     }
@@ -331,6 +332,14 @@ def lm_metamesh_launch_shape(h):
     out = (ctypes.c_int32 * 8)()
     _ck(load().lm_metamesh_launch_shape(h, out), "lm_metamesh_launch_shape")
     return [(out[2 * b], out[2 * b + 1]) for b in range(3)]
+
+
+def lm_metamesh_build_times(h):
+    """Device ms of the build: (CSR and tuning, count-pass kernel, sizing +
+    gather + emit pass)."""
+    out = (ctypes.c_float * 3)()
+    _ck(load().lm_metamesh_build_times(h, out), "lm_metamesh_build_times")
+    return float(out[0]), float(out[1]), float(out[2])
 
 
 def lm_metamesh_emit_nodes(h):
