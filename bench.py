@@ -205,7 +205,8 @@ def run_step(torch, liblm, xyz, ends, radii, ks, out, stream, want_times=False):
         stream.synchronize()
         times = {"metamesh_ms": ev[0].elapsed_time(ev[1])}
         bt = liblm.lm_metamesh_build_times(mm.h)
-        times["metamesh_csr_tune_ms"], times["metamesh_count_kernel_ms"], times["metamesh_emit_ms"] = bt
+        (times["metamesh_csr_tune_ms"], times["metamesh_count_kernel_ms"], times["metamesh_size_alloc_ms"],
+         times["metamesh_gather_ms"], times["metamesh_emit_ms"]) = bt
         for q, k in enumerate(ks):
             times[f"tri_k{k}_ms"] = ev[2 + 2 * q].elapsed_time(ev[3 + 2 * q])
             times[f"count_k{k}_ms"] = (ev[1] if q == 0 else ev[1 + 2 * q]).elapsed_time(ev[2 + 2 * q])
@@ -342,6 +343,10 @@ def bench_gpu(args):
     dev = torch.device("cuda", local)
     build.build()
     liblm.load()
+    if not args.no_pool_retain:
+        # builds of the same size reuse the pool's mapped memory from step to
+        # step (as a service that rebuilds meta-meshes would configure it)
+        liblm.lm_pool_retain((1 << 64) - 1)
     wl = WORKLOADS[args.workload]
     ks = wl["ks"]
     xyz, ends, radii = make_lattice_device(wl, dev, torch)
@@ -569,16 +574,20 @@ def bench_e2e(torch, liblm, xyz, ends, radii, ks, stream, dev, args):
     torch.cuda.synchronize()
     dt = (time.perf_counter() - t0) / steps
     E = ends.shape[0]
-    # the device-to-host bandwidth this link gives one large copy into pinned
-    # memory (the bound of the streaming phases)
-    probe_d = torch.empty(1 << 32, dtype=torch.uint8, device=dev)
-    probe_h = ring[: 1 << 32] if ring.numel() >= 1 << 32 else torch.empty(1 << 32, dtype=torch.uint8, pin_memory=True)
-    probe_h.copy_(probe_d, non_blocking=True)
-    torch.cuda.synchronize()
-    t_c = time.perf_counter()
-    probe_h.copy_(probe_d, non_blocking=True)
-    torch.cuda.synchronize()
-    c2c = probe_d.numel() / (time.perf_counter() - t_c) / 1e9
+    # the device-to-host bandwidth this link gives large copies into the
+    # (already written) pinned ring: best of several 4 x 1 GiB copies, timed
+    # with CUDA events on the stream (the bound of the streaming phases)
+    probe_d = torch.empty(slot, dtype=torch.uint8, device=dev)
+    probe_d.fill_(1)
+    c2c = 0.0
+    for _ in range(4):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for q in range(n_slots):
+            ring[q * slot:(q + 1) * slot].copy_(probe_d, non_blocking=True)
+        e1.record(stream)
+        e1.synchronize()
+        c2c = max(c2c, n_slots * slot / (e0.elapsed_time(e1) / 1e3) / 1e9)
     del probe_d
     return {"value": E / dt, "unit": "struts/s", "ms_per_step": dt * 1e3,
             "h2d_bytes_per_step": int(hx.numel() * hx.element_size() + he.numel() * he.element_size()
@@ -586,6 +595,7 @@ def bench_e2e(torch, liblm, xyz, ends, radii, ks, stream, dev, args):
             "d2h_bytes_per_step": int(50 * tot), "steps": steps, "phases": phases,
             "d2h_copy_gbs_measured": c2c,
             "d2h_bound_s": 50.0 * tot / (c2c * 1e9),
+            "d2h_link_frac": {f"k{k}": phases[f"d2h_gbs_k{k}"] / c2c for k in ks},
             "path": "pinned host lattice -> lm_build_metamesh -> lm_triangulate_stream (pinned ring)"}
 
 
@@ -875,6 +885,8 @@ def main():
     ap.add_argument("--cpu-configs", action="store_true",
                     help="time the oracle on every configuration (all host cores) and exit")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-pool-retain", action="store_true",
+                    help="let the memory pool give freed memory back at every synchronisation")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-adjoint", action="store_true")
     ap.add_argument("--no-extras", action="store_true",

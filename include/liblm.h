@@ -269,17 +269,21 @@ lm_status lm_metamesh_backward(lm_metamesh* mm, int32_t k, double w_area, double
  * workload balancing, done by measurement); 0 for buckets without nodes.
  * out[6] = nodes the emit pass computed a second time (those the count
  * pass's arena could not hold; every node when the build ran without an
- * arena), out[7] = 0 (reserved).  Host values; no device work.          */
+ * arena), out[7] = 1 if the emit pass took only those nodes from the lists
+ * the count pass made of them, 0 if it went over every node (no arena, or
+ * more nodes missed than the lists hold: 1/16 of the nodes + 1,024 per
+ * valence bucket).  Host values; no device work.                        */
 lm_status lm_metamesh_launch_shape(const lm_metamesh* mm, int32_t out[8]);
 
 /* Device time of the build's phases, milliseconds from CUDA events on the
  * build's stream: out[0] = input checks, CSR, bucketing and (with
  * lm_options.autotune) the tuner's sample launches; out[1] = the persistent
  * count-pass launch of the meta-mesh kernel alone (every node computed once);
- * out[2] = sizing, the arena gather and the emit pass of the nodes the arena
- * could not hold.  Host values; no device work.  Returns
+ * out[2] = sizing (offset scans, the one host synchronisation, allocation of
+ * the output arrays); out[3] = the arena gather; out[4] = the emit pass of
+ * the nodes the arena could not hold.  Host values; no device work.  Returns
  * LM_ERR_INVALID_ARG for a NULL handle or array.                          */
-lm_status lm_metamesh_build_times(const lm_metamesh* mm, float out[3]);
+lm_status lm_metamesh_build_times(const lm_metamesh* mm, float out[5]);
 
 /* First asynchronous error recorded on the handle by a device-side check
  * (LM_ERR_CAPACITY); synchronises `stream`, then clears it.              */
@@ -344,6 +348,18 @@ lm_status lm_fp64_counts(const lm_metamesh* mm, int64_t out[LM_N_FP64_COUNTS]);
 /* Utility (no counterpart in the paper): number of CUDA kernels this library
  * has launched in the process so far (host-side counter).                */
 long long lm_launch_count(void);
+
+/* Utility (no counterpart in the paper): the library allocates its device
+ * memory from the current device's default memory pool (CUDA's stream-ordered
+ * allocator), which by default gives freed memory back to the driver at every
+ * synchronisation, so that a build after a freed one maps its memory again.
+ * lm_pool_retain(bytes) lets that pool keep up to `bytes` of freed memory
+ * mapped for reuse (0 restores the default).  The setting belongs to the pool,
+ * so it applies to every user of the current device's default pool; memory it
+ * keeps is not available to other allocators (PyTorch's, for one) until the
+ * threshold is lowered again.  Returns LM_ERR_CUDA if the pool cannot be
+ * queried or set.                                                         */
+lm_status lm_pool_retain(uint64_t bytes);
 
 /* Utility (no counterpart in the paper): text of the CUDA error behind the
  * last LM_ERR_CUDA or LM_ERR_OOM that a call of this library returned on the

@@ -295,7 +295,7 @@ lm_status build_impl(lm_metamesh* mm, cudaStream_t st) {
   const int64_t N = mm->N, E = mm->E;
   const T* xyz = (const T*)mm->xyz;
   const T* radii = (const T*)mm->radii;
-  cudaEvent_t ev[4];
+  cudaEvent_t ev[6];
   for (auto& e : ev) cudaEventCreate(&e);
   cudaEventRecord(ev[0], st);
   int* deg = nullptr;
@@ -377,26 +377,45 @@ lm_status build_impl(lm_metamesh* mm, cudaStream_t st) {
   MMArena arena{};
   void* arena_buf = nullptr;
   const double arena_want = (double)(sizeof(T) == 4 ? 300 : 400) * (double)E + 64.0 * (double)N + 65536.0;
+  // per bucket, room to list up to 1/16 of the nodes that the arena could
+  // not hold (the emit pass then computes only those)
+  const int64_t mcap = N / 16 + 1024;
   auto arena_room = [&]() {
     size_t fr = 0, tot = 0;
     cudaMemGetInfo(&fr, &tot);
+    {
+      // memory the default pool keeps mapped but unused (lm_pool_retain) is
+      // free for this build's allocations too
+      int dev = 0;
+      cudaMemPool_t pool;
+      unsigned long long resv = 0, inuse = 0;
+      if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess &&
+          cudaMemPoolGetAttribute(pool, cudaMemPoolAttrReservedMemCurrent, &resv) == cudaSuccess &&
+          cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &inuse) == cudaSuccess && resv > inuse)
+        fr += (size_t)(resv - inuse);
+      (void)cudaGetLastError();
+    }
     const double offs = 8.0 * (4.0 * (double)(N + 1) + 2.0 * (double)E + 1.0);
     double budget = 0.45 * std::max(0.0, (double)fr - offs);
     if (mm->opt.arena_bytes > 0) budget = std::min(budget, (double)mm->opt.arena_bytes);
-    return budget - 8.0 * (double)std::max<int64_t>(N, 1) - 4096.0;
+    return budget - 8.0 * (double)std::max<int64_t>(N, 1) - 4.0 * NB_BUCKETS * (double)mcap - 4096.0;
   };
   if (mm->opt.arena_bytes >= 0) {
     double capb = std::min(arena_room(), arena_want);
     if (capb > 4096.0) {
       const size_t cap_bytes = ((size_t)capb) & ~(size_t)255;
       const size_t start_off = cap_bytes, ctr_off = start_off + (((size_t)8 * std::max<int64_t>(N, 1) + 255) & ~(size_t)255);
-      if (mm_malloc(mm, &arena_buf, ctr_off + 256, st) == cudaSuccess) {
+      const size_t ml_off = ctr_off + 256;
+      if (mm_malloc(mm, &arena_buf, ml_off + (size_t)4 * NB_BUCKETS * (size_t)mcap, st) == cudaSuccess) {
         unsigned char* b = (unsigned char*)arena_buf;
         arena.buf = b;
         arena.cap = (int64_t)cap_bytes;
         arena.start = (int64_t*)(b + start_off);
         arena.used = (unsigned long long*)(b + ctr_off);
         arena.miss = (int*)(b + ctr_off + 8);
+        arena.mcnt = (int*)(b + ctr_off + 16);
+        arena.mlist = (int32_t*)(b + ml_off);
+        arena.mcap = mcap;
         LM_CK(cudaMemsetAsync(b + ctr_off, 0, 64, st));
       } else {
         (void)cudaGetLastError();
@@ -457,10 +476,13 @@ lm_status build_impl(lm_metamesh* mm, cudaStream_t st) {
   LM_CK(cudaMemcpyAsync(&tot[3], mm->hent_off_n + N, 8, cudaMemcpyDeviceToHost, st));
   LM_CK(cudaMemcpyAsync(&tot[4], mm->end_off + 2 * E, 8, cudaMemcpyDeviceToHost, st));
   int hmisc[4] = {0, 0, 0, 0};  // [0] max valence, [1] overflow
-  int herr = 0, arena_miss = 0;
+  int herr = 0, arena_miss = 0, mcnt[NB_BUCKETS] = {0, 0, 0};
   LM_CK(cudaMemcpyAsync(hmisc, mm->d_misc, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
   LM_CK(cudaMemcpyAsync(&herr, mm->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
-  if (arena_buf) LM_CK(cudaMemcpyAsync(&arena_miss, arena.miss, sizeof(int), cudaMemcpyDeviceToHost, st));
+  if (arena_buf) {
+    LM_CK(cudaMemcpyAsync(&arena_miss, arena.miss, sizeof(int), cudaMemcpyDeviceToHost, st));
+    LM_CK(cudaMemcpyAsync(mcnt, arena.mcnt, NB_BUCKETS * sizeof(int), cudaMemcpyDeviceToHost, st));
+  }
   LM_CK(cudaStreamSynchronize(st));
   mm->max_valence = hmisc[0];
   if (herr != 0 || hmisc[1] != 0) {
@@ -528,16 +550,32 @@ lm_status build_impl(lm_metamesh* mm, cudaStream_t st) {
   L.hole_ent = mm->hole_ent;
   // ---- outputs: nodes held by the arena go to their CSR ranges; the emit
   // pass computes only the others (none when the arena held every node)
+  cudaEventRecord(ev[3], st);
   if (arena_buf) {
     L.arena = arena;
     LM_CK(launch_mm_gather<T>(L, st));
   }
+  cudaEventRecord(ev[4], st);
   mm->emit_nodes = arena_buf ? arena_miss : N;
+  mm->emit_listed = 0;
   if (!arena_buf || arena_miss > 0) {
     LM_CK(cudaMemsetAsync(bk.queues, 0, NB_BUCKETS * sizeof(int), st));
-    LM_CK(launch_metamesh<T>(true, L, bk, ctas, st, &used));
+    bool listed = arena_buf != nullptr;
+    for (int b = 0; b < NB_BUCKETS; b++) listed = listed && mcnt[b] <= mcap;
+    mm->emit_listed = listed ? 1 : 0;
+    if (listed) {
+      // only the listed nodes (those the arena could not hold)
+      MMBuckets bm = bk;
+      bm.lists = arena.mlist;
+      bm.cap = mcap;
+      bm.counts = arena.mcnt;
+      for (int b = 0; b < NB_BUCKETS; b++) bm.limit[b] = 0;
+      LM_CK(launch_metamesh<T>(true, L, bm, ctas, st, &used));
+    } else {
+      LM_CK(launch_metamesh<T>(true, L, bk, ctas, st, &used));
+    }
   }
-  cudaEventRecord(ev[3], st);
+  cudaEventRecord(ev[5], st);
   if (arena_buf) cudaFreeAsync(arena_buf, st);
   // statistics
   unsigned long long* dstat = nullptr;
@@ -560,7 +598,9 @@ lm_status build_impl(lm_metamesh* mm, cudaStream_t st) {
   mm->max_loop_entries = (int)hs[3];
   cudaEventElapsedTime(&mm->t_csr, ev[0], ev[1]);
   cudaEventElapsedTime(&mm->t_count, ev[1], ev[2]);
-  cudaEventElapsedTime(&mm->t_emit, ev[2], ev[3]);
+  cudaEventElapsedTime(&mm->t_size, ev[2], ev[3]);
+  cudaEventElapsedTime(&mm->t_gather, ev[3], ev[4]);
+  cudaEventElapsedTime(&mm->t_emit, ev[4], ev[5]);
   for (auto& e : ev) cudaEventDestroy(e);
   dfree(dstat, st);
   dfree(node_cnt, st);
@@ -903,11 +943,13 @@ lm_status lm_objective(lm_metamesh* mm, int32_t k, void* stream, double* h_area,
   return LM_OK;
 }
 
-lm_status lm_metamesh_build_times(const lm_metamesh* mm, float out[3]) {
+lm_status lm_metamesh_build_times(const lm_metamesh* mm, float out[5]) {
   if (!mm || !out) return LM_ERR_INVALID_ARG;
   out[0] = mm->t_csr;
   out[1] = mm->t_count;
-  out[2] = mm->t_emit;
+  out[2] = mm->t_size;
+  out[3] = mm->t_gather;
+  out[4] = mm->t_emit;
   return LM_OK;
 }
 
@@ -918,7 +960,7 @@ lm_status lm_metamesh_launch_shape(const lm_metamesh* mm, int32_t out[8]) {
     out[2 * b + 1] = mm->tuned[b][1];
   }
   out[6] = (int32_t)mm->emit_nodes;
-  out[7] = 0;
+  out[7] = mm->emit_listed;
   return LM_OK;
 }
 
@@ -1044,6 +1086,16 @@ lm_status lm_triangulate_stream(lm_metamesh* mm, int32_t k, int64_t chunk_items,
 long long lm_launch_count(void) { return g_launches.load(); }
 
 const char* lm_cuda_error_string(void) { return cudaGetErrorString(g_last_cuda); }
+
+lm_status lm_pool_retain(uint64_t bytes) {
+  int dev = 0;
+  cudaMemPool_t pool;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetDefaultMemPool(&pool, dev);
+  if (e == cudaSuccess) e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &bytes);
+  if (e == cudaSuccess && bytes == 0) e = cudaMemPoolTrimTo(pool, 0);
+  return e == cudaSuccess ? LM_OK : st_cuda(e);
+}
 
 lm_status lm_eval_angle_fns(const float* d_y, const float* d_x, const float* d_a, int64_t n, float* d_atan2,
                             float* d_sin, float* d_cos, void* stream) {

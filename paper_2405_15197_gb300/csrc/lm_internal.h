@@ -30,6 +30,11 @@ struct MMArena {
   int64_t cap;               // bytes
   int64_t* start;            // [N] byte offset of each node's block; < 0: not stored
   int* miss;                 // nodes not stored
+  // the nodes not stored, listed per valence bucket ([3][mcap]; counts in
+  // mcnt[3], which may exceed mcap: the emit pass then takes every node)
+  int32_t* mlist;
+  int* mcnt;
+  int64_t mcap;
 };
 
 // Layout of one node's block (byte offsets): vertex positions, keys,
@@ -210,6 +215,7 @@ struct lm_metamesh {
   uint32_t* hole_ent;
   int64_t V, A, LE, H, HE;
   int64_t emit_nodes;  // nodes the build's emit pass computed again
+  int emit_listed;     // the emit pass took only the listed missed nodes
   int64_t n_ell, n_circ, n_degenerate;
   uint32_t flags_or;
   // triangulation state (one k at a time)
@@ -229,8 +235,9 @@ struct lm_metamesh {
   double* d_acc;
   int64_t* scan_ws;
   int64_t scan_ws_n;
-  // timing of the last build (device ms): csr, count, emit
-  float t_csr, t_count, t_emit;
+  // timing of the last build (device ms): csr, count, sizing (scans, host
+  // sync, output allocation), arena gather, emit pass
+  float t_csr, t_count, t_size, t_gather, t_emit;
   // FP64 stability-step counters: [0..7] meta-mesh build, [8..15] triangulation
   unsigned long long* d_fb;
   // launch shape of the meta-mesh kernel per valence bucket (block warps,

@@ -1069,8 +1069,15 @@ __device__ __forceinline__ void mm_bucket(const MMArgs<T>& A, const MMBuckets& B
     if (first >= n) break;
     const int64_t last = first + npt < n ? first + npt : n;
     for (int64_t t = first; t < last; t++) {
-      node_metamesh<T, C>(S, A, list[t], lane);
+      const int32_t nd = list[t];
+      node_metamesh<T, C>(S, A, nd, lane);
       __syncwarp();
+      // count pass: a node the arena could not hold joins its bucket's list
+      // for the emit pass (lane 0 wrote its arena start)
+      if (!A.emit && A.ar.mlist && lane == 0 && A.ar.start[nd] < 0) {
+        const int q = atomicAdd(A.ar.mcnt + b, 1);
+        if (q < A.ar.mcap) A.ar.mlist[(int64_t)b * A.ar.mcap + q] = nd;
+      }
     }
   }
 }

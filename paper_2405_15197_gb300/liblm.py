@@ -24,7 +24,7 @@ EXPORTS = ["lm_build_metamesh", "lm_metamesh_counts", "lm_metamesh_export", "lm_
            "lm_objective", "lm_metamesh_backward", "lm_last_error", "lm_metamesh_free",
            "lm_status_string", "lm_copy_to_host", "lm_launch_count", "lm_triangulate_noalloc",
            "lm_fp64_counts", "lm_metamesh_launch_shape", "lm_metamesh_build_times", "lm_eval_angle_fns",
-           "lm_cuda_error_string"]
+           "lm_cuda_error_string", "lm_pool_retain"]
 
 
 class LmError(RuntimeError):
@@ -98,6 +98,7 @@ def load():
         "lm_metamesh_build_times": ([V, ctypes.POINTER(ctypes.c_float)], ctypes.c_int),
         "lm_eval_angle_fns": ([V, V, V, I64, V, V, V, V], ctypes.c_int),
         "lm_cuda_error_string": ([], ctypes.c_char_p),
+        "lm_pool_retain": ([ctypes.c_uint64], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -243,6 +244,12 @@ def lm_launch_count():
     return int(load().lm_launch_count())
 
 
+def lm_pool_retain(nbytes):
+    """Let the current device's default memory pool keep up to `nbytes` of
+    the memory the library frees (0: give it back at every synchronisation)."""
+    _ck(load().lm_pool_retain(int(nbytes)), "lm_pool_retain")
+
+
 def lm_copy_to_host(dptr, nbytes, dtype):
     """Download `nbytes` from a device pointer into a new numpy array."""
     arr = np.empty(int(nbytes) // np.dtype(dtype).itemsize, dtype=dtype)
@@ -335,15 +342,17 @@ def lm_metamesh_launch_shape(h):
 
 
 def lm_metamesh_build_times(h):
-    """Device ms of the build: (CSR and tuning, count-pass kernel, sizing +
-    gather + emit pass)."""
-    out = (ctypes.c_float * 3)()
+    """Device ms of the build: (CSR and tuning, count-pass kernel, sizing and
+    output allocation, arena gather, emit pass)."""
+    out = (ctypes.c_float * 5)()
     _ck(load().lm_metamesh_build_times(h, out), "lm_metamesh_build_times")
-    return float(out[0]), float(out[1]), float(out[2])
+    return tuple(float(x) for x in out)
 
 
-def lm_metamesh_emit_nodes(h):
-    """Nodes the build computed a second time (not held by its arena)."""
+def lm_metamesh_emit_nodes(h, listed=False):
+    """Nodes the build computed a second time (not held by its arena); with
+    listed=True also whether the emit pass took only those from the count
+    pass's lists (True) or went over every node (False)."""
     out = (ctypes.c_int32 * 8)()
     _ck(load().lm_metamesh_launch_shape(h, out), "lm_metamesh_launch_shape")
-    return int(out[6])
+    return (int(out[6]), bool(out[7])) if listed else int(out[6])

@@ -283,10 +283,18 @@ def test_arena_gather_is_identical(dtype):
     lat = P.lattice_as(LATTICES["irregular"](), dtype)
     xyz, ends, radii = P.to_device(lat, dtype)
     meshes = []
-    for nbytes in (-1, 1 << 17, 0):
+    for nbytes in (-1, 1 << 17, 3 << 18, 0):
         opt = liblm.lm_options()
         opt.arena_bytes = nbytes
         meshes.append(liblm.MetaMesh(xyz, ends, radii, options=opt))
+    # the emit pass went over every node (no arena; a tiny one whose missed
+    # nodes overflow the lists) and over the listed missed nodes only
+    shapes = [liblm.lm_metamesh_emit_nodes(mm.h, listed=True) for mm in meshes]
+    n_nodes = int(xyz.shape[0])
+    assert shapes[0] == (n_nodes, False)
+    assert shapes[1][1] is False and shapes[1][0] > n_nodes // 16 + 1024
+    assert shapes[2][1] is True and 0 < shapes[2][0] < n_nodes
+    assert shapes[3] == (0, False)
     ref = meshes[0].download()
     for mm in meshes[1:]:
         got = mm.download()
