@@ -45,8 +45,9 @@ typedef enum {
   LM_ERR_TIMEOUT = 7,         /* reserved: no kernel of this library waits on
                                  another, so no call returns it */
   LM_ERR_VALENCE = 8,         /* a node with more than LM_MAX_VALENCE struts */
-  LM_ERR_STATE = 9            /* call order violated (e.g. triangulate before
+  LM_ERR_STATE = 9,           /* call order violated (e.g. triangulate before
                                  lm_tri_count for that k) */
+  LM_ERR_IO = 10              /* a file could not be opened or written */
 } lm_status;
 
 enum { LM_F32 = 0, LM_F64 = 1 };
@@ -236,6 +237,32 @@ typedef void (*lm_chunk_cb)(int64_t chunk, int64_t first_item, int64_t n_tris, v
 lm_status lm_triangulate_stream(lm_metamesh* mm, int32_t k, int64_t chunk_items, void* h_ring,
                                 int64_t slot_bytes, int32_t n_slots, lm_chunk_cb cb, void* user,
                                 void* stream, int64_t* h_total);
+
+/* The same triangles written to a binary-STL file at `path` (created or
+ * truncated) through the three-stage pipeline of Section 4.2.2: GPU
+ * triangulation of chunk c + 1, device-to-host copy of chunk c into the
+ * caller's pinned ring, and the file write of earlier chunks by a host
+ * writer thread, all overlapped (Fig. pipeline (a) and (b)).  The file is the
+ * 84-byte header of lm_stl_header followed by every record in triangle
+ * order (84 + 50 n bytes).  chunk_items <= 0 sizes the chunks by Eq.
+ * chunk-size, N_batch = S_buffer / (S_triangle N_strut), with S_buffer = 80 %
+ * of a slot and N_strut = the mean triangle count of an item; a chunk whose
+ * records exceed a slot returns LM_ERR_CAPACITY.  Synchronising; runs
+ * lm_tri_count(k) first when needed.
+ *   h_ring  : host, pinned (cudaHostAlloc), n_slots (>= 2) x slot_bytes, owned
+ *             by the caller; its contents are undefined afterwards
+ *   flags   : LM_FILE_SYNC: fsync the file before returning
+ *   h_total : host, receives the triangle count (may be NULL)
+ *   h_stats : host, may be NULL; [0] seconds of the whole call, [1] seconds
+ *             the writer spent in write calls, [2] seconds the streaming
+ *             loop waited for the writer to free a slot (disk-bound when
+ *             large), [3] seconds of the final fsync (0 without the flag)
+ * Returns LM_ERR_IO if the file cannot be opened, written or synced (what
+ * was written up to the failure stays in the file).                      */
+enum { LM_FILE_SYNC = 1 };
+lm_status lm_triangulate_to_file(lm_metamesh* mm, int32_t k, const char* path, int64_t chunk_items,
+                                 void* h_ring, int64_t slot_bytes, int32_t n_slots, int32_t flags,
+                                 void* stream, int64_t* h_total, double h_stats[4]);
 
 /* Binary-STL file header for the records of lm_triangulate (Section 5 and
  * Algorithm 1 write the triangles as STL; Table 1 reports the STL file

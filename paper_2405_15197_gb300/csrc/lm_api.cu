@@ -3,7 +3,15 @@
 // Paper: arXiv 2405.15197 (Sections 4.2.2, 4.3, 5).
 #include <cuda_runtime.h>
 
+#include <fcntl.h>
+#include <unistd.h>
+
 #include <algorithm>
+#include <cerrno>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <thread>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -783,6 +791,7 @@ const char* lm_status_string(lm_status s) {
     case LM_ERR_TIMEOUT: return "device wait timed out";
     case LM_ERR_VALENCE: return "node valence above LM_MAX_VALENCE";
     case LM_ERR_STATE: return "call order violated";
+    case LM_ERR_IO: return "file could not be opened or written";
   }
   return "unknown status";
 }
@@ -985,11 +994,107 @@ void lm_stl_header(uint8_t hdr[84], int64_t n_tris) {
   hdr[83] = (c >> 24) & 255;
 }
 
-lm_status lm_triangulate_stream(lm_metamesh* mm, int32_t k, int64_t chunk_items, void* h_ring,
-                                int64_t slot_bytes, int32_t n_slots, lm_chunk_cb cb, void* user,
-                                void* stream, int64_t* h_total) {
-  if (!mm || !valid_k(k) || chunk_items <= 0 || !h_ring || slot_bytes <= 0 || n_slots < 2)
-    return LM_ERR_INVALID_ARG;
+}  // extern "C"
+
+namespace {
+// Writer of a binary-STL file, the third stage of the pipeline of Section
+// 4.2.2 (GPU triangulation, device-to-host copy, disk): a host thread takes
+// the chunks in order, waits for each chunk's copy into its pinned slot, and
+// writes the records at their file offset; the streaming loop reuses a slot
+// only once the writer has written it.
+struct StlFileSink {
+  struct Job {
+    int64_t c;
+    cudaEvent_t ev;
+    const uint8_t* src;
+    int64_t nbytes, off;
+  };
+  int fd = -1;
+  std::mutex mu;
+  std::condition_variable cv;
+  std::deque<Job> q;
+  int64_t written = 0;  // chunks written (in order)
+  bool closed = false;
+  int err = 0;  // errno of the first failed write
+  double busy_s = 0.0, wait_s = 0.0;
+  int64_t bytes = 0;
+  std::thread th;
+
+  static double now() {
+    return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+  }
+  // write all of [p, p + n) at offset off; errno on failure, else 0
+  static int write_all(int fd, const uint8_t* p, int64_t n, int64_t off) {
+    while (n > 0) {
+      const ssize_t r = pwrite(fd, p, (size_t)std::min<int64_t>(n, (int64_t)1 << 30), (off_t)off);
+      if (r < 0) {
+        if (errno == EINTR) continue;
+        return errno;
+      }
+      if (r == 0) return EIO;
+      p += r;
+      n -= r;
+      off += r;
+    }
+    return 0;
+  }
+  void run() {
+    while (true) {
+      Job j;
+      {
+        std::unique_lock<std::mutex> lk(mu);
+        cv.wait(lk, [&] { return !q.empty() || closed; });
+        if (q.empty()) break;
+        j = q.front();
+        q.pop_front();
+      }
+      cudaEventSynchronize(j.ev);
+      cudaEventDestroy(j.ev);
+      int e = 0;
+      double t0 = now();
+      if (err == 0 && j.nbytes > 0) e = write_all(fd, j.src, j.nbytes, j.off);
+      double dt = now() - t0;
+      {
+        std::lock_guard<std::mutex> lk(mu);
+        busy_s += dt;
+        if (e == 0 && err == 0) bytes += j.nbytes;
+        if (e != 0 && err == 0) err = e;
+        written = j.c + 1;
+      }
+      cv.notify_all();
+    }
+  }
+  void start() { th = std::thread([this] { run(); }); }
+  void push(const Job& j) {
+    {
+      std::lock_guard<std::mutex> lk(mu);
+      q.push_back(j);
+    }
+    cv.notify_all();
+  }
+  // main thread: block until `n` chunks are written; false on a write error
+  bool wait_written(int64_t n) {
+    double t0 = now();
+    std::unique_lock<std::mutex> lk(mu);
+    cv.wait(lk, [&] { return written >= n || err != 0; });
+    wait_s += now() - t0;
+    return err == 0;
+  }
+  void close_and_join() {
+    {
+      std::lock_guard<std::mutex> lk(mu);
+      closed = true;
+    }
+    cv.notify_all();
+    if (th.joinable()) th.join();
+  }
+};
+
+// Chunked triangulation into a pinned host ring (lm_triangulate_stream), the
+// chunks handed to the callback or, with `fs`, to a file writer.
+lm_status stream_impl(lm_metamesh* mm, int32_t k, int64_t chunk_items, void* h_ring, int64_t slot_bytes,
+                      int32_t n_slots, lm_chunk_cb cb, void* user, void* stream, int64_t* h_total,
+                      StlFileSink* fs) {
   cudaStream_t st = (cudaStream_t)stream;
   lm_status s = LM_OK;
   if (mm->tri_k != k) {
@@ -1042,8 +1147,14 @@ lm_status lm_triangulate_stream(lm_metamesh* mm, int32_t k, int64_t chunk_items,
     count_launch((int)kpl);
     cudaEventRecord(done_comp[q], st);
     // the host slot of chunk c was last used by chunk c - n_slots: wait for
-    // its copy and hand it to the caller first
-    if (c >= n_slots) {
+    // its copy and hand it to the caller first (or, writing a file, wait
+    // until the writer has written it)
+    if (c >= n_slots && fs) {
+      if (!fs->wait_written(c - n_slots + 1)) {
+        s = LM_ERR_IO;
+        break;
+      }
+    } else if (c >= n_slots) {
       cudaEventSynchronize(copied[c - n_slots]);
       cudaEventDestroy(copied[c - n_slots]);
       copied[c - n_slots] = nullptr;
@@ -1060,8 +1171,18 @@ lm_status lm_triangulate_stream(lm_metamesh* mm, int32_t k, int64_t chunk_items,
     cudaEventRecord(done_copy[q], cs);
     cudaEventCreateWithFlags(&copied[c], cudaEventDisableTiming);
     cudaEventRecord(copied[c], cs);
+    if (fs) {
+      // the writer owns the event from here
+      fs->push(StlFileSink::Job{c, copied[c], (const uint8_t*)h_ring + (c % n_slots) * slot_bytes, nb,
+                                84 + 50 * bnd[c]});
+      copied[c] = nullptr;
+    }
   }
-  for (int64_t c = std::max<int64_t>(0, n_chunks - n_slots); c < n_chunks; c++) {
+  if (fs) {
+    fs->close_and_join();
+    if (s == LM_OK && fs->err != 0) s = LM_ERR_IO;
+  }
+  for (int64_t c = std::max<int64_t>(0, n_chunks - n_slots); c < n_chunks && !fs; c++) {
     if (!copied[c]) continue;
     cudaEventSynchronize(copied[c]);
     cudaEventDestroy(copied[c]);
@@ -1080,6 +1201,83 @@ lm_status lm_triangulate_stream(lm_metamesh* mm, int32_t k, int64_t chunk_items,
   cudaStreamDestroy(cs);
   if (h_total) *h_total = bnd[n_chunks];
   if (s == LM_OK) s = lm_last_error(mm, stream);
+  return s;
+}
+}  // namespace
+
+extern "C" {
+
+lm_status lm_triangulate_stream(lm_metamesh* mm, int32_t k, int64_t chunk_items, void* h_ring,
+                                int64_t slot_bytes, int32_t n_slots, lm_chunk_cb cb, void* user,
+                                void* stream, int64_t* h_total) {
+  if (!mm || !valid_k(k) || chunk_items <= 0 || !h_ring || slot_bytes <= 0 || n_slots < 2)
+    return LM_ERR_INVALID_ARG;
+  return stream_impl(mm, k, chunk_items, h_ring, slot_bytes, n_slots, cb, user, stream, h_total, nullptr);
+}
+
+lm_status lm_triangulate_to_file(lm_metamesh* mm, int32_t k, const char* path, int64_t chunk_items,
+                                 void* h_ring, int64_t slot_bytes, int32_t n_slots, int32_t flags,
+                                 void* stream, int64_t* h_total, double h_stats[4]) {
+  if (!mm || !valid_k(k) || !path || !h_ring || slot_bytes < 50 || n_slots < 2) return LM_ERR_INVALID_ARG;
+  lm_status s = LM_OK;
+  if (mm->tri_k != k) {
+    s = lm_tri_count(mm, k, stream, nullptr);
+    if (s != LM_OK) return s;
+  }
+  const int64_t n_items = mm->E + mm->N;
+  cudaStream_t st = (cudaStream_t)stream;
+  int64_t total = 0, strut_tris = 0;
+  LM_CK(cudaMemcpyAsync(&total, mm->tri_off + n_items, 8, cudaMemcpyDeviceToHost, st));
+  LM_CK(cudaMemcpyAsync(&strut_tris, mm->tri_off + mm->E, 8, cudaMemcpyDeviceToHost, st));
+  LM_CK(cudaStreamSynchronize(st));
+  if (chunk_items <= 0) {
+    // Eq. chunk-size: N_batch = S_buffer / (S_triangle N_strut), with the
+    // mean triangle count of a strut for N_strut and 80 % of a slot for
+    // S_buffer; halved while some chunk's records would not fit a slot
+    const double per_strut = std::max(1.0, (double)strut_tris / (double)std::max<int64_t>(mm->E, 1));
+    chunk_items = std::max<int64_t>(1, (int64_t)(0.8 * (double)slot_bytes / (50.0 * per_strut)));
+    while (chunk_items > 1) {
+      const int64_t nc = (n_items + chunk_items - 1) / chunk_items;
+      std::vector<int64_t> b(nc + 1);
+      for (int64_t c = 0; c <= nc; c++)
+        LM_CK(cudaMemcpyAsync(&b[c], mm->tri_off + std::min(c * chunk_items, n_items), 8, cudaMemcpyDeviceToHost, st));
+      LM_CK(cudaStreamSynchronize(st));
+      int64_t mx = 0;
+      for (int64_t c = 0; c < nc; c++) mx = std::max(mx, b[c + 1] - b[c]);
+      if (50 * mx <= slot_bytes) break;
+      chunk_items /= 2;
+    }
+  }
+  const int fd = open(path, O_WRONLY | O_CREAT | O_TRUNC, 0644);
+  if (fd < 0) return LM_ERR_IO;
+  uint8_t hdr[84];
+  lm_stl_header(hdr, total);
+  StlFileSink fs;
+  fs.fd = fd;
+  const double t0 = StlFileSink::now();
+  if (StlFileSink::write_all(fd, hdr, 84, 0) != 0) {
+    close(fd);
+    return LM_ERR_IO;
+  }
+  fs.bytes = 84;
+  fs.start();
+  int64_t got = 0;
+  s = stream_impl(mm, k, chunk_items, h_ring, slot_bytes, n_slots, nullptr, nullptr, stream, &got, &fs);
+  fs.close_and_join();
+  double sync_s = 0.0;
+  if (s == LM_OK && (flags & LM_FILE_SYNC)) {
+    const double ts = StlFileSink::now();
+    if (fsync(fd) != 0) s = LM_ERR_IO;
+    sync_s = StlFileSink::now() - ts;
+  }
+  if (close(fd) != 0 && s == LM_OK) s = LM_ERR_IO;
+  if (h_total) *h_total = got;
+  if (h_stats) {
+    h_stats[0] = StlFileSink::now() - t0;
+    h_stats[1] = fs.busy_s;
+    h_stats[2] = fs.wait_s;
+    h_stats[3] = sync_s;
+  }
   return s;
 }
 

@@ -18,13 +18,13 @@ LIB_PATH = os.path.join(_HERE, "_liblm.so")
 LM_F32, LM_F64 = 0, 1
 STATUS = {0: "LM_OK", 1: "LM_ERR_INVALID_ARG", 2: "LM_ERR_RADIUS_MISMATCH", 3: "LM_ERR_DEGENERATE",
           4: "LM_ERR_CAPACITY", 5: "LM_ERR_OOM", 6: "LM_ERR_CUDA", 7: "LM_ERR_TIMEOUT",
-          8: "LM_ERR_VALENCE", 9: "LM_ERR_STATE"}
+          8: "LM_ERR_VALENCE", 9: "LM_ERR_STATE", 10: "LM_ERR_IO"}
 EXPORTS = ["lm_build_metamesh", "lm_metamesh_counts", "lm_metamesh_export", "lm_tri_count",
            "lm_tri_range", "lm_triangulate", "lm_triangulate_stream", "lm_stl_header",
            "lm_objective", "lm_metamesh_backward", "lm_last_error", "lm_metamesh_free",
            "lm_status_string", "lm_copy_to_host", "lm_launch_count", "lm_triangulate_noalloc",
            "lm_fp64_counts", "lm_metamesh_launch_shape", "lm_metamesh_build_times", "lm_eval_angle_fns",
-           "lm_cuda_error_string", "lm_pool_retain"]
+           "lm_cuda_error_string", "lm_pool_retain", "lm_triangulate_to_file"]
 
 
 class LmError(RuntimeError):
@@ -99,6 +99,9 @@ def load():
         "lm_eval_angle_fns": ([V, V, V, I64, V, V, V, V], ctypes.c_int),
         "lm_cuda_error_string": ([], ctypes.c_char_p),
         "lm_pool_retain": ([ctypes.c_uint64], ctypes.c_int),
+        "lm_triangulate_to_file": ([V, ctypes.c_int32, ctypes.c_char_p, ctypes.c_int64, V, ctypes.c_int64,
+                                    ctypes.c_int32, ctypes.c_int32, V, ctypes.POINTER(ctypes.c_int64),
+                                    ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -175,6 +178,21 @@ def lm_triangulate_stream(h, k, chunk_items, ring_ptr, slot_bytes, n_slots, call
                                      int(slot_bytes), int(n_slots), cb, None, _stream_ptr(stream),
                                      ctypes.byref(tot)), "lm_triangulate_stream")
     return tot.value
+
+
+LM_FILE_SYNC = 1
+
+
+def lm_triangulate_to_file(h, k, path, ring_ptr, slot_bytes, n_slots, chunk_items=0, sync=False, stream=None):
+    """Binary-STL file of the triangulation at k through the pinned ring
+    (GPU triangulation, device-to-host copy and file writes overlapped).
+    Returns (triangles, {"total_s", "write_s", "wait_s", "fsync_s"})."""
+    tot = ctypes.c_int64()
+    st = (ctypes.c_double * 4)()
+    _ck(load().lm_triangulate_to_file(h, int(k), os.fsencode(path), int(chunk_items), ctypes.c_void_p(int(ring_ptr)),
+                                      int(slot_bytes), int(n_slots), LM_FILE_SYNC if sync else 0,
+                                      _stream_ptr(stream), ctypes.byref(tot), st), "lm_triangulate_to_file")
+    return tot.value, {"total_s": st[0], "write_s": st[1], "wait_s": st[2], "fsync_s": st[3]}
 
 
 def lm_triangulate_noalloc(h, k, item_begin, item_end, out_ptr, capacity_tris, stream=None):
