@@ -31,6 +31,10 @@
 //     angle and mapped onto the arc; the two loops of a strut are stitched;
 //     hole contours are fanned to the barycentre projected on the nodal
 //     sphere (Section 5, hole-filling equation).
+//   * Annular holes: the hole filling assumes disc-shaped holes; where two
+//     contours bound one exposed component of a nodal sphere (two narrowing
+//     cones with disjoint caps) the band between them is stitched like a
+//     strut's lateral band instead (band_tris).
 //
 // Readings of points where the paper is silent or garbled (all listed in the
 // design notes of the repository):
@@ -660,6 +664,10 @@ struct Frozen {
   std::vector<std::vector<int>> N;        // [node][arc] segment count
   std::vector<std::vector<uint8_t>> zip;  // [strut] stitching steps, 1 = A advances
   std::vector<std::vector<uint8_t>> fan;  // [node][hole] centre rule (see hole_tris)
+  // [node] stitching steps of an annular band (see band_tris), 1 = q0
+  // advances; empty: the node's holes are fanned
+  std::vector<std::vector<uint8_t>> band;
+  std::vector<uint8_t> is_band;  // [node] the two contours were stitched as a band
 };
 
 // a, b, c relative to o (an exact node centre) give the STL normal, the area
@@ -744,6 +752,94 @@ void strut_tris(const Mesh& M, int64_t e, int k, std::vector<Tri>& T, Frozen* fz
   }
 }
 
+// Annular exposed component (reading 10): the band between its two contours
+// q0 and q1 (node-relative points in hole order, each contour with the
+// component on its left seen from outside), stitched like a strut's lateral
+// band (reading 8).  Both contours are taken in the angle around the axis a
+// from q0's barycentre to q1's (frame as the strut frames: e1 = a x E_ax
+// with ax the axis of smallest |a_ax|, e2 = a x e1), q0 forward and q1
+// backward, so that both turn once positively; q0 starts at its first point,
+// q1's keys are moved into the window [th0 - ETA_ZIP, th0 + 2pi - ETA_ZIP)
+// and q1 starts at its smallest key (ties within ETA_PHI: the first); an
+// event of q0 comes first unless it exceeds q1's by more than ETA_ZIP.
+// Returns false (the holes are then fanned) when the barycentres are within
+// ETA_BARY R of each other or a contour does not turn once around a.
+// rec / rep: record / replay the stitching steps (frozen structure).
+bool band_tris(const NodeGeo& g, const std::vector<V3>& q0, const std::vector<V3>& q1, std::vector<Tri>& T,
+               std::vector<uint8_t>* rec, const std::vector<uint8_t>* rep) {
+  const int M0 = (int)q0.size(), M1 = (int)q1.size();
+  if (M0 < 1 || M1 < 1) return false;
+  V3 b0 = mk(0, 0, 0), b1 = mk(0, 0, 0);
+  for (const V3& p : q0) b0 = add(b0, p);
+  for (const V3& p : q1) b1 = add(b1, p);
+  V3 a = sub(mul(b1, 1.0 / M1), mul(b0, 1.0 / M0));
+  const double al = norm(a);
+  if (!rep && al <= ETA_BARY * g.R) return false;
+  a = mul(a, 1.0 / al);
+  double aa[3] = {std::fabs(a.x), std::fabs(a.y), std::fabs(a.z)};
+  int ax = 0;
+  if (aa[1] < aa[ax]) ax = 1;
+  if (aa[2] < aa[ax]) ax = 2;
+  V3 c1 = cross(a, mk(ax == 0, ax == 1, ax == 2));
+  const V3 e1 = mul(c1, 1.0 / norm(c1)), e2 = cross(a, e1);
+  auto ang = [&](V3 p) { return std::atan2(dot(p, e2), dot(p, e1)); };
+  // q1 backward from its first point
+  auto qb = [&](int j) { return q1[((M1 - j) % M1 + M1) % M1]; };
+  // each contour turns once positively around a
+  auto turn = [&](int M, auto pt) {
+    double t = 0.0;
+    for (int i = 0; i < M; i++) {
+      double r = ang(pt((i + 1) % M)) - ang(pt(i));
+      while (r <= -0.5 * PI2) r += PI2;
+      while (r > 0.5 * PI2) r -= PI2;
+      t += r;
+    }
+    return t;
+  };
+  if (!rep && (std::fabs(turn(M0, [&](int i) { return q0[i]; }) - PI2) > 1e-6 ||
+               std::fabs(turn(M1, qb) - PI2) > 1e-6))
+    return false;
+  const double th0 = ang(q0[0]);
+  std::vector<double> kA(M0), kB(M1);
+  for (int i = 0; i < M0; i++) {
+    double r = ang(q0[i]) - th0;
+    while (r < -ETA_PHI) r += PI2;
+    while (r >= PI2 - ETA_PHI) r -= PI2;
+    kA[i] = th0 + r;
+  }
+  double kmin = INFINITY;
+  for (int j = 0; j < M1; j++) {
+    double x = ang(qb(j));
+    while (x < th0 - ETA_ZIP) x += PI2;
+    while (x >= th0 + PI2 - ETA_ZIP) x -= PI2;
+    kB[j] = x;
+    kmin = std::min(kmin, x);
+  }
+  int sB = 0;
+  while (kB[sB] > kmin + ETA_PHI) sB++;
+  auto thA = [&](int i) { return i < M0 ? kA[i] : th0 + PI2; };
+  auto thB = [&](int j) { return kB[(sB + j) % M1]; };
+  auto pA = [&](int i) { return q0[i % M0]; };
+  auto pB = [&](int j) { return qb((sB + j + M1) % M1); };
+  int ia = 0, ib = -1;
+  size_t step = 0;
+  if (rec) rec->clear();
+  while (ia < M0 || ib < M1 - 1) {
+    bool takeA = (ib == M1 - 1) || (ia < M0 && thA(ia + 1) <= thB(ib + 1) + ETA_ZIP);
+    if (rep) takeA = step < rep->size() ? (*rep)[step] != 0 : (ia < M0);
+    if (rec) rec->push_back(takeA ? 1 : 0);
+    step++;
+    if (takeA) {
+      emit(T, g.c, pA(ia), pA(ia + 1), pB(ib), add(g.c, pA(ia)), add(g.c, pA(ia + 1)), add(g.c, pB(ib)));
+      ia++;
+    } else {
+      emit(T, g.c, pA(ia), pB(ib + 1), pB(ib), add(g.c, pA(ia)), add(g.c, pB(ib + 1)), add(g.c, pB(ib)));
+      ib++;
+    }
+  }
+  return true;
+}
+
 // hole fans of node n (Section 5 hole filling)
 // fz: record (replay = false) or replay (replay = true) the centre rule of
 // every hole and the segment counts; NULL: plain evaluation
@@ -753,14 +849,33 @@ void hole_tris(const Mesh& M, int64_t n, int k, std::vector<Tri>& T, Frozen* fz 
   if (no.holes.empty()) return;
   NodeGeo g = node_geo(M, n);
   if (fz && !replay) fz->fan[n].assign(no.holes.size(), 0);
-  for (size_t hh = 0; hh < no.holes.size(); hh++) {
-    const auto& hole = no.holes[hh];
+  // contour points of hole hh (node-relative, hole order)
+  auto contour = [&](size_t hh) {
     std::vector<V3> q;
-    for (const Entry& en : hole) {
+    for (const Entry& en : no.holes[hh]) {
       const Arc& a = no.A[en.arc];
       int N = replay ? fz->N[n][en.arc] : seg_count(a.dphi, k);
       for (int s = 0; s < N; s++) q.push_back(arc_point(g, no, a, en.rev ? N - s : s, N));
     }
+    return q;
+  };
+  // reading 10: two contours that bound one exposed component of the nodal
+  // sphere (the node's partition of its sphere into d loops and the exposed
+  // components gives V - A + d + 2F - H = 2, so F = 1 when
+  // A - V - d + 4 = 2 with H = 2) are stitched as a band
+  if (fz && !replay) fz->is_band[n] = 0;
+  if (no.holes.size() == 2 && (int64_t)no.A.size() - (int64_t)no.V.size() - (int64_t)g.E.size() + 4 == 2) {
+    const bool rep_band = replay && fz->is_band[n];
+    if (!replay || rep_band) {
+      std::vector<uint8_t>* rec = fz && !replay ? &fz->band[n] : nullptr;
+      if (band_tris(g, contour(0), contour(1), T, rec, rep_band ? &fz->band[n] : nullptr)) {
+        if (fz && !replay) fz->is_band[n] = 1;
+        return;
+      }
+    }
+  }
+  for (size_t hh = 0; hh < no.holes.size(); hh++) {
+    std::vector<V3> q = contour(hh);
     int Mq = (int)q.size();
     V3 b = mk(0, 0, 0);
     for (auto& p : q) b = add(b, p);
@@ -1158,6 +1273,8 @@ void* lmo_frozen_record(void* h, int k) {
   fz->N.resize(N);
   fz->zip.resize(E);
   fz->fan.resize(N);
+  fz->band.resize(N);
+  fz->is_band.assign(N, 0);
   for (int64_t n = 0; n < N; n++)
     for (const Arc& a : M->nodes[n].A) fz->N[n].push_back(seg_count(a.dphi, k));
   std::vector<Tri> T;

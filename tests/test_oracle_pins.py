@@ -125,6 +125,105 @@ def test_euler_and_watertight(name):
         assert vol > 0 and area > 0
 
 
+# ------------------------------------- annular holes (reading 10): a band
+def _annular_stars():
+    c150 = (math.cos(math.radians(150)), math.sin(math.radians(150)), 0.0)
+    return {
+        # two antipodal narrowing cones: the exposed sphere between their
+        # tangency circles is one band with two contours
+        "antipodal": (L.star([(1, 0, 0), (-1, 0, 0)], radius=0.2, far_radii=[0.1, 0.1]), 0.4),
+        # 150 degrees apart, cap half-angles 72.5 degrees: disjoint caps
+        "tilted150": (L.star([(1, 0, 0), c150], radius=0.2, far_radii=[0.05, 0.05], length=0.5), 0.22),
+        "asym": (L.star([(1, 0.05, 0.02), (-1, 0.03, -0.04)], radius=0.2, far_radii=[0.08, 0.12]), 0.4),
+    }
+
+
+@pytest.mark.parametrize("name", ["antipodal", "tilted150", "asym"])
+def test_annular_band_closed_manifold(name):
+    """A centre node whose two strut caps are disjoint: its exposed sphere is
+    one component bounded by two contours (V - A + d + 2F - H = 2 with V = A
+    = H = d = 2 gives F = 1), stitched as one band, so the mesh is a single
+    closed, consistently oriented 2-manifold with chi = 2 (N - E) and a
+    positive volume, the band having as many triangles as the two contours
+    have points."""
+    lat, _ = _annular_stars()[name]
+    o = oracle.Oracle(lat)
+    s = o.node_sizes()
+    assert (s[:, 0] == 0).all()
+    assert s[0, 1:].tolist() == [2, 2, 2, 2, 2]
+    V, A, H, d = s[0, 1], s[0, 2], s[0, 4], 2
+    assert (2 - V + A - d + H) // 2 == 1
+    for k in (8, 16, 32):
+        tris, area, vol = o.triangulate(k)
+        ids, nv = mc.weld(tris[:, 1:])
+        chi, rep = mc.euler(ids, nv)
+        assert rep["mult"] == {2: rep["edges"]}
+        assert rep["dup_directed"] == 0 and rep["degenerate"] == 0
+        assert chi == 2 * (o.N - o.E)
+        assert vol > 0 and area > 0
+        cnt = o.tri_counts(k)
+        assert cnt[o.E] == 2 * k
+
+
+@pytest.mark.parametrize("k", [8, 16, 48])
+def test_annular_band_area_closed_form(k):
+    """Two antipodal cones with one half-angle (sin a = (R - r)/L): the two
+    tangency circles are coaxial, radius R cos a at heights +-R sin a, and
+    their k points lie at the same angles (both strut frames are built from
+    the same axis), so the band is k rectangles of 2 R cos a sin(pi/k) by
+    2 R sin a: area 4 k R^2 cos a sin a sin(pi/k), and every band vertex lies
+    on one of the circles."""
+    lat, _ = _annular_stars()["antipodal"]
+    R, r, Ls = 0.2, 0.1, 1.0
+    sa = (R - r) / Ls
+    ca = math.sqrt(1 - sa * sa)
+    o = oracle.Oracle(lat)
+    tris, _, _ = o.triangulate(k)
+    cnt = o.tri_counts(k)
+    off = int(cnt[:o.E].sum())
+    band = tris[off:off + int(cnt[o.E])]
+    assert len(band) == 2 * k
+    pts = band[:, 1:].reshape(-1, 3)
+    assert np.allclose(np.abs(pts[:, 0]), R * sa, rtol=0, atol=1e-14)
+    assert np.allclose(np.hypot(pts[:, 1], pts[:, 2]), R * ca, rtol=0, atol=1e-14)
+    e1, e2 = band[:, 2] - band[:, 1], band[:, 3] - band[:, 1]
+    area = 0.5 * np.linalg.norm(np.cross(e1, e2), axis=1).sum()
+    assert area == pytest.approx(4 * k * R * R * ca * sa * math.sin(math.pi / k), rel=1e-12)
+    # outward: every band normal points away from the axis
+    mid = band[:, 1:].mean(1)
+    nrm = np.cross(e1, e2)
+    assert np.all(nrm[:, 1] * mid[:, 1] + nrm[:, 2] * mid[:, 2] > 0)
+
+
+@pytest.mark.parametrize("name", ["antipodal", "tilted150", "asym"])
+def test_annular_point_in_union_vs_winding(name):
+    """Monte-Carlo points around the centre node (away from the far nodes'
+    hole caps): inside the exact solid iff the mesh winds around them once,
+    for points farther from the surface than the band's and the struts'
+    sagittas.  Fanning each contour on its own would close each strut and
+    leave the band of sphere between them outside the mesh."""
+    lat, box = _annular_stars()[name]
+    o = oracle.Oracle(lat)
+    k = 48
+    tris, _, _ = o.triangulate(k)
+    rng = np.random.default_rng(3)
+    pts = rng.uniform(-box, box, size=(4000, 3))
+    ins = mc.inside_union(lat, pts)
+    marg = mc.union_margin(lat, pts)
+    assert np.all((marg > 0) == ins)
+    # the band's chords sit at most R (1 - cos(g / 2)) inside the sphere,
+    # g the widest angular gap between the two circles
+    R = 0.2
+    safe = np.abs(marg) > 0.2 * R + 4 * R * (1 - math.cos(math.pi / k))
+    w = mc.winding(tris[:, 1:], pts[safe])
+    assert safe.sum() > 1000 and ins[safe].sum() > 100
+    assert np.all(np.abs(w - ins[safe]) < 1e-6)
+    # points of the band region itself (inside the sphere, outside both
+    # cones' caps, near the sphere) are inside the mesh
+    band_pts = pts[safe & ins & (np.linalg.norm(pts, axis=1) < R) & (np.linalg.norm(pts, axis=1) > 0.5 * R)]
+    assert len(band_pts) > 10
+
+
 # --------------------------------------------- P2: isolated straight strut
 @pytest.mark.parametrize("k", [6, 8, 16, 32, 64, 256])
 def test_isolated_cylinder(k):
@@ -459,6 +558,24 @@ def test_frozen_gradient_straight_strut(k):
         assert np.allclose(gv[q, :3], sgn * dV_dL * u, rtol=1e-7, atol=1e-8)
         assert ga[q, 3] == pytest.approx(dA_dr / 2, rel=1e-7)
         assert gv[q, 3] == pytest.approx(dV_dr / 2, rel=1e-7)
+
+
+@pytest.mark.parametrize("name", ["tilted150", "asym"])
+def test_frozen_band_objective_and_gradient(name):
+    """The frozen structure replays an annular band (reading 10) too: it
+    reproduces the triangulation's area and volume, and its central
+    differences agree at h and h/2 to O(h^2)."""
+    lat, _ = _annular_stars()[name]
+    o = oracle.Oracle(lat)
+    for k in (8, 24):
+        _, a, v = o.triangulate(k, want_tris=False)
+        fz = oracle.Frozen(o, k)
+        a2, v2 = fz.objective(o.xyz, _node_R(o))
+        assert a2 == pytest.approx(a, rel=1e-13) and v2 == pytest.approx(v, rel=1e-13)
+        ga1, gv1 = fz.fd(1e-4, np.arange(o.N))
+        ga2, gv2 = fz.fd(5e-5, np.arange(o.N))
+        assert np.abs(ga1 - ga2).max() < 1e-6 * np.abs(ga1).max()
+        assert np.abs(gv1 - gv2).max() < 1e-6 * np.abs(gv1).max()
 
 
 def test_frozen_gradient_smooth_and_local():
