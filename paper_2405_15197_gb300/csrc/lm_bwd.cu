@@ -67,16 +67,171 @@ __global__ void __launch_bounds__(256) k_bwd_arc_counts(TriArgs<T> A, int32_t* a
   if ((threadIdx.x & 31) == 0 && mv > 0) atomicMax(max_v, mv);
 }
 
+// contour points of hole h (node-relative) and their point ids into
+// Q[0, cap), PQ[0, cap); returns the contour's point count
+template <typename T>
+__device__ int bwd_contour(const TriArgs<T>& A, const int32_t* arc_N, int64_t nd, int64_t h, int64_t ao,
+                           int64_t rb, T R, V3<T>* Q, int64_t* PQ, int cap, int lane) {
+  const LatDev<T>& L = A.lat;
+  int M = 0;
+  for (int64_t q = A.hole_off[h]; q < A.hole_off[h + 1]; q++) {
+    uint32_t ent = A.hole_ent[q];
+    int64_t ga = ao + (ent & 0x7fffffffu);
+    int rev = ent >> 31;
+    int Nq = arc_N[ga];
+    EntryS<T> en;
+    en.g = arc_geo<T>(make_end<T, T>(L, nd, L.adj[rb + ((A.arc_vtx[ga] >> 16) & 255)]), nullptr, R);
+    en.phi0 = A.arc_phi[2 * ga];
+    en.dphi = A.arc_phi[2 * ga + 1];
+    en.psi = T(0);
+    en.N = Nq;
+    en.pre = M;
+    en.ga = ga;
+    en.rev = (uint8_t)rev;
+    en.own = 1;
+    uint32_t av = A.arc_vtx[ga];
+    for (int s = lane; s < Nq; s += 32) {
+      if (M + s >= cap) continue;
+      V3<T> z;
+      T th;
+      entry_point<T>(A, nd, en, nullptr, s, z, th);
+      int m = rev ? Nq - s : s;
+      Q[M + s] = z;
+      PQ[M + s] = (m == 0 || m == Nq) ? A.vtx_off[nd] + (m == 0 ? (av & 255) : ((av >> 8) & 255))
+                                      : A.n_vtx + A.arc_pt_off[ga] + m - 1;
+    }
+    M += Nq;
+  }
+  return M;
+}
+
+// Point adjoints of an annular band (the forward pass's band_node, reading
+// 10): the same stitching, with its decisions taken from FP64 angles of the
+// contour points in the lattice's precision.  Returns false when the band
+// does not apply (the holes are fanned).
+template <typename T>
+__device__ __noinline__ bool bwd_band(const TriArgs<T>& A, const int32_t* arc_N, int64_t nd, int64_t h0,
+                                      int64_t ao, int64_t rb, T R, V3<T>* Q, int64_t* PQ, double* K,
+                                      int32_t* DEC, int lane) {
+  const int M0 = bwd_contour<T>(A, arc_N, nd, h0, ao, rb, R, Q, PQ, A.pmax, lane);
+  const int off = M0 < A.pmax ? M0 : A.pmax;
+  const int M1 = bwd_contour<T>(A, arc_N, nd, h0 + 1, ao, rb, R, Q + off, PQ + off, A.pmax - off, lane);
+  if (M0 < 1 || M1 < 1 || M0 + M1 > A.pmax) return false;
+  __syncwarp();
+  V3<double> bs[2] = {mk3(0.0, 0.0, 0.0), mk3(0.0, 0.0, 0.0)};
+  for (int p = lane; p < M0 + M1; p += 32) {
+    const V3<T> z = Q[p];
+    bs[p < M0 ? 0 : 1] = bs[p < M0 ? 0 : 1] + mk3((double)z.x, (double)z.y, (double)z.z);
+  }
+  for (int cc = 0; cc < 2; cc++)
+    for (int o = 16; o > 0; o >>= 1) {
+      bs[cc].x += __shfl_xor_sync(0xffffffffu, bs[cc].x, o);
+      bs[cc].y += __shfl_xor_sync(0xffffffffu, bs[cc].y, o);
+      bs[cc].z += __shfl_xor_sync(0xffffffffu, bs[cc].z, o);
+    }
+  const V3<double> a = bs[1] * (1.0 / (double)M1) - bs[0] * (1.0 / (double)M0);
+  const double al = norm3(a);
+  if (!(al > ETA_BARY * (double)R)) return false;
+  const V3<double> ua = a * (1.0 / al);
+  const double aa[3] = {fabs(ua.x), fabs(ua.y), fabs(ua.z)};
+  int ax = 0;
+  if (aa[1] < aa[ax]) ax = 1;
+  if (aa[2] < aa[ax]) ax = 2;
+  const V3<double> c1 = cross(ua, mk3<double>(ax == 0, ax == 1, ax == 2));
+  const V3<double> e1 = c1 * (1.0 / norm3(c1)), e2 = cross(ua, e1);
+  for (int p = lane; p < M0 + M1; p += 32) {
+    const V3<double> z = mk3((double)Q[p].x, (double)Q[p].y, (double)Q[p].z);
+    K[p] = atan2(dot(z, e2), dot(z, e1));
+  }
+  __syncwarp();
+  double t0 = 0.0, t1 = 0.0;
+  const double HP = 0.5 * PI2;
+  for (int i = lane; i < M0; i += 32) {
+    double r = K[i + 1 < M0 ? i + 1 : 0] - K[i];
+    while (r <= -HP) r += PI2;
+    while (r > HP) r -= PI2;
+    t0 += r;
+  }
+  for (int j = lane; j < M1; j += 32) {
+    double r = K[M0 + (j + 1 < M1 ? j + 1 : 0)] - K[M0 + j];
+    while (r <= -HP) r += PI2;
+    while (r > HP) r -= PI2;
+    t1 += r;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    t0 += __shfl_xor_sync(0xffffffffu, t0, o);
+    t1 += __shfl_xor_sync(0xffffffffu, t1, o);
+  }
+  if (fabs(t0 - PI2) > 1e-6 || fabs(t1 + PI2) > 1e-6) return false;
+  const double th0 = K[0];
+  __syncwarp();
+  for (int i = lane; i < M0; i += 32) {
+    double r = K[i] - th0;
+    while (r < -ETA_PHI) r += PI2;
+    while (r >= PI2 - ETA_PHI) r -= PI2;
+    K[i] = th0 + r;
+  }
+  double kmin = 1e300;
+  for (int x = lane; x < M1; x += 32) {
+    double v = K[M0 + x];
+    while (v < th0 - ETA_ZIP) v += PI2;
+    while (v >= th0 + PI2 - ETA_ZIP) v -= PI2;
+    K[M0 + x] = v;
+    kmin = fmin(kmin, v);
+  }
+  for (int o = 16; o > 0; o >>= 1) kmin = fmin(kmin, __shfl_xor_sync(0xffffffffu, kmin, o));
+  __syncwarp();
+  int sB = 0x7fffffff;
+  for (int x = lane; x < M1; x += 32)
+    if (K[M0 + x] <= kmin + ETA_PHI) sB = min(sB, (M1 - x) % M1);
+  for (int o = 16; o > 0; o >>= 1) sB = min(sB, __shfl_xor_sync(0xffffffffu, sB, o));
+  auto bpos = [&](int j) { return M0 + (M1 - ((sB + j + M1) % M1)) % M1; };
+  const int ntri = M0 + M1;
+  if (lane == 0) {
+    int ia = 0, ib = -1;
+    for (int p = 0; p < ntri; p++) {
+      const bool takeA = (ib == M1 - 1) || (ia < M0 && (ia + 1 < M0 ? K[ia + 1] : th0 + PI2) <= K[bpos(ib + 1)] + ETA_ZIP);
+      DEC[p] = (ia << 1) | (takeA ? 1 : 0);
+      if (takeA) ia++;
+      else ib++;
+    }
+  }
+  __syncwarp();
+  for (int p = lane; p < ntri; p += 32) {
+    const int v = DEC[p], ia = v >> 1, ib = p - ia - 1;
+    const int qa = ia % M0, qb = (v & 1) ? (ia + 1) % M0 : bpos(ib + 1), qc = bpos(ib);
+    const V3<T> ra = Q[qa], rb2 = Q[qb], rc = Q[qc];
+    V3<T> cr = cross(rb2 - ra, rc - ra);
+    T len = norm3(cr);
+    V3<T> nh = len > T(0) ? cr * (T(1) / len) : mk3(T(0), T(0), T(0));
+    tri_point_adjoints<T>(A, ra, rb2, rc, nh, cr, PQ[qa], PQ[qb], PQ[qc]);
+  }
+  __syncwarp();
+  return true;
+}
+
+// Per-warp workspace of k_bwd_holes: contour points, point ids, FP64 keys
+// and stitching steps (bands)
+template <typename T>
+__host__ __device__ constexpr size_t bwd_holes_qb(int pmax) { return ((size_t)pmax * sizeof(V3<T>) + 7) & ~(size_t)7; }
+template <typename T>
+__host__ __device__ constexpr size_t bwd_holes_ws(int pmax) {
+  return (bwd_holes_qb<T>(pmax) + 8 * (size_t)pmax + 8 * (size_t)pmax + 4 * (size_t)pmax + 15) & ~(size_t)15;
+}
+
 // Fan triangles of every hole: point adjoints of the contour points and of
-// the centre (point id n_vtx + interior points + hole id).  Warp per node.
+// the centre (point id n_vtx + interior points + hole id); the band of an
+// annular node instead.  Warp per node.
 template <typename T>
 __global__ void __launch_bounds__(128) k_bwd_holes(TriArgs<T> A, const int32_t* arc_N, int64_t centre_base) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const size_t qb = ((size_t)A.pmax * sizeof(V3<T>) + 7) & ~(size_t)7;
-  const size_t wsb = (qb + 8 * (size_t)A.pmax + 15) & ~(size_t)15;
+  const size_t qb = bwd_holes_qb<T>(A.pmax);
+  const size_t wsb = bwd_holes_ws<T>(A.pmax);
   V3<T>* Q = reinterpret_cast<V3<T>*>(smem_raw + (size_t)w * wsb);
   int64_t* PQ = reinterpret_cast<int64_t*>(smem_raw + (size_t)w * wsb + qb);
+  double* K = reinterpret_cast<double*>(smem_raw + (size_t)w * wsb + qb + 8 * (size_t)A.pmax);
+  int32_t* DEC = reinterpret_cast<int32_t*>(smem_raw + (size_t)w * wsb + qb + 16 * (size_t)A.pmax);
   const LatDev<T>& L = A.lat;
   const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -86,36 +241,14 @@ __global__ void __launch_bounds__(128) k_bwd_holes(TriArgs<T> A, const int32_t* 
     int64_t ao = A.arc_off[nd], rb = L.row_ptr[nd];
     int d = (int)(L.row_ptr[nd + 1] - rb);
     T R = L.node_R[nd];
-    for (int64_t h = h0; h < h1; h++) {
-      int M = 0;
-      for (int64_t q = A.hole_off[h]; q < A.hole_off[h + 1]; q++) {
-        uint32_t ent = A.hole_ent[q];
-        int64_t ga = ao + (ent & 0x7fffffffu);
-        int rev = ent >> 31;
-        int Nq = arc_N[ga];
-        EntryS<T> en;
-        en.g = arc_geo<T>(make_end<T, T>(L, nd, L.adj[rb + ((A.arc_vtx[ga] >> 16) & 255)]), nullptr, R);
-        en.phi0 = A.arc_phi[2 * ga];
-        en.dphi = A.arc_phi[2 * ga + 1];
-        en.psi = T(0);
-        en.N = Nq;
-        en.pre = M;
-        en.ga = ga;
-        en.rev = (uint8_t)rev;
-        en.own = 1;
-        uint32_t av = A.arc_vtx[ga];
-        for (int s = lane; s < Nq; s += 32) {
-          if (M + s >= A.pmax) continue;
-          V3<T> z;
-          T th;
-          entry_point<T>(A, nd, en, nullptr, s, z, th);
-          int m = rev ? Nq - s : s;
-          Q[M + s] = z;
-          PQ[M + s] = (m == 0 || m == Nq) ? A.vtx_off[nd] + (m == 0 ? (av & 255) : ((av >> 8) & 255))
-                                          : A.n_vtx + A.arc_pt_off[ga] + m - 1;
-        }
-        M += Nq;
-      }
+    bool band = false;
+    if (h1 - h0 == 2 &&
+        (A.arc_off[nd + 1] - ao) - (A.vtx_off[nd + 1] - A.vtx_off[nd]) - (int64_t)d + 4 == 2) {
+      band = bwd_band<T>(A, arc_N, nd, h0, ao, rb, R, Q, PQ, K, DEC, lane);
+      __syncwarp();
+    }
+    for (int64_t h = band ? h1 : h0; h < h1; h++) {
+      const int M = bwd_contour<T>(A, arc_N, nd, h, ao, rb, R, Q, PQ, A.pmax, lane);
       __syncwarp();
       if (M > A.pmax) {
         if (lane == 0) atomicCAS(A.err, 0, 4);
@@ -470,15 +603,19 @@ cudaError_t metamesh_backward(lm_metamesh* mm, int k, double w_area, double w_vo
   }
   // 2. point adjoints of the hole fans
   if (mm->H > 0) {
-    const size_t qb = ((size_t)A.pmax * sizeof(V3<T>) + 7) & ~(size_t)7;
-    const size_t wsb = (qb + 8 * (size_t)A.pmax + 15) & ~(size_t)15;
-    size_t smem = 4 * wsb;
+    const size_t wsb = bwd_holes_ws<T>(A.pmax);
+    // four warps per block, fewer when a warp's contour points need more
+    // shared memory (fine resolutions)
+    int warps = 4;
+    while (warps > 1 && (size_t)warps * wsb > 200 * 1024) warps >>= 1;
+    if (wsb > 200 * 1024) BK(cudaErrorInvalidValue);
+    size_t smem = (size_t)warps * wsb;
     BK(cudaFuncSetAttribute(k_bwd_holes<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    int64_t grid = (N + 3) / 4;
+    int64_t grid = (N + warps - 1) / warps;
     if (grid > (int64_t)sms * 16) grid = (int64_t)sms * 16;
     if (grid < 1) grid = 1;
     count_launch();
-    k_bwd_holes<T><<<(unsigned)grid, 128, smem, st>>>(A, arc_N, mm->V + P);
+    k_bwd_holes<T><<<(unsigned)grid, warps * 32, smem, st>>>(A, arc_N, mm->V + P);
     BK(cudaGetLastError());
   }
   // 3. parameter adjoints, node by node

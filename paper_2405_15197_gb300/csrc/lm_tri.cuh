@@ -1688,6 +1688,230 @@ static __global__ void k_redo_clear(const int64_t* range, uint32_t* redo, int64_
 }
 
 // ---------------------------------------------------------- hole fans
+// Per-warp shared workspace of the hole kernel: contour points (both
+// contours of a band), 32 staged records, FP64 angles or keys of the points,
+// and the band's stitching steps.
+template <typename T>
+__host__ __device__ constexpr size_t holes_ws_q(int pmax) { return (((size_t)pmax * sizeof(V3<T>)) + 15) & ~(size_t)15; }
+__host__ __device__ constexpr size_t holes_ws_stage() { return (32 * 50 + 64 + 15) & ~(size_t)15; }
+template <typename T>
+__host__ __device__ constexpr size_t holes_ws_bytes(int pmax) {
+  return holes_ws_q<T>(pmax) + holes_ws_stage() + (((size_t)pmax * 8 + 15) & ~(size_t)15) +
+         (((size_t)pmax * 4 + 15) & ~(size_t)15);
+}
+
+// Contour points of hole h (node-relative, hole order) into Q[0, cap), lanes
+// over each entry's points; returns the contour's point count (points past
+// cap are not stored).
+template <typename T>
+__device__ int hole_contour(const TriArgs<T>& A, int64_t nd, int64_t h, int64_t ao, int64_t rb, T R, Node64* ctx,
+                            V3<T>* Q, int cap, int lane) {
+  const LatDev<T>& L = A.lat;
+  int M = 0;
+  for (int64_t q = A.hole_off[h]; q < A.hole_off[h + 1]; q++) {
+    uint32_t ent = A.hole_ent[q];
+    int64_t ga = ao + (ent & 0x7fffffffu);
+    int rev = ent >> 31;
+    bool unc;
+    int Nq = seg_count<T>(A.arc_phi[2 * ga + 1], A.k, unc);
+    if (unc) {  // the same for every lane of the warp
+      if (ctx->node != nd) {
+        load_node64(L, nd, ctx, lane);
+        __syncwarp();
+      }
+      Nq = arc_segments<T>(A, nd, ga, ctx, 0);
+    }
+    EntryS<T> en;
+    en.g = node_arc_geo<T>(L, nd, L.adj[rb + ((A.arc_vtx[ga] >> 16) & 255)], -1, R);
+    en.phi0 = A.arc_phi[2 * ga];
+    en.dphi = A.arc_phi[2 * ga + 1];
+    en.psi = T(0);
+    en.N = Nq;
+    en.pre = M;
+    en.ga = ga;
+    en.rev = (uint8_t)rev;
+    en.own = 1;
+    for (int s = lane; s < Nq; s += 32) {
+      V3<T> z;
+      T th;
+      if (M + s < cap) {
+        entry_point<T>(A, nd, en, nullptr, s, z, th);
+        Q[M + s] = z;
+      }
+    }
+    M += Nq;
+  }
+  return M;
+}
+
+// FP64 point s of a hole entry (circular arc ga, owner end o; arc angles a0,
+// dd from arc_dphi64) from the node's FP64 strut ends (rare paths)
+template <typename T>
+__device__ __forceinline__ V3<double> hole_point64(const TriArgs<T>& A, const Node64* ctx, int64_t ga, int rev,
+                                                   int Nq, double a0, double dd, int s) {
+  const uint32_t av = A.arc_vtx[ga];
+  const int o = (av >> 16) & 255;
+  const int64_t vo = A.vtx_off[ctx->node];
+  const int m = rev ? Nq - s : s;
+  if (m == 0) return vertex_from_gen<double>(ctx->E, ctx->d, ctx->R, A.vtx_gen[vo + (av & 255)]);
+  if (m == Nq) return vertex_from_gen<double>(ctx->E, ctx->d, ctx->R, A.vtx_gen[vo + ((av >> 8) & 255)]);
+  double ph = a0 + dd * (double)m / (double)Nq, cs, sn;
+  sincos(ph, &sn, &cs);
+  return surf_point(ctx->E[o], cs, sn, 0.0, ctx->R);
+}
+
+// Annular exposed component of node nd (reading 10): two contours bounding
+// one component of the nodal sphere are stitched as a band like a strut's
+// lateral band: q0 = hole h0 forward, q1 = hole h0 + 1 backward, both in the
+// angle around the axis from q0's barycentre to q1's (frame: e1 = a x E_ax
+// with ax the axis of smallest |a_ax|, ties lowest; e2 = a x e1); q0 starts
+// at its first point, q1's keys are moved into [th0 - ETA_ZIP,
+// th0 + 2pi - ETA_ZIP) and q1 starts at its smallest key (ties within
+// ETA_PHI: the first); an event of q0 comes first unless it exceeds q1's by
+// more than ETA_ZIP.  Every decision is taken in FP64 from points recomputed
+// from the inputs; the records use the FP32 contour points, which the struts
+// share bit for bit.  Returns the triangles emitted, -1 when the band does
+// not apply (barycentres within ETA_BARY R, or a contour that does not turn
+// once around the axis: the holes are fanned), -2 on a capacity error.
+template <typename T>
+__device__ __noinline__ int band_node(const TriArgs<T>& A, int64_t nd, int64_t h0, V3<T> c, T R, int64_t ao,
+                                      int64_t rb, Node64* ctx, V3<T>* Q, double* K, int32_t* DEC,
+                                      unsigned char* stage, int64_t tbase, int lane, double& sa, double& sv) {
+  const LatDev<T>& L = A.lat;
+  const int M0 = hole_contour<T>(A, nd, h0, ao, rb, R, ctx, Q, A.pmax, lane);
+  const int M1 = hole_contour<T>(A, nd, h0 + 1, ao, rb, R, ctx, Q + (M0 < A.pmax ? M0 : A.pmax),
+                                 A.pmax - M0, lane);
+  if (M0 < 1 || M1 < 1) return -1;
+  if (M0 + M1 > A.pmax) {
+    if (lane == 0) atomicCAS(A.err, 0, 4);
+    return -2;
+  }
+  if (ctx->node != nd) load_node64(L, nd, ctx, lane);
+  __syncwarp();
+  // FP64 points: barycentres (pass 0), then angles around the axis (pass 1)
+  V3<double> ax_ = mk3(0.0, 0.0, 0.0), e1 = ax_, e2 = ax_;
+  for (int pass = 0; pass < 2; pass++) {
+    V3<double> bs[2] = {mk3(0.0, 0.0, 0.0), mk3(0.0, 0.0, 0.0)};
+    int p = 0;
+    for (int cc = 0; cc < 2; cc++) {
+      for (int64_t q = A.hole_off[h0 + cc]; q < A.hole_off[h0 + cc + 1]; q++) {
+        const uint32_t ent = A.hole_ent[q];
+        const int64_t ga = ao + (ent & 0x7fffffffu);
+        const int rev = ent >> 31;
+        const int Nq = arc_segments<T>(A, nd, ga, ctx, 0);
+        double a0;
+        const double dd = arc_dphi64(A, ctx, ga, &a0);
+        for (int s = lane; s < Nq; s += 32) {
+          const V3<double> z = hole_point64<T>(A, ctx, ga, rev, Nq, a0, dd, s);
+          if (pass == 0) bs[cc] = bs[cc] + z;
+          else K[p + s] = atan2(dot(z, e2), dot(z, e1));
+        }
+        p += Nq;
+      }
+    }
+    if (pass == 0) {
+      for (int cc = 0; cc < 2; cc++)
+        for (int o = 16; o > 0; o >>= 1) {
+          bs[cc].x += __shfl_xor_sync(0xffffffffu, bs[cc].x, o);
+          bs[cc].y += __shfl_xor_sync(0xffffffffu, bs[cc].y, o);
+          bs[cc].z += __shfl_xor_sync(0xffffffffu, bs[cc].z, o);
+        }
+      const V3<double> a = bs[1] * (1.0 / (double)M1) - bs[0] * (1.0 / (double)M0);
+      const double al = norm3(a);
+      if (!(al > ETA_BARY * ctx->R)) return -1;
+      ax_ = a * (1.0 / al);
+      const double aa[3] = {fabs(ax_.x), fabs(ax_.y), fabs(ax_.z)};
+      int ax = 0;
+      if (aa[1] < aa[ax]) ax = 1;
+      if (aa[2] < aa[ax]) ax = 2;
+      const V3<double> c1 = cross(ax_, mk3<double>(ax == 0, ax == 1, ax == 2));
+      e1 = c1 * (1.0 / norm3(c1));
+      e2 = cross(ax_, e1);
+    }
+  }
+  __syncwarp();
+  // q0 turns once positively around the axis, q1 once negatively (q1
+  // backward turns positively)
+  double t0 = 0.0, t1 = 0.0;
+  const double HP = 0.5 * PI2;
+  for (int i = lane; i < M0; i += 32) {
+    double r = K[i + 1 < M0 ? i + 1 : 0] - K[i];
+    while (r <= -HP) r += PI2;
+    while (r > HP) r -= PI2;
+    t0 += r;
+  }
+  for (int j = lane; j < M1; j += 32) {
+    double r = K[M0 + (j + 1 < M1 ? j + 1 : 0)] - K[M0 + j];
+    while (r <= -HP) r += PI2;
+    while (r > HP) r -= PI2;
+    t1 += r;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    t0 += __shfl_xor_sync(0xffffffffu, t0, o);
+    t1 += __shfl_xor_sync(0xffffffffu, t1, o);
+  }
+  if (fabs(t0 - PI2) > 1e-6 || fabs(t1 + PI2) > 1e-6) return -1;
+  // keys: q0's angles relative to its first point, q1's in the window (in
+  // place, each at its contour-1 position x; its backward index is (M1 - x) % M1)
+  const double th0 = K[0];
+  __syncwarp();
+  for (int i = lane; i < M0; i += 32) {
+    double r = K[i] - th0;
+    while (r < -ETA_PHI) r += PI2;
+    while (r >= PI2 - ETA_PHI) r -= PI2;
+    K[i] = th0 + r;
+  }
+  double kmin = 1e300;
+  for (int x = lane; x < M1; x += 32) {
+    double v = K[M0 + x];
+    while (v < th0 - ETA_ZIP) v += PI2;
+    while (v >= th0 + PI2 - ETA_ZIP) v -= PI2;
+    K[M0 + x] = v;
+    kmin = fmin(kmin, v);
+  }
+  for (int o = 16; o > 0; o >>= 1) kmin = fmin(kmin, __shfl_xor_sync(0xffffffffu, kmin, o));
+  __syncwarp();
+  int sB = 0x7fffffff;
+  for (int x = lane; x < M1; x += 32)
+    if (K[M0 + x] <= kmin + ETA_PHI) sB = min(sB, (M1 - x) % M1);
+  for (int o = 16; o > 0; o >>= 1) sB = min(sB, __shfl_xor_sync(0xffffffffu, sB, o));
+  auto bpos = [&](int j) { return M0 + (M1 - ((sB + j + M1) % M1)) % M1; };  // q1 backward, rotated
+  const int ntri = M0 + M1;
+  if (lane == 0) {
+    int ia = 0, ib = -1;
+    for (int p = 0; p < ntri; p++) {
+      const bool takeA = (ib == M1 - 1) || (ia < M0 && (ia + 1 < M0 ? K[ia + 1] : th0 + PI2) <= K[bpos(ib + 1)] + ETA_ZIP);
+      DEC[p] = (ia << 1) | (takeA ? 1 : 0);
+      if (takeA) ia++;
+      else ib++;
+    }
+  }
+  __syncwarp();
+  for (int c0 = 0; c0 < ntri; c0 += 32) {
+    const int p = c0 + lane;
+    if (p < ntri) {
+      const int v = DEC[p], ia = v >> 1, ib = p - ia - 1;
+      const V3<T> ra = Q[ia % M0];
+      const V3<T> rb = (v & 1) ? Q[(ia + 1) % M0] : Q[bpos(ib + 1)];
+      const V3<T> rc = Q[bpos(ib)];
+      double ar, vo;
+      stl_record<T>(A.out ? stage + 50 * lane : nullptr, c, ra, rb, rc, c + ra, c + rb, c + rc, &ar, &vo);
+      sa += ar;
+      sv += vo;
+    }
+    __syncwarp();
+    if (A.out) {
+      const int nrec = ntri - c0 < 32 ? ntri - c0 : 32;
+      const int64_t gt = tbase + c0;
+      if (gt + nrec <= A.capacity) flush_stage(A.out + 50 * gt, stage, 50 * nrec, lane);
+      else if (lane == 0) atomicCAS(A.err, 0, 4);
+    }
+    __syncwarp();
+  }
+  return ntri;
+}
+
+// ---------------------------------------------------------- hole fans
 // One warp per node with holes: for each hole, the contour points (circular arcs in
 // hole order), their barycentre b, b_project = o + R (b - o)/|b - o| (Section
 // 5), falling back to the direction away from the struts when b sits at the
@@ -1703,10 +1927,12 @@ __global__ void __launch_bounds__(256) k_tri_holes(TriArgs<T> A, Node64* scratch
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const size_t wsb = (size_t)A.pmax * sizeof(V3<T>) + 32 * 50 + 64;
-  unsigned char* base = smem_raw + (size_t)w * ((wsb + 15) & ~(size_t)15);
+  unsigned char* base = smem_raw + (size_t)w * holes_ws_bytes<T>(A.pmax);
   V3<T>* Q = reinterpret_cast<V3<T>*>(base);
-  unsigned char* stage = base + (((size_t)A.pmax * sizeof(V3<T>) + 15) & ~(size_t)15);
+  unsigned char* stage = base + holes_ws_q<T>(A.pmax);
+  double* K = reinterpret_cast<double*>(stage + holes_ws_stage());
+  int32_t* DEC = reinterpret_cast<int32_t*>(reinterpret_cast<unsigned char*>(K) +
+                                            ((((size_t)A.pmax * 8) + 15) & ~(size_t)15));
   Node64* ctx = scratch + 2 * gw;
   const LatDev<T>& L = A.lat;
   const int64_t E = L.n_struts;
@@ -1739,43 +1965,19 @@ __global__ void __launch_bounds__(256) k_tri_holes(TriArgs<T> A, Node64* scratch
     V3<T> c = node_xyz<T, T>(L, nd);
     int64_t tbase = A.tri_off[E + nd] - out_first;
     double sa = 0.0, sv = 0.0;
-    for (int64_t h = h0; h < h1; h++) {
+    // two contours bounding one exposed component (the node's partition of
+    // its sphere: V - A + d + 2F - H = 2, so F = 1 when A - V - d + 4 = 2
+    // with H = 2): stitched as a band when the geometry allows
+    int band = -1;
+    if (h1 - h0 == 2 &&
+        (A.arc_off[nd + 1] - ao) - (A.vtx_off[nd + 1] - A.vtx_off[nd]) - (int64_t)d + 4 == 2) {
+      band = band_node<T>(A, nd, h0, c, R, ao, rb, ctx, Q, K, DEC, stage, tbase, lane, sa, sv);
+      __syncwarp();
+    }
+    for (int64_t h = band == -1 ? h0 : h1; h < h1; h++) {
       // contour points: entries in order, N points each
       int64_t q0 = A.hole_off[h], q1 = A.hole_off[h + 1];
-      int M = 0;
-      for (int64_t q = q0; q < q1; q++) {
-        uint32_t ent = A.hole_ent[q];
-        int64_t ga = ao + (ent & 0x7fffffffu);
-        int rev = ent >> 31;
-        bool unc;
-        int Nq = seg_count<T>(A.arc_phi[2 * ga + 1], A.k, unc);
-        if (unc) {  // the same for every lane of the warp
-          if (ctx->node != nd) {
-            load_node64(L, nd, ctx, lane);
-            __syncwarp();
-          }
-          Nq = arc_segments<T>(A, nd, ga, ctx, 0);
-        }
-        EntryS<T> en;
-        en.g = node_arc_geo<T>(L, nd, L.adj[rb + ((A.arc_vtx[ga] >> 16) & 255)], -1, R);
-        en.phi0 = A.arc_phi[2 * ga];
-        en.dphi = A.arc_phi[2 * ga + 1];
-        en.psi = T(0);
-        en.N = Nq;
-        en.pre = M;
-        en.ga = ga;
-        en.rev = (uint8_t)rev;
-        en.own = 1;
-        for (int s = lane; s < Nq; s += 32) {
-          V3<T> z;
-          T th;
-          if (M + s < A.pmax) {
-            entry_point<T>(A, nd, en, nullptr, s, z, th);
-            Q[M + s] = z;
-          }
-        }
-        M += Nq;
-      }
+      const int M = hole_contour<T>(A, nd, h, ao, rb, R, ctx, Q, A.pmax, lane);
       if (M > A.pmax) {
         if (lane == 0) atomicCAS(A.err, 0, 4);
         break;

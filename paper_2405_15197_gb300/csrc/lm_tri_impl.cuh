@@ -76,8 +76,7 @@ template <typename T>
 cudaError_t launch_tri_holes(const TriLaunch<T>& a, cudaStream_t st) {
   TriArgs<T> A = tri_args(a);
   const int sms = sm_count();
-  size_t wsb = (size_t)a.pmax * sizeof(V3<T>) + 32 * 50 + 64;
-  wsb = (wsb + 15) & ~(size_t)15;
+  const size_t wsb = holes_ws_bytes<T>(a.pmax);
   // eight warps per block, fewer when a warp's contour points need more
   // shared memory (fine resolutions)
   int warps = 8;

@@ -62,6 +62,32 @@ def test_adjoint_vs_frozen_fd(dtype):
             assert e < 1e-3
 
 
+@pytest.mark.parametrize("name,dtype", [("annular150", np.float64), ("annular_asym", np.float64),
+                                        ("annular150", np.float32)])
+def test_adjoint_annular_band(name, dtype):
+    """A node whose two contours are stitched as a band (reading 10): the
+    adjoint of its triangles against the frozen-structure FD of the oracle."""
+    from tests.test_gpu_parity import LATTICES
+    lat = P.lattice_as(LATTICES[name](), dtype)
+    o = oracle.Oracle(lat)
+    fz = oracle.Frozen(o, 24)
+    ga1, gv1 = fz.fd(1e-4, np.arange(o.N))
+    ga2, gv2 = fz.fd(5e-5, np.arange(o.N))
+    ga, gv = (4.0 * ga2 - ga1) / 3.0, (4.0 * gv2 - gv1) / 3.0
+    xyz, ends, radii = P.to_device(lat, dtype)
+    mm = liblm.MetaMesh(xyz, ends, radii)
+    _, oa, ov = o.triangulate(24, want_tris=False)
+    for w, ref in (((1.0, 0.0), ga), ((0.0, 1.0), gv)):
+        gx, gr, a, v = mm.backward(24, *w)
+        assert a == pytest.approx(oa, rel=1e-5) and v == pytest.approx(ov, rel=1e-5)
+        g = np.concatenate([gx.cpu().numpy(), gr.cpu().numpy()[:, None]], 1).astype(np.float64)
+        if dtype == np.float64:
+            assert elementwise_err(g, ref) < 1e-6
+        else:
+            assert rel_err(g, ref) < 1e-3
+    mm.close()
+
+
 def test_adjoint_accumulates_and_autograd():
     lat, o, ga, gv = setup(np.float32)
     xyz, ends, radii = P.to_device(lat, np.float32)

@@ -32,6 +32,12 @@ LATTICES = {
     "cone": lambda: L.single_strut((0.1, 0.2, 0.3), (1.0, 0.7, 0.5), 0.12, 0.05),
     "star5": lambda: L.star([(1, 0, 0), (0, 1, 0.2), (-1, 0.3, 0), (0.2, -1, 0.5), (0, 0, 1)],
                             radius=0.12, far_radii=[0.05, 0.09, 0.12, 0.07, 0.1]),
+    # annular exposed spheres (reading 10): two narrowing cones with disjoint
+    # caps, their two contours stitched as one band
+    "annular": lambda: L.star([(1, 0, 0), (-1, 0, 0)], radius=0.2, far_radii=[0.1, 0.1]),
+    "annular150": lambda: L.star([(1, 0, 0), (math.cos(math.radians(150)), math.sin(math.radians(150)), 0.0)],
+                                 radius=0.2, far_radii=[0.05, 0.05], length=0.5),
+    "annular_asym": lambda: L.star([(1, 0.05, 0.02), (-1, 0.03, -0.04)], radius=0.2, far_radii=[0.08, 0.12]),
 }
 _cache = {}
 
@@ -96,7 +102,9 @@ def item_counts(mm, n_items):
                                           ("irregular", np.float64, 16), ("irr03", np.float64, 8),
                                           ("strut", np.float32, 8),
                                           ("cone", np.float32, 33), ("star5", np.float32, 16),
-                                          ("octet3", np.float64, 32)])
+                                          ("octet3", np.float64, 32), ("annular", np.float32, 16),
+                                          ("annular150", np.float32, 32), ("annular_asym", np.float32, 8),
+                                          ("annular150", np.float64, 16)])
 def test_triangles_parity(name, dtype, k):
     """Triangle counts per item bit-exact and every record of every item
     that touches no near-tangent node within tolerance (vertices 2e-5
@@ -143,7 +151,8 @@ def test_triangles_parity(name, dtype, k):
 @pytest.mark.parametrize("name,dtype,k", [("bcc3", np.float32, 8), ("bcc10", np.float32, 16),
                                           ("octet3", np.float32, 8), ("octet3", np.float32, 32),
                                           ("bccjit4", np.float32, 32), ("octet3", np.float64, 32),
-                                          ("star5", np.float32, 16)])
+                                          ("star5", np.float32, 16), ("annular", np.float32, 16),
+                                          ("annular150", np.float32, 32), ("annular_asym", np.float32, 8)])
 def test_gpu_mesh_is_watertight(name, dtype, k):
     """The GPU's triangles weld bitwise into a closed, consistently oriented
     2-manifold (every edge used once in each direction) with chi = 2 (nodes -
