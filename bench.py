@@ -405,6 +405,7 @@ def bench_gpu(args):
             extras["octet100"] = bench_other(torch, liblm, dev, stream, "octet100")
         extras["irregular2m"] = bench_irregular(torch, liblm, dev, stream)
         extras["stl_file"] = bench_stl_file(torch, liblm, dev, stream)
+        extras["ablation_warp_vs_thread"] = bench_ablation(torch, liblm, dev, stream)
     res = {
         "metric": METRIC,
         "value": value, "unit": "struts/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -625,6 +626,38 @@ def bench_stl_file(torch, liblm, dev, stream, n=80, k=32):
     return {"workload": f"BCC {n}^3 cells, R=0.05, k={k}, binary STL to the local disk (fsync before the clock stops)",
             "triangles": ntri, "file_bytes": size, "seconds": dt, "file_gbs": size / dt / 1e9,
             "writer": st, "ring": "4 x 1 GiB pinned slots, chunks by Eq. chunk-size"}
+
+
+def bench_ablation(torch, liblm, dev, stream, name="octet100", samples=32, reps=3):
+    """Warp-centric vs thread-centric trimming (the paper's Section 6
+    ablation): the envelope of Section 4.3.1 at `samples` angles of every
+    strut end, in both work mappings, same arithmetic (lm_envelope_samples)."""
+    wl = WORKLOADS[name]
+    xyz, ends, radii = make_lattice_device(wl, dev, torch)
+    mm = liblm.MetaMesh(xyz, ends, radii, options=tuned_options(liblm), stream=stream)
+    n_ends = 2 * mm.n_struts
+    t = torch.empty(n_ends * samples, dtype=torch.float32, device=dev)
+    lab = torch.empty(n_ends * samples, dtype=torch.int16, device=dev)
+    deg = torch.bincount(ends.reshape(-1).long(), minlength=mm.n_nodes).double()
+    evals = float((deg * (deg - 1)).sum().item()) * samples  # h_j evaluations
+    res = {}
+    for mode, key in ((liblm.LM_ENV_WARP, "warp_centric"), (liblm.LM_ENV_THREAD, "thread_centric")):
+        liblm.lm_envelope_samples(mm.h, samples, mode, t.data_ptr(), lab.data_ptr(), stream)
+        ms = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            liblm.lm_envelope_samples(mm.h, samples, mode, t.data_ptr(), lab.data_ptr(), stream)
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        m = statistics.median(ms)
+        res[key] = {"ms": m, "h_evals_per_s": evals / (m / 1e3)}
+    mm.close()
+    return {"workload": f"{wl['desc']}: envelope t*(phi) = max(0, max_j h_j(phi)) at {samples} angles of each "
+                        f"of {n_ends} strut ends (trimming, Section 4.3.1)",
+            **res, "thread_over_warp": res["thread_centric"]["ms"] / res["warp_centric"]["ms"],
+            "paper": "35x (warp-centric over thread-centric meta-meshing, RTX 3090, Section 6)"}
 
 
 def bench_adjoint(torch, liblm, dev, stream):

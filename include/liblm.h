@@ -372,6 +372,29 @@ lm_status lm_copy_to_host(void* h_dst, const void* d_src, int64_t bytes);
 enum { LM_N_FP64_COUNTS = 18 };
 lm_status lm_fp64_counts(const lm_metamesh* mm, int64_t out[LM_N_FP64_COUNTS]);
 
+/* Ablation of Section 6 (Fig. thread-vs-warp: the paper's warp-centric
+ * meta-meshing kernel ran 35x faster than a thread-centric one, which
+ * allocates a thread per arc calculation and lets every thread read the
+ * strut parameters it needs from global memory by itself).  The trimming
+ * step of Section 4.3.1 with the same arithmetic in both work mappings: for
+ * every strut end i of the handle's lattice and S sample angles
+ * phi_q = 2 pi q / S on its end circle (strut frame), t*(phi_q) =
+ * max(0, max_{j != i} h_j(phi_q)) -- the generator length where the kept
+ * surface starts, the envelope of the auxiliary planes P_ij -- and its
+ * arg-max (node-local index of j; -1 where the nodal sphere wins).
+ *   mode    : LM_ENV_WARP: one warp per node, its strut ends built once into
+ *             shared memory, lanes over (end, angle); LM_ENV_THREAD: one
+ *             thread per (end, angle), which builds its own end and every
+ *             other end of its node from the lattice in global memory
+ *   samples : S, 1..4096
+ *   d_t     : device, [2E][S] in the lattice's dtype, index end_id * S + q
+ *   d_label : device, [2E][S] int16
+ * Asynchronous on `stream`; valences above LM_MAX_VALENCE are reported by
+ * lm_last_error (LM_ERR_VALENCE, warp mode).                              */
+enum { LM_ENV_WARP = 0, LM_ENV_THREAD = 1 };
+lm_status lm_envelope_samples(const lm_metamesh* mm, int32_t samples, int32_t mode, void* d_t,
+                              int16_t* d_label, void* stream);
+
 /* Utility (no counterpart in the paper): number of CUDA kernels this library
  * has launched in the process so far (host-side counter).                */
 long long lm_launch_count(void);

@@ -22,7 +22,7 @@ FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", 
          "--diag-error=20011,20012,20013,20014,20015",
          f"-I{os.path.join(ROOT, 'include')}"]
 UNITS = ["lm_api.cu", "lm_mm_f32.cu", "lm_mm_f64.cu", "lm_tri_f32.cu", "lm_tri_f64.cu",
-         "lm_bwd.cu", "lm_noalloc.cu"]
+         "lm_bwd.cu", "lm_noalloc.cu", "lm_ablation.cu"]
 
 
 def _nvcc():

@@ -24,7 +24,7 @@ EXPORTS = ["lm_build_metamesh", "lm_metamesh_counts", "lm_metamesh_export", "lm_
            "lm_objective", "lm_metamesh_backward", "lm_last_error", "lm_metamesh_free",
            "lm_status_string", "lm_copy_to_host", "lm_launch_count", "lm_triangulate_noalloc",
            "lm_fp64_counts", "lm_metamesh_launch_shape", "lm_metamesh_build_times", "lm_eval_angle_fns",
-           "lm_cuda_error_string", "lm_pool_retain", "lm_triangulate_to_file"]
+           "lm_cuda_error_string", "lm_pool_retain", "lm_triangulate_to_file", "lm_envelope_samples"]
 
 
 class LmError(RuntimeError):
@@ -99,6 +99,7 @@ def load():
         "lm_eval_angle_fns": ([V, V, V, I64, V, V, V, V], ctypes.c_int),
         "lm_cuda_error_string": ([], ctypes.c_char_p),
         "lm_pool_retain": ([ctypes.c_uint64], ctypes.c_int),
+        "lm_envelope_samples": ([V, ctypes.c_int32, ctypes.c_int32, V, V, V], ctypes.c_int),
         "lm_triangulate_to_file": ([V, ctypes.c_int32, ctypes.c_char_p, ctypes.c_int64, V, ctypes.c_int64,
                                     ctypes.c_int32, ctypes.c_int32, V, ctypes.POINTER(ctypes.c_int64),
                                     ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
@@ -181,6 +182,15 @@ def lm_triangulate_stream(h, k, chunk_items, ring_ptr, slot_bytes, n_slots, call
 
 
 LM_FILE_SYNC = 1
+LM_ENV_WARP, LM_ENV_THREAD = 0, 1
+
+
+def lm_envelope_samples(h, samples, mode, t_ptr, label_ptr, stream=None):
+    """Trimming envelope t*(phi_q) and its arg-max at `samples` angles of
+    every strut end, warp-centric (LM_ENV_WARP) or thread-centric
+    (LM_ENV_THREAD); outputs [2E][samples] at the given device pointers."""
+    _ck(load().lm_envelope_samples(h, int(samples), int(mode), ctypes.c_void_p(int(t_ptr)),
+                                   ctypes.c_void_p(int(label_ptr)), _stream_ptr(stream)), "lm_envelope_samples")
 
 
 def lm_triangulate_to_file(h, k, path, ring_ptr, slot_bytes, n_slots, chunk_items=0, sync=False, stream=None):
