@@ -286,9 +286,9 @@ def valence_hist(torch, ends, n_nodes):
 # pipe fractions, issue-active fraction, active lanes per warp instruction,
 # instruction-cache (GCC) hit rate.  Absent: not measured with the current
 # kernel (reported as null).
-METAMESH_NCU = {"bcc": {"dram_bytes_per_node": 507.6, "fp32_issue_frac_ncu": 0.133, "alu_pipe_frac_ncu": 0.259,
+METAMESH_NCU = {"bcc": {"dram_bytes_per_node": 527.8, "fp32_issue_frac_ncu": 0.131, "alu_pipe_frac_ncu": 0.256,
                         "fp64_pipe_frac_ncu": 0.013, "issue_active_ncu": 0.371, "lanes_per_inst_ncu": 11.5,
-                        "icache_gcc_hit_ncu": 0.865}}
+                        "icache_gcc_hit_ncu": 0.871}}
 
 
 def rooflines(wl, ks, totals, phase, counts, vhist, N, E, peaks, peak_kind):
