@@ -100,8 +100,9 @@ typedef struct {
  *   nodes_per_task: nodes a warp pops from the work queue at once (0 = 1)
  *   arena_bytes   : device memory for the count pass to keep each node's
  *                   meta-mesh, so that a gather into the CSR layout replaces
- *                   the emit pass for the nodes it holds (0 = up to 35 % of
- *                   the memory free beside the CSR offsets; < 0 = none:
+ *                   the emit pass for the nodes it holds (0 = up to 45 % of
+ *                   the memory free beside the CSR offsets, memory the pool
+ *                   keeps mapped included; < 0 = none:
  *                   every node is emitted);
  *                   the result is the same either way
  *   redo_list_cap : capacity of the list of struts the FP32 stitching pass
