@@ -67,8 +67,8 @@ __host__ __device__ inline ArenaBlock arena_block(int64_t nv, int64_t na, int64_
   o += 4 * nhe;
   b.vfl = o;
   o = (o + nv + 3) & ~(int64_t)3;
-  b.le = o;
-  o += 4 * nle;
+  b.le = o;  // loop entries as 16 bits: node-local arc (< 2^15) | rev << 15, 0xffff unmatched
+  o += 2 * nle;
   b.bytes = arena_a8(o);
   return b;
 }

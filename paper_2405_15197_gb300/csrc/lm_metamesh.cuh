@@ -992,13 +992,17 @@ __device__ void node_metamesh(WarpSmem<T, C>& S, const MMArgs<T>& A, int64_t n, 
         }
         uint32_t* ho = reinterpret_cast<uint32_t*>(blk + B.ho);
         uint32_t* he = reinterpret_cast<uint32_t*>(blk + B.he);
-        uint32_t* le = reinterpret_cast<uint32_t*>(blk + B.le);
+        uint16_t* le = reinterpret_cast<uint16_t*>(blk + B.le);
         for (int h = lane; h < nh; h += 32) ho[h] = S.h_off[h];
         for (int q = lane; q < nhe; q += 32) {
           uint32_t e = S.h_ent[q];
           he[q] = (e & 0x7fffu) | ((e & 0x8000u) ? 0x80000000u : 0u);
         }
-        for (int q = lane; q < nle; q += 32) le[q] = (uint32_t)S.le_arc[q] | ((uint32_t)S.le_rev[q] << 31);
+        // 16 bits per entry: arc | rev << 15, 0xffff for an unmatched entry
+        // (arc -1, which the emit pass writes as 0xffffffff)
+        for (int q = lane; q < nle; q += 32)
+          le[q] = S.le_arc[q] < 0 ? (uint16_t)0xffffu
+                                  : (uint16_t)((uint32_t)S.le_arc[q] | ((uint32_t)S.le_rev[q] << 15));
       }
     }
     return;
@@ -1039,6 +1043,8 @@ __device__ void node_metamesh(WarpSmem<T, C>& S, const MMArgs<T>& A, int64_t n, 
 using Cap16 = Cap<16, 64, 192, 160>;
 using Cap32 = Cap<32, 128, 384, 320>;
 using Cap64 = Cap<64, 224, 640, 480>;
+// arena loop entries hold a node-local arc id in 15 bits (0x7fff and up unused)
+static_assert(Cap16::A < 0x7fff && Cap32::A < 0x7fff && Cap64::A < 0x7fff, "arc ids fit 15 bits");
 
 template <typename T>
 __host__ __device__ constexpr size_t mm_smem_bytes() {

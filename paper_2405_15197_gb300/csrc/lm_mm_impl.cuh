@@ -99,13 +99,16 @@ __global__ void __launch_bounds__(256) k_mm_gather(MMLaunch<T> a) {
     const uint32_t* hes = reinterpret_cast<const uint32_t*>(blk + B.he);
     for (int64_t h = lane; h < nh; h += 32) a.hole_off[ho + h] = heo + hos[h];
     for (int64_t q = lane; q < nhe; q += 32) a.hole_ent[heo + q] = hes[q];
-    const uint32_t* le = reinterpret_cast<const uint32_t*>(blk + B.le);
+    const uint16_t* le = reinterpret_cast<const uint16_t*>(blk + B.le);
     const int64_t rb = a.row_ptr[n], d = a.row_ptr[n + 1] - rb;
     int64_t run = 0;
     for (int64_t li = 0; li < d; li++) {
       const int32_t eid = a.adj[rb + li];
       const int64_t eo = a.end_off[eid], ne = a.end_off[eid + 1] - eo;
-      for (int64_t q = lane; q < ne; q += 32) a.loop_ent[eo + q] = le[run + q];
+      for (int64_t q = lane; q < ne; q += 32) {
+        const uint32_t v = le[run + q];
+        a.loop_ent[eo + q] = v == 0xffffu ? 0xffffffffu : (v & 0x7fffu) | ((v & 0x8000u) << 16);
+      }
       run += ne;
     }
   }
