@@ -101,15 +101,28 @@ __global__ void __launch_bounds__(256) k_mm_gather(MMLaunch<T> a) {
     for (int64_t q = lane; q < nhe; q += 32) a.hole_ent[heo + q] = hes[q];
     const uint16_t* le = reinterpret_cast<const uint16_t*>(blk + B.le);
     const int64_t rb = a.row_ptr[n], d = a.row_ptr[n + 1] - rb;
-    int64_t run = 0;
-    for (int64_t li = 0; li < d; li++) {
-      const int32_t eid = a.adj[rb + li];
-      const int64_t eo = a.end_off[eid], ne = a.end_off[eid + 1] - eo;
-      for (int64_t q = lane; q < ne; q += 32) {
+    // a lane per strut end: its loop's entries start in the block at the
+    // exclusive prefix of the entry counts of the ends before it
+    int64_t run0 = 0;
+    for (int64_t l0 = 0; l0 < d; l0 += 32) {
+      const int64_t li = l0 + lane;
+      int64_t eo = 0, ne = 0;
+      if (li < d) {
+        const int32_t eid = a.adj[rb + li];
+        eo = a.end_off[eid];
+        ne = a.end_off[eid + 1] - eo;
+      }
+      int64_t inc = ne;
+      for (int o = 1; o < 32; o <<= 1) {
+        const int64_t t = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += t;
+      }
+      const int64_t run = run0 + inc - ne;
+      for (int64_t q = 0; q < ne; q++) {
         const uint32_t v = le[run + q];
         a.loop_ent[eo + q] = v == 0xffffu ? 0xffffffffu : (v & 0x7fffu) | ((v & 0x8000u) << 16);
       }
-      run += ne;
+      run0 += __shfl_sync(0xffffffffu, inc, 31);
     }
   }
 }
