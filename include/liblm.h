@@ -239,6 +239,35 @@ lm_status lm_triangulate_stream(lm_metamesh* mm, int32_t k, int64_t chunk_items,
                                 int64_t slot_bytes, int32_t n_slots, lm_chunk_cb cb, void* user,
                                 void* stream, int64_t* h_total);
 
+/* The lattice meta-meshed and triangulated chunk by chunk with the build of
+ * the next chunk overlapped with the streaming of the current one (the
+ * pipeline of Section 4.2.2, Fig. pipeline (a): meta-meshing of one batch
+ * beside the triangulation and transfer of the previous one).  Struts are
+ * taken in chunks of build_struts; a chunk's sub-lattice holds its struts
+ * and every strut incident to their end nodes, in increasing global order,
+ * so the meta-mesh of each end node, and every triangle, has the same bits
+ * as in a whole-lattice build.  A chunk emits, at each k of ks in turn, its
+ * own struts (ascending id) and then the hole fans of the nodes whose
+ * lowest-id strut it holds (ascending id); the records go through the
+ * caller's pinned ring as in lm_triangulate_stream, and cb (may be NULL)
+ * gets (sequence number, k, first item of the streamed piece in the chunk's
+ * sub-lattice, triangle count, slot pointer, user) after each piece's copy.
+ * The set of records per k equals lm_triangulate's; their order differs.
+ * Synchronising; the work starts after the work already queued on `stream`
+ * (which may have produced the lattice).
+ *   lat         : device arrays as for lm_build_metamesh (fewer than 2^30
+ *                 struts, 2^31 nodes); opt: as for lm_build_metamesh
+ *   ks, n_k     : resolutions, each emitted per chunk
+ *   h_ring      : host, pinned, n_slots (>= 2) x slot_bytes
+ *   h_tris      : host, [n_k] triangles emitted per k
+ * Returns LM_ERR_INVALID_ARG for an end outside [0, N), LM_ERR_CAPACITY if
+ * one strut's or node's records exceed a slot, or a chunk build's status. */
+typedef void (*lm_kchunk_cb)(int64_t seq, int32_t k, int64_t first_item, int64_t n_tris, void* h_slot,
+                             void* user);
+lm_status lm_stream_chunked(const lm_lattice* lat, const lm_options* opt, const int32_t* ks, int32_t n_k,
+                            int64_t build_struts, void* h_ring, int64_t slot_bytes, int32_t n_slots,
+                            lm_kchunk_cb cb, void* user, void* stream, int64_t* h_tris);
+
 /* The same triangles written to a binary-STL file at `path` (created or
  * truncated) through the three-stage pipeline of Section 4.2.2: GPU
  * triangulation of chunk c + 1, device-to-host copy of chunk c into the

@@ -657,6 +657,7 @@ TriLaunch<T> tri_launch(lm_metamesh* mm) {
   L.aux = mm->aux_st;
   L.ev_fork = mm->ev_fork;
   L.ev_join = mm->ev_join;
+  L.node_mask = mm->node_mask;
   return L;
 }
 
@@ -724,8 +725,8 @@ lm_status tri_emit_impl(lm_metamesh* mm, int k, int64_t b, int64_t e, void* out,
 // of its parity with no host work besides the launch.
 //   dev: device int64 [6] = cursor[2], range[2][2]
 template <typename T>
-lm_status chunk_graphs(lm_metamesh* mm, int k, int64_t chunk, int64_t n_items, uint8_t* dbuf[2], int64_t cap,
-                       int64_t* dev, cudaGraphExec_t ex[2], long long* kernels_per_launch) {
+lm_status chunk_graphs(lm_metamesh* mm, int k, int64_t chunk, int64_t i0, int64_t i1, uint8_t* dbuf[2],
+                       int64_t cap, int64_t* dev, cudaGraphExec_t ex[2], long long* kernels_per_launch) {
   LM_CK(ensure_aux(mm));
   cudaStream_t cs;
   LM_CK(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
@@ -733,8 +734,8 @@ lm_status chunk_graphs(lm_metamesh* mm, int k, int64_t chunk, int64_t n_items, u
   for (int q = 0; q < 2 && s == LM_OK; q++) {
     TriLaunch<T> L = tri_launch<T>(mm);
     L.k = k;
-    L.item_begin = 0;
-    L.item_end = n_items;  // host-side sizing only; the kernels read the range
+    L.item_begin = i0;
+    L.item_end = i1;  // host-side sizing only; the kernels read the range
     L.capacity = cap;
     L.first_ptr = nullptr;
     L.out = dbuf[q];
@@ -743,7 +744,7 @@ lm_status chunk_graphs(lm_metamesh* mm, int k, int64_t chunk, int64_t n_items, u
     long long n0 = g_launches.load();
     cudaGraph_t g = nullptr;
     if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed) != cudaSuccess) { s = LM_ERR_CUDA; break; }
-    cudaError_t e0 = launch_chunk_begin(dev + q, 2, chunk, n_items, dev + 2 + 2 * q, cs);
+    cudaError_t e0 = launch_chunk_begin(dev + q, 2, chunk, i0, i1, dev + 2 + 2 * q, cs);
     cudaError_t e1 = cudaMemsetAsync(mm->d_queue, 0, 2 * sizeof(int), cs);
     cudaError_t e2 = launch_tri_emit<T>(L, cs);
     cudaError_t e3 = cudaStreamEndCapture(cs, &g);
@@ -1094,19 +1095,22 @@ struct StlFileSink {
 // chunks handed to the callback or, with `fs`, to a file writer.
 lm_status stream_impl(lm_metamesh* mm, int32_t k, int64_t chunk_items, void* h_ring, int64_t slot_bytes,
                       int32_t n_slots, lm_chunk_cb cb, void* user, void* stream, int64_t* h_total,
-                      StlFileSink* fs) {
+                      StlFileSink* fs, int64_t i0 = 0, int64_t i1 = -1) {
   cudaStream_t st = (cudaStream_t)stream;
   lm_status s = LM_OK;
   if (mm->tri_k != k) {
     s = lm_tri_count(mm, k, stream, nullptr);
     if (s != LM_OK) return s;
   }
-  const int64_t n_items = mm->E + mm->N;
+  // items [i0, i1) (default: every item)
+  if (i1 < 0) i1 = mm->E + mm->N;
+  if (i0 < 0 || i0 > i1 || i1 > mm->E + mm->N) return LM_ERR_INVALID_ARG;
+  const int64_t n_items = i1 - i0;
   const int64_t n_chunks = (n_items + chunk_items - 1) / chunk_items;
   // chunk boundaries (host copy of the offsets at chunk starts)
   std::vector<int64_t> bnd(n_chunks + 1);
   for (int64_t c = 0; c <= n_chunks; c++) {
-    int64_t it = std::min(c * chunk_items, n_items);
+    int64_t it = i0 + std::min(c * chunk_items, n_items);
     if (cudaMemcpyAsync(&bnd[c], mm->tri_off + it, 8, cudaMemcpyDeviceToHost, st) != cudaSuccess)
       return LM_ERR_CUDA;
   }
@@ -1133,8 +1137,8 @@ lm_status stream_impl(lm_metamesh* mm, int32_t k, int64_t chunk_items, void* h_r
     const int64_t init[6] = {0, 1, 0, 0, 0, 0};
     LM_CK(cudaMemcpyAsync(gdev, init, sizeof(init), cudaMemcpyHostToDevice, st));
     LM_CK(cudaStreamSynchronize(st));
-    s = mm->dtype == LM_F32 ? chunk_graphs<float>(mm, k, chunk_items, n_items, dbuf, max_tris, gdev, gex, &kpl)
-                            : chunk_graphs<double>(mm, k, chunk_items, n_items, dbuf, max_tris, gdev, gex, &kpl);
+    s = mm->dtype == LM_F32 ? chunk_graphs<float>(mm, k, chunk_items, i0, i1, dbuf, max_tris, gdev, gex, &kpl)
+                            : chunk_graphs<double>(mm, k, chunk_items, i0, i1, dbuf, max_tris, gdev, gex, &kpl);
   }
   for (int64_t c = 0; c < n_chunks && s == LM_OK; c++) {
     int q = (int)(c & 1);
@@ -1159,7 +1163,7 @@ lm_status stream_impl(lm_metamesh* mm, int32_t k, int64_t chunk_items, void* h_r
       cudaEventDestroy(copied[c - n_slots]);
       copied[c - n_slots] = nullptr;
       int64_t pc = c - n_slots;
-      if (cb) cb(pc, pc * chunk_items, bnd[pc + 1] - bnd[pc], (uint8_t*)h_ring + (pc % n_slots) * slot_bytes, user);
+      if (cb) cb(pc, i0 + pc * chunk_items, bnd[pc + 1] - bnd[pc], (uint8_t*)h_ring + (pc % n_slots) * slot_bytes, user);
     }
     cudaStreamWaitEvent(cs, done_comp[q], 0);
     int64_t nb = (bnd[c + 1] - bnd[c]) * 50;
@@ -1186,7 +1190,7 @@ lm_status stream_impl(lm_metamesh* mm, int32_t k, int64_t chunk_items, void* h_r
     if (!copied[c]) continue;
     cudaEventSynchronize(copied[c]);
     cudaEventDestroy(copied[c]);
-    if (cb && s == LM_OK) cb(c, c * chunk_items, bnd[c + 1] - bnd[c], (uint8_t*)h_ring + (c % n_slots) * slot_bytes, user);
+    if (cb && s == LM_OK) cb(c, i0 + c * chunk_items, bnd[c + 1] - bnd[c], (uint8_t*)h_ring + (c % n_slots) * slot_bytes, user);
   }
   cudaStreamSynchronize(cs);
   for (int q = 0; q < 2; q++)
@@ -1203,6 +1207,274 @@ lm_status stream_impl(lm_metamesh* mm, int32_t k, int64_t chunk_items, void* h_r
   if (s == LM_OK) s = lm_last_error(mm, stream);
   return s;
 }
+
+// ---- chunked meta-meshing and streaming (lm_stream_chunked)
+// The lattice is meta-meshed in chunks of struts [s0, s1): the sub-lattice of
+// a chunk holds its struts and every strut incident to their end nodes (the
+// halo), renumbered in increasing global order, so each end node of the
+// chunk's struts sees the same incident struts in the same order as in the
+// whole lattice and its meta-mesh has the same bits.  The chunk emits its own
+// struts and the hole fans of the nodes whose lowest-id strut is its own.
+
+// degree of every node (ends outside [0, N) are reported, not counted)
+__global__ void k_ck_deg(const int32_t* ends, int64_t E2, int64_t N, int* deg, int* err) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < E2; i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t n = ends[i];
+    if (n < 0 || n >= N) {
+      atomicCAS(err, 0, (int)LM_ERR_INVALID_ARG);
+      continue;
+    }
+    atomicAdd(deg + n, 1);
+  }
+}
+// strut ends of every node (order within a node irrelevant here)
+__global__ void k_ck_fill(const int32_t* ends, int64_t E2, int64_t N, const int64_t* row, int* fill, int32_t* adj) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < E2; i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t n = ends[i];
+    if (n < 0 || n >= N) continue;
+    adj[row[n] + atomicAdd(fill + n, 1)] = (int32_t)i;
+  }
+}
+// mark the struts incident to the end nodes of struts [s0, s1) (their own
+// included) and the window of their ids
+// the window of ids (below 2^31) seen by the threads of a warp: one atomic
+// pair per warp
+__device__ __forceinline__ void ck_window(unsigned lo, unsigned hi, unsigned long long* win) {
+  lo = __reduce_min_sync(0xffffffffu, lo);
+  hi = __reduce_max_sync(0xffffffffu, hi);
+  if ((threadIdx.x & 31) == 0 && lo <= hi) {
+    atomicMin(win, (unsigned long long)lo);
+    atomicMax(win + 1, (unsigned long long)hi);
+  }
+}
+__global__ void k_ck_mark_struts(const int32_t* ends, int64_t s0, int64_t s1, const int64_t* row,
+                                 const int32_t* adj, uint8_t* smark, unsigned long long* win) {
+  unsigned lo = 0xffffffffu, hi = 0u;
+  const int64_t st = (int64_t)gridDim.x * blockDim.x;
+  // every thread of the grid runs the same number of rounds (the warp
+  // reductions below need all lanes)
+  for (int64_t s0t = s0 + blockIdx.x * (int64_t)blockDim.x; s0t < s1; s0t += st) {
+    const int64_t s = s0t + threadIdx.x;
+    if (s >= s1) continue;
+    for (int side = 0; side < 2; side++) {
+      const int64_t n = ends[2 * s + side];
+      for (int64_t q = row[n]; q < row[n + 1]; q++) {
+        const unsigned t = (unsigned)(adj[q] >> 1);
+        smark[t] = 1;
+        lo = t < lo ? t : lo;
+        hi = t > hi ? t : hi;
+      }
+    }
+  }
+  ck_window(lo, hi, win);
+}
+// ids (lo + i) of the marked entries of mark[lo, lo + W), in increasing order
+__global__ void k_ck_compact(const uint8_t* mark, int64_t lo, int64_t W, const int64_t* pos, int32_t* ids) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < W; i += (int64_t)gridDim.x * blockDim.x)
+    if (mark[lo + i]) ids[pos[i]] = (int32_t)(lo + i);
+}
+// mark the end nodes of the sub-lattice's struts and the window of their ids
+__global__ void k_ck_mark_nodes(const int32_t* ends, const int32_t* sub_struts, int64_t Es, uint8_t* nmark,
+                                unsigned long long* win) {
+  unsigned lo = 0xffffffffu, hi = 0u;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < Es; i += (int64_t)gridDim.x * blockDim.x)
+    for (int side = 0; side < 2; side++) {
+      const unsigned n = (unsigned)ends[2 * (int64_t)sub_struts[i] + side];
+      nmark[n] = 1;
+      lo = n < lo ? n : lo;
+      hi = n > hi ? n : hi;
+    }
+  ck_window(lo, hi, win);
+}
+// node renumbering and the sub-lattice's arrays
+__global__ void k_ck_remap(const int32_t* sub_nodes, int64_t Ns, int32_t* remap) {
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < Ns; j += (int64_t)gridDim.x * blockDim.x)
+    remap[sub_nodes[j]] = (int32_t)j;
+}
+template <typename T>
+__global__ void k_ck_gather(const T* xyz, const int32_t* ends, const T* radii, const int32_t* sub_struts, int64_t Es,
+                            const int32_t* sub_nodes, int64_t Ns, const int32_t* remap, T* xyz_s, int32_t* ends_s,
+                            T* radii_s) {
+  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x, st = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t j = tid; j < Ns; j += st)
+    for (int c = 0; c < 3; c++) xyz_s[3 * j + c] = xyz[3 * (int64_t)sub_nodes[j] + c];
+  for (int64_t i = tid; i < Es; i += st) {
+    const int64_t g = sub_struts[i];
+    ends_s[2 * i] = remap[ends[2 * g]];
+    ends_s[2 * i + 1] = remap[ends[2 * g + 1]];
+    radii_s[2 * i] = radii[2 * g];
+    radii_s[2 * i + 1] = radii[2 * g + 1];
+  }
+}
+// a node is owned by the chunk whose struts include its lowest-id strut
+__global__ void k_ck_owned(const int64_t* row, const int32_t* adj, int64_t Ns, int64_t a, int64_t b, uint8_t* own) {
+  for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < Ns; n += (int64_t)gridDim.x * blockDim.x) {
+    int64_t lo = -1;
+    for (int64_t q = row[n]; q < row[n + 1]; q++) {
+      const int64_t t = adj[q] >> 1;
+      if (lo < 0 || t < lo) lo = t;
+    }
+    own[n] = (uint8_t)(lo >= a && lo < b);
+  }
+}
+
+int ck_grid(int64_t n) {
+  int64_t g = (n + 255) / 256;
+  if (g > 152 * 32) g = 152 * 32;
+  return (int)(g < 1 ? 1 : g);
+}
+
+// one chunk's sub-lattice and meta-mesh
+struct CkChunk {
+  int64_t s0 = 0, s1 = 0, Es = 0, Ns = 0, a = 0, b = 0;
+  void *xyz = nullptr, *radii = nullptr;
+  int32_t* ends = nullptr;
+  uint8_t* own = nullptr;
+  lm_metamesh* mm = nullptr;
+  lm_status st = LM_OK;
+};
+
+struct CkShared {
+  const lm_lattice* lat;
+  const lm_options* opt;
+  int64_t N, E;
+  size_t tsz;
+  int64_t *row, *pos, *ws;
+  int32_t *adj, *remap, *sub_struts, *sub_nodes;
+  uint8_t *smark, *nmark;
+  unsigned long long* win;  // [4]: strut window, node window
+  cudaStream_t st;
+};
+
+lm_status ck_free(CkChunk& c, cudaStream_t st) {
+  if (c.mm) lm_metamesh_free(c.mm);
+  c.mm = nullptr;
+  if (c.xyz) cudaFreeAsync(c.xyz, st);
+  if (c.radii) cudaFreeAsync(c.radii, st);
+  if (c.ends) cudaFreeAsync(c.ends, st);
+  if (c.own) cudaFreeAsync(c.own, st);
+  c.xyz = c.radii = nullptr;
+  c.ends = nullptr;
+  c.own = nullptr;
+  return cudaStreamSynchronize(st) == cudaSuccess ? LM_OK : LM_ERR_CUDA;
+}
+
+// sub-lattice of struts [s0, s1) with its halo, then its meta-mesh and the
+// ownership mask of its nodes (every call synchronises sh.st)
+lm_status ck_prepare(CkShared& sh, CkChunk& c) {
+  cudaStream_t st = sh.st;
+  const unsigned long long init[4] = {~0ull, 0ull, ~0ull, 0ull};
+  LM_CK(cudaMemcpyAsync(sh.win, init, sizeof(init), cudaMemcpyHostToDevice, st));
+  const int32_t* ends = sh.lat->strut_ends;
+  count_launch();
+  k_ck_mark_struts<<<ck_grid(c.s1 - c.s0), 256, 0, st>>>(ends, c.s0, c.s1, sh.row, sh.adj, sh.smark, sh.win);
+  unsigned long long w[4];
+  LM_CK(cudaMemcpyAsync(w, sh.win, sizeof(w), cudaMemcpyDeviceToHost, st));
+  LM_CK(cudaStreamSynchronize(st));
+  const int64_t slo = (int64_t)w[0], sW = (int64_t)w[1] - slo + 1;
+  LM_CK(scan_excl<uint8_t>(sh.smark + slo, 1, sW, sh.pos, sh.ws, st));
+  int64_t ab[2];
+  LM_CK(cudaMemcpyAsync(&ab[0], sh.pos + (c.s0 - slo), 8, cudaMemcpyDeviceToHost, st));
+  LM_CK(cudaMemcpyAsync(&ab[1], sh.pos + sW, 8, cudaMemcpyDeviceToHost, st));
+  count_launch();
+  k_ck_compact<<<ck_grid(sW), 256, 0, st>>>(sh.smark, slo, sW, sh.pos, sh.sub_struts);
+  LM_CK(cudaStreamSynchronize(st));
+  c.a = ab[0];
+  c.b = c.a + (c.s1 - c.s0);
+  c.Es = ab[1];
+  // every strut of [s0, s1) is incident to its own end nodes, so all are in
+  // the sub-lattice (a defensive check before the ranges are used)
+  if (c.b > c.Es || c.a < 0) return LM_ERR_STATE;
+  count_launch();
+  k_ck_mark_nodes<<<ck_grid(c.Es), 256, 0, st>>>(ends, sh.sub_struts, c.Es, sh.nmark, sh.win + 2);
+  LM_CK(cudaMemcpyAsync(w, sh.win, sizeof(w), cudaMemcpyDeviceToHost, st));
+  LM_CK(cudaStreamSynchronize(st));
+  const int64_t nlo = (int64_t)w[2], nW = (int64_t)w[3] - nlo + 1;
+  LM_CK(scan_excl<uint8_t>(sh.nmark + nlo, 1, nW, sh.pos, sh.ws, st));
+  LM_CK(cudaMemcpyAsync(&c.Ns, sh.pos + nW, 8, cudaMemcpyDeviceToHost, st));
+  count_launch();
+  k_ck_compact<<<ck_grid(nW), 256, 0, st>>>(sh.nmark, nlo, nW, sh.pos, sh.sub_nodes);
+  LM_CK(cudaStreamSynchronize(st));
+  count_launch();
+  k_ck_remap<<<ck_grid(c.Ns), 256, 0, st>>>(sh.sub_nodes, c.Ns, sh.remap);
+  LM_CK(cudaMallocAsync(&c.xyz, sh.tsz * 3 * (size_t)std::max<int64_t>(c.Ns, 1), st));
+  LM_CK(cudaMallocAsync(&c.radii, sh.tsz * 2 * (size_t)std::max<int64_t>(c.Es, 1), st));
+  LM_CK(cudaMallocAsync((void**)&c.ends, 8 * (size_t)std::max<int64_t>(c.Es, 1), st));
+  count_launch();
+  if (sh.tsz == 4)
+    k_ck_gather<float><<<ck_grid(std::max(c.Es, c.Ns)), 256, 0, st>>>(
+        (const float*)sh.lat->node_xyz, ends, (const float*)sh.lat->end_radii, sh.sub_struts, c.Es, sh.sub_nodes,
+        c.Ns, sh.remap, (float*)c.xyz, c.ends, (float*)c.radii);
+  else
+    k_ck_gather<double><<<ck_grid(std::max(c.Es, c.Ns)), 256, 0, st>>>(
+        (const double*)sh.lat->node_xyz, ends, (const double*)sh.lat->end_radii, sh.sub_struts, c.Es, sh.sub_nodes,
+        c.Ns, sh.remap, (double*)c.xyz, c.ends, (double*)c.radii);
+  LM_CK(cudaGetLastError());
+  // clear the marks for the next chunk
+  LM_CK(cudaMemsetAsync(sh.smark + slo, 0, (size_t)sW, st));
+  LM_CK(cudaMemsetAsync(sh.nmark + nlo, 0, (size_t)nW, st));
+  lm_lattice sub{};
+  sub.n_nodes = c.Ns;
+  sub.n_struts = c.Es;
+  sub.dtype = sh.lat->dtype;
+  sub.node_xyz = c.xyz;
+  sub.strut_ends = c.ends;
+  sub.end_radii = c.radii;
+  lm_status s = lm_build_metamesh(&sub, sh.opt, (void*)st, &c.mm);
+  if (s != LM_OK) return s;
+  LM_CK(cudaMallocAsync((void**)&c.own, (size_t)std::max<int64_t>(c.Ns, 1), st));
+  count_launch();
+  k_ck_owned<<<ck_grid(c.Ns), 256, 0, st>>>(c.mm->row_ptr, c.mm->adj, c.Ns, c.a, c.b, c.own);
+  LM_CK(cudaGetLastError());
+  LM_CK(cudaStreamSynchronize(st));
+  c.mm->node_mask = c.own;
+  return LM_OK;
+}
+
+struct CkCb {
+  lm_kchunk_cb cb;
+  void* user;
+  int32_t k;
+  int64_t* seq;
+};
+void ck_trampoline(int64_t, int64_t first_item, int64_t n_tris, void* slot, void* u) {
+  CkCb* w = (CkCb*)u;
+  if (w->cb) w->cb((*w->seq)++, w->k, first_item, n_tris, slot, w->user);
+}
+
+// one chunk's triangles at every k: its own struts, then its owned nodes'
+// holes, through the ring (items per streamed chunk from the slot and the
+// mean triangle count of the range, halved until the largest chunk fits)
+lm_status ck_stream(CkChunk& c, const int32_t* ks, int32_t n_k, void* h_ring, int64_t slot_bytes,
+                    int32_t n_slots, lm_kchunk_cb cb, void* user, cudaStream_t st, int64_t* seq, int64_t* tris) {
+  for (int32_t q = 0; q < n_k; q++) {
+    lm_status s = lm_tri_count(c.mm, ks[q], (void*)st, nullptr);
+    if (s != LM_OK) return s;
+    const int64_t rng[2][2] = {{c.a, c.b}, {c.Es, c.Es + c.Ns}};
+    for (int r = 0; r < 2; r++) {
+      const int64_t i0 = rng[r][0], i1 = rng[r][1];
+      if (i1 <= i0) continue;
+      int64_t t0 = 0, t1 = 0;
+      LM_CK(cudaMemcpyAsync(&t0, c.mm->tri_off + i0, 8, cudaMemcpyDeviceToHost, st));
+      LM_CK(cudaMemcpyAsync(&t1, c.mm->tri_off + i1, 8, cudaMemcpyDeviceToHost, st));
+      LM_CK(cudaStreamSynchronize(st));
+      if (t1 == t0) continue;
+      const double per = std::max(1.0, (double)(t1 - t0) / (double)(i1 - i0));
+      int64_t chunk = std::max<int64_t>(1, (int64_t)(0.5 * (double)slot_bytes / (50.0 * per)));
+      CkCb w{cb, user, ks[q], seq};
+      int64_t got = 0;
+      while (true) {
+        s = stream_impl(c.mm, ks[q], chunk, h_ring, slot_bytes, n_slots, ck_trampoline, &w, (void*)st, &got,
+                        nullptr, i0, i1);
+        if (s != LM_ERR_CAPACITY || chunk == 1) break;
+        chunk /= 2;
+      }
+      if (s != LM_OK) return s;
+      tris[q] += got - t0;
+    }
+  }
+  return LM_OK;
+}
 }  // namespace
 
 extern "C" {
@@ -1213,6 +1485,127 @@ lm_status lm_triangulate_stream(lm_metamesh* mm, int32_t k, int64_t chunk_items,
   if (!mm || !valid_k(k) || chunk_items <= 0 || !h_ring || slot_bytes <= 0 || n_slots < 2)
     return LM_ERR_INVALID_ARG;
   return stream_impl(mm, k, chunk_items, h_ring, slot_bytes, n_slots, cb, user, stream, h_total, nullptr);
+}
+
+lm_status lm_stream_chunked(const lm_lattice* lat, const lm_options* opt, const int32_t* ks, int32_t n_k,
+                            int64_t build_struts, void* h_ring, int64_t slot_bytes, int32_t n_slots,
+                            lm_kchunk_cb cb, void* user, void* stream, int64_t* h_tris) {
+  if (!lat || !ks || n_k < 1 || build_struts < 1 || !h_ring || slot_bytes < 50 || n_slots < 2 || !h_tris ||
+      lat->n_nodes < 0 || lat->n_struts < 0 || lat->n_nodes >= 2147483647ll || lat->n_struts >= 1073741823ll ||
+      (lat->dtype != LM_F32 && lat->dtype != LM_F64) ||
+      (lat->n_struts > 0 && (!lat->node_xyz || !lat->strut_ends || !lat->end_radii)))
+    return LM_ERR_INVALID_ARG;
+  for (int32_t q = 0; q < n_k; q++) {
+    if (!valid_k(ks[q])) return LM_ERR_INVALID_ARG;
+    h_tris[q] = 0;
+  }
+  const int64_t N = lat->n_nodes, E = lat->n_struts;
+  if (E == 0) return LM_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  // the chunk builds run on a stream of their own (on a helper thread, beside
+  // the previous chunk's streaming)
+  cudaStream_t bst;
+  LM_CK(cudaStreamCreateWithFlags(&bst, cudaStreamNonBlocking));
+  {
+    // the build stream starts after the caller's stream has produced the
+    // lattice (a non-blocking stream does not wait for the legacy stream)
+    cudaEvent_t ready;
+    if (cudaEventCreateWithFlags(&ready, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventRecord(ready, st) != cudaSuccess || cudaStreamWaitEvent(bst, ready, 0) != cudaSuccess) {
+      cudaStreamDestroy(bst);
+      return LM_ERR_CUDA;
+    }
+    cudaEventDestroy(ready);
+  }
+  CkShared sh{};
+  sh.lat = lat;
+  sh.opt = opt;
+  sh.N = N;
+  sh.E = E;
+  sh.tsz = lat->dtype == LM_F32 ? 4 : 8;
+  sh.st = bst;
+  lm_status s = LM_OK;
+  int* dev_int = nullptr;  // [N] degrees / fill counters, [1] error
+  auto fail = [&](lm_status x) {
+    if (s == LM_OK) s = x;
+  };
+  const int64_t wsn = scan_ws_elems(std::max(N, E) + 1);
+  auto al = [&](void** p, size_t b) {
+    if (s == LM_OK && cudaMallocAsync(p, std::max<size_t>(b, 1), bst) != cudaSuccess) fail(LM_ERR_OOM);
+  };
+  al((void**)&dev_int, 4 * (size_t)(N + 1));
+  al((void**)&sh.row, 8 * (size_t)(N + 1));
+  al((void**)&sh.adj, 4 * (size_t)(2 * E));
+  al((void**)&sh.pos, 8 * (size_t)(std::max(N, E) + 1));
+  al((void**)&sh.ws, 8 * (size_t)wsn);
+  al((void**)&sh.remap, 4 * (size_t)N);
+  al((void**)&sh.sub_struts, 4 * (size_t)E);
+  al((void**)&sh.sub_nodes, 4 * (size_t)N);
+  al((void**)&sh.smark, (size_t)E);
+  al((void**)&sh.nmark, (size_t)N);
+  al((void**)&sh.win, 4 * sizeof(unsigned long long));
+  if (s == LM_OK) {
+    // full CSR of the strut ends (the halo of every chunk comes from it)
+    int herr = 0;
+    if (cudaMemsetAsync(dev_int, 0, 4 * (size_t)(N + 1), bst) != cudaSuccess) fail(LM_ERR_CUDA);
+    count_launch();
+    k_ck_deg<<<ck_grid(2 * E), 256, 0, bst>>>(lat->strut_ends, 2 * E, N, dev_int, dev_int + N);
+    if (s == LM_OK && scan_excl<int>(dev_int, 1, N, sh.row, sh.ws, bst) != cudaSuccess) fail(LM_ERR_CUDA);
+    if (s == LM_OK && cudaMemcpyAsync(&herr, dev_int + N, 4, cudaMemcpyDeviceToHost, bst) != cudaSuccess)
+      fail(LM_ERR_CUDA);
+    if (s == LM_OK && cudaMemsetAsync(dev_int, 0, 4 * (size_t)N, bst) != cudaSuccess) fail(LM_ERR_CUDA);
+    count_launch();
+    k_ck_fill<<<ck_grid(2 * E), 256, 0, bst>>>(lat->strut_ends, 2 * E, N, sh.row, dev_int, sh.adj);
+    if (s == LM_OK && cudaMemsetAsync(sh.smark, 0, (size_t)E, bst) != cudaSuccess) fail(LM_ERR_CUDA);
+    if (s == LM_OK && cudaMemsetAsync(sh.nmark, 0, (size_t)N, bst) != cudaSuccess) fail(LM_ERR_CUDA);
+    if (cudaStreamSynchronize(bst) != cudaSuccess) fail(LM_ERR_CUDA);
+    if (herr != 0) fail((lm_status)herr);
+  }
+  const int64_t n_chunks = (E + build_struts - 1) / build_struts;
+  CkChunk cur, nxt;
+  int64_t seq = 0;
+  if (s == LM_OK) {
+    cur.s0 = 0;
+    cur.s1 = std::min(E, build_struts);
+    fail(ck_prepare(sh, cur));
+  }
+  for (int64_t c = 0; c < n_chunks && s == LM_OK; c++) {
+    std::thread helper;
+    lm_status hs = LM_OK;
+    if (c + 1 < n_chunks) {
+      nxt = CkChunk{};
+      nxt.s0 = (c + 1) * build_struts;
+      nxt.s1 = std::min(E, nxt.s0 + build_struts);
+      int dev = 0;
+      cudaGetDevice(&dev);
+      helper = std::thread([&, dev] {
+        cudaSetDevice(dev);
+        hs = ck_prepare(sh, nxt);
+      });
+    }
+    fail(ck_stream(cur, ks, n_k, h_ring, slot_bytes, n_slots, cb, user, st, &seq, h_tris));
+    if (helper.joinable()) helper.join();
+    fail(ck_free(cur, bst));
+    fail(hs);
+    cur = nxt;
+    nxt = CkChunk{};
+  }
+  ck_free(cur, bst);
+  ck_free(nxt, bst);
+  cudaFreeAsync(dev_int, bst);
+  cudaFreeAsync(sh.row, bst);
+  cudaFreeAsync(sh.adj, bst);
+  cudaFreeAsync(sh.pos, bst);
+  cudaFreeAsync(sh.ws, bst);
+  cudaFreeAsync(sh.remap, bst);
+  cudaFreeAsync(sh.sub_struts, bst);
+  cudaFreeAsync(sh.sub_nodes, bst);
+  cudaFreeAsync(sh.smark, bst);
+  cudaFreeAsync(sh.nmark, bst);
+  cudaFreeAsync(sh.win, bst);
+  cudaStreamSynchronize(bst);
+  cudaStreamDestroy(bst);
+  return s;
 }
 
 lm_status lm_triangulate_to_file(lm_metamesh* mm, int32_t k, const char* path, int64_t chunk_items,

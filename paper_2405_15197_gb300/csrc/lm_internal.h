@@ -160,6 +160,7 @@ struct TriLaunch {
   unsigned long long* rlist;  // [1 + rcap]: count, then the deferred struts (NULL: bitmap only)
   int64_t rcap;
   const int64_t* range;  // device-side [begin, end) overriding item_begin/end, or NULL
+  const uint8_t* node_mask;  // [N]: hole items of nodes with 0 count no triangles (NULL: all)
   // second stream for the hole fans, which then run beside the strut passes
   // (fork and join through the two events); NULL: everything on one stream
   cudaStream_t aux;
@@ -176,7 +177,7 @@ template <typename T>
 cudaError_t metamesh_backward(lm_metamesh* mm, int k, double w_area, double w_vol, void* gxyz, void* gr,
                               cudaStream_t st);
 // first node of a chunk graph (see lm_triangulate_stream)
-cudaError_t launch_chunk_begin(int64_t* cursor, int64_t stride, int64_t chunk, int64_t n_items, int64_t* range,
+cudaError_t launch_chunk_begin(int64_t* cursor, int64_t stride, int64_t chunk, int64_t i0, int64_t i1, int64_t* range,
                                cudaStream_t st);
 size_t node64_bytes();
 int64_t tri_scratch_warps();
@@ -214,6 +215,7 @@ struct lm_metamesh {
   int64_t* hole_off;
   uint32_t* hole_ent;
   int64_t V, A, LE, H, HE;
+  const uint8_t* node_mask;  // [N] or NULL: see TriLaunch::node_mask (chunked streaming)
   int64_t emit_nodes;  // nodes the build's emit pass computed again
   int emit_listed;     // the emit pass took only the listed missed nodes
   int64_t n_ell, n_circ, n_degenerate;

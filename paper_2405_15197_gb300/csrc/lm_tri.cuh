@@ -44,6 +44,9 @@ struct TriArgs {
   // device-side item range [2] (chunks replayed from one CUDA graph), or NULL:
   // item_begin / item_end and first_ptr then apply
   const int64_t* range;
+  // [N]: the hole items of nodes whose mask is 0 have no triangles (NULL:
+  // every node's holes are filled)
+  const uint8_t* node_mask;
   // struts deferred to the FP64 stitching pass, listed: [0] count, then up to
   // rcap strut ids (NULL: the pass scans the deferral bitmap instead; so it
   // does when the count exceeds rcap)
@@ -167,7 +170,7 @@ __global__ void __launch_bounds__(256) k_tri_count(TriArgs<T> A, Node64* scratch
             if (unc) { need = true; nodes[s] = nd; }
           }
         }
-      } else {
+      } else if (!A.node_mask || A.node_mask[it - E]) {
         int64_t nd = it - E;
         int64_t ao = A.arc_off[nd];
         for (int64_t h = A.node_hole_off[nd]; h < A.node_hole_off[nd + 1]; h++)
@@ -1665,12 +1668,13 @@ __global__ void __launch_bounds__(EXACT ? 64 : 128, EXACT ? 4 : 7)
 // ------------------------------------------------ chunks replayed by graph
 // First node of a chunk graph: the next chunk of this graph's sequence
 // (cursor[0], stepped by `stride`) as a device-side item range.
-static __global__ void k_chunk_begin(int64_t* cursor, int64_t stride, int64_t chunk, int64_t n_items, int64_t* range) {
+static __global__ void k_chunk_begin(int64_t* cursor, int64_t stride, int64_t chunk, int64_t i0, int64_t i1,
+                                     int64_t* range) {
   if (threadIdx.x == 0 && blockIdx.x == 0) {
     int64_t c = cursor[0];
-    int64_t b = c * chunk, e = b + chunk;
-    range[0] = b < n_items ? b : n_items;
-    range[1] = e < n_items ? e : n_items;
+    int64_t b = i0 + c * chunk, e = b + chunk;
+    range[0] = b < i1 ? b : i1;
+    range[1] = e < i1 ? e : i1;
     cursor[0] = c + stride;
   }
 }
@@ -1952,7 +1956,8 @@ __global__ void __launch_bounds__(256) k_tri_holes(TriArgs<T> A, Node64* scratch
       g0 = __shfl_sync(0xffffffffu, g0, 0);
       if (g0 >= stride) break;
       const int64_t mine = n0 + g0 + lane * stride;
-      todo = __ballot_sync(0xffffffffu, mine < n1 && A.node_hole_off[mine] != A.node_hole_off[mine + 1]);
+      todo = __ballot_sync(0xffffffffu, mine < n1 && A.node_hole_off[mine] != A.node_hole_off[mine + 1] &&
+                                            (!A.node_mask || A.node_mask[mine]));
       if (!todo) continue;
     }
     const int64_t nd = n0 + g0 + (__ffs(todo) - 1) * stride;

@@ -43,6 +43,7 @@ TriArgs<T> tri_args(const TriLaunch<T>& a) {
   A.dmax = a.dmax > 0 ? a.dmax : 1;
   A.max_pts = a.max_pts;
   A.range = a.range;
+  A.node_mask = a.node_mask;
   A.rlist = a.rlist;
   A.rcap = a.rlist ? a.rcap : 0;
   A.fb = a.fb;

@@ -24,7 +24,8 @@ EXPORTS = ["lm_build_metamesh", "lm_metamesh_counts", "lm_metamesh_export", "lm_
            "lm_objective", "lm_metamesh_backward", "lm_last_error", "lm_metamesh_free",
            "lm_status_string", "lm_copy_to_host", "lm_launch_count", "lm_triangulate_noalloc",
            "lm_fp64_counts", "lm_metamesh_launch_shape", "lm_metamesh_build_times", "lm_eval_angle_fns",
-           "lm_cuda_error_string", "lm_pool_retain", "lm_triangulate_to_file", "lm_envelope_samples"]
+           "lm_cuda_error_string", "lm_pool_retain", "lm_triangulate_to_file", "lm_envelope_samples",
+           "lm_stream_chunked"]
 
 
 class LmError(RuntimeError):
@@ -61,6 +62,8 @@ class lm_metamesh_view(ctypes.Structure):
 
 CHUNK_CB = ctypes.CFUNCTYPE(None, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p,
                             ctypes.c_void_p)
+KCHUNK_CB = ctypes.CFUNCTYPE(None, ctypes.c_int64, ctypes.c_int32, ctypes.c_int64, ctypes.c_int64,
+                             ctypes.c_void_p, ctypes.c_void_p)
 _lib = None
 
 
@@ -99,6 +102,9 @@ def load():
         "lm_eval_angle_fns": ([V, V, V, I64, V, V, V, V], ctypes.c_int),
         "lm_cuda_error_string": ([], ctypes.c_char_p),
         "lm_pool_retain": ([ctypes.c_uint64], ctypes.c_int),
+        "lm_stream_chunked": ([ctypes.POINTER(lm_lattice), ctypes.POINTER(lm_options), ctypes.POINTER(ctypes.c_int32),
+                               ctypes.c_int32, ctypes.c_int64, V, ctypes.c_int64, ctypes.c_int32, KCHUNK_CB, V, V,
+                               ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
         "lm_envelope_samples": ([V, ctypes.c_int32, ctypes.c_int32, V, V, V], ctypes.c_int),
         "lm_triangulate_to_file": ([V, ctypes.c_int32, ctypes.c_char_p, ctypes.c_int64, V, ctypes.c_int64,
                                     ctypes.c_int32, ctypes.c_int32, V, ctypes.POINTER(ctypes.c_int64),
@@ -140,6 +146,30 @@ def lm_build_metamesh(xyz, ends, radii, options=None, stream=None):
     _ck(load().lm_build_metamesh(ctypes.byref(lat), ctypes.byref(opt), _stream_ptr(stream), ctypes.byref(h)),
         "lm_build_metamesh")
     return h
+
+
+def lm_stream_chunked(xyz, ends, radii, ks, build_struts, ring_ptr, slot_bytes, n_slots, callback=None,
+                      options=None, stream=None):
+    """Meta-mesh and triangulate the lattice chunk by chunk (the next chunk's
+    build beside the current chunk's streaming) through the pinned ring;
+    callback(seq, k, first_item, n_tris, slot_ptr, user).  Returns the
+    triangles emitted per k."""
+    import torch
+    for t in (xyz, ends, radii):
+        if not (t.is_cuda and t.is_contiguous()):
+            raise ValueError("lattice tensors must be contiguous CUDA tensors")
+    if ends.dtype != torch.int32 or xyz.dtype != radii.dtype or xyz.dtype not in (torch.float32, torch.float64):
+        raise ValueError("ends must be int32; xyz and radii float32 or float64 of one dtype")
+    lat = lm_lattice(xyz.shape[0], ends.shape[0], LM_F32 if xyz.dtype == torch.float32 else LM_F64, 0,
+                     xyz.data_ptr(), ends.data_ptr(), radii.data_ptr())
+    opt = options if options is not None else lm_options()
+    kk = (ctypes.c_int32 * len(ks))(*[int(k) for k in ks])
+    tris = (ctypes.c_int64 * len(ks))()
+    cb = KCHUNK_CB(callback) if callback is not None else KCHUNK_CB()
+    _ck(load().lm_stream_chunked(ctypes.byref(lat), ctypes.byref(opt), kk, len(ks), int(build_struts),
+                                 ctypes.c_void_p(int(ring_ptr)), int(slot_bytes), int(n_slots), cb, None,
+                                 _stream_ptr(stream), tris), "lm_stream_chunked")
+    return list(tris)
 
 
 def lm_metamesh_counts(h):
