@@ -144,59 +144,10 @@ __device__ __noinline__ bool bwd_band(const TriArgs<T>& A, const int32_t* arc_N,
     K[p] = atan2(dot(z, e2), dot(z, e1));
   }
   __syncwarp();
-  double t0 = 0.0, t1 = 0.0;
-  const double HP = 0.5 * PI2;
-  for (int i = lane; i < M0; i += 32) {
-    double r = K[i + 1 < M0 ? i + 1 : 0] - K[i];
-    while (r <= -HP) r += PI2;
-    while (r > HP) r -= PI2;
-    t0 += r;
-  }
-  for (int j = lane; j < M1; j += 32) {
-    double r = K[M0 + (j + 1 < M1 ? j + 1 : 0)] - K[M0 + j];
-    while (r <= -HP) r += PI2;
-    while (r > HP) r -= PI2;
-    t1 += r;
-  }
-  for (int o = 16; o > 0; o >>= 1) {
-    t0 += __shfl_xor_sync(0xffffffffu, t0, o);
-    t1 += __shfl_xor_sync(0xffffffffu, t1, o);
-  }
-  if (fabs(t0 - PI2) > 1e-6 || fabs(t1 + PI2) > 1e-6) return false;
-  const double th0 = K[0];
-  __syncwarp();
-  for (int i = lane; i < M0; i += 32) {
-    double r = K[i] - th0;
-    while (r < -ETA_PHI) r += PI2;
-    while (r >= PI2 - ETA_PHI) r -= PI2;
-    K[i] = th0 + r;
-  }
-  double kmin = 1e300;
-  for (int x = lane; x < M1; x += 32) {
-    double v = K[M0 + x];
-    while (v < th0 - ETA_ZIP) v += PI2;
-    while (v >= th0 + PI2 - ETA_ZIP) v -= PI2;
-    K[M0 + x] = v;
-    kmin = fmin(kmin, v);
-  }
-  for (int o = 16; o > 0; o >>= 1) kmin = fmin(kmin, __shfl_xor_sync(0xffffffffu, kmin, o));
-  __syncwarp();
-  int sB = 0x7fffffff;
-  for (int x = lane; x < M1; x += 32)
-    if (K[M0 + x] <= kmin + ETA_PHI) sB = min(sB, (M1 - x) % M1);
-  for (int o = 16; o > 0; o >>= 1) sB = min(sB, __shfl_xor_sync(0xffffffffu, sB, o));
-  auto bpos = [&](int j) { return M0 + (M1 - ((sB + j + M1) % M1)) % M1; };
+  const int sB = band_zip(K, M0, M1, DEC, lane);
+  if (sB < 0) return false;
+  auto bpos = [&](int j) { return band_bpos(M0, M1, sB, j); };
   const int ntri = M0 + M1;
-  if (lane == 0) {
-    int ia = 0, ib = -1;
-    for (int p = 0; p < ntri; p++) {
-      const bool takeA = (ib == M1 - 1) || (ia < M0 && (ia + 1 < M0 ? K[ia + 1] : th0 + PI2) <= K[bpos(ib + 1)] + ETA_ZIP);
-      DEC[p] = (ia << 1) | (takeA ? 1 : 0);
-      if (takeA) ia++;
-      else ib++;
-    }
-  }
-  __syncwarp();
   for (int p = lane; p < ntri; p += 32) {
     const int v = DEC[p], ia = v >> 1, ib = p - ia - 1;
     const int qa = ia % M0, qb = (v & 1) ? (ia + 1) % M0 : bpos(ib + 1), qc = bpos(ib);

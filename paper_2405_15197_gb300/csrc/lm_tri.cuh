@@ -1764,6 +1764,77 @@ __device__ __forceinline__ V3<double> hole_point64(const TriArgs<T>& A, const No
   return surf_point(ctx->E[o], cs, sn, 0.0, ctx->R);
 }
 
+// Stitching of an annular band (reading 10) from the angles K[0, M0) of
+// contour 0 and K[M0, M0 + M1) of contour 1 around the band's axis (both in
+// hole order, FP64): checks that contour 0 turns once positively and contour
+// 1 once negatively, turns K into the zipper keys (contour 0 relative to its
+// first point; contour 1 moved into [th0 - ETA_ZIP, th0 + 2pi - ETA_ZIP), in
+// place), rotates contour 1 backward to its smallest key (ties within
+// ETA_PHI: the first) and writes the decision of each triangle p to DEC[p]
+// (ia << 1 | contour-0 advances).  Returns contour 1's start sB, or -1 when a
+// contour does not turn once.  Called by the whole warp.
+__device__ __forceinline__ int band_zip(double* K, int M0, int M1, int32_t* DEC, int lane) {
+  double t0 = 0.0, t1 = 0.0;
+  const double HP = 0.5 * PI2;
+  for (int i = lane; i < M0; i += 32) {
+    double r = K[i + 1 < M0 ? i + 1 : 0] - K[i];
+    while (r <= -HP) r += PI2;
+    while (r > HP) r -= PI2;
+    t0 += r;
+  }
+  for (int j = lane; j < M1; j += 32) {
+    double r = K[M0 + (j + 1 < M1 ? j + 1 : 0)] - K[M0 + j];
+    while (r <= -HP) r += PI2;
+    while (r > HP) r -= PI2;
+    t1 += r;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    t0 += __shfl_xor_sync(0xffffffffu, t0, o);
+    t1 += __shfl_xor_sync(0xffffffffu, t1, o);
+  }
+  if (fabs(t0 - PI2) > 1e-6 || fabs(t1 + PI2) > 1e-6) return -1;
+  const double th0 = K[0];
+  __syncwarp();
+  for (int i = lane; i < M0; i += 32) {
+    double r = K[i] - th0;
+    while (r < -ETA_PHI) r += PI2;
+    while (r >= PI2 - ETA_PHI) r -= PI2;
+    K[i] = th0 + r;
+  }
+  double kmin = 1e300;
+  for (int x = lane; x < M1; x += 32) {
+    double v = K[M0 + x];
+    while (v < th0 - ETA_ZIP) v += PI2;
+    while (v >= th0 + PI2 - ETA_ZIP) v -= PI2;
+    K[M0 + x] = v;
+    kmin = fmin(kmin, v);
+  }
+  for (int o = 16; o > 0; o >>= 1) kmin = fmin(kmin, __shfl_xor_sync(0xffffffffu, kmin, o));
+  __syncwarp();
+  int sB = 0x7fffffff;
+  for (int x = lane; x < M1; x += 32)
+    if (K[M0 + x] <= kmin + ETA_PHI) sB = min(sB, (M1 - x) % M1);
+  for (int o = 16; o > 0; o >>= 1) sB = min(sB, __shfl_xor_sync(0xffffffffu, sB, o));
+  if (lane == 0) {
+    int ia = 0, ib = -1;
+    for (int p = 0; p < M0 + M1; p++) {
+      const int xb = M0 + (M1 - ((sB + ib + 1 + M1) % M1)) % M1;
+      const bool takeA = (ib == M1 - 1) || (ia < M0 && (ia + 1 < M0 ? K[ia + 1] : th0 + PI2) <= K[xb] + ETA_ZIP);
+      DEC[p] = (ia << 1) | (takeA ? 1 : 0);
+      if (takeA) ia++;
+      else ib++;
+    }
+  }
+  __syncwarp();
+  return sB;
+}
+
+// position in the contour arrays of point j of contour 1 backward from its
+// start sB (j >= -1)
+__device__ __forceinline__ int band_bpos(int M0, int M1, int sB, int j) {
+  return M0 + (M1 - ((sB + j + M1) % M1)) % M1;
+}
+
 // Annular exposed component of node nd (reading 10): two contours bounding
 // one component of the nodal sphere are stitched as a band like a strut's
 // lateral band: q0 = hole h0 forward, q1 = hole h0 + 1 backward, both in the
@@ -1834,63 +1905,10 @@ __device__ __noinline__ int band_node(const TriArgs<T>& A, int64_t nd, int64_t h
     }
   }
   __syncwarp();
-  // q0 turns once positively around the axis, q1 once negatively (q1
-  // backward turns positively)
-  double t0 = 0.0, t1 = 0.0;
-  const double HP = 0.5 * PI2;
-  for (int i = lane; i < M0; i += 32) {
-    double r = K[i + 1 < M0 ? i + 1 : 0] - K[i];
-    while (r <= -HP) r += PI2;
-    while (r > HP) r -= PI2;
-    t0 += r;
-  }
-  for (int j = lane; j < M1; j += 32) {
-    double r = K[M0 + (j + 1 < M1 ? j + 1 : 0)] - K[M0 + j];
-    while (r <= -HP) r += PI2;
-    while (r > HP) r -= PI2;
-    t1 += r;
-  }
-  for (int o = 16; o > 0; o >>= 1) {
-    t0 += __shfl_xor_sync(0xffffffffu, t0, o);
-    t1 += __shfl_xor_sync(0xffffffffu, t1, o);
-  }
-  if (fabs(t0 - PI2) > 1e-6 || fabs(t1 + PI2) > 1e-6) return -1;
-  // keys: q0's angles relative to its first point, q1's in the window (in
-  // place, each at its contour-1 position x; its backward index is (M1 - x) % M1)
-  const double th0 = K[0];
-  __syncwarp();
-  for (int i = lane; i < M0; i += 32) {
-    double r = K[i] - th0;
-    while (r < -ETA_PHI) r += PI2;
-    while (r >= PI2 - ETA_PHI) r -= PI2;
-    K[i] = th0 + r;
-  }
-  double kmin = 1e300;
-  for (int x = lane; x < M1; x += 32) {
-    double v = K[M0 + x];
-    while (v < th0 - ETA_ZIP) v += PI2;
-    while (v >= th0 + PI2 - ETA_ZIP) v -= PI2;
-    K[M0 + x] = v;
-    kmin = fmin(kmin, v);
-  }
-  for (int o = 16; o > 0; o >>= 1) kmin = fmin(kmin, __shfl_xor_sync(0xffffffffu, kmin, o));
-  __syncwarp();
-  int sB = 0x7fffffff;
-  for (int x = lane; x < M1; x += 32)
-    if (K[M0 + x] <= kmin + ETA_PHI) sB = min(sB, (M1 - x) % M1);
-  for (int o = 16; o > 0; o >>= 1) sB = min(sB, __shfl_xor_sync(0xffffffffu, sB, o));
-  auto bpos = [&](int j) { return M0 + (M1 - ((sB + j + M1) % M1)) % M1; };  // q1 backward, rotated
+  const int sB = band_zip(K, M0, M1, DEC, lane);
+  if (sB < 0) return -1;
+  auto bpos = [&](int j) { return band_bpos(M0, M1, sB, j); };
   const int ntri = M0 + M1;
-  if (lane == 0) {
-    int ia = 0, ib = -1;
-    for (int p = 0; p < ntri; p++) {
-      const bool takeA = (ib == M1 - 1) || (ia < M0 && (ia + 1 < M0 ? K[ia + 1] : th0 + PI2) <= K[bpos(ib + 1)] + ETA_ZIP);
-      DEC[p] = (ia << 1) | (takeA ? 1 : 0);
-      if (takeA) ia++;
-      else ib++;
-    }
-  }
-  __syncwarp();
   for (int c0 = 0; c0 < ntri; c0 += 32) {
     const int p = c0 + lane;
     if (p < ntri) {

@@ -6,7 +6,8 @@ C ABI and against the FP64 oracle where there is a result to compare:
 * the meta-mesh launch of the d <= 64 valence bucket (a node of valence 40);
 * the deferred-strut list overflowing into the deferral-bitmap scan;
 * an allocation failure (a host-side device-memory budget, no GPU fault);
-* the library's FP32 arctangent and sine / cosine against FP64 references.
+* the library's FP32 arctangent and sine / cosine against FP64 references;
+* builds with the pool's freed memory retained (lm_pool_retain).
 """
 import math
 
@@ -134,3 +135,28 @@ def test_angle_functions_error_bounds():
     a64 = a.astype(np.float64)
     assert np.abs(sn - np.sin(a64)).max() <= 7e-7
     assert np.abs(cs - np.cos(a64)).max() <= 7e-7
+
+
+def test_pool_retain_and_build_times():
+    """lm_pool_retain keeps freed device memory mapped in the default pool
+    between builds (the arena's room counts it): builds after it are the same
+    array for array; lm_metamesh_build_times reports five non-negative
+    phases; the default is restored afterwards."""
+    from tests.test_gpu_parity import LATTICES
+    lat = P.lattice_as(LATTICES["irregular"](), np.float32)
+    xyz, ends, radii = P.to_device(lat, np.float32)
+    ref = liblm.MetaMesh(xyz, ends, radii)
+    a = ref.download()
+    ref.close()
+    liblm.lm_pool_retain((1 << 64) - 1)
+    try:
+        for _ in range(2):
+            mm = liblm.MetaMesh(xyz, ends, radii)
+            b = mm.download()
+            for key in a:
+                assert np.array_equal(a[key], b[key]), key
+            t = liblm.lm_metamesh_build_times(mm.h)
+            assert len(t) == 5 and all(x >= 0 for x in t)
+            mm.close()
+    finally:
+        liblm.lm_pool_retain(0)
