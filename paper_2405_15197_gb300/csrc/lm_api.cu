@@ -2,6 +2,7 @@
 // triangulation, objective, streaming to pinned host memory.
 // Paper: arXiv 2405.15197 (Sections 4.2.2, 4.3, 5).
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <fcntl.h>
 #include <unistd.h>
@@ -42,6 +43,15 @@ namespace {
 
 // the CUDA error behind the last LM_ERR_CUDA / LM_ERR_OOM of this thread
 thread_local cudaError_t g_last_cuda = cudaSuccess;
+
+// NVTX range of one call or build phase (visible to a profiler attached to
+// the process; no effect otherwise)
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 lm_status st_cuda(cudaError_t e) {
   g_last_cuda = e;
@@ -464,7 +474,10 @@ lm_status build_impl(lm_metamesh* mm, cudaStream_t st) {
   LM_CK(cudaMemsetAsync(bk.queues, 0, NB_BUCKETS * sizeof(int), st));
   int used = 0;
   cudaEventRecord(ev[1], st);
-  LM_CK(launch_metamesh<T>(false, L, bk, ctas, st, &used));
+  {
+    NvtxRange r("meta-mesh count pass");
+    LM_CK(launch_metamesh<T>(false, L, bk, ctas, st, &used));
+  }
   cudaEventRecord(ev[2], st);
   // ---- sizing: offsets from the counts, and the one synchronisation
   LM_CK(dalloc(mm, &mm->vtx_off, N + 1, st));
@@ -820,6 +833,7 @@ void lm_metamesh_free(lm_metamesh* mm) {
 
 lm_status lm_build_metamesh(const lm_lattice* lat, const lm_options* opt, void* stream,
                             lm_metamesh** out) {
+  NvtxRange nvtx_("lm_build_metamesh");
   if (!out) return LM_ERR_INVALID_ARG;
   *out = nullptr;
   if (!lat || lat->n_nodes < 0 || lat->n_struts < 0 || (lat->dtype != LM_F32 && lat->dtype != LM_F64))
@@ -908,6 +922,7 @@ lm_status lm_metamesh_export(lm_metamesh* mm, lm_metamesh_view* v) {
 }
 
 lm_status lm_tri_count(lm_metamesh* mm, int32_t k, void* stream, int64_t* h_total) {
+  NvtxRange nvtx_("lm_tri_count");
   if (!mm || !valid_k(k)) return LM_ERR_INVALID_ARG;
   cudaStream_t st = (cudaStream_t)stream;
   return mm->dtype == LM_F32 ? tri_count_impl<float>(mm, k, st, h_total)
@@ -927,6 +942,7 @@ lm_status lm_tri_range(const lm_metamesh* mm, int64_t b, int64_t e, int64_t* h_f
 
 lm_status lm_triangulate(lm_metamesh* mm, int32_t k, int64_t b, int64_t e, void* d_out, int64_t cap,
                          void* stream) {
+  NvtxRange nvtx_("lm_triangulate");
   if (!mm || !valid_k(k) || b < 0 || e < b || e > mm->E + mm->N || cap < 0) return LM_ERR_INVALID_ARG;
   if (mm->tri_k != k) return LM_ERR_STATE;
   if (!d_out && cap > 0) return LM_ERR_INVALID_ARG;
@@ -1362,6 +1378,7 @@ lm_status ck_free(CkChunk& c, cudaStream_t st) {
 // sub-lattice of struts [s0, s1) with its halo, then its meta-mesh and the
 // ownership mask of its nodes (every call synchronises sh.st)
 lm_status ck_prepare(CkShared& sh, CkChunk& c) {
+  NvtxRange nvtx_("chunk build");
   cudaStream_t st = sh.st;
   const unsigned long long init[4] = {~0ull, 0ull, ~0ull, 0ull};
   LM_CK(cudaMemcpyAsync(sh.win, init, sizeof(init), cudaMemcpyHostToDevice, st));
@@ -1482,6 +1499,7 @@ extern "C" {
 lm_status lm_triangulate_stream(lm_metamesh* mm, int32_t k, int64_t chunk_items, void* h_ring,
                                 int64_t slot_bytes, int32_t n_slots, lm_chunk_cb cb, void* user,
                                 void* stream, int64_t* h_total) {
+  NvtxRange nvtx_("lm_triangulate_stream");
   if (!mm || !valid_k(k) || chunk_items <= 0 || !h_ring || slot_bytes <= 0 || n_slots < 2)
     return LM_ERR_INVALID_ARG;
   return stream_impl(mm, k, chunk_items, h_ring, slot_bytes, n_slots, cb, user, stream, h_total, nullptr);
@@ -1490,6 +1508,7 @@ lm_status lm_triangulate_stream(lm_metamesh* mm, int32_t k, int64_t chunk_items,
 lm_status lm_stream_chunked(const lm_lattice* lat, const lm_options* opt, const int32_t* ks, int32_t n_k,
                             int64_t build_struts, void* h_ring, int64_t slot_bytes, int32_t n_slots,
                             lm_kchunk_cb cb, void* user, void* stream, int64_t* h_tris) {
+  NvtxRange nvtx_("lm_stream_chunked");
   if (!lat || !ks || n_k < 1 || build_struts < 1 || !h_ring || slot_bytes < 50 || n_slots < 2 || !h_tris ||
       lat->n_nodes < 0 || lat->n_struts < 0 || lat->n_nodes >= 2147483647ll || lat->n_struts >= 1073741823ll ||
       (lat->dtype != LM_F32 && lat->dtype != LM_F64) ||
@@ -1611,6 +1630,7 @@ lm_status lm_stream_chunked(const lm_lattice* lat, const lm_options* opt, const 
 lm_status lm_triangulate_to_file(lm_metamesh* mm, int32_t k, const char* path, int64_t chunk_items,
                                  void* h_ring, int64_t slot_bytes, int32_t n_slots, int32_t flags,
                                  void* stream, int64_t* h_total, double h_stats[4]) {
+  NvtxRange nvtx_("lm_triangulate_to_file");
   if (!mm || !valid_k(k) || !path || !h_ring || slot_bytes < 50 || n_slots < 2) return LM_ERR_INVALID_ARG;
   lm_status s = LM_OK;
   if (mm->tri_k != k) {
@@ -1713,6 +1733,7 @@ lm_status lm_copy_to_host(void* h_dst, const void* d_src, int64_t bytes) {
 
 lm_status lm_metamesh_backward(lm_metamesh* mm, int32_t k, double w_area, double w_vol, void* d_grad_xyz,
                                void* d_grad_r, void* stream, double* h_area, double* h_volume) {
+  NvtxRange nvtx_("lm_metamesh_backward");
   if (!mm || !valid_k(k)) return LM_ERR_INVALID_ARG;
   lm_status s = LM_OK;
   if (mm->tri_k != k) {
