@@ -1334,9 +1334,16 @@ __global__ void k_ck_owned(const int64_t* row, const int32_t* adj, int64_t Ns, i
   }
 }
 
+// grid of 256-thread blocks for n grid-strided items: at most 32 blocks per SM
 int ck_grid(int64_t n) {
+  static thread_local int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) sms = 1;
+  }
   int64_t g = (n + 255) / 256;
-  if (g > 152 * 32) g = 152 * 32;
+  if (g > (int64_t)sms * 32) g = (int64_t)sms * 32;
   return (int)(g < 1 ? 1 : g);
 }
 
