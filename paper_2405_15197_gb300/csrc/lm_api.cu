@@ -1618,17 +1618,9 @@ lm_status lm_stream_chunked(const lm_lattice* lat, const lm_options* opt, const 
   }
   ck_free(cur, bst);
   ck_free(nxt, bst);
-  cudaFreeAsync(dev_int, bst);
-  cudaFreeAsync(sh.row, bst);
-  cudaFreeAsync(sh.adj, bst);
-  cudaFreeAsync(sh.pos, bst);
-  cudaFreeAsync(sh.ws, bst);
-  cudaFreeAsync(sh.remap, bst);
-  cudaFreeAsync(sh.sub_struts, bst);
-  cudaFreeAsync(sh.sub_nodes, bst);
-  cudaFreeAsync(sh.smark, bst);
-  cudaFreeAsync(sh.nmark, bst);
-  cudaFreeAsync(sh.win, bst);
+  for (void* p : {(void*)dev_int, (void*)sh.row, (void*)sh.adj, (void*)sh.pos, (void*)sh.ws, (void*)sh.remap,
+                  (void*)sh.sub_struts, (void*)sh.sub_nodes, (void*)sh.smark, (void*)sh.nmark, (void*)sh.win})
+    if (p) cudaFreeAsync(p, bst);
   cudaStreamSynchronize(bst);
   cudaStreamDestroy(bst);
   return s;
